@@ -1,0 +1,500 @@
+// C ABI entry points (include/quwarp.h): argument checks, exception-to-status
+// conversion, and forwarding to the planner and the engine.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "plan.h"
+
+namespace qw {
+void build_plan(qw_plan *P, Engine *E, const Workload &W);
+void plan_execute(qw_plan *P, void *stream);
+void plan_wait(qw_plan *P);
+void plan_release(qw_plan *P);
+void *plan_state_ptr(const qw_plan *P, uint64_t t);
+void engine_init(Engine *E, const qw_engine_opts *o);
+void engine_release(Engine *E);
+void costmodel_train(Engine *E, const float *feat, const float *tgt, uint64_t n, uint32_t epochs,
+                     uint32_t batch, float lr, uint64_t seed, float *final_loss);
+void costmodel_set(Engine *E, const float *params, const float *mean, const float *scale);
+void costmodel_probe(Engine *E, const Workload &W, float *feat, float *tgt, uint64_t cap, uint64_t *n_rows);
+qw_status sv_apply_dev(Engine *E, uint32_t mode, uint32_t n, void *state, const qw_gate *gates,
+                       uint64_t n_gates, bool init, void *stream);
+qw_status sv_energy_dev(Engine *E, uint32_t mode, uint32_t n, const void *state, const qw_pauli_term *terms,
+                        uint64_t n_terms, double *energy, double *norm2, void *stream);
+qw_status sv_sample_dev(Engine *E, uint32_t mode, uint32_t n, const void *state, const double *u,
+                        uint32_t shots, uint64_t *out, void *stream);
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string &m) { g_last_error = m; }
+}  // namespace qw
+
+using namespace qw;
+
+#define QW_GUARD(body)                               \
+  try {                                              \
+    qw::set_last_error("");                          \
+    body;                                            \
+    return QW_OK;                                    \
+  } catch (const qw::Error &e_) {                    \
+    qw::set_last_error(e_.msg);                      \
+    return e_.code;                                  \
+  } catch (const std::bad_alloc &) {                 \
+    qw::set_last_error("host allocation failed");    \
+    return QW_ERR_OOM;                               \
+  } catch (const std::exception &e_) {               \
+    qw::set_last_error(e_.what());                   \
+    return QW_ERR_INVALID_ARG;                       \
+  } catch (...) {                                    \
+    qw::set_last_error("unknown internal error");    \
+    return QW_ERR_INVALID_ARG;                       \
+  }
+
+extern "C" {
+
+const char *qw_last_error(void) { return qw::g_last_error.c_str(); }
+
+qw_status qw_engine_create(const qw_engine_opts *opts, qw_engine **out) {
+  QW_GUARD({
+    if (!out) fail(QW_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n_dev = 0;
+    if (cudaGetDeviceCount(&n_dev) != cudaSuccess || n_dev == 0)
+      fail(QW_ERR_CUDA, "no CUDA device available");
+    if (opts && (opts->device < 0 || opts->device >= n_dev))
+      fail(QW_ERR_INVALID_ARG, "device %d out of range (%d devices)", opts->device, n_dev);
+    qw_engine *e = new qw_engine();
+    try {
+      engine_init(&e->e, opts);
+    } catch (...) {
+      delete e;
+      throw;
+    }
+    *out = e;
+  })
+}
+
+void qw_engine_destroy(qw_engine *e) {
+  if (!e) return;
+  try { engine_release(&e->e); } catch (...) {}
+  delete e;
+}
+
+qw_status qw_engine_info(const qw_engine *e, double *hbm_gbs, int32_t *sm_count, uint64_t *l2_bytes) {
+  QW_GUARD({
+    if (!e) fail(QW_ERR_INVALID_ARG, "engine is NULL");
+    if (hbm_gbs) *hbm_gbs = e->e.hbm_gbs;
+    if (sm_count) *sm_count = e->e.sm_count;
+    if (l2_bytes) *l2_bytes = e->e.l2_bytes;
+  })
+}
+
+qw_status qw_workload_create(qw_workload **out) {
+  QW_GUARD({
+    if (!out) fail(QW_ERR_INVALID_ARG, "out is NULL");
+    *out = new qw_workload();
+  })
+}
+
+void qw_workload_destroy(qw_workload *w) { delete w; }
+
+static void validate_gate(const qw_gate &g, uint32_t mode, uint32_t n, uint64_t idx) {
+  const bool two = is_two_qubit_op(g.op);
+  if (g.q0 >= n) fail(QW_ERR_INVALID_ARG, "gate %llu: qubit %u out of range (n=%u)", (unsigned long long)idx, g.q0, n);
+  if (two && (g.q1 >= n || g.q1 == g.q0))
+    fail(QW_ERR_INVALID_ARG, "gate %llu: bad second qubit %u", (unsigned long long)idx, g.q1);
+  if (!std::isfinite(g.theta)) fail(QW_ERR_INVALID_ARG, "gate %llu: non-finite parameter", (unsigned long long)idx);
+  const bool known = (g.op >= QW_OP_H && g.op <= QW_OP_PHASE) || two || is_barrier_op(g.op);
+  if (!known) fail(QW_ERR_INVALID_ARG, "gate %llu: unknown op %u", (unsigned long long)idx, g.op);
+  if (mode == QW_MODE_TABLEAU) {
+    if (!is_clifford_op(g.op)) fail(QW_ERR_INVALID_ARG, "gate %llu: op %u is not a tableau (Clifford) op", (unsigned long long)idx, g.op);
+    if (is_barrier_op(g.op) && g.theta != 0.0 && g.theta != 1.0)
+      fail(QW_ERR_INVALID_ARG, "gate %llu: outcome bit must be 0 or 1", (unsigned long long)idx);
+  } else if (is_barrier_op(g.op)) {
+    fail(QW_ERR_UNSUPPORTED, "gate %llu: MEASURE/RESET are supported in tableau mode only", (unsigned long long)idx);
+  }
+}
+
+qw_status qw_workload_add_task(qw_workload *w, const qw_task *t, uint64_t *task_id) {
+  QW_GUARD({
+    if (!w || !t) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    if (t->mode > QW_MODE_TABLEAU) fail(QW_ERR_INVALID_ARG, "unknown mode %u", t->mode);
+    const uint32_t n = t->n_qubits;
+    if (t->mode == QW_MODE_TABLEAU) {
+      if (n < 1 || n > QW_TABLEAU_MAX_QUBITS) fail(QW_ERR_INVALID_ARG, "tableau qubits %u outside [1, %d]", n, QW_TABLEAU_MAX_QUBITS);
+      if (t->n_terms || t->shots) fail(QW_ERR_INVALID_ARG, "tableau tasks take no energy terms or shots");
+    } else {
+      if (n < 1 || n > QW_SV_MAX_QUBITS) fail(QW_ERR_INVALID_ARG, "statevector qubits %u outside [1, %d]", n, QW_SV_MAX_QUBITS);
+    }
+    if (t->n_spans && !t->spans) fail(QW_ERR_INVALID_ARG, "spans is NULL");
+    if (t->n_terms && !t->terms) fail(QW_ERR_INVALID_ARG, "terms is NULL");
+    if (t->shots && !t->uniforms) fail(QW_ERR_INVALID_ARG, "uniforms is NULL");
+    TaskData d;
+    d.mode = t->mode;
+    d.n = n;
+    d.flags = t->flags;
+    d.shots = t->shots;
+    uint64_t total = 0;
+    for (uint32_t s = 0; s < t->n_spans; s++) {
+      const qw_gate_span &sp = t->spans[s];
+      if (sp.n_gates && !sp.gates) fail(QW_ERR_INVALID_ARG, "span %u has NULL gates", s);
+      for (uint64_t i = 0; i < sp.n_gates; i++) validate_gate(sp.gates[i], t->mode, n, total + i);
+      if (sp.n_gates) {
+        d.spans.push_back({sp.gates, sp.n_gates});
+        total += sp.n_gates;
+        d.span_end.push_back(total);
+      }
+    }
+    d.n_gates = total;
+    const uint64_t mask = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+    for (uint64_t k = 0; k < t->n_terms; k++) {
+      const qw_pauli_term &p = t->terms[k];
+      if ((p.xmask | p.zmask) & ~mask) fail(QW_ERR_INVALID_ARG, "term %llu acts outside the %u qubits", (unsigned long long)k, n);
+      if (!std::isfinite(p.coef)) fail(QW_ERR_INVALID_ARG, "term %llu: non-finite coefficient", (unsigned long long)k);
+      d.terms.push_back(p);
+    }
+    for (uint32_t k = 0; k < t->shots; k++) {
+      const double u = t->uniforms[k];
+      if (!(u >= 0.0 && u < 1.0)) fail(QW_ERR_INVALID_ARG, "uniform %u outside [0,1)", k);
+      d.uniforms.push_back(u);
+    }
+    w->w.tasks.push_back(std::move(d));
+    if (task_id) *task_id = w->w.tasks.size() - 1;
+  })
+}
+
+void qw_plan_opts_default(qw_plan_opts *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->reuse = 1;
+  o->batched = 1;
+  o->legality = 1;
+  o->cost_model = QW_COST_ANALYTIC;
+  o->delta_frac = 0.10;
+  o->min_group = 2;
+  o->min_prefix_gates = 1;
+  o->min_prefix_cost_ns = 0.0;
+  o->use_graph = 1;
+}
+
+qw_status qw_plan_create(qw_engine *e, const qw_workload *w, const qw_plan_opts *o, qw_plan **out) {
+  QW_GUARD({
+    if (!w || !out) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    qw_plan *p = new qw_plan();
+    if (o) p->opts = *o; else qw_plan_opts_default(&p->opts);
+    if (p->opts.delta_frac < 0 || !std::isfinite(p->opts.delta_frac)) { delete p; fail(QW_ERR_INVALID_ARG, "delta_frac must be >= 0"); }
+    if (p->opts.cost_model != QW_COST_ANALYTIC && p->opts.cost_model != QW_COST_MLP) { delete p; fail(QW_ERR_INVALID_ARG, "unknown cost model"); }
+    p->eng = e ? &e->e : nullptr;
+    try {
+      if (e) cudaSetDevice(e->e.device);
+      build_plan(p, p->eng, w->w);
+    } catch (...) {
+      delete p;
+      throw;
+    }
+    *out = p;
+  })
+}
+
+void qw_plan_destroy(qw_plan *p) {
+  if (!p) return;
+  try { plan_release(p); } catch (...) {}
+  delete p;
+}
+
+qw_status qw_execute(qw_plan *p, void *stream) {
+  QW_GUARD({
+    if (!p) fail(QW_ERR_INVALID_ARG, "plan is NULL");
+    plan_execute(p, stream);
+  })
+}
+
+qw_status qw_wait(qw_plan *p) {
+  QW_GUARD({
+    if (!p) fail(QW_ERR_INVALID_ARG, "plan is NULL");
+    if (!p->executed) fail(QW_ERR_STATE, "qw_wait before qw_execute");
+    plan_wait(p);
+  })
+}
+
+static const TaskPlan &task_of(const qw_plan *p, uint64_t t) {
+  if (!p) fail(QW_ERR_INVALID_ARG, "plan is NULL");
+  if (t >= p->tasks.size()) fail(QW_ERR_NOT_FOUND, "task %llu does not exist", (unsigned long long)t);
+  if (p->timed == 0) fail(QW_ERR_STATE, "no results yet (call qw_execute and qw_wait)");
+  return p->tasks[t];
+}
+
+qw_status qw_get_energy(const qw_plan *p, uint64_t task, double *energy, double *norm2) {
+  QW_GUARD({
+    const TaskPlan &tp = task_of(p, task);
+    if (tp.ham < 0) fail(QW_ERR_NOT_FOUND, "task %llu has no energy terms", (unsigned long long)task);
+    if (energy) *energy = p->energy[task];
+    if (norm2) *norm2 = p->norm2[task];
+  })
+}
+
+qw_status qw_get_samples(const qw_plan *p, uint64_t task, uint64_t *out, size_t cap, size_t *n) {
+  QW_GUARD({
+    const TaskPlan &tp = task_of(p, task);
+    if (n) *n = tp.shots;
+    if (cap < tp.shots) fail(QW_ERR_BUFFER_TOO_SMALL, "need %u entries", tp.shots);
+    if (tp.shots && !out) fail(QW_ERR_INVALID_ARG, "out is NULL");
+    std::copy(p->samples.begin() + p->sample_off[task], p->samples.begin() + p->sample_off[task + 1], out);
+  })
+}
+
+qw_status qw_get_syndrome(const qw_plan *p, uint64_t task, uint8_t *bits, size_t cap, size_t *n_bits) {
+  QW_GUARD({
+    const TaskPlan &tp = task_of(p, task);
+    if (tp.mode != QW_MODE_TABLEAU) fail(QW_ERR_NOT_FOUND, "task %llu is not a tableau task", (unsigned long long)task);
+    if (n_bits) *n_bits = tp.total_outs;
+    if (cap < tp.total_outs) fail(QW_ERR_BUFFER_TOO_SMALL, "need %u bytes", tp.total_outs);
+    if (tp.total_outs && !bits) fail(QW_ERR_INVALID_ARG, "bits is NULL");
+    // outcomes of the materialized chain from the root, then the task's own
+    std::vector<int> chain;
+    for (int m = tp.src; m >= 0; m = p->mats[m].parent) chain.push_back(m);
+    size_t o = 0;
+    for (auto it = chain.rbegin(); it != chain.rend(); ++it) {
+      const int m = *it;
+      for (uint32_t i = p->outs_mat_off[m]; i < p->outs_mat_off[m + 1]; i++) bits[o++] = p->outs_mat[i];
+    }
+    for (uint32_t i = p->outs_off[task]; i < p->outs_off[task + 1]; i++) bits[o++] = p->outs_suffix[i];
+  })
+}
+
+qw_status qw_get_state(const qw_plan *p, uint64_t task, void *host_dst, size_t bytes) {
+  QW_GUARD({
+    const TaskPlan &tp = task_of(p, task);
+    if (tp.mode == QW_MODE_TABLEAU) fail(QW_ERR_NOT_FOUND, "tableau tasks have no amplitudes");
+    if (!(tp.flags & QW_TASK_KEEP_STATE) && !(tp.sv.passes.empty() && tp.src >= 0))
+      fail(QW_ERR_NOT_FOUND, "task %llu was not submitted with QW_TASK_KEEP_STATE", (unsigned long long)task);
+    const size_t es = (tp.mode == QW_MODE_SV_FP64) ? 16 : 8;
+    const size_t want = es << tp.n;
+    if (bytes != want) fail(QW_ERR_INVALID_ARG, "state of task %llu has %zu bytes", (unsigned long long)task, want);
+    if (!host_dst) fail(QW_ERR_INVALID_ARG, "host_dst is NULL");
+    cudaSetDevice(p->eng->device);
+    // padded qubits (n < 5) stay |0>: the state is the first 2^n amplitudes
+    if (cudaMemcpy(host_dst, plan_state_ptr(p, task), want, cudaMemcpyDeviceToHost) != cudaSuccess)
+      fail(QW_ERR_CUDA, "state copy failed");
+  })
+}
+
+static qw_status put_json(const std::string &s, char *buf, size_t cap, size_t *needed) {
+  if (needed) *needed = s.size() + 1;
+  if (!buf || cap < s.size() + 1) {
+    set_last_error("buffer too small");
+    return QW_ERR_BUFFER_TOO_SMALL;
+  }
+  memcpy(buf, s.c_str(), s.size() + 1);
+  return QW_OK;
+}
+
+qw_status qw_explain_json(const qw_plan *p, char *buf, size_t cap, size_t *needed) {
+  if (!p) { set_last_error("plan is NULL"); return QW_ERR_INVALID_ARG; }
+  set_last_error("");
+  return put_json(p->explain, buf, cap, needed);
+}
+
+qw_status qw_cost_record_json(const qw_plan *p, char *buf, size_t cap, size_t *needed) {
+  if (!p) { set_last_error("plan is NULL"); return QW_ERR_INVALID_ARG; }
+  set_last_error("");
+  std::string s = strf(
+      "{\"type\":\"QuWARP:CostRecord\",\"planning_ms\":%.6f,\"estimated_direct_ms\":%.6f,"
+      "\"estimated_plan_ms\":%.6f,\"estimated_speedup\":%.4f,\"executions\":%d,"
+      "\"upload_ms\":%.6f,\"prefix_ms\":%.6f,\"suffix_ms\":%.6f,\"energy_ms\":%.6f,"
+      "\"sampling_ms\":%.6f,\"tableau_tasks_ms\":%.6f,\"device_total_ms\":%.6f,"
+      "\"artifacts\":%zu,\"artifact_bytes\":%llu,\"batch_ms\":[",
+      p->planning_ns * 1e-6, p->est_direct_ns * 1e-6, p->est_plan_ns * 1e-6,
+      p->est_plan_ns > 0 ? p->est_direct_ns / p->est_plan_ns : 1.0, p->timed, p->t_upload_ms,
+      p->t_prefix_ms, p->t_suffix_ms, p->t_energy_ms, p->t_sample_ms, p->t_tab_ms, p->t_total_ms,
+      p->mats.size(), [&] {
+        unsigned long long b = 0;
+        for (auto &m : p->mats) b += m.bytes;
+        return b;
+      }());
+  for (size_t i = 0; i < p->batch_ms.size(); i++) s += strf(i ? ",%.6f" : "%.6f", p->batch_ms[i]);
+  s += "]}";
+  return put_json(s, buf, cap, needed);
+}
+
+qw_status qw_sha256(const void *data, size_t len, uint8_t out[32]) {
+  QW_GUARD({
+    if ((!data && len) || !out) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    sha256(data, len, out);
+  })
+}
+
+qw_status qw_fingerprint(uint32_t n_qubits, uint32_t mode, const qw_gate *gates, uint64_t n_gates,
+                         uint8_t out[32]) {
+  QW_GUARD({
+    if ((!gates && n_gates) || !out) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    TaskData t;
+    t.n = n_qubits;
+    t.mode = mode;
+    if (n_gates) {
+      t.spans.push_back({gates, n_gates});
+      t.span_end.push_back(n_gates);
+    }
+    t.n_gates = n_gates;
+    fingerprint(n_qubits, mode, t, 0, n_gates, out);
+  })
+}
+
+qw_status qw_reuse_decision(const qw_cost_tuple *c, int32_t *reuse, double *lhs, double *rhs) {
+  QW_GUARD({
+    if (!c || !reuse) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    if (c->n_tasks < 0) fail(QW_ERR_INVALID_ARG, "negative task count");
+    const double l = (c->n_tasks - 1.0) * c->c_prefix;
+    const double r = c->c_materialize + c->n_tasks * (c->c_reload + c->c_handoff) + c->delta;
+    *reuse = l > r ? 1 : 0;
+    if (lhs) *lhs = l;
+    if (rhs) *rhs = r;
+  })
+}
+
+qw_status qw_legality_check(const qw_artifact_desc *a, uint32_t target_backend,
+                            const uint8_t expected_provenance[32], int32_t *legal, qw_refusal *out) {
+  QW_GUARD({
+    if (!a || !legal || !out) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    *legal = legality(*a, target_backend, expected_provenance, out) ? 1 : 0;
+  })
+}
+
+// ---- learned cost model ---------------------------------------------------------
+qw_status qw_mlp_forward_dev(const float *params, const float *x, float *y, uint32_t batch, void *stream) {
+  QW_GUARD({
+    if (!params || (batch && (!x || !y))) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    launch_mlp_forward(params, x, y, batch, stream);
+    if (cudaGetLastError() != cudaSuccess) fail(QW_ERR_CUDA, "mlp forward launch failed");
+  })
+}
+
+qw_status qw_mlp_loss_grad_dev(const float *params, const float *x, const float *target, uint32_t batch,
+                               float *loss, float *grad, void *stream) {
+  QW_GUARD({
+    if (!params || !grad || !loss || (batch && (!x || !target))) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    if (batch == 0) fail(QW_ERR_INVALID_ARG, "empty batch");
+    float *scratch = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMallocAsync((void **)&scratch, mlp_scratch_floats(batch) * sizeof(float), s) != cudaSuccess)
+      fail(QW_ERR_OOM, "scratch allocation failed");
+    launch_mlp_loss_grad(params, x, target, batch, loss, grad, scratch, stream);
+    cudaFreeAsync(scratch, s);
+    if (cudaGetLastError() != cudaSuccess) fail(QW_ERR_CUDA, "mlp backward launch failed");
+  })
+}
+
+qw_status qw_mlp_adam_dev(float *params, const float *grad, float *m, float *v, uint32_t n_params,
+                          uint32_t t, float lr, float beta1, float beta2, float eps, void *stream) {
+  QW_GUARD({
+    if (!params || !grad || !m || !v) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    if (t < 1) fail(QW_ERR_INVALID_ARG, "Adam step must be >= 1");
+    launch_mlp_adam(params, grad, m, v, n_params, t, lr, beta1, beta2, eps, stream);
+    if (cudaGetLastError() != cudaSuccess) fail(QW_ERR_CUDA, "adam launch failed");
+  })
+}
+
+qw_status qw_costmodel_train(qw_engine *e, const float *features, const float *targets, uint64_t n,
+                             uint32_t epochs, uint32_t batch, float lr, uint64_t seed, float *final_loss) {
+  QW_GUARD({
+    if (!e || !features || !targets) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    costmodel_train(&e->e, features, targets, n, epochs, batch, lr, seed, final_loss);
+  })
+}
+
+qw_status qw_costmodel_predict(qw_engine *e, const float *features, uint64_t n, float *out) {
+  QW_GUARD({
+    if (!e || (n && (!features || !out))) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    if (!e->e.cm.trained) fail(QW_ERR_STATE, "cost model not trained");
+    if (n) e->e.predict_log2ns(features, (uint32_t)n, out);
+  })
+}
+
+qw_status qw_costmodel_get(const qw_engine *e, float *params, float *feat_mean, float *feat_scale) {
+  QW_GUARD({
+    if (!e || !params) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    if (!e->e.cm.trained) fail(QW_ERR_STATE, "cost model not trained");
+    std::copy(e->e.cm.params.begin(), e->e.cm.params.end(), params);
+    if (feat_mean) memcpy(feat_mean, e->e.cm.mean, sizeof(e->e.cm.mean));
+    if (feat_scale) memcpy(feat_scale, e->e.cm.scale, sizeof(e->e.cm.scale));
+  })
+}
+
+qw_status qw_costmodel_set(qw_engine *e, const float *params, const float *feat_mean, const float *feat_scale) {
+  QW_GUARD({
+    if (!e || !params || !feat_mean || !feat_scale) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    costmodel_set(&e->e, params, feat_mean, feat_scale);
+  })
+}
+
+qw_status qw_costmodel_probe(qw_engine *e, const qw_workload *w, float *features, float *targets,
+                             uint64_t cap, uint64_t *n_rows) {
+  QW_GUARD({
+    if (!e || !w || !features || !targets || !n_rows) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    costmodel_probe(&e->e, w->w, features, targets, cap, n_rows);
+  })
+}
+
+qw_status qw_costmodel_features(const qw_engine *e, const qw_workload *w, uint64_t task, uint64_t gate_begin,
+                                uint64_t gate_end, uint32_t n_sharing, float out[12]) {
+  QW_GUARD({
+    if (!w || !out) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    if (task >= w->w.tasks.size()) fail(QW_ERR_NOT_FOUND, "no such task");
+    const TaskData &t = w->w.tasks[task];
+    if (gate_begin > gate_end || gate_end > t.n_gates) fail(QW_ERR_INVALID_ARG, "bad gate range");
+    TileConfig tc;
+    tc.k_max = (t.mode == QW_MODE_SV_FP64) ? SV_MAX_TILE_FP64 : SV_MAX_TILE_FP32;
+    tc.b = 4;
+    if (e) {
+      auto it = e->e.tiles.find(((uint64_t)std::min<uint32_t>(std::max<uint32_t>(t.n, SV_G), 26) << 1) |
+                                (t.mode == QW_MODE_SV_FP64 ? 1 : 0));
+      if (it != e->e.tiles.end()) tc = it->second;
+    }
+    features_for(t, gate_begin, gate_end, n_sharing, tc, 0.0, out);
+  })
+}
+
+// ---- statevector kernels on caller buffers ----------------------------------------
+qw_status qw_sv_apply_dev(qw_engine *e, uint32_t mode, uint32_t n, void *state, const qw_gate *gates,
+                          uint64_t n_gates, const int32_t *init, void *stream) {
+  QW_GUARD({
+    if (!e || !state || (n_gates && !gates)) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    if (mode > QW_MODE_SV_FP32) fail(QW_ERR_INVALID_ARG, "statevector modes only");
+    if (n < SV_G || n > QW_SV_MAX_QUBITS) fail(QW_ERR_INVALID_ARG, "n must be in [%d, %d] for device buffers", SV_G, QW_SV_MAX_QUBITS);
+    for (uint64_t i = 0; i < n_gates; i++) validate_gate(gates[i], mode, n, i);
+    qw_status st = sv_apply_dev(&e->e, mode, n, state, gates, n_gates, init && *init == 1, stream);
+    if (st != QW_OK) return st;
+  })
+}
+
+qw_status qw_sv_energy_dev(qw_engine *e, uint32_t mode, uint32_t n, const void *state,
+                           const qw_pauli_term *terms, uint64_t n_terms, double *energy, double *norm2,
+                           void *stream) {
+  QW_GUARD({
+    if (!e || !state || (n_terms && !terms) || !energy) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    if (mode > QW_MODE_SV_FP32) fail(QW_ERR_INVALID_ARG, "statevector modes only");
+    if (n < SV_G || n > QW_SV_MAX_QUBITS) fail(QW_ERR_INVALID_ARG, "n must be in [%d, %d] for device buffers", SV_G, QW_SV_MAX_QUBITS);
+    const uint64_t mask = (1ull << n) - 1;
+    for (uint64_t k = 0; k < n_terms; k++)
+      if ((terms[k].xmask | terms[k].zmask) & ~mask) fail(QW_ERR_INVALID_ARG, "term %llu outside the register", (unsigned long long)k);
+    qw_status st = sv_energy_dev(&e->e, mode, n, state, terms, n_terms, energy, norm2, stream);
+    if (st != QW_OK) return st;
+  })
+}
+
+qw_status qw_sv_sample_dev(qw_engine *e, uint32_t mode, uint32_t n, const void *state, const double *uniforms,
+                           uint32_t shots, uint64_t *out, void *stream) {
+  QW_GUARD({
+    if (!e || !state || (shots && (!uniforms || !out))) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    if (mode > QW_MODE_SV_FP32) fail(QW_ERR_INVALID_ARG, "statevector modes only");
+    if (n < SV_G || n > QW_SV_MAX_QUBITS) fail(QW_ERR_INVALID_ARG, "n must be in [%d, %d] for device buffers", SV_G, QW_SV_MAX_QUBITS);
+    for (uint32_t k = 0; k < shots; k++)
+      if (!(uniforms[k] >= 0.0 && uniforms[k] < 1.0)) fail(QW_ERR_INVALID_ARG, "uniform %u outside [0,1)", k);
+    qw_status st = sv_sample_dev(&e->e, mode, n, state, uniforms, shots, out, stream);
+    if (st != QW_OK) return st;
+  })
+}
+
+}  // extern "C"

@@ -1,0 +1,1110 @@
+// Engine: device memory, boundary-state store, execution of a plan,
+// CUDA-graph capture, autotuning of the tile schedule and the learned cost
+// model's training loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <functional>
+#include <map>
+#include <random>
+
+#include "plan.h"
+
+namespace qw {
+
+#define CK(x)                                                                       \
+  do {                                                                              \
+    cudaError_t e_ = (x);                                                           \
+    if (e_ != cudaSuccess)                                                          \
+      fail(e_ == cudaErrorMemoryAllocation ? QW_ERR_OOM : QW_ERR_CUDA, "%s: %s (%s:%d)", #x, \
+           cudaGetErrorString(e_), __FILE__, __LINE__);                             \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+__global__ void convert_kernel(const void *src, bool src64, void *dst, bool dst64, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double re, im;
+  if (src64) { const double2 v = ((const double2 *)src)[i]; re = v.x; im = v.y; }
+  else { const float2 v = ((const float2 *)src)[i]; re = v.x; im = v.y; }
+  if (dst64) ((double2 *)dst)[i] = make_double2(re, im);
+  else ((float2 *)dst)[i] = make_float2((float)re, (float)im);
+}
+
+void launch_copy(const void *src, void *dst, size_t bytes, void *stream) {
+  if (bytes) cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// device-side tables of a set of statevector programs
+// ---------------------------------------------------------------------------
+struct SvTableBuilder {
+  std::vector<SvPassDesc> passes;
+  std::vector<SvStageDesc> stages;
+  std::vector<SvOpDesc<float>> ops32;
+  std::vector<SvOpDesc<double>> ops64;
+  bool fp64;
+  explicit SvTableBuilder(bool f) : fp64(f) {}
+  // appends the program; returns the index of its first pass
+  uint32_t add(const SvProgram &pr) {
+    const uint32_t first = (uint32_t)passes.size();
+    for (const HostPass &hp : pr.passes) {
+      SvPassDesc d;
+      memset(&d, 0, sizeof(d));
+      d.k = (uint32_t)hp.q.size();
+      d.b = hp.b;
+      d.n_stages = (uint32_t)hp.stages.size();
+      d.stage_begin = (uint32_t)stages.size();
+      uint32_t inq = 0;
+      for (uint32_t q : hp.q) inq |= 1u << q;
+      uint32_t nh = 0;
+      for (uint32_t q = 0; q < pr.n; q++)
+        if (!(inq & (1u << q))) d.hi_pos[nh++] = (uint8_t)q;
+      d.n_hi = nh;
+      // local bit i (>= b) -> global qubit hp.q[i]
+      for (uint32_t v = 0; v < 64; v++) {
+        uint32_t g = 0;
+        for (uint32_t j = 0; j < 6; j++)
+          if ((v >> j) & 1u) { const uint32_t li = d.b + j; if (li < d.k) g |= 1u << hp.q[li]; }
+        d.lo_tab[v] = g;
+      }
+      for (uint32_t v = 0; v < 32; v++) {
+        uint32_t g = 0;
+        for (uint32_t j = 0; j < 5; j++)
+          if ((v >> j) & 1u) { const uint32_t li = d.b + 6 + j; if (li < d.k) g |= 1u << hp.q[li]; }
+        d.hi_tab[v] = g;
+      }
+      for (const HostStage &hs : hp.stages) {
+        SvStageDesc sd;
+        memset(&sd, 0, sizeof(sd));
+        for (int j = 0; j < SV_G; j++) sd.pos[j] = hs.pos[j];
+        sd.n_ops = (uint16_t)hs.ops.size();
+        sd.op_begin = (uint32_t)(fp64 ? ops64.size() : ops32.size());
+        for (const HostOp &o : hs.ops) {
+          const uint32_t code = (uint32_t)o.kind | ((uint32_t)o.a << 8) | ((uint32_t)o.b << 16);
+          if (fp64) {
+            SvOpDesc<double> od{};
+            od.code = code;
+            for (int t = 0; t < 8; t++) od.m[t] = o.m[t];
+            ops64.push_back(od);
+          } else {
+            SvOpDesc<float> od{};
+            od.code = code;
+            for (int t = 0; t < 8; t++) od.m[t] = (float)o.m[t];
+            ops32.push_back(od);
+          }
+        }
+        stages.push_back(sd);
+      }
+      passes.push_back(d);
+    }
+    return first;
+  }
+};
+
+// device allocation tracked for release
+struct DevArena {
+  std::vector<void *> ptrs;
+  void *alloc(size_t bytes) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    CK(cudaMalloc(&p, bytes));
+    ptrs.push_back(p);
+    return p;
+  }
+  template <typename T>
+  T *upload(const std::vector<T> &v, cudaStream_t s) {
+    T *p = (T *)alloc(v.size() * sizeof(T));
+    if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return p;
+  }
+  void release() {
+    for (void *p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+struct Wave {
+  bool fp64 = false;
+  uint32_t k_max = 13;
+  int grid = 0;
+  std::vector<uint32_t> tasks;            // tasks run in this wave (own buffers)
+  std::vector<uint32_t> obs_tasks;        // tasks whose observables are evaluated in this wave
+  std::vector<SvJob> jobs;
+  uint32_t total_items = 0;
+  SvJob *d_jobs = nullptr;
+  unsigned int *d_ctr = nullptr;
+  size_t ctr_words = 0;
+  std::vector<EnJob> en;
+  uint32_t en_blocks = 0;
+  EnJob *d_en = nullptr;
+  std::vector<SmpSource> src;
+  uint32_t smp_blocks = 0;
+  SmpSource *d_src = nullptr;
+  std::vector<SmpShot> shots;
+  SmpShot *d_shots = nullptr;
+  std::vector<std::pair<uint32_t, std::pair<const void *, void *>>> converts;  // task, (src, dst)
+};
+
+struct DeviceState {
+  DevArena arena;
+  cudaStream_t stream = nullptr;
+  SvTables t32{}, t64{};
+  std::vector<uint32_t> mat_pass0, task_pass0;
+  std::vector<void *> mat_buf;
+  std::vector<void *> task_state;  // state a task's observables read
+  std::vector<Wave> waves;
+  EnClass *d_classes = nullptr;
+  EnTerm *d_terms = nullptr;
+  std::vector<uint32_t> ham_class_off;
+  double *d_partials = nullptr;
+  double *d_bsum = nullptr, *d_boff = nullptr;
+  int32_t *d_blast = nullptr;
+  int64_t *d_lastnz = nullptr;
+  double *d_energy = nullptr;
+  uint64_t *d_samples = nullptr;
+  // tableau
+  TabProgram *d_progs = nullptr;
+  TabLayer *d_layers = nullptr;
+  TabSlot *d_slots = nullptr;
+  uint8_t *d_bits = nullptr;
+  uint8_t *d_outs = nullptr, *d_mat_outs = nullptr;
+  struct TabLaunch {
+    TabArgs a;
+    uint32_t n_tasks;
+  };
+  std::vector<TabLaunch> tab_mat_launches, tab_task_launches;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t ev[8] = {nullptr};
+  std::vector<cudaEvent_t> wave_ev;  // 4 per wave: start, after suffix, after energy, after sampling
+  ~DeviceState() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto &e : ev) if (e) cudaEventDestroy(e);
+    for (auto &e : wave_ev) cudaEventDestroy(e);
+    arena.release();
+  }
+};
+
+static size_t sv_state_bytes(bool fp64, uint32_t n_eff) { return (size_t)(fp64 ? 16 : 8) << n_eff; }
+
+// ---------------------------------------------------------------------------
+// prepare: allocate, upload, build launch descriptors
+// ---------------------------------------------------------------------------
+static void prepare(qw_plan *P) {
+  Engine *E = P->eng;
+  DeviceState *D = new DeviceState();
+  P->dev = D;
+  D->stream = (cudaStream_t)E->stream;
+  cudaStream_t s = D->stream;
+  const uint32_t nt = (uint32_t)P->tasks.size();
+
+  // statevector programs
+  SvTableBuilder b32(false), b64(true);
+  D->mat_pass0.assign(P->mats.size(), 0);
+  D->task_pass0.assign(nt, 0);
+  for (size_t m = 0; m < P->mats.size(); m++) {
+    const MatNode &M = P->mats[m];
+    if (M.mode == QW_MODE_TABLEAU) continue;
+    D->mat_pass0[m] = (M.mode == QW_MODE_SV_FP64 ? b64 : b32).add(M.sv);
+  }
+  for (uint32_t t = 0; t < nt; t++) {
+    const TaskPlan &tp = P->tasks[t];
+    if (tp.mode == QW_MODE_TABLEAU) continue;
+    D->task_pass0[t] = (tp.mode == QW_MODE_SV_FP64 ? b64 : b32).add(tp.sv);
+  }
+  D->t32.passes = D->arena.upload(b32.passes, s);
+  D->t32.stages = D->arena.upload(b32.stages, s);
+  D->t32.ops = D->arena.upload(b32.ops32, s);
+  D->t64.passes = D->arena.upload(b64.passes, s);
+  D->t64.stages = D->arena.upload(b64.stages, s);
+  D->t64.ops = D->arena.upload(b64.ops64, s);
+
+  // boundary store (budget was enforced by the planner)
+  D->mat_buf.assign(P->mats.size(), nullptr);
+  for (size_t m = 0; m < P->mats.size(); m++) {
+    const MatNode &M = P->mats[m];
+    if (M.mode == QW_MODE_TABLEAU) {
+      const uint32_t W = (M.n + 63) / 64;
+      D->mat_buf[m] = D->arena.alloc((size_t)2 * M.n * 2 * W * 8 + 2 * M.n + 64);
+    } else {
+      D->mat_buf[m] = D->arena.alloc(sv_state_bytes(M.mode == QW_MODE_SV_FP64, M.n_eff));
+    }
+  }
+
+  // Hamiltonians
+  std::vector<EnClass> cls;
+  std::vector<EnTerm> trm;
+  for (auto &H : P->hams) {
+    D->ham_class_off.push_back((uint32_t)cls.size());
+    const uint32_t toff = (uint32_t)trm.size();
+    for (EnClass c : H.classes) {
+      c.term_begin += toff;
+      c.term_end += toff;
+      cls.push_back(c);
+    }
+    trm.insert(trm.end(), H.terms.begin(), H.terms.end());
+  }
+  D->d_classes = D->arena.upload(cls, s);
+  D->d_terms = D->arena.upload(trm, s);
+
+  // results
+  D->d_energy = (double *)D->arena.alloc(sizeof(double) * 2 * std::max<uint32_t>(nt, 1));
+  P->sample_off.assign(nt + 1, 0);
+  for (uint32_t t = 0; t < nt; t++) P->sample_off[t + 1] = P->sample_off[t] + P->tasks[t].shots;
+  D->d_samples = (uint64_t *)D->arena.alloc(sizeof(uint64_t) * std::max<uint64_t>(1, P->sample_off[nt]));
+
+  // ---- statevector tasks: buffers and waves --------------------------------
+  D->task_state.assign(nt, nullptr);
+  std::map<std::pair<int, uint32_t>, std::vector<uint32_t>> groups;  // (fp64, n_eff) -> tasks
+  for (uint32_t t = 0; t < nt; t++) {
+    const TaskPlan &tp = P->tasks[t];
+    if (tp.mode == QW_MODE_TABLEAU) continue;
+    groups[{tp.mode == QW_MODE_SV_FP64 ? 1 : 0, tp.n_eff}].push_back(t);
+  }
+  size_t max_partials = 1, max_smp_blocks = 1, max_src = 1;
+  const bool batched = P->opts.batched != 0;
+  for (auto &g : groups) {
+    const bool fp64 = g.first.first != 0;
+    const uint32_t n_eff = g.first.second;
+    const size_t S = sv_state_bytes(fp64, n_eff);
+    std::vector<uint32_t> own, shared_src;
+    for (uint32_t t : g.second) {
+      const TaskPlan &tp = P->tasks[t];
+      const bool convert = tp.src >= 0 && P->mats[tp.src].mode != tp.mode;
+      if (!tp.sv.passes.empty() || convert) own.push_back(t);
+      else { shared_src.push_back(t); D->task_state[t] = D->mat_buf[tp.src]; }
+    }
+    // KEEP_STATE tasks get dedicated buffers; the others share a pool
+    size_t per_wave = batched ? std::max<size_t>(1, E->task_budget / std::max<size_t>(S, 1)) : 1;
+    std::vector<uint32_t> pooled;
+    for (uint32_t t : own) {
+      if (P->tasks[t].flags & QW_TASK_KEEP_STATE) D->task_state[t] = D->arena.alloc(S);
+      else pooled.push_back(t);
+    }
+    const size_t pool_n = std::min(per_wave, pooled.size());
+    std::vector<void *> pool(pool_n);
+    for (auto &p : pool) p = D->arena.alloc(S);
+    // waves: dedicated tasks first (one wave), then pooled chunks
+    std::vector<std::vector<uint32_t>> wave_tasks;
+    std::vector<uint32_t> dedicated;
+    for (uint32_t t : own) if (P->tasks[t].flags & QW_TASK_KEEP_STATE) dedicated.push_back(t);
+    if (batched) {
+      if (!dedicated.empty()) wave_tasks.push_back(dedicated);
+      for (size_t i = 0; i < pooled.size(); i += pool_n)
+        wave_tasks.push_back(std::vector<uint32_t>(pooled.begin() + i,
+                                                   pooled.begin() + std::min(pooled.size(), i + pool_n)));
+    } else {
+      for (uint32_t t : own) wave_tasks.push_back({t});
+    }
+    if (wave_tasks.empty()) wave_tasks.push_back({});
+    for (size_t w = 0; w < wave_tasks.size(); w++) {
+      Wave W;
+      W.fp64 = fp64;
+      W.tasks = wave_tasks[w];
+      uint32_t kmax = 5;
+      for (size_t i = 0; i < W.tasks.size(); i++) {
+        const uint32_t t = W.tasks[i];
+        if (!(P->tasks[t].flags & QW_TASK_KEEP_STATE)) D->task_state[t] = pool[i % std::max<size_t>(1, pool_n)];
+        for (const HostPass &hp : P->tasks[t].sv.passes) kmax = std::max<uint32_t>(kmax, (uint32_t)hp.q.size());
+      }
+      W.k_max = kmax;
+      W.obs_tasks = W.tasks;
+      if (w == 0) W.obs_tasks.insert(W.obs_tasks.end(), shared_src.begin(), shared_src.end());
+      // jobs, round-robin over pass index (window = all tasks of the wave)
+      uint32_t window = P->opts.window ? P->opts.window : (uint32_t)W.tasks.size();
+      window = std::max<uint32_t>(1, window);
+      for (size_t w0 = 0; w0 < W.tasks.size(); w0 += window) {
+        const size_t w1 = std::min(W.tasks.size(), w0 + window);
+        size_t max_p = 0;
+        for (size_t i = w0; i < w1; i++) max_p = std::max(max_p, P->tasks[W.tasks[i]].sv.passes.size());
+        std::vector<int> last(W.tasks.size(), -1);
+        for (size_t p = 0; p < max_p; p++) {
+          for (size_t i = w0; i < w1; i++) {
+            const uint32_t t = W.tasks[i];
+            const TaskPlan &tp = P->tasks[t];
+            if (p >= tp.sv.passes.size()) continue;
+            SvJob j{};
+            const bool convert = tp.src >= 0 && P->mats[tp.src].mode != tp.mode;
+            j.src = (p == 0 && !convert) ? (tp.src >= 0 ? D->mat_buf[tp.src] : nullptr) : D->task_state[t];
+            j.dst = D->task_state[t];
+            j.pass = D->task_pass0[t] + (uint32_t)p;
+            j.n_tiles = 1u << (tp.n_eff - (uint32_t)tp.sv.passes[p].q.size());
+            j.dep = last[i];
+            j.item_begin = W.total_items;
+            j.n = tp.n_eff;
+            W.total_items += j.n_tiles;
+            last[i] = (int)W.jobs.size();
+            W.jobs.push_back(j);
+          }
+        }
+      }
+      for (uint32_t t : W.tasks) {
+        const TaskPlan &tp = P->tasks[t];
+        if (tp.src >= 0 && P->mats[tp.src].mode != tp.mode)
+          W.converts.push_back({t, {D->mat_buf[tp.src], D->task_state[t]}});
+      }
+      // energy jobs
+      for (uint32_t t : W.obs_tasks) {
+        const TaskPlan &tp = P->tasks[t];
+        if (tp.ham < 0) continue;
+        const HamLayout &H = P->hams[tp.ham];
+        EnJob j{};
+        j.state = D->task_state[t];
+        j.out = D->d_energy + 2 * (size_t)t;
+        j.n = H.n_eff;
+        j.chunk_bits = H.chunk_bits;
+        j.class_begin = D->ham_class_off[tp.ham];
+        j.n_classes = (uint32_t)H.classes.size();
+        j.block_begin = W.en_blocks;
+        j.n_blocks = H.n_blocks;
+        W.en_blocks += H.n_blocks;
+        W.en.push_back(j);
+      }
+      max_partials = std::max<size_t>(max_partials, W.en_blocks);
+      // sampling sources (deduplicated by state) and shots
+      std::map<const void *, uint32_t> sid;
+      for (uint32_t t : W.obs_tasks) {
+        const TaskPlan &tp = P->tasks[t];
+        if (!tp.shots) continue;
+        const void *st = D->task_state[t];
+        auto it = sid.find(st);
+        uint32_t si;
+        if (it == sid.end()) {
+          SmpSource so{};
+          so.state = st;
+          so.n = tp.n_eff;
+          so.n_blocks = (tp.n_eff >= (uint32_t)SMP_BLOCK_BITS) ? (1u << (tp.n_eff - SMP_BLOCK_BITS)) : 1u;
+          so.block_begin = W.smp_blocks;
+          W.smp_blocks += so.n_blocks;
+          si = (uint32_t)W.src.size();
+          W.src.push_back(so);
+          sid[st] = si;
+        } else {
+          si = it->second;
+        }
+        for (uint32_t k = 0; k < tp.shots; k++) {
+          SmpShot q{};
+          q.u = tp.uniforms[k];
+          q.source = si;
+          q.out = D->d_samples + P->sample_off[t] + k;
+          W.shots.push_back(q);
+        }
+      }
+      max_smp_blocks = std::max<size_t>(max_smp_blocks, W.smp_blocks);
+      max_src = std::max<size_t>(max_src, W.src.size());
+      // device copies
+      W.d_jobs = D->arena.upload(W.jobs, s);
+      W.ctr_words = 2 + W.jobs.size();
+      W.d_ctr = (unsigned int *)D->arena.alloc(W.ctr_words * sizeof(unsigned int));
+      CK(cudaMemsetAsync(W.d_ctr, 0, W.ctr_words * sizeof(unsigned int), s));
+      W.d_en = D->arena.upload(W.en, s);
+      W.d_src = D->arena.upload(W.src, s);
+      W.d_shots = D->arena.upload(W.shots, s);
+      W.grid = batched ? sv_batch_grid(fp64, W.k_max, E->sm_count) : 0;
+      D->waves.push_back(std::move(W));
+    }
+  }
+  D->d_partials = (double *)D->arena.alloc(sizeof(double) * 2 * max_partials);
+  D->d_bsum = (double *)D->arena.alloc(sizeof(double) * max_smp_blocks);
+  D->d_blast = (int32_t *)D->arena.alloc(sizeof(int32_t) * max_smp_blocks);
+  D->d_boff = (double *)D->arena.alloc(sizeof(double) * (max_smp_blocks + max_src));
+  D->d_lastnz = (int64_t *)D->arena.alloc(sizeof(int64_t) * max_src);
+
+  // ---- tableau --------------------------------------------------------------
+  std::vector<TabProgram> progs;
+  std::vector<TabLayer> layers;
+  std::vector<TabSlot> slots;
+  for (const TabHostProgram &hp : P->tab_progs) {
+    TabProgram pg{};
+    pg.layer_begin = (uint32_t)layers.size();
+    pg.n_layers = (uint32_t)hp.layers.size();
+    pg.n_bits = hp.n_bits;
+    pg.n_outs = hp.n_outs;
+    const uint32_t soff = (uint32_t)slots.size();
+    for (TabLayer L : hp.layers) { L.slot_begin += soff; layers.push_back(L); }
+    slots.insert(slots.end(), hp.slots.begin(), hp.slots.end());
+    progs.push_back(pg);
+  }
+  bool any_tab = !P->tab_progs.empty();
+  if (any_tab) {
+    D->d_progs = D->arena.upload(progs, s);
+    D->d_layers = D->arena.upload(layers, s);
+    D->d_slots = D->arena.upload(slots, s);
+    D->d_bits = D->arena.upload(P->tab_bits, s);
+    // outcome layout
+    P->outs_off.assign(nt + 1, 0);
+    for (uint32_t t = 0; t < nt; t++) P->outs_off[t + 1] = P->outs_off[t] + P->tasks[t].tab_outs;
+    P->outs_mat_off.assign(P->mats.size() + 1, 0);
+    for (size_t m = 0; m < P->mats.size(); m++) P->outs_mat_off[m + 1] = P->outs_mat_off[m] + P->mats[m].tab_outs;
+    D->d_outs = (uint8_t *)D->arena.alloc(std::max<uint32_t>(1, P->outs_off[nt]));
+    D->d_mat_outs = (uint8_t *)D->arena.alloc(std::max<uint32_t>(1, P->outs_mat_off[P->mats.size()]));
+    auto add_launch = [&](std::vector<DeviceState::TabLaunch> &dst, uint32_t n, const void *init,
+                          void *out_buf, const std::vector<TabTaskDesc> &descs,
+                          const std::vector<TabSegment> &segs, uint8_t *outs) {
+      TabArgs a{};
+      a.n = n;
+      a.W = (n + 63) / 64;
+      a.lpp = a.W <= 8 ? 8 : (a.W <= 16 ? 16 : 32);
+      a.rows = 2 * n;
+      const size_t words = (size_t)a.rows * 2 * a.W;
+      a.init_rows = (const uint64_t *)init;
+      a.init_sign = init ? (const uint8_t *)((const uint64_t *)init + words) : nullptr;
+      a.out_rows = (uint64_t *)out_buf;
+      a.out_sign = out_buf ? (uint8_t *)((uint64_t *)out_buf + words) : nullptr;
+      a.tasks = D->arena.upload(descs, s);
+      a.segs = D->arena.upload(segs, s);
+      a.progs = D->d_progs;
+      a.layers = D->d_layers;
+      a.slots = D->d_slots;
+      a.bits = D->d_bits;
+      a.outs = outs;
+      dst.push_back({a, (uint32_t)descs.size()});
+    };
+    for (size_t m = 0; m < P->mats.size(); m++) {
+      const MatNode &M = P->mats[m];
+      if (M.mode != QW_MODE_TABLEAU) continue;
+      std::vector<TabSegment> segs;
+      uint32_t oo = 0;
+      for (auto &sg : M.tab_segs) {
+        segs.push_back({sg.first, sg.second, oo, 0});
+        oo += P->tab_progs[sg.first].n_outs;
+      }
+      std::vector<TabTaskDesc> d{{0, (uint32_t)segs.size(), 0, P->outs_mat_off[m]}};
+      add_launch(D->tab_mat_launches, M.n, M.parent >= 0 ? D->mat_buf[M.parent] : nullptr,
+                 D->mat_buf[m], d, segs, D->d_mat_outs);
+    }
+    std::map<std::pair<int, uint32_t>, std::vector<uint32_t>> by_src;
+    for (uint32_t t = 0; t < nt; t++)
+      if (P->tasks[t].mode == QW_MODE_TABLEAU) by_src[{P->tasks[t].src, P->tasks[t].n}].push_back(t);
+    for (auto &g : by_src) {
+      std::vector<TabTaskDesc> descs;
+      std::vector<TabSegment> segs;
+      for (uint32_t t : g.second) {
+        const TaskPlan &tp = P->tasks[t];
+        TabTaskDesc d{};
+        d.seg_begin = (uint32_t)segs.size();
+        d.out_base = P->outs_off[t];
+        uint32_t oo = 0;
+        for (auto &sg : tp.tab_segs) {
+          segs.push_back({sg.first, sg.second, oo, 0});
+          oo += P->tab_progs[sg.first].n_outs;
+        }
+        d.n_segs = (uint32_t)segs.size() - d.seg_begin;
+        descs.push_back(d);
+      }
+      add_launch(D->tab_task_launches, g.first.second,
+                 g.first.first >= 0 ? D->mat_buf[g.first.first] : nullptr, nullptr, descs, segs,
+                 D->d_outs);
+    }
+  }
+  for (auto &e : D->ev) CK(cudaEventCreate(&e));
+  CK(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------------------
+// launch sequence of a prepared plan (captured once into a graph)
+// ---------------------------------------------------------------------------
+static void enqueue(qw_plan *P, cudaStream_t s) {
+  DeviceState *D = P->dev;
+  CK(cudaEventRecord(D->ev[0], s));
+  // 1) shared prefixes (boundary states), in creation order (parents first)
+  for (size_t m = 0; m < P->mats.size(); m++) {
+    const MatNode &M = P->mats[m];
+    if (M.mode == QW_MODE_TABLEAU) continue;
+    const bool fp64 = M.mode == QW_MODE_SV_FP64;
+    const SvTables &T = fp64 ? D->t64 : D->t32;
+    const void *psrc = (M.parent >= 0) ? D->mat_buf[M.parent] : nullptr;
+    if (M.parent >= 0 && P->mats[M.parent].mode != M.mode) psrc = nullptr;  // never crosses families
+    if (M.sv.passes.empty()) {
+      if (psrc) launch_copy(psrc, D->mat_buf[m], sv_state_bytes(fp64, M.n_eff), s);
+      continue;
+    }
+    for (size_t p = 0; p < M.sv.passes.size(); p++) {
+      launch_sv_pass(fp64, T, D->mat_pass0[m] + (uint32_t)p, (uint32_t)M.sv.passes[p].q.size(), M.n_eff,
+                     p == 0 ? psrc : D->mat_buf[m], D->mat_buf[m], s);
+    }
+  }
+  for (auto &L : D->tab_mat_launches) launch_tab(L.a, L.n_tasks, s);
+  CK(cudaEventRecord(D->ev[1], s));
+  // 2) task suffixes, observables
+  size_t wi = 0;
+  for (auto &W : D->waves) {
+    const SvTables &T = W.fp64 ? D->t64 : D->t32;
+    CK(cudaEventRecord(D->wave_ev[4 * wi], s));
+    for (auto &c : W.converts) {
+      const TaskPlan &tp = P->tasks[c.first];
+      const size_t n = (size_t)1 << tp.n_eff;
+      convert_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+          c.second.first, P->mats[tp.src].mode == QW_MODE_SV_FP64, c.second.second, W.fp64, n);
+    }
+    if (P->opts.batched) {
+      if (W.total_items) {
+        CK(cudaMemsetAsync(W.d_ctr, 0, W.ctr_words * sizeof(unsigned int), s));
+        launch_sv_batch(W.fp64, T, W.d_jobs, (uint32_t)W.jobs.size(), W.total_items, W.k_max, W.d_ctr,
+                        W.grid, s);
+      }
+    } else {
+      for (const SvJob &j : W.jobs) {
+        const uint32_t k = j.n - (uint32_t)std::log2((double)j.n_tiles);
+        launch_sv_pass(W.fp64, T, j.pass, k, j.n, j.src, j.dst, s);
+      }
+    }
+    CK(cudaEventRecord(D->wave_ev[4 * wi + 1], s));
+    launch_energy(W.fp64, W.d_en, (uint32_t)W.en.size(), W.en_blocks, D->d_classes, D->d_terms,
+                  D->d_partials, s);
+    CK(cudaEventRecord(D->wave_ev[4 * wi + 2], s));
+    launch_sampling(W.fp64, W.d_src, (uint32_t)W.src.size(), W.smp_blocks, D->d_bsum, D->d_blast, D->d_boff,
+                    D->d_lastnz, W.d_shots, (uint32_t)W.shots.size(), s);
+    CK(cudaEventRecord(D->wave_ev[4 * wi + 3], s));
+    wi++;
+  }
+  CK(cudaEventRecord(D->ev[2], s));
+  // 3) tableau tasks
+  for (auto &L : D->tab_task_launches) launch_tab(L.a, L.n_tasks, s);
+  CK(cudaEventRecord(D->ev[3], s));
+  CK(cudaGetLastError());
+}
+
+void plan_execute(qw_plan *P, void *stream) {
+  Engine *E = P->eng;
+  if (!E) fail(QW_ERR_STATE, "plan was created without an engine");
+  CK(cudaSetDevice(E->device));
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!P->dev) {
+    prepare(P);
+    P->t_upload_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    DeviceState *D = P->dev;
+    for (size_t w = 0; w < 4 * D->waves.size(); w++) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      D->wave_ev.push_back(e);
+    }
+  }
+  DeviceState *D = P->dev;
+  cudaStream_t s = stream ? (cudaStream_t)stream : D->stream;
+  if (P->opts.use_graph) {
+    if (!D->gexec) {
+      cudaStream_t cs = D->stream;
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      try {
+        enqueue(P, cs);
+      } catch (...) {
+        cudaGraph_t g;
+        cudaStreamEndCapture(cs, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+      }
+      CK(cudaStreamEndCapture(cs, &D->graph));
+      CK(cudaGraphInstantiate(&D->gexec, D->graph, 0));
+    }
+    CK(cudaGraphLaunch(D->gexec, s));
+  } else {
+    enqueue(P, s);
+  }
+  P->executed = true;
+}
+
+void plan_wait(qw_plan *P) {
+  DeviceState *D = P->dev;
+  if (!D) fail(QW_ERR_STATE, "qw_wait before qw_execute");
+  CK(cudaSetDevice(P->eng->device));
+  CK(cudaEventSynchronize(D->ev[3]));
+  CK(cudaGetLastError());
+  const uint32_t nt = (uint32_t)P->tasks.size();
+  // device error flags of the persistent launches
+  for (auto &W : D->waves) {
+    if (!W.total_items || !P->opts.batched) continue;
+    unsigned int flag = 0;
+    CK(cudaMemcpy(&flag, W.d_ctr + 1, sizeof(flag), cudaMemcpyDeviceToHost));
+    if (flag) fail(QW_ERR_DEVICE_TIMEOUT, "a bounded dependency wait of the persistent batch expired");
+  }
+  std::vector<double> en(2 * (size_t)nt);
+  if (nt) CK(cudaMemcpy(en.data(), D->d_energy, en.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  P->energy.assign(nt, 0);
+  P->norm2.assign(nt, 0);
+  for (uint32_t t = 0; t < nt; t++) { P->energy[t] = en[2 * t]; P->norm2[t] = en[2 * t + 1]; }
+  P->samples.assign(P->sample_off[nt], 0);
+  if (!P->samples.empty())
+    CK(cudaMemcpy(P->samples.data(), D->d_samples, P->samples.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  if (D->d_outs) {
+    P->outs_suffix.assign(P->outs_off[nt], 0);
+    if (!P->outs_suffix.empty())
+      CK(cudaMemcpy(P->outs_suffix.data(), D->d_outs, P->outs_suffix.size(), cudaMemcpyDeviceToHost));
+    P->outs_mat.assign(P->outs_mat_off.back(), 0);
+    if (!P->outs_mat.empty())
+      CK(cudaMemcpy(P->outs_mat.data(), D->d_mat_outs, P->outs_mat.size(), cudaMemcpyDeviceToHost));
+  }
+  float ms = 0;
+  cudaEventElapsedTime(&ms, D->ev[0], D->ev[1]);
+  P->t_prefix_ms = ms;
+  P->t_suffix_ms = P->t_energy_ms = P->t_sample_ms = 0;
+  P->batch_ms.assign(D->waves.size(), 0.0);
+  for (size_t w = 0; w < D->waves.size(); w++) {
+    cudaEventElapsedTime(&ms, D->wave_ev[4 * w], D->wave_ev[4 * w + 1]);
+    P->t_suffix_ms += ms;
+    P->batch_ms[w] = ms;
+    cudaEventElapsedTime(&ms, D->wave_ev[4 * w + 1], D->wave_ev[4 * w + 2]);
+    P->t_energy_ms += ms;
+    cudaEventElapsedTime(&ms, D->wave_ev[4 * w + 2], D->wave_ev[4 * w + 3]);
+    P->t_sample_ms += ms;
+  }
+  cudaEventElapsedTime(&ms, D->ev[2], D->ev[3]);
+  P->t_tab_ms = ms;
+  cudaEventElapsedTime(&ms, D->ev[0], D->ev[3]);
+  P->t_total_ms = ms;
+  P->timed++;
+}
+
+void plan_release(qw_plan *P) {
+  if (P->dev) {
+    if (P->eng) cudaSetDevice(P->eng->device);
+    cudaStreamSynchronize(P->dev->stream);
+    delete P->dev;
+    P->dev = nullptr;
+  }
+}
+
+void *plan_state_ptr(const qw_plan *P, uint64_t t) {
+  return P->dev ? P->dev->task_state[t] : nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// engine
+// ---------------------------------------------------------------------------
+__global__ void bw_probe_kernel(const float4 *a, float4 *b, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+void engine_init(Engine *E, const qw_engine_opts *o) {
+  E->device = o ? o->device : 0;
+  CK(cudaSetDevice(E->device));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, E->device));
+  E->sm_count = prop.multiProcessorCount;
+  E->l2_bytes = prop.l2CacheSize;
+  cudaStream_t s;
+  CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  E->stream = s;
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  E->store_budget = (o && o->store_budget_bytes) ? o->store_budget_bytes : (uint64_t)(0.4 * fr);
+  E->task_budget = (o && o->task_budget_bytes) ? o->task_budget_bytes : (uint64_t)(0.4 * fr);
+  if (o && o->hbm_gbs > 0) {
+    E->hbm_gbs = o->hbm_gbs;
+  } else {
+    const size_t n = (size_t)1 << 26;  // 1 GiB of float4 per buffer
+    float4 *a = nullptr, *b = nullptr;
+    CK(cudaMalloc(&a, n * sizeof(float4)));
+    CK(cudaMalloc(&b, n * sizeof(float4)));
+    CK(cudaMemsetAsync(a, 0, n * sizeof(float4), s));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int r = 0; r < 4; r++) {
+      cudaEventRecord(e0, s);
+      bw_probe_kernel<<<E->sm_count * 8, 256, 0, s>>>(a, b, n);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r) best = std::min(best, ms);
+    }
+    E->hbm_gbs = 2.0 * n * sizeof(float4) / (best * 1e-3) / 1e9;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(a);
+    cudaFree(b);
+  }
+  // kernel attributes are set before any capture
+  sv_batch_grid(false, 13, E->sm_count);
+  sv_batch_grid(true, 12, E->sm_count);
+  CK(cudaGetLastError());
+}
+
+void engine_release(Engine *E) {
+  cudaSetDevice(E->device);
+  if (E->scratch) cudaFree(E->scratch);
+  if (E->d_mlp) cudaFree(E->d_mlp);
+  if (E->stream) cudaStreamDestroy((cudaStream_t)E->stream);
+}
+
+void *Engine::ensure_scratch(size_t bytes) {
+  if (bytes > scratch_bytes) {
+    if (scratch) { cudaStreamSynchronize((cudaStream_t)stream); cudaFree(scratch); scratch = nullptr; }
+    CK(cudaMalloc(&scratch, bytes));
+    scratch_bytes = bytes;
+  }
+  return scratch;
+}
+
+// Autotuner: times one synthetic hardware-efficient layer stack under each
+// candidate (tile qubits, contiguous low qubits) and keeps the fastest per
+// (qubit count, precision).
+TileConfig Engine::tile_config(uint32_t n_eff, bool fp64) {
+  const uint32_t key_n = std::min<uint32_t>(n_eff, 26);
+  const uint64_t key = ((uint64_t)key_n << 1) | (fp64 ? 1 : 0);
+  auto it = tiles.find(key);
+  if (it != tiles.end()) return it->second;
+  TileConfig best;
+  best.k_max = fp64 ? SV_MAX_TILE_FP64 : SV_MAX_TILE_FP32;
+  best.b = 4;
+  if (key_n <= best.k_max) { tiles[key] = best; return best; }
+  CK(cudaSetDevice(device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::mt19937_64 rng(12345);
+  std::uniform_real_distribution<double> U(0, 6.283185307179586);
+  std::vector<qw_gate> g;
+  for (int l = 0; l < 3; l++) {
+    for (uint32_t q = 0; q < key_n; q++) g.push_back({QW_OP_RY, q, 0, 0, U(rng)});
+    for (uint32_t q = 0; q < key_n; q++) g.push_back({QW_OP_RZ, q, 0, 0, U(rng)});
+    for (uint32_t q = 0; q + 1 < key_n; q++) g.push_back({QW_OP_CNOT, q, q + 1, 0, 0.0});
+  }
+  for (int i = 0; i < 40 * (int)key_n; i++) {
+    const uint32_t a = (uint32_t)(rng() % key_n), b = (uint32_t)((a + 1 + rng() % (key_n - 1)) % key_n);
+    g.push_back({i % 3 == 0 ? (uint32_t)QW_OP_CZ : (uint32_t)QW_OP_RX, a, i % 3 == 0 ? b : 0, 0, U(rng)});
+  }
+  const size_t S = sv_state_bytes(fp64, key_n);
+  void *buf = nullptr;
+  CK(cudaMalloc(&buf, S));
+  CK(cudaMemsetAsync(buf, 0, S, s));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const uint32_t ks32[3] = {12, 13, 14}, ks64[3] = {11, 12, 13}, bs[3] = {3, 4, 5};
+  float best_ms = 1e30f;
+  for (int ki = 0; ki < 3; ki++) {
+    for (int bi = 0; bi < 3; bi++) {
+      TileConfig tc;
+      tc.k_max = fp64 ? ks64[ki] : ks32[ki];
+      tc.b = bs[bi];
+      if (tc.b + 2 > tc.k_max) continue;
+      SvProgram pr = fuse_sv(g.data(), g.size(), key_n, tc);
+      SvTableBuilder tb(fp64);
+      tb.add(pr);
+      SvTables T;
+      DevArena ar;
+      T.passes = ar.upload(tb.passes, s);
+      T.stages = ar.upload(tb.stages, s);
+      T.ops = fp64 ? (const void *)ar.upload(tb.ops64, s) : (const void *)ar.upload(tb.ops32, s);
+      float tot = 0;
+      for (int r = 0; r < 3; r++) {
+        cudaEventRecord(e0, s);
+        for (size_t p = 0; p < pr.passes.size(); p++)
+          launch_sv_pass(fp64, T, (uint32_t)p, (uint32_t)pr.passes[p].q.size(), key_n, buf, buf, s);
+        cudaEventRecord(e1, s);
+        CK(cudaEventSynchronize(e1));
+        float ms;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r) tot += ms;
+      }
+      CK(cudaStreamSynchronize(s));
+      ar.release();
+      if (tot < best_ms) { best_ms = tot; best = tc; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  CK(cudaGetLastError());
+  tiles[key] = best;
+  return best;
+}
+
+double Engine::predict_log2ns(const float *feat, uint32_t rows, float *out) {
+  CK(cudaSetDevice(device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<float> x((size_t)rows * QW_MLP_IN);
+  for (uint32_t r = 0; r < rows; r++)
+    for (int i = 0; i < QW_MLP_IN; i++)
+      x[(size_t)r * QW_MLP_IN + i] = (feat[(size_t)r * QW_MLP_IN + i] - cm.mean[i]) / cm.scale[i];
+  float *d = (float *)ensure_scratch(sizeof(float) * (x.size() + rows) + 256);
+  float *dy = d + x.size();
+  CK(cudaMemcpyAsync(d, x.data(), x.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  launch_mlp_forward(d_mlp, d, dy, rows, s);
+  CK(cudaMemcpyAsync(out, dy, rows * sizeof(float), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return out[0];
+}
+
+void costmodel_train(Engine *E, const float *feat, const float *tgt, uint64_t n, uint32_t epochs,
+                     uint32_t batch, float lr, uint64_t seed, float *final_loss) {
+  if (n == 0 || batch == 0) fail(QW_ERR_INVALID_ARG, "empty training set");
+  CK(cudaSetDevice(E->device));
+  cudaStream_t s = (cudaStream_t)E->stream;
+  CostModel &cm = E->cm;
+  // feature normalization and training ranges
+  for (int i = 0; i < QW_MLP_IN; i++) {
+    double mu = 0, sq = 0;
+    float lo = 1e30f, hi = -1e30f;
+    for (uint64_t r = 0; r < n; r++) {
+      const float v = feat[r * QW_MLP_IN + i];
+      mu += v; sq += (double)v * v;
+      lo = std::min(lo, v); hi = std::max(hi, v);
+    }
+    mu /= n;
+    const double var = std::max(0.0, sq / n - mu * mu);
+    cm.mean[i] = (float)mu;
+    cm.scale[i] = (float)(var > 1e-12 ? std::sqrt(var) : 1.0);
+    cm.f_lo[i] = lo;
+    cm.f_hi[i] = hi;
+  }
+  cm.y_lo = *std::min_element(tgt, tgt + n);
+  cm.y_hi = *std::max_element(tgt, tgt + n);
+  // init (He-uniform), bias of the output at the target mean
+  std::mt19937_64 rng(seed);
+  cm.params.assign(QW_MLP_PARAMS, 0.f);
+  auto fill = [&](int off, int count, int fan_in) {
+    const double a = std::sqrt(6.0 / fan_in);
+    std::uniform_real_distribution<double> U(-a, a);
+    for (int i = 0; i < count; i++) cm.params[off + i] = (float)U(rng);
+  };
+  fill(0, QW_MLP_IN * QW_MLP_HID, QW_MLP_IN);
+  fill(QW_MLP_IN * QW_MLP_HID + QW_MLP_HID, QW_MLP_HID * QW_MLP_HID, QW_MLP_HID);
+  fill(QW_MLP_IN * QW_MLP_HID + 2 * QW_MLP_HID + QW_MLP_HID * QW_MLP_HID, QW_MLP_HID, QW_MLP_HID);
+  double ym = 0;
+  for (uint64_t r = 0; r < n; r++) ym += tgt[r];
+  cm.params[QW_MLP_PARAMS - 1] = (float)(ym / n);
+  std::vector<float> xn(n * QW_MLP_IN);
+  for (uint64_t r = 0; r < n; r++)
+    for (int i = 0; i < QW_MLP_IN; i++) xn[r * QW_MLP_IN + i] = (feat[r * QW_MLP_IN + i] - cm.mean[i]) / cm.scale[i];
+  DevArena ar;
+  float *dX = ar.upload(xn, s);
+  std::vector<float> tv(tgt, tgt + n);
+  float *dT = ar.upload(tv, s);
+  if (E->d_mlp) { cudaFree(E->d_mlp); E->d_mlp = nullptr; }
+  CK(cudaMalloc(&E->d_mlp, QW_MLP_PARAMS * sizeof(float)));
+  CK(cudaMemcpyAsync(E->d_mlp, cm.params.data(), QW_MLP_PARAMS * sizeof(float), cudaMemcpyHostToDevice, s));
+  float *dG = (float *)ar.alloc(QW_MLP_PARAMS * sizeof(float));
+  float *dM = (float *)ar.alloc(QW_MLP_PARAMS * sizeof(float));
+  float *dV = (float *)ar.alloc(QW_MLP_PARAMS * sizeof(float));
+  float *dL = (float *)ar.alloc(sizeof(float));
+  float *dS = (float *)ar.alloc(mlp_scratch_floats(batch) * sizeof(float));
+  float *dXb = (float *)ar.alloc((size_t)batch * QW_MLP_IN * sizeof(float));
+  float *dTb = (float *)ar.alloc((size_t)batch * sizeof(float));
+  CK(cudaMemsetAsync(dM, 0, QW_MLP_PARAMS * sizeof(float), s));
+  CK(cudaMemsetAsync(dV, 0, QW_MLP_PARAMS * sizeof(float), s));
+  std::vector<uint32_t> perm(n);
+  for (uint64_t i = 0; i < n; i++) perm[i] = (uint32_t)i;
+  std::vector<float> bx((size_t)batch * QW_MLP_IN), bt(batch);
+  uint32_t step = 0;
+  for (uint32_t ep = 0; ep < epochs; ep++) {
+    std::shuffle(perm.begin(), perm.end(), rng);
+    for (uint64_t b0 = 0; b0 < n; b0 += batch) {
+      const uint32_t bs = (uint32_t)std::min<uint64_t>(batch, n - b0);
+      for (uint32_t i = 0; i < bs; i++) {
+        memcpy(&bx[(size_t)i * QW_MLP_IN], &xn[(size_t)perm[b0 + i] * QW_MLP_IN], QW_MLP_IN * sizeof(float));
+        bt[i] = tgt[perm[b0 + i]];
+      }
+      CK(cudaMemcpyAsync(dXb, bx.data(), (size_t)bs * QW_MLP_IN * sizeof(float), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(dTb, bt.data(), (size_t)bs * sizeof(float), cudaMemcpyHostToDevice, s));
+      launch_mlp_loss_grad(E->d_mlp, dXb, dTb, bs, dL, dG, dS, s);
+      launch_mlp_adam(E->d_mlp, dG, dM, dV, QW_MLP_PARAMS, ++step, lr, 0.9f, 0.999f, 1e-8f, s);
+      CK(cudaStreamSynchronize(s));  // bx/bt are reused by the next batch
+    }
+  }
+  // final full-set loss
+  float *dSall = (float *)ar.alloc(mlp_scratch_floats((uint32_t)n) * sizeof(float));
+  launch_mlp_loss_grad(E->d_mlp, dX, dT, (uint32_t)n, dL, dG, dSall, s);
+  float L = 0;
+  CK(cudaMemcpyAsync(&L, dL, sizeof(float), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(cm.params.data(), E->d_mlp, QW_MLP_PARAMS * sizeof(float), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  ar.release();
+  cm.trained = true;
+  if (final_loss) *final_loss = L;
+}
+
+void costmodel_set(Engine *E, const float *params, const float *mean, const float *scale) {
+  CK(cudaSetDevice(E->device));
+  E->cm.params.assign(params, params + QW_MLP_PARAMS);
+  memcpy(E->cm.mean, mean, sizeof(E->cm.mean));
+  memcpy(E->cm.scale, scale, sizeof(E->cm.scale));
+  for (int i = 0; i < QW_MLP_IN; i++) { E->cm.f_lo[i] = -1e30f; E->cm.f_hi[i] = 1e30f; }
+  if (!E->d_mlp) CK(cudaMalloc(&E->d_mlp, QW_MLP_PARAMS * sizeof(float)));
+  CK(cudaMemcpy(E->d_mlp, params, QW_MLP_PARAMS * sizeof(float), cudaMemcpyHostToDevice));
+  E->cm.trained = true;
+}
+
+// timing probe: runs segments of the workload's statevector tasks on a
+// scratch state and records (features, log2 ns)
+void costmodel_probe(Engine *E, const Workload &W, float *feat, float *tgt, uint64_t cap, uint64_t *n_rows) {
+  CK(cudaSetDevice(E->device));
+  cudaStream_t s = (cudaStream_t)E->stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  uint64_t rows = 0;
+  std::mt19937_64 rng(777);
+  std::vector<qw_gate> buf;
+  for (const TaskData &T : W.tasks) {
+    if (rows >= cap) break;
+    if (T.mode == QW_MODE_TABLEAU || T.n_gates == 0) continue;
+    const bool fp64 = T.mode == QW_MODE_SV_FP64;
+    const uint32_t n_eff = std::max<uint32_t>(T.n, SV_G);
+    TileConfig tc = E->tile_config(n_eff, fp64);
+    const size_t S = sv_state_bytes(fp64, n_eff);
+    void *st = E->ensure_scratch(S);
+    CK(cudaMemsetAsync(st, 0, S, s));
+    // segments: full list, and a prefix / suffix split at a random point
+    const uint64_t c = 1 + rng() % std::max<uint64_t>(1, T.n_gates - 1);
+    const std::pair<uint64_t, uint64_t> segs[3] = {{0, T.n_gates}, {0, c}, {c, T.n_gates}};
+    for (auto sg : segs) {
+      if (rows >= cap || sg.second <= sg.first) continue;
+      T.copy_gates(sg.first, sg.second, buf);
+      SvProgram pr = fuse_sv(buf.data(), buf.size(), n_eff, tc);
+      SvTableBuilder tb(fp64);
+      tb.add(pr);
+      DevArena ar;
+      SvTables Tt;
+      Tt.passes = ar.upload(tb.passes, s);
+      Tt.stages = ar.upload(tb.stages, s);
+      Tt.ops = fp64 ? (const void *)ar.upload(tb.ops64, s) : (const void *)ar.upload(tb.ops32, s);
+      float best = 1e30f;
+      for (int r = 0; r < 3; r++) {
+        cudaEventRecord(e0, s);
+        for (size_t p = 0; p < pr.passes.size(); p++)
+          launch_sv_pass(fp64, Tt, (uint32_t)p, (uint32_t)pr.passes[p].q.size(), n_eff, st, st, s);
+        cudaEventRecord(e1, s);
+        CK(cudaEventSynchronize(e1));
+        float ms;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r) best = std::min(best, ms);
+      }
+      ar.release();
+      features_for(T, sg.first, sg.second, 1, tc, 0.0, feat + rows * QW_MLP_IN);
+      tgt[rows] = (float)std::log2(std::max(1.0, (double)best * 1e6));
+      rows++;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  *n_rows = rows;
+}
+
+}  // namespace qw
+
+// ---------------------------------------------------------------------------
+// kernels on caller-owned device buffers
+// ---------------------------------------------------------------------------
+namespace qw {
+
+template <typename T>
+static T *stream_upload(const std::vector<T> &v, cudaStream_t s) {
+  T *p = nullptr;
+  CK(cudaMallocAsync((void **)&p, std::max<size_t>(16, v.size() * sizeof(T)), s));
+  if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return p;
+}
+
+qw_status sv_apply_dev(Engine *E, uint32_t mode, uint32_t n, void *state, const qw_gate *gates,
+                       uint64_t n_gates, bool init, void *stream) {
+  CK(cudaSetDevice(E->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool fp64 = mode == QW_MODE_SV_FP64;
+  TileConfig tc = E->tile_config(n, fp64);
+  SvProgram pr = fuse_sv(gates, n_gates, n, tc);
+  if (pr.passes.empty()) {
+    if (!init) return QW_OK;
+    HostPass hp;
+    const uint32_t k = std::min(tc.k_max, n);
+    for (uint32_t q = 0; q < k; q++) hp.q.push_back(q);
+    hp.b = (n <= tc.k_max) ? n : std::min(tc.b, k - 2);
+    pr.passes.push_back(hp);
+  }
+  SvTableBuilder tb(fp64);
+  tb.add(pr);
+  SvTables T;
+  SvPassDesc *dp = stream_upload(tb.passes, s);
+  SvStageDesc *ds = stream_upload(tb.stages, s);
+  void *dop = fp64 ? (void *)stream_upload(tb.ops64, s) : (void *)stream_upload(tb.ops32, s);
+  T.passes = dp;
+  T.stages = ds;
+  T.ops = dop;
+  for (size_t p = 0; p < pr.passes.size(); p++)
+    launch_sv_pass(fp64, T, (uint32_t)p, (uint32_t)pr.passes[p].q.size(), n,
+                   (p == 0 && init) ? nullptr : state, state, s);
+  CK(cudaGetLastError());
+  CK(cudaFreeAsync(dp, s));
+  CK(cudaFreeAsync(ds, s));
+  CK(cudaFreeAsync(dop, s));
+  return QW_OK;
+}
+
+qw_status sv_energy_dev(Engine *E, uint32_t mode, uint32_t n, const void *state, const qw_pauli_term *terms,
+                        uint64_t n_terms, double *energy, double *norm2, void *stream) {
+  CK(cudaSetDevice(E->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool fp64 = mode == QW_MODE_SV_FP64;
+  HamLayout H;
+  build_energy_layout(terms, n_terms, n, &H.chunk_bits, H.classes, H.terms, &H.n_blocks);
+  EnClass *dc = stream_upload(H.classes, s);
+  EnTerm *dt = stream_upload(H.terms, s);
+  double *dout = nullptr, *dpart = nullptr;
+  CK(cudaMallocAsync((void **)&dout, 2 * sizeof(double), s));
+  CK(cudaMallocAsync((void **)&dpart, 2 * sizeof(double) * H.n_blocks, s));
+  EnJob j{};
+  j.state = state;
+  j.out = dout;
+  j.n = n;
+  j.chunk_bits = H.chunk_bits;
+  j.class_begin = 0;
+  j.n_classes = (uint32_t)H.classes.size();
+  j.block_begin = 0;
+  j.n_blocks = H.n_blocks;
+  EnJob *dj = stream_upload(std::vector<EnJob>{j}, s);
+  launch_energy(fp64, dj, 1, H.n_blocks, dc, dt, dpart, s);
+  double res[2];
+  CK(cudaMemcpyAsync(res, dout, sizeof(res), cudaMemcpyDeviceToHost, s));
+  CK(cudaFreeAsync(dc, s));
+  CK(cudaFreeAsync(dt, s));
+  CK(cudaFreeAsync(dout, s));
+  CK(cudaFreeAsync(dpart, s));
+  CK(cudaFreeAsync(dj, s));
+  CK(cudaStreamSynchronize(s));
+  *energy = res[0];
+  if (norm2) *norm2 = res[1];
+  return QW_OK;
+}
+
+qw_status sv_sample_dev(Engine *E, uint32_t mode, uint32_t n, const void *state, const double *u,
+                        uint32_t shots, uint64_t *out, void *stream) {
+  CK(cudaSetDevice(E->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (shots == 0) return QW_OK;
+  const bool fp64 = mode == QW_MODE_SV_FP64;
+  SmpSource so{};
+  so.state = state;
+  so.n = n;
+  so.n_blocks = (n >= (uint32_t)SMP_BLOCK_BITS) ? (1u << (n - SMP_BLOCK_BITS)) : 1u;
+  so.block_begin = 0;
+  uint64_t *dres = nullptr;
+  CK(cudaMallocAsync((void **)&dres, shots * sizeof(uint64_t), s));
+  std::vector<SmpShot> sh(shots);
+  for (uint32_t k = 0; k < shots; k++) { sh[k].u = u[k]; sh[k].source = 0; sh[k].out = dres + k; }
+  SmpSource *dsrc = stream_upload(std::vector<SmpSource>{so}, s);
+  SmpShot *dsh = stream_upload(sh, s);
+  double *bsum = nullptr, *boff = nullptr;
+  int32_t *blast = nullptr;
+  int64_t *lastnz = nullptr;
+  CK(cudaMallocAsync((void **)&bsum, so.n_blocks * sizeof(double), s));
+  CK(cudaMallocAsync((void **)&boff, (so.n_blocks + 1) * sizeof(double), s));
+  CK(cudaMallocAsync((void **)&blast, so.n_blocks * sizeof(int32_t), s));
+  CK(cudaMallocAsync((void **)&lastnz, sizeof(int64_t), s));
+  launch_sampling(fp64, dsrc, 1, so.n_blocks, bsum, blast, boff, lastnz, dsh, shots, s);
+  CK(cudaMemcpyAsync(out, dres, shots * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  for (void *p : {(void *)dres, (void *)dsrc, (void *)dsh, (void *)bsum, (void *)boff, (void *)blast, (void *)lastnz})
+    CK(cudaFreeAsync(p, s));
+  CK(cudaStreamSynchronize(s));
+  return QW_OK;
+}
+
+}  // namespace qw

@@ -1,0 +1,172 @@
+// Planner and engine objects (internal).
+#pragma once
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "qw_internal.h"
+
+struct qw_workload {
+  qw::Workload w;
+};
+
+namespace qw {
+
+// ---- cost model --------------------------------------------------------------
+struct CostModel {
+  bool trained = false;
+  std::vector<float> params;    // QW_MLP_PARAMS FP32 master weights
+  float mean[QW_MLP_IN] = {0};
+  float scale[QW_MLP_IN] = {0};
+  float y_lo = 0, y_hi = 0;     // training-target range (log2 ns)
+  float f_lo[QW_MLP_IN] = {0}, f_hi[QW_MLP_IN] = {0};  // training feature range
+};
+
+// ---- trie -----------------------------------------------------------------------
+struct TNode {
+  int parent = -1;
+  uint64_t depth = 0;       // gates from the root
+  uint32_t rep = 0;         // representative task; edge = rep's gates [edge_begin, depth)
+  uint64_t edge_begin = 0;
+  uint32_t n = 0;           // qubits of the group
+  std::vector<int> kids;
+  std::vector<uint32_t> ending;
+  uint32_t below = 0;
+  uint32_t mode_count[3] = {0, 0, 0};
+};
+
+struct Candidate {
+  uint64_t cut = 0;   // gate index (absolute) of the boundary
+  int kind = 0;       // 0 LCP, 1 Clifford transition, 2 barrier / checkpoint
+  uint32_t n_tasks = 0;
+  double c_prefix = 0, c_mat = 0, c_reload = 0, c_handoff = 0, delta = 0, lhs = 0, rhs = 0;
+  bool holds = false;
+};
+
+struct RefusalRec {
+  uint32_t task;
+  qw_refusal r;
+};
+
+struct Decision {
+  int node = -1;
+  uint32_t n = 0;
+  uint64_t depth = 0;
+  uint32_t n_tasks = 0;
+  int decision = 0;  // 0 REUSE, 1 ABSTAIN, 2 REFUSE
+  std::string reason;
+  std::vector<Candidate> cands;
+  int chosen = -1;
+  int mat = -1;
+  double est_direct = 0, est_reuse = 0;
+  std::vector<RefusalRec> refusals;
+  bool cost_from_mlp = false;
+};
+
+struct MatNode {
+  int node = -1;
+  int parent = -1;          // parent materialized node, -1 = |0...0> / identity
+  uint64_t begin = 0, end = 0;  // gate range (of rep task) this node evolves
+  uint32_t rep = 0;
+  uint32_t mode = 0, n = 0, n_eff = 0;
+  uint64_t bytes = 0;
+  uint8_t provenance[32];
+  // compiled
+  SvProgram sv;
+  std::vector<std::pair<uint32_t, uint32_t>> tab_segs;  // (program, bit_base)
+  uint32_t tab_outs = 0;    // outcomes this segment produces
+  uint32_t out_offset = 0;  // cumulative outcomes from the root to the start of this node
+};
+
+struct TaskPlan {
+  uint32_t mode = 0, n = 0, n_eff = 0, flags = 0, shots = 0;
+  int src = -1;             // materialized source node, -1 = from scratch
+  uint64_t begin = 0;       // first gate executed by the task itself
+  uint64_t n_gates = 0;
+  bool refused = false;
+  bool legality_bypassed = false;  // converted artifact (legality disabled)
+  int ham = -1;             // Hamiltonian layout id, -1 = no energy
+  std::vector<double> uniforms;
+  SvProgram sv;             // suffix program (SV modes)
+  std::vector<std::pair<uint32_t, uint32_t>> tab_segs;
+  uint32_t tab_outs = 0;    // suffix outcomes
+  uint32_t total_outs = 0;  // all MEASURE outcomes of the task
+};
+
+struct HamLayout {
+  uint32_t n_eff = 0, chunk_bits = 0, n_blocks = 0;
+  std::vector<EnClass> classes;
+  std::vector<EnTerm> terms;
+};
+
+struct Engine;
+struct DeviceState;  // engine.cu
+
+std::string json_escape(const std::string &s);
+std::string hex32(const uint8_t h[32]);
+void sha256(const void *data, size_t len, uint8_t out[32]);
+void fingerprint(uint32_t n, uint32_t mode, const TaskData &t, uint64_t b, uint64_t e, uint8_t out[32]);
+bool legality(const qw_artifact_desc &a, uint32_t target_backend, const uint8_t *expected,
+              qw_refusal *out);
+const char *backend_name(uint32_t b);
+const char *kind_name(uint32_t k);
+void features_for(const TaskData &t, uint64_t b, uint64_t e, uint32_t n_sharing, const TileConfig &tc,
+                  double occupancy, float out[QW_MLP_IN]);
+
+struct Engine {
+  int device = 0;
+  int sm_count = 0;
+  uint64_t l2_bytes = 0;
+  double hbm_gbs = 0;
+  double launch_ns = 4000;
+  uint64_t store_budget = 0, task_budget = 0;
+  void *stream = nullptr;
+  std::map<uint64_t, TileConfig> tiles;  // key: n << 1 | fp64
+  CostModel cm;
+  float *d_mlp = nullptr;  // device copy of the MLP params
+  // scratch for the *_dev entry points
+  void *scratch = nullptr;
+  size_t scratch_bytes = 0;
+  TileConfig tile_config(uint32_t n_eff, bool fp64);
+  double predict_log2ns(const float *feat, uint32_t rows, float *out);
+  void *ensure_scratch(size_t bytes);
+};
+
+}  // namespace qw
+
+struct qw_engine {
+  qw::Engine e;
+};
+
+struct qw_plan {
+  qw::Engine *eng = nullptr;
+  qw_plan_opts opts;
+  std::vector<qw::TaskPlan> tasks;
+  std::vector<qw::MatNode> mats;
+  std::vector<qw::Decision> decisions;
+  std::vector<qw::HamLayout> hams;
+  std::vector<qw::TabHostProgram> tab_progs;
+  std::vector<uint8_t> tab_bits;  // random bits of every compiled tableau program instance
+  std::string explain, cost;
+  double planning_ns = 0;
+  double est_direct_ns = 0, est_plan_ns = 0;
+  bool fast_path = false;
+  uint64_t total_gates = 0;
+  // execution
+  qw::DeviceState *dev = nullptr;
+  bool executed = false;
+  // host results
+  std::vector<double> energy, norm2;
+  std::vector<uint64_t> samples;
+  std::vector<uint64_t> sample_off;  // per task offset into samples
+  std::vector<uint8_t> outs_suffix;   // per task suffix outcomes
+  std::vector<uint32_t> outs_off;
+  std::vector<uint8_t> outs_mat;      // per mat node outcomes
+  std::vector<uint32_t> outs_mat_off;
+  // realized timings (ms) of the last execution
+  double t_upload_ms = 0, t_prefix_ms = 0, t_suffix_ms = 0, t_energy_ms = 0, t_sample_ms = 0,
+         t_tab_ms = 0, t_total_ms = 0;
+  int timed = 0;
+  std::vector<double> batch_ms;  // per wave: suffix launch(es) only
+};

@@ -1,0 +1,276 @@
+// Internal types shared by the translation units of libquwarp.so.
+// Nothing here is part of the public ABI (include/quwarp.h is).
+#pragma once
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "quwarp.h"
+
+#ifdef __CUDACC__
+#define QW_HD __host__ __device__
+#else
+#define QW_HD
+#endif
+
+namespace qw {
+
+// ---------------------------------------------------------------------------
+// errors: thrown inside the library, converted to qw_status at the C ABI
+// ---------------------------------------------------------------------------
+struct Error {
+  qw_status code;
+  std::string msg;
+};
+std::string strf(const char *fmt, ...);
+[[noreturn]] void fail(qw_status code, const char *fmt, ...);
+void set_last_error(const std::string &msg);
+
+// ---------------------------------------------------------------------------
+// workload (host)
+// ---------------------------------------------------------------------------
+struct Span {
+  const qw_gate *g;
+  uint64_t n;
+};
+
+struct TaskData {
+  uint32_t mode = 0, n = 0, flags = 0, shots = 0;
+  std::vector<Span> spans;
+  std::vector<uint64_t> span_end;  // cumulative gate count at the end of each span
+  uint64_t n_gates = 0;
+  std::vector<qw_pauli_term> terms;
+  std::vector<double> uniforms;
+  // pointer to gate i (binary search over spans)
+  const qw_gate *gate(uint64_t i) const;
+  // copies gates [b, e) into `out`
+  void copy_gates(uint64_t b, uint64_t e, std::vector<qw_gate> &out) const;
+};
+
+struct Workload {
+  std::vector<TaskData> tasks;
+};
+
+bool is_clifford_op(uint32_t op);
+bool is_two_qubit_op(uint32_t op);
+bool is_barrier_op(uint32_t op);  // MEASURE / RESET
+
+// ---------------------------------------------------------------------------
+// statevector program (host-side fusion result and device descriptors)
+// ---------------------------------------------------------------------------
+// Operation kinds applied to the 32 register amplitudes of a stage group.
+enum SvKind : uint8_t {
+  K_U1 = 1,    // general 2x2 on position a: m = {u00r,u00i,u01r,u01i,u10r,u10i,u11r,u11i}
+  K_D1 = 2,    // diagonal on a: m = {d0r,d0i,d1r,d1i}
+  K_CX = 3,    // controlled-X, control a, target b
+  K_CD = 4,    // multiply amplitudes with bits a and b set by m = {pr, pi}
+  K_SWAP = 5,  // swap positions a, b
+};
+constexpr int SV_G = 5;            // positions per stage (32 register amplitudes)
+constexpr int SV_MAX_TILE_FP32 = 14;
+constexpr int SV_MAX_TILE_FP64 = 13;
+
+struct HostOp {
+  uint8_t kind, a, b;
+  double m[8];
+};
+struct HostStage {
+  uint8_t pos[SV_G];  // local tile bit positions (distinct)
+  std::vector<HostOp> ops;
+};
+struct HostPass {
+  std::vector<uint32_t> q;  // local bit -> global qubit (ascending; q[i] = i for i < b)
+  uint32_t b = 0;           // contiguous low qubits
+  std::vector<HostStage> stages;
+  uint32_t n_gates = 0;     // gates of the source list absorbed by this pass
+};
+struct SvProgram {
+  uint32_t n = 0;  // effective qubit count (>= SV_G)
+  std::vector<HostPass> passes;
+  uint64_t n_gates = 0;
+};
+
+struct TileConfig {
+  uint32_t k_max = 13;  // tile qubits
+  uint32_t b = 4;       // contiguous low qubits in every tile
+};
+
+// Device descriptors (plain structs, identical layout on host and device).
+struct SvPassDesc {
+  uint32_t k, b, n_stages, stage_begin;
+  uint32_t n_hi, pad0, pad1, pad2;
+  uint8_t hi_pos[32];     // global positions of the n-k non-tile bits, ascending
+  uint32_t lo_tab[64];    // deposit of local bits b..b+5   (index = lh & 63)
+  uint32_t hi_tab[32];    // deposit of local bits b+6..    (index = lh >> 6)
+};
+struct SvStageDesc {
+  uint8_t pos[SV_G];
+  uint8_t pad;
+  uint16_t n_ops;
+  uint32_t op_begin;
+};
+template <typename T>
+struct SvOpDesc {
+  uint32_t code;  // kind | a << 8 | b << 16
+  uint32_t pad;
+  T m[8];
+};
+
+// Fusion planner: gates -> passes -> stages (host).
+SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const TileConfig &tc);
+// Number of passes a segment would take (cheap estimate used by the planner).
+uint32_t estimate_passes(uint64_t n_gates, uint32_t n, const TileConfig &tc, double gates_per_pass);
+// Gate matrix in double precision (host). Returns false for non-1q ops.
+bool gate_matrix_1q(const qw_gate &g, double m[8], bool *diagonal);
+
+// ---------------------------------------------------------------------------
+// energy descriptors
+// ---------------------------------------------------------------------------
+struct EnTerm {
+  uint32_t xm, zm, skip, flags;  // flags bit0: imaginary component of conj(p)*a
+  double coef;                   // c_k * sign(i^{#Y}) * (2 if xm != 0)
+};
+struct EnClass {
+  uint32_t term_begin, term_end;
+  uint32_t hb;           // highest bit of the class's flip pattern, 0xFFFFFFFF for class 0
+  uint32_t n_own;        // own chunks
+  uint32_t block_begin;  // first block of this class within its Hamiltonian layout
+  uint32_t pad;
+};
+struct EnJob {
+  const void *state;
+  double *out;                     // {energy, norm2}
+  uint32_t n, chunk_bits;
+  uint32_t class_begin, n_classes;
+  uint32_t block_begin, n_blocks;  // global block range of this job
+};
+constexpr int EN_THREADS = 256;
+constexpr int EN_EPT = 8;  // amplitudes per thread
+constexpr int EN_BLOCK_BITS = 11;
+
+// ---------------------------------------------------------------------------
+// sampling descriptors
+// ---------------------------------------------------------------------------
+constexpr int SMP_BLOCK_BITS = 12;  // 4096 amplitudes per CDF block
+struct SmpSource {
+  const void *state;
+  uint32_t n, n_blocks;
+  uint32_t block_begin;  // offset into the block-sum / block-offset arrays
+  uint32_t pad;
+};
+struct SmpShot {
+  double u;
+  uint32_t source;
+  uint32_t pad;
+  uint64_t *out;
+};
+// Hamiltonian layout: classes of terms grouped by the flip-pattern bits above
+// the chunk size, so that one class touches pairs of chunks only.
+void build_energy_layout(const qw_pauli_term *terms, uint64_t n_terms, uint32_t n,
+                         uint32_t *chunk_bits, std::vector<EnClass> &classes,
+                         std::vector<EnTerm> &en_terms, uint32_t *n_blocks);
+
+// ---------------------------------------------------------------------------
+// tableau program (inverse-tableau formulation)
+// ---------------------------------------------------------------------------
+enum TabKind : uint8_t { T_PROD = 1, T_SWAP2 = 2, T_SIGN = 3, T_MEAS = 4 };
+struct TabSlot {
+  uint8_t kind;
+  uint8_t flags;     // T_PROD: extra phase exponent (mod 4); T_MEAS: bit0 = reset
+  uint16_t dst, s1, s2;
+  uint32_t aux;      // T_MEAS: random-bit index (segment relative)
+  uint32_t aux2;     // T_MEAS: outcome index (segment relative) or 0xFFFFFFFF
+};
+struct TabLayer {
+  uint32_t slot_begin, n_slots, is_measure, pad;
+};
+struct TabProgram {
+  uint32_t layer_begin, n_layers, n_bits, n_outs;
+};
+struct TabSegment {
+  uint32_t prog, bit_base, out_base, pad;
+};
+struct TabTaskDesc {
+  uint32_t seg_begin, n_segs;
+  uint32_t bits_base;   // into the byte array of random bits
+  uint32_t out_base;    // into the outcome byte array
+};
+struct TabHostProgram {
+  std::vector<TabLayer> layers;
+  std::vector<TabSlot> slots;
+  uint32_t n_bits = 0, n_outs = 0;
+};
+// compiles a Clifford gate run (n qubits) into layers of independent row ops
+TabHostProgram compile_tab(const qw_gate *gates, uint64_t n_gates, uint32_t n);
+
+// ---------------------------------------------------------------------------
+// kernel launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+struct SvTables {
+  const SvPassDesc *passes;
+  const SvStageDesc *stages;
+  const void *ops;  // SvOpDesc<T>*
+};
+struct SvJob {
+  const void *src;   // NULL: start from |0...0>
+  void *dst;
+  uint32_t pass;     // index into the pass table
+  uint32_t n_tiles;
+  int32_t dep;       // job that must finish first, -1 none
+  uint32_t item_begin;
+  uint32_t n;        // effective qubits
+  uint32_t pad;
+};
+
+int sv_threads_for_k(uint32_t k);
+size_t sv_smem_bytes(bool fp64, uint32_t k);
+// one pass over one state (grid = tiles)
+void launch_sv_pass(bool fp64, const SvTables &t, uint32_t pass_idx, uint32_t k, uint32_t n,
+                    const void *src, void *dst, void *stream);
+// persistent batch over jobs; counters: [0] = next item, [1] = error flag,
+// [2..] = per-job completed tiles (all zeroed by the caller beforehand)
+void launch_sv_batch(bool fp64, const SvTables &t, const SvJob *jobs, uint32_t n_jobs,
+                     uint32_t total_items, uint32_t k_max, unsigned int *counters,
+                     int grid, void *stream);
+int sv_batch_grid(bool fp64, uint32_t k, int sm_count);
+void launch_copy(const void *src, void *dst, size_t bytes, void *stream);
+
+// energy: per-block partials (2 doubles per block), then one reduction
+// kernel writes {energy, norm2} of every job
+void launch_energy(bool fp64, const EnJob *jobs, uint32_t n_jobs, uint32_t total_blocks,
+                   const EnClass *classes, const EnTerm *terms, double *partials, void *stream);
+// sampling: block sums -> per-source sequential offsets -> shots
+void launch_sampling(bool fp64, const SmpSource *srcs, uint32_t n_src, uint32_t total_blocks,
+                     double *bsum, int32_t *blast, double *boff, int64_t *lastnz,
+                     const SmpShot *shots, uint32_t n_shots, void *stream);
+
+// tableau
+struct TabArgs {
+  uint32_t n, W, lpp, rows;
+  const uint64_t *init_rows;   // boundary tableau (NULL = identity)
+  const uint8_t *init_sign;
+  uint64_t *out_rows;          // written back when non-NULL (boundary producer)
+  uint8_t *out_sign;
+  const TabTaskDesc *tasks;
+  const TabSegment *segs;
+  const TabProgram *progs;
+  const TabLayer *layers;
+  const TabSlot *slots;
+  const uint8_t *bits;
+  uint8_t *outs;
+};
+size_t tab_smem_bytes(uint32_t n);
+void launch_tab(const TabArgs &a, uint32_t n_tasks, void *stream);
+
+// learned cost model
+void launch_mlp_forward(const float *params, const float *x, float *y, uint32_t batch, void *stream);
+void launch_mlp_loss_grad(const float *params, const float *x, const float *target, uint32_t batch,
+                          float *loss, float *grad, float *scratch, void *stream);
+void launch_mlp_adam(float *params, const float *grad, float *m, float *v, uint32_t n, uint32_t t,
+                     float lr, float b1, float b2, float eps, void *stream);
+size_t mlp_scratch_floats(uint32_t batch);
+}  // namespace qw

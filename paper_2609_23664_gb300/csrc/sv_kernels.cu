@@ -1,0 +1,333 @@
+// Statevector gate-application kernels (sm_103a).
+//
+// One CTA processes one TILE of a pass: 2^k amplitudes whose non-tile bits
+// are fixed.  The tile is read from HBM in contiguous runs of 2^b amplitudes,
+// kept in shared memory (XOR-swizzled to spread the strided stage accesses
+// over the banks), and every STAGE of the pass is applied with the stage's
+// 32 amplitudes of a group held in registers, so that the gates of a stage
+// cost no shared-memory traffic.  The prefix is executed once (Sec. III-A,
+// Fig. 1); the first suffix pass of every task reads its tile from the
+// boundary state and writes the task's own buffer, so the reload of the
+// boundary (C_reload of Eq. 2) costs no separate copy.
+//
+// sv_batch_kernel runs the suffixes of many tasks in ONE persistent launch:
+// CTAs take tiles from a global work list in order; a tile of pass p of a
+// task waits (bounded) until every tile of pass p-1 of that task is done.
+#include <cuda_runtime.h>
+
+#include "qw_internal.h"
+
+namespace qw {
+
+template <typename T> struct V2;
+template <> struct V2<float> { typedef float2 t; };
+template <> struct V2<double> { typedef double2 t; };
+
+template <typename T> __device__ __forceinline__ uint32_t swz(uint32_t l);
+template <> __device__ __forceinline__ uint32_t swz<float>(uint32_t l) {
+  return l ^ (((l >> 4) ^ (l >> 8) ^ (l >> 12)) & 15u);
+}
+template <> __device__ __forceinline__ uint32_t swz<double>(uint32_t l) {
+  return l ^ (((l >> 3) ^ (l >> 6) ^ (l >> 9) ^ (l >> 12)) & 7u);
+}
+
+// ---- register operations on the 32 amplitudes of a stage group -------------
+template <typename C, typename T, int P>
+__device__ __forceinline__ void op_u1(C (&a)[32], const T (&m)[8]) {
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    if (i & (1 << P)) continue;
+    const int j = i | (1 << P);
+    const C x = a[i], y = a[j];
+    a[i].x = m[0] * x.x - m[1] * x.y + m[2] * y.x - m[3] * y.y;
+    a[i].y = m[0] * x.y + m[1] * x.x + m[2] * y.y + m[3] * y.x;
+    a[j].x = m[4] * x.x - m[5] * x.y + m[6] * y.x - m[7] * y.y;
+    a[j].y = m[4] * x.y + m[5] * x.x + m[6] * y.y + m[7] * y.x;
+  }
+}
+template <typename C, typename T, int P>
+__device__ __forceinline__ void op_d1(C (&a)[32], const T (&m)[8]) {
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    const T dr = (i & (1 << P)) ? m[2] : m[0];
+    const T di = (i & (1 << P)) ? m[3] : m[1];
+    const C x = a[i];
+    a[i].x = dr * x.x - di * x.y;
+    a[i].y = dr * x.y + di * x.x;
+  }
+}
+template <typename C, int CT, int TG>
+__device__ __forceinline__ void op_cx(C (&a)[32]) {
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    if (!(i & (1 << CT)) || (i & (1 << TG))) continue;
+    const int j = i | (1 << TG);
+    const C t = a[i];
+    a[i] = a[j];
+    a[j] = t;
+  }
+}
+template <typename C, typename T, int A, int B>
+__device__ __forceinline__ void op_cd(C (&a)[32], const T (&m)[8]) {
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    if (!(i & (1 << A)) || !(i & (1 << B))) continue;
+    const C x = a[i];
+    a[i].x = m[0] * x.x - m[1] * x.y;
+    a[i].y = m[0] * x.y + m[1] * x.x;
+  }
+}
+template <typename C, int A, int B>
+__device__ __forceinline__ void op_swap(C (&a)[32]) {
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    if (!(i & (1 << A)) || (i & (1 << B))) continue;
+    const int j = (i & ~(1 << A)) | (1 << B);
+    const C t = a[i];
+    a[i] = a[j];
+    a[j] = t;
+  }
+}
+
+#define QW_CODE(kind, a, b) ((uint32_t)(kind) | ((uint32_t)(a) << 8) | ((uint32_t)(b) << 16))
+
+template <typename C, typename T>
+__device__ __forceinline__ void apply_op(uint32_t code, const T (&m)[8], C (&a)[32]) {
+  switch (code) {
+#define U1(P) case QW_CODE(K_U1, P, 0): op_u1<C, T, P>(a, m); break;
+#define D1(P) case QW_CODE(K_D1, P, 0): op_d1<C, T, P>(a, m); break;
+    U1(0) U1(1) U1(2) U1(3) U1(4)
+    D1(0) D1(1) D1(2) D1(3) D1(4)
+#undef U1
+#undef D1
+#define CX(c, t) case QW_CODE(K_CX, c, t): op_cx<C, c, t>(a); break;
+    CX(0, 1) CX(0, 2) CX(0, 3) CX(0, 4) CX(1, 0) CX(1, 2) CX(1, 3) CX(1, 4)
+    CX(2, 0) CX(2, 1) CX(2, 3) CX(2, 4) CX(3, 0) CX(3, 1) CX(3, 2) CX(3, 4)
+    CX(4, 0) CX(4, 1) CX(4, 2) CX(4, 3)
+#undef CX
+#define CD(x, y) case QW_CODE(K_CD, x, y): op_cd<C, T, x, y>(a, m); break;
+#define SW(x, y) case QW_CODE(K_SWAP, x, y): op_swap<C, x, y>(a); break;
+    CD(0, 1) CD(0, 2) CD(0, 3) CD(0, 4) CD(1, 2) CD(1, 3) CD(1, 4) CD(2, 3) CD(2, 4) CD(3, 4)
+    SW(0, 1) SW(0, 2) SW(0, 3) SW(0, 4) SW(1, 2) SW(1, 3) SW(1, 4) SW(2, 3) SW(2, 4) SW(3, 4)
+#undef CD
+#undef SW
+    default: break;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ typename V2<T>::t ld_amp(const typename V2<T>::t *p, bool cg) {
+  return cg ? __ldcg(p) : *p;
+}
+
+// Processes one tile of one pass.  src == nullptr starts from |0...0>.
+template <typename T>
+__device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__restrict__ stages,
+                        const SvOpDesc<T> *__restrict__ ops, typename V2<T>::t *sm,
+                        const typename V2<T>::t *src, typename V2<T>::t *dst, uint32_t tile,
+                        bool cg) {
+  typedef typename V2<T>::t C;
+  const uint32_t k = pd->k, b = pd->b, n_hi = pd->n_hi;
+  uint32_t base = 0;
+  for (uint32_t i = 0; i < n_hi; i++) base |= ((tile >> i) & 1u) << pd->hi_pos[i];
+  const uint32_t ntile = 1u << k, lomask = (1u << b) - 1u;
+  const uint32_t nt = blockDim.x;
+
+  for (uint32_t l = threadIdx.x; l < ntile; l += nt) {
+    const uint32_t lh = l >> b;
+    const uint32_t g = base | __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) |
+                       (l & lomask);
+    C v;
+    if (src) {
+      v = ld_amp<T>(src + g, cg);
+    } else {
+      v.x = (g == 0) ? T(1) : T(0);
+      v.y = T(0);
+    }
+    sm[swz<T>(l)] = v;
+  }
+  __syncthreads();
+
+  const uint32_t n_groups = 1u << (k - SV_G);
+  const uint32_t n_st = pd->n_stages, st0 = pd->stage_begin;
+  for (uint32_t s = 0; s < n_st; s++) {
+    const SvStageDesc st = stages[st0 + s];
+    uint32_t pos[SV_G], sp[SV_G];
+#pragma unroll
+    for (int j = 0; j < SV_G; j++) {
+      pos[j] = st.pos[j];
+      sp[j] = swz<T>(1u << pos[j]);
+    }
+    for (uint32_t grp = threadIdx.x; grp < n_groups; grp += nt) {
+      uint32_t bse = grp;
+#pragma unroll
+      for (int j = 0; j < SV_G; j++) {
+        const uint32_t p = pos[j];
+        bse = ((bse >> p) << (p + 1)) | (bse & ((1u << p) - 1u));
+      }
+      const uint32_t sb = swz<T>(bse);
+      C a[32];
+#pragma unroll
+      for (int i = 0; i < 32; i++) {
+        const uint32_t idx = sb ^ ((i & 1) ? sp[0] : 0u) ^ ((i & 2) ? sp[1] : 0u) ^
+                             ((i & 4) ? sp[2] : 0u) ^ ((i & 8) ? sp[3] : 0u) ^
+                             ((i & 16) ? sp[4] : 0u);
+        a[i] = sm[idx];
+      }
+      for (uint32_t o = 0; o < st.n_ops; o++) {
+        const SvOpDesc<T> *op = ops + st.op_begin + o;
+        const uint32_t code = __ldg(&op->code);
+        T m[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++) m[t] = __ldg(&op->m[t]);
+        apply_op<C, T>(code, m, a);
+      }
+#pragma unroll
+      for (int i = 0; i < 32; i++) {
+        const uint32_t idx = sb ^ ((i & 1) ? sp[0] : 0u) ^ ((i & 2) ? sp[1] : 0u) ^
+                             ((i & 4) ? sp[2] : 0u) ^ ((i & 8) ? sp[3] : 0u) ^
+                             ((i & 16) ? sp[4] : 0u);
+        sm[idx] = a[i];
+      }
+    }
+    __syncthreads();
+  }
+
+  for (uint32_t l = threadIdx.x; l < ntile; l += nt) {
+    const uint32_t lh = l >> b;
+    const uint32_t g = base | __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) |
+                       (l & lomask);
+    dst[g] = sm[swz<T>(l)];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2)
+sv_pass_kernel(SvTables t, uint32_t pass, const typename V2<T>::t *src, typename V2<T>::t *dst) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  typedef typename V2<T>::t C;
+  sv_tile<T>(t.passes + pass, t.stages, (const SvOpDesc<T> *)t.ops, (C *)smraw, src, dst,
+             blockIdx.x, false);
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const unsigned int *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per dependency wait
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2)
+sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, uint32_t n_jobs, uint32_t total,
+                unsigned int *ctr) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  typedef typename V2<T>::t C;
+  __shared__ uint32_t s_item, s_job;
+  __shared__ int s_abort;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t it = atomicAdd(&ctr[0], 1u);
+      s_item = it;
+      s_abort = 0;
+      if (it < total) {
+        uint32_t lo = 0, hi = n_jobs;
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (jobs[mid].item_begin <= it) lo = mid; else hi = mid;
+        }
+        s_job = lo;
+        const int dep = jobs[lo].dep;
+        if (dep >= 0) {
+          const uint32_t need = jobs[dep].n_tiles;
+          const uint64_t t0 = globaltimer_ns();
+          while (ld_acquire_u32(&ctr[2 + dep]) < need) {
+            if (ld_acquire_u32(&ctr[1]) != 0u) { s_abort = 1; break; }
+            if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
+              atomicExch(&ctr[1], 1u);  // reported to the host as a device timeout
+              s_abort = 1;
+              break;
+            }
+            __nanosleep(100);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (s_item >= total || s_abort) break;
+    const SvJob job = jobs[s_job];
+    sv_tile<T>(t.passes + job.pass, t.stages, (const SvOpDesc<T> *)t.ops, (C *)smraw,
+               (const C *)job.src, (C *)job.dst, s_item - job.item_begin, true);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&ctr[2 + s_job], 1u);
+  }
+}
+
+// ---- host launchers -----------------------------------------------------------
+int sv_threads_for_k(uint32_t k) {
+  const uint32_t g = 1u << (k - SV_G);
+  return (int)(g < 32 ? 32 : (g > 256 ? 256 : g));
+}
+size_t sv_smem_bytes(bool fp64, uint32_t k) { return (size_t)(fp64 ? 16 : 8) << k; }
+
+template <typename T>
+static void set_smem_attr(const void *fn) {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    done = true;
+  }
+}
+
+void launch_sv_pass(bool fp64, const SvTables &t, uint32_t pass_idx, uint32_t k, uint32_t n,
+                    const void *src, void *dst, void *stream) {
+  const uint32_t tiles = 1u << (n - k);
+  const int threads = sv_threads_for_k(k);
+  const size_t smem = sv_smem_bytes(fp64, k);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (fp64) {
+    set_smem_attr<double>((const void *)sv_pass_kernel<double>);
+    sv_pass_kernel<double><<<tiles, threads, smem, s>>>(t, pass_idx, (const double2 *)src,
+                                                        (double2 *)dst);
+  } else {
+    set_smem_attr<float>((const void *)sv_pass_kernel<float>);
+    sv_pass_kernel<float><<<tiles, threads, smem, s>>>(t, pass_idx, (const float2 *)src,
+                                                       (float2 *)dst);
+  }
+}
+
+int sv_batch_grid(bool fp64, uint32_t k, int sm_count) {
+  const int threads = sv_threads_for_k(k);
+  const size_t smem = sv_smem_bytes(fp64, k);
+  int per_sm = 0;
+  if (fp64) {
+    set_smem_attr<double>((const void *)sv_batch_kernel<double>);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<double>, threads, smem);
+  } else {
+    set_smem_attr<float>((const void *)sv_batch_kernel<float>);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float>, threads, smem);
+  }
+  if (per_sm < 1) per_sm = 1;
+  return per_sm * sm_count;
+}
+
+void launch_sv_batch(bool fp64, const SvTables &t, const SvJob *jobs, uint32_t n_jobs,
+                     uint32_t total_items, uint32_t k_max, unsigned int *counters, int grid,
+                     void *stream) {
+  const int threads = sv_threads_for_k(k_max);
+  const size_t smem = sv_smem_bytes(fp64, k_max);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (fp64)
+    sv_batch_kernel<double><<<grid, threads, smem, s>>>(t, jobs, n_jobs, total_items, counters);
+  else
+    sv_batch_kernel<float><<<grid, threads, smem, s>>>(t, jobs, n_jobs, total_items, counters);
+}
+
+}  // namespace qw

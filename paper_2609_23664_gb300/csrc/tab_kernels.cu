@@ -1,0 +1,260 @@
+// Stabilizer-tableau kernels (sm_103a), 64-bit words.
+//
+// The GPU keeps the INVERSE tableau T: for every generator X_i / Z_i of the
+// initial frame it stores the Pauli string T(P) = C^-1 P C (C = circuit so
+// far) as x-words, z-words and a sign, row-major, 2n rows in shared memory.
+// A gate G of the circuit updates T by T'(P) = T(G^-1 P G), which is a
+// product or a swap of ROWS (word-parallel over all qubits: W = ceil(n/64)
+// words per half-row).  Measuring Z_a reads row T(Z_a): without an X part
+// the outcome is its sign (deterministic); otherwise the outcome is random
+// and the tableau is collapsed by conjugating every row with a few column
+// operations in the initial frame (CNOTs, S^dagger, H, X), which leave
+// |0...0> invariant up to the projected outcome.  This is the Heisenberg-
+// picture formulation used by the stabilizer simulator the paper cites
+// [gidney2021stim]; the CPU oracle uses the textbook forward tableau
+// [aaronson2004stabilizer], so the two share no algorithm.  Measurement
+// outcomes agree bit for bit: a deterministic outcome is fixed by the state,
+// and a random one takes the outcome bit carried by the gate record.
+//
+// Row products keep Paulis in the Hermitian form (-1)^r i^{x.z} X^x Z^z:
+// P1 P2 = (-1)^{r1+r2} i^{x1.z1 + x2.z2 - x3.z3 + 2 z1.x2 + e0} P3 where e0
+// is an extra power of i (S: 3, S^dagger: 1) and the exponent is 0 or 2.
+#include <cuda_runtime.h>
+
+#include "qw_internal.h"
+
+namespace qw {
+
+struct TabSm {
+  uint64_t *R;     // rows * 2W words
+  uint8_t *sign;   // rows
+  uint8_t *pending;
+  uint64_t *xs;    // W words (collapse scratch)
+};
+
+__device__ __forceinline__ int getb(const uint64_t *row, uint32_t q) {
+  return (int)((row[q >> 6] >> (q & 63)) & 1ull);
+}
+__device__ __forceinline__ void flipb(uint64_t *row, uint32_t q) { row[q >> 6] ^= 1ull << (q & 63); }
+
+// column op in the initial frame: CNOT(c -> t) conjugation of one row
+__device__ __forceinline__ void col_cnot(uint64_t *x, uint64_t *z, uint8_t *r, uint32_t c, uint32_t t) {
+  const int xc = getb(x, c), zc = getb(z, c), xt = getb(x, t), zt = getb(z, t);
+  *r ^= (uint8_t)(xc & zt & (xt ^ zc ^ 1));
+  if (xc) flipb(x, t);
+  if (zt) flipb(z, c);
+}
+
+__device__ void tab_collapse(const TabArgs &A, TabSm &S, const TabSlot &sl, uint32_t bits_base,
+                             uint32_t out_base) {
+  const uint32_t n = A.n, W = A.W, rows = A.rows, row = sl.dst;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid < (int)W) S.xs[tid] = S.R[(size_t)row * 2 * W + tid];
+  __syncthreads();
+  int first = -1;
+  for (uint32_t w = 0; w < W; w++)
+    if (S.xs[w]) { first = (int)(w * 64 + __ffsll((long long)S.xs[w]) - 1); break; }
+  const uint8_t m = A.bits[bits_base + sl.aux] & 1;
+  if (first < 0) {  // became deterministic
+    __syncthreads();
+    if (tid == 0) {
+      const uint8_t o = S.sign[row];
+      if (sl.aux2 != 0xFFFFFFFFu) A.outs[out_base + sl.aux2] = o;
+      if ((sl.flags & 1) && o) S.sign[row] ^= 1;
+    }
+    __syncthreads();
+    return;
+  }
+  const uint32_t p = (uint32_t)first;
+  (void)n;
+  // 1) CNOT(p -> q) for every other q in the X part of T(Z_a)
+  for (uint32_t r = tid; r < rows; r += nt) {
+    uint64_t *x = S.R + (size_t)r * 2 * W, *z = x + W;
+    uint8_t sg = S.sign[r];
+    for (uint32_t w = 0; w < W; w++) {
+      uint64_t bitsw = S.xs[w];
+      if (w == (p >> 6)) bitsw &= ~(1ull << (p & 63));
+      while (bitsw) {
+        const uint32_t q = w * 64 + __ffsll((long long)bitsw) - 1;
+        bitsw &= bitsw - 1;
+        col_cnot(x, z, &sg, p, q);
+      }
+    }
+    S.sign[r] = sg;
+  }
+  __syncthreads();
+  // 2) Y -> X at p by S^dagger conjugation when T(Z_a) has Z at p
+  const int zp = getb(S.R + (size_t)row * 2 * W + W, p);
+  __syncthreads();
+  if (zp) {
+    for (uint32_t r = tid; r < rows; r += nt) {
+      uint64_t *x = S.R + (size_t)r * 2 * W, *z = x + W;
+      const int xb = getb(x, p), zb = getb(z, p);
+      S.sign[r] ^= (uint8_t)(xb & (zb ^ 1));
+      if (xb) flipb(z, p);
+    }
+    __syncthreads();
+  }
+  // 3) T(Z_a) = (-1)^s X_p Z_Q: conjugate by H_p then X_p^(m xor s)
+  const uint8_t s = S.sign[row];
+  __syncthreads();
+  const int bb = (int)(m ^ s);
+  for (uint32_t r = tid; r < rows; r += nt) {
+    uint64_t *x = S.R + (size_t)r * 2 * W, *z = x + W;
+    const int xb = getb(x, p), zb = getb(z, p);
+    uint8_t sg = S.sign[r] ^ (uint8_t)(xb & zb);
+    if (xb != zb) { flipb(x, p); flipb(z, p); }
+    if (bb) sg ^= (uint8_t)xb;  // new z bit at p equals the old x bit
+    S.sign[r] = sg;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (sl.aux2 != 0xFFFFFFFFu) A.outs[out_base + sl.aux2] = m;
+    if ((sl.flags & 1) && m) S.sign[row] ^= 1;
+  }
+  __syncthreads();
+}
+
+__device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P, uint32_t bits_base,
+                                uint32_t out_base) {
+  const uint32_t W = A.W, lpp = A.lpp;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, ln = threadIdx.x & 31;
+  const uint32_t gpw = 32 / lpp;  // slot groups per warp
+  const uint32_t w = ln % lpp;
+  for (uint32_t li = 0; li < P.n_layers; li++) {
+    const TabLayer L = A.layers[P.layer_begin + li];
+    if (!L.is_measure) {
+      for (uint32_t sb = warp * gpw; sb < L.n_slots; sb += nwarps * gpw) {
+        const uint32_t si = sb + ln / lpp;
+        const bool act = si < L.n_slots;
+        TabSlot sl{};
+        if (act) sl = A.slots[L.slot_begin + si];
+        int t = 0;
+        if (act && sl.kind == T_PROD) {
+          if (w < W) {
+            uint64_t *d = S.R + (size_t)sl.dst * 2 * W;
+            const uint64_t *p1 = S.R + (size_t)sl.s1 * 2 * W, *p2 = S.R + (size_t)sl.s2 * 2 * W;
+            const uint64_t x1 = p1[w], z1 = p1[W + w], x2 = p2[w], z2 = p2[W + w];
+            const uint64_t x3 = x1 ^ x2, z3 = z1 ^ z2;
+            t = __popcll(x1 & z1) + __popcll(x2 & z2) - __popcll(x3 & z3) + 2 * __popcll(z1 & x2);
+            d[w] = x3;
+            d[W + w] = z3;
+          }
+        } else if (act && sl.kind == T_SWAP2) {
+          if (w < W) {
+            uint64_t *r1 = S.R + (size_t)sl.dst * 2 * W, *r2 = S.R + (size_t)sl.s2 * 2 * W;
+            uint64_t a0 = r1[w], a1 = r1[W + w];
+            r1[w] = r2[w];
+            r1[W + w] = r2[W + w];
+            r2[w] = a0;
+            r2[W + w] = a1;
+          }
+        }
+        for (uint32_t o = lpp >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o, lpp);
+        if (act && w == 0) {
+          if (sl.kind == T_PROD) {
+            S.sign[sl.dst] = S.sign[sl.s1] ^ S.sign[sl.s2] ^ (uint8_t)((((t + sl.flags) & 3) >> 1) & 1);
+          } else if (sl.kind == T_SWAP2) {
+            const uint8_t tmp = S.sign[sl.dst];
+            S.sign[sl.dst] = S.sign[sl.s2];
+            S.sign[sl.s2] = tmp;
+          } else if (sl.kind == T_SIGN) {
+            S.sign[sl.dst] ^= 1;
+          }
+        }
+      }
+      __syncthreads();
+    } else {
+      // phase 1: deterministic outcomes in parallel, random ones flagged
+      for (uint32_t sb = warp * gpw; sb < L.n_slots; sb += nwarps * gpw) {
+        const uint32_t si = sb + ln / lpp;
+        const bool act = si < L.n_slots;
+        TabSlot sl{};
+        if (act) sl = A.slots[L.slot_begin + si];
+        uint64_t v = 0;
+        if (act && w < W) v = S.R[(size_t)sl.dst * 2 * W + w];
+        for (uint32_t o = lpp >> 1; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o, lpp);
+        if (act && w == 0) {
+          if (v == 0) {
+            const uint8_t oc = S.sign[sl.dst];
+            if (sl.aux2 != 0xFFFFFFFFu) A.outs[out_base + sl.aux2] = oc;
+            if ((sl.flags & 1) && oc) S.sign[sl.dst] ^= 1;
+            S.pending[si] = 0;
+          } else {
+            S.pending[si] = 1;
+          }
+        }
+      }
+      __syncthreads();
+      // phase 2: random outcomes one at a time, in program order
+      for (uint32_t si = 0; si < L.n_slots; si++) {
+        if (S.pending[si]) {
+          const TabSlot sl = A.slots[L.slot_begin + si];
+          tab_collapse(A, S, sl, bits_base, out_base);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) tab_kernel(TabArgs A) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const uint32_t W = A.W, rows = A.rows;
+  TabSm S;
+  S.R = (uint64_t *)smraw;
+  S.sign = (uint8_t *)(S.R + (size_t)rows * 2 * W);
+  S.pending = S.sign + ((rows + 15) & ~15u);
+  S.xs = (uint64_t *)(S.pending + ((A.n + 15) & ~15u));
+  const size_t nwords = (size_t)rows * 2 * W;
+  const TabTaskDesc T = A.tasks[blockIdx.x];
+  if (A.init_rows) {
+    for (size_t i = threadIdx.x; i < nwords; i += blockDim.x) S.R[i] = __ldg(A.init_rows + i);
+    for (uint32_t i = threadIdx.x; i < rows; i += blockDim.x) S.sign[i] = __ldg(A.init_sign + i);
+  } else {
+    for (size_t i = threadIdx.x; i < nwords; i += blockDim.x) {
+      const uint32_t r = (uint32_t)(i / (2 * W)), c = (uint32_t)(i % (2 * W));
+      // row r < n: X_r (bit r in the x half); row n+i: Z_i (bit i in the z half)
+      uint64_t v = 0;
+      if (r < A.n) {
+        if (c < W && (r >> 6) == c) v = 1ull << (r & 63);
+      } else {
+        const uint32_t q = r - A.n;
+        if (c >= W && (q >> 6) == c - W) v = 1ull << (q & 63);
+      }
+      S.R[i] = v;
+    }
+    for (uint32_t i = threadIdx.x; i < rows; i += blockDim.x) S.sign[i] = 0;
+  }
+  __syncthreads();
+  for (uint32_t si = 0; si < T.n_segs; si++) {
+    const TabSegment sg = A.segs[T.seg_begin + si];
+    const TabProgram P = A.progs[sg.prog];
+    tab_run_program(A, S, P, sg.bit_base, T.out_base + sg.out_base);
+  }
+  if (A.out_rows) {
+    uint64_t *o = A.out_rows + (size_t)blockIdx.x * nwords;
+    for (size_t i = threadIdx.x; i < nwords; i += blockDim.x) o[i] = S.R[i];
+    uint8_t *os = A.out_sign + (size_t)blockIdx.x * rows;
+    for (uint32_t i = threadIdx.x; i < rows; i += blockDim.x) os[i] = S.sign[i];
+  }
+}
+
+size_t tab_smem_bytes(uint32_t n) {
+  const uint32_t W = (n + 63) / 64, rows = 2 * n;
+  return (size_t)rows * 2 * W * 8 + ((rows + 15) & ~15u) + ((n + 15) & ~15u) + (size_t)W * 8 + 16;
+}
+
+void launch_tab(const TabArgs &a, uint32_t n_tasks, void *stream) {
+  if (n_tasks == 0) return;
+  const size_t smem = tab_smem_bytes(a.n);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute((const void *)tab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    attr = true;
+  }
+  tab_kernel<<<n_tasks, 256, smem, (cudaStream_t)stream>>>(a);
+}
+
+}  // namespace qw

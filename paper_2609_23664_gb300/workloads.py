@@ -50,17 +50,27 @@ BASE_SEED = 20260923
 
 @dataclasses.dataclass
 class Task:
+    """One task.  Its gate list is the concatenation of `spans`; tasks that
+    share a prefix share the same span array (the engine references spans
+    instead of copying them)."""
     mode: int
     n: int
-    gates: np.ndarray                       # GATE_DTYPE[n_gates]
+    spans: List[np.ndarray]
     terms: Optional[np.ndarray] = None      # TERM_DTYPE[n_terms] (energy)
     uniforms: Optional[np.ndarray] = None   # float64[shots] in [0,1)
     shots: int = 0
     want_state: bool = False
 
     @property
+    def gates(self) -> np.ndarray:
+        parts = [s for s in self.spans if len(s)]
+        if len(parts) == 1:
+            return parts[0]
+        return concat(*parts)
+
+    @property
     def n_gates(self) -> int:
-        return int(self.gates.shape[0])
+        return int(sum(len(s) for s in self.spans))
 
 
 def gates_from_list(lst) -> np.ndarray:
@@ -148,27 +158,36 @@ def random_circuit(rng: np.random.Generator, n: int, n_gates: int) -> np.ndarray
 _PAULI_OPS = (None, OP_X, OP_Y, OP_Z)
 
 
-def insert_pauli_noise(rng: np.random.Generator, gates: np.ndarray,
-                       p: float) -> np.ndarray:
-    """After each gate, with probability p, a uniformly random non-identity
-    Pauli on the gate's support (3 choices for 1q, 15 for 2q), emitted as
-    single-qubit Pauli gates."""
+def pauli_error_gates(rng: np.random.Generator, g) -> np.ndarray:
+    """A uniformly random non-identity Pauli on the support of gate g (3
+    choices for 1q, 15 for 2q) as single-qubit Pauli gates."""
     out = []
-    for g in gates:
-        out.append((int(g["op"]), int(g["q0"]), int(g["q1"]), float(g["theta"]),
-                    int(g["flags"])))
-        if rng.random() < p:
-            if int(g["op"]) in TWO_QUBIT_OPS:
-                k = int(rng.integers(1, 16))
-                pa, pb = k // 4, k % 4
-                if pa:
-                    out.append((_PAULI_OPS[pa], int(g["q0"]), 0, 0.0))
-                if pb:
-                    out.append((_PAULI_OPS[pb], int(g["q1"]), 0, 0.0))
-            else:
-                k = int(rng.integers(1, 4))
-                out.append((_PAULI_OPS[k], int(g["q0"]), 0, 0.0))
+    if int(g["op"]) in TWO_QUBIT_OPS:
+        k = int(rng.integers(1, 16))
+        pa, pb = k // 4, k % 4
+        if pa:
+            out.append((_PAULI_OPS[pa], int(g["q0"]), 0, 0.0))
+        if pb:
+            out.append((_PAULI_OPS[pb], int(g["q1"]), 0, 0.0))
+    else:
+        k = int(rng.integers(1, 4))
+        out.append((_PAULI_OPS[k], int(g["q0"]), 0, 0.0))
     return gates_from_list(out)
+
+
+def noisy_spans(rng: np.random.Generator, base: np.ndarray, p: float) -> List[np.ndarray]:
+    """After each gate of `base`, with probability p, a random Pauli error
+    on its support.  Returned as spans: slices (views) of `base` between
+    error insertions, interleaved with the error gates."""
+    spans = []
+    last = 0
+    for i in range(len(base)):
+        if rng.random() < p:
+            spans.append(base[last:i + 1])
+            spans.append(pauli_error_gates(rng, base[i]))
+            last = i + 1
+    spans.append(base[last:])
+    return [s for s in spans if len(s)]
 
 
 # ---- closed-form circuits used as pins ----------------------------------------
@@ -302,7 +321,7 @@ def config1_vqe12(seed: int = BASE_SEED + 1, n: int = 12, layers: int = 6,
     for _ in range(n_tasks):
         suf = hea_layer(n, rng.uniform(0, 2 * math.pi, n),
                         rng.uniform(0, 2 * math.pi, n), cnot_chain=False)
-        tasks.append(Task(mode=mode, n=n, gates=concat(prefix, suf), terms=ham))
+        tasks.append(Task(mode=mode, n=n, spans=[prefix, suf], terms=ham))
     return tasks
 
 
@@ -317,8 +336,7 @@ def config2_vqe24(seed: int = BASE_SEED + 2, n: int = 24, prefix_layers: int = 2
     tasks = []
     for _ in range(n_tasks):
         L = int(rng.integers(1, max_suffix_layers + 1))
-        tasks.append(Task(mode=mode, n=n, gates=concat(prefix, hea_circuit(rng, n, L)),
-                          terms=ham))
+        tasks.append(Task(mode=mode, n=n, spans=[prefix, hea_circuit(rng, n, L)], terms=ham))
     return tasks
 
 
@@ -331,9 +349,9 @@ def config3_noisy22(seed: int = BASE_SEED + 3, n: int = 22, n_gates: int = 400,
     base = random_circuit(rng, n, n_gates)
     tasks = []
     for _ in range(n_traj):
-        g = insert_pauli_noise(rng, base, p)
+        spans = noisy_spans(rng, base, p)
         u = rng.random(shots)
-        tasks.append(Task(mode=mode, n=n, gates=g, uniforms=u, shots=shots))
+        tasks.append(Task(mode=mode, n=n, spans=spans, uniforms=u, shots=shots))
     return tasks
 
 
@@ -346,13 +364,16 @@ def config4_qec(seed: int = BASE_SEED + 4, d: int = 15, shared_rounds: int = 100
     rng = np.random.default_rng(seed)
     code = rotated_surface_code(d)
     prefix = concat(*[syndrome_round(code, rng) for _ in range(shared_rounds)])
+    # every measurement after the first round is determined by the state, so
+    # one round record (with its outcome bits) serves all later rounds
+    round_g = syndrome_round(code, rng)
     tasks = []
     for _ in range(n_tasks):
-        parts = [prefix]
+        spans = [prefix]
         for _ in range(task_rounds):
-            parts.append(data_errors(code, rng, p))
-            parts.append(syndrome_round(code, rng))
-        tasks.append(Task(mode=MODE_TABLEAU, n=code.n, gates=concat(*parts)))
+            spans.append(data_errors(code, rng, p))
+            spans.append(round_g)
+        tasks.append(Task(mode=MODE_TABLEAU, n=code.n, spans=[s for s in spans if len(s)]))
     return tasks
 
 
@@ -378,12 +399,12 @@ def config5_mixed(seed: int = BASE_SEED + 5, n_tasks: int = 2000,
         pre = random_circuit(rng, n, int(rng.integers(prefix_len[0], prefix_len[1] + 1)))
         for _ in range(gsz):
             suf = random_circuit(rng, n, int(rng.integers(suffix_len[0], suffix_len[1] + 1)))
-            tasks.append(Task(mode=mode, n=n, gates=concat(pre, suf),
+            tasks.append(Task(mode=mode, n=n, spans=[pre, suf],
                               terms=random_pauli_hamiltonian(rng, n, n_terms)))
     tasks = tasks[:n_shared]
     for _ in range(n_tasks - n_shared):
         n = int(rng.integers(n_min, n_max + 1))
         g = random_circuit(rng, n, int(rng.integers(free_len[0], free_len[1] + 1)))
-        tasks.append(Task(mode=mode, n=n, gates=g,
+        tasks.append(Task(mode=mode, n=n, spans=[g],
                           terms=random_pauli_hamiltonian(rng, n, n_terms)))
     return tasks
