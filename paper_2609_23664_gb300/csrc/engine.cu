@@ -595,9 +595,9 @@ void plan_execute(qw_plan *P, void *stream) {
       try {
         enqueue(P, cs);
       } catch (...) {
-        cudaGraph_t g;
-        cudaStreamEndCapture(cs, &g);
-        if (g) cudaGraphDestroy(g);
+        cudaGraph_t g = nullptr;
+        if (cudaStreamEndCapture(cs, &g) == cudaSuccess && g) cudaGraphDestroy(g);
+        cudaGetLastError();
         throw;
       }
       CK(cudaStreamEndCapture(cs, &D->graph));
@@ -724,8 +724,8 @@ void engine_init(Engine *E, const qw_engine_opts *o) {
     cudaFree(b);
   }
   // kernel attributes are set before any capture
-  sv_batch_grid(false, 13, E->sm_count);
-  sv_batch_grid(true, 12, E->sm_count);
+  sv_init_attrs();
+  tab_init_attrs();
   CK(cudaGetLastError());
 }
 

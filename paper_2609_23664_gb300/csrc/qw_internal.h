@@ -226,6 +226,8 @@ struct SvJob {
   uint32_t pad;
 };
 
+void sv_init_attrs();
+void tab_init_attrs();
 int sv_threads_for_k(uint32_t k);
 size_t sv_smem_bytes(bool fp64, uint32_t k);
 // one pass over one state (grid = tiles)

@@ -277,13 +277,14 @@ int sv_threads_for_k(uint32_t k) {
 }
 size_t sv_smem_bytes(bool fp64, uint32_t k) { return (size_t)(fp64 ? 16 : 8) << k; }
 
-template <typename T>
-static void set_smem_attr(const void *fn) {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    done = true;
-  }
+// Kernel attributes are set once, before any stream capture (a capture
+// fails on attribute changes).
+void sv_init_attrs() {
+  const int bytes = 200 * 1024;
+  cudaFuncSetAttribute((const void *)sv_pass_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute((const void *)sv_pass_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute((const void *)sv_batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute((const void *)sv_batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 void launch_sv_pass(bool fp64, const SvTables &t, uint32_t pass_idx, uint32_t k, uint32_t n,
@@ -293,11 +294,9 @@ void launch_sv_pass(bool fp64, const SvTables &t, uint32_t pass_idx, uint32_t k,
   const size_t smem = sv_smem_bytes(fp64, k);
   cudaStream_t s = (cudaStream_t)stream;
   if (fp64) {
-    set_smem_attr<double>((const void *)sv_pass_kernel<double>);
     sv_pass_kernel<double><<<tiles, threads, smem, s>>>(t, pass_idx, (const double2 *)src,
                                                         (double2 *)dst);
   } else {
-    set_smem_attr<float>((const void *)sv_pass_kernel<float>);
     sv_pass_kernel<float><<<tiles, threads, smem, s>>>(t, pass_idx, (const float2 *)src,
                                                        (float2 *)dst);
   }
@@ -308,10 +307,8 @@ int sv_batch_grid(bool fp64, uint32_t k, int sm_count) {
   const size_t smem = sv_smem_bytes(fp64, k);
   int per_sm = 0;
   if (fp64) {
-    set_smem_attr<double>((const void *)sv_batch_kernel<double>);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<double>, threads, smem);
   } else {
-    set_smem_attr<float>((const void *)sv_batch_kernel<float>);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float>, threads, smem);
   }
   if (per_sm < 1) per_sm = 1;

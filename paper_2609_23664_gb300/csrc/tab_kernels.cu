@@ -245,16 +245,13 @@ size_t tab_smem_bytes(uint32_t n) {
   return (size_t)rows * 2 * W * 8 + ((rows + 15) & ~15u) + ((n + 15) & ~15u) + (size_t)W * 8 + 16;
 }
 
+void tab_init_attrs() {
+  cudaFuncSetAttribute((const void *)tab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
 void launch_tab(const TabArgs &a, uint32_t n_tasks, void *stream) {
   if (n_tasks == 0) return;
-  const size_t smem = tab_smem_bytes(a.n);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute((const void *)tab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         227 * 1024);
-    attr = true;
-  }
-  tab_kernel<<<n_tasks, 256, smem, (cudaStream_t)stream>>>(a);
+  tab_kernel<<<n_tasks, 256, tab_smem_bytes(a.n), (cudaStream_t)stream>>>(a);
 }
 
 }  // namespace qw
