@@ -512,7 +512,7 @@ static void prepare(qw_plan *P) {
 // ---------------------------------------------------------------------------
 static void enqueue(qw_plan *P, cudaStream_t s) {
   DeviceState *D = P->dev;
-  CK(cudaEventRecord(D->ev[0], s));
+  CK(cudaEventRecordWithFlags(D->ev[0], s, cudaEventRecordExternal));
   // 1) shared prefixes (boundary states), in creation order (parents first)
   for (size_t m = 0; m < P->mats.size(); m++) {
     const MatNode &M = P->mats[m];
@@ -531,12 +531,12 @@ static void enqueue(qw_plan *P, cudaStream_t s) {
     }
   }
   for (auto &L : D->tab_mat_launches) launch_tab(L.a, L.n_tasks, s);
-  CK(cudaEventRecord(D->ev[1], s));
+  CK(cudaEventRecordWithFlags(D->ev[1], s, cudaEventRecordExternal));
   // 2) task suffixes, observables
   size_t wi = 0;
   for (auto &W : D->waves) {
     const SvTables &T = W.fp64 ? D->t64 : D->t32;
-    CK(cudaEventRecord(D->wave_ev[4 * wi], s));
+    CK(cudaEventRecordWithFlags(D->wave_ev[4 * wi], s, cudaEventRecordExternal));
     for (auto &c : W.converts) {
       const TaskPlan &tp = P->tasks[c.first];
       const size_t n = (size_t)1 << tp.n_eff;
@@ -555,19 +555,19 @@ static void enqueue(qw_plan *P, cudaStream_t s) {
         launch_sv_pass(W.fp64, T, j.pass, k, j.n, j.src, j.dst, s);
       }
     }
-    CK(cudaEventRecord(D->wave_ev[4 * wi + 1], s));
+    CK(cudaEventRecordWithFlags(D->wave_ev[4 * wi + 1], s, cudaEventRecordExternal));
     launch_energy(W.fp64, W.d_en, (uint32_t)W.en.size(), W.en_blocks, D->d_classes, D->d_terms,
                   D->d_partials, s);
-    CK(cudaEventRecord(D->wave_ev[4 * wi + 2], s));
+    CK(cudaEventRecordWithFlags(D->wave_ev[4 * wi + 2], s, cudaEventRecordExternal));
     launch_sampling(W.fp64, W.d_src, (uint32_t)W.src.size(), W.smp_blocks, D->d_bsum, D->d_blast, D->d_boff,
                     D->d_lastnz, W.d_shots, (uint32_t)W.shots.size(), s);
-    CK(cudaEventRecord(D->wave_ev[4 * wi + 3], s));
+    CK(cudaEventRecordWithFlags(D->wave_ev[4 * wi + 3], s, cudaEventRecordExternal));
     wi++;
   }
-  CK(cudaEventRecord(D->ev[2], s));
+  CK(cudaEventRecordWithFlags(D->ev[2], s, cudaEventRecordExternal));
   // 3) tableau tasks
   for (auto &L : D->tab_task_launches) launch_tab(L.a, L.n_tasks, s);
-  CK(cudaEventRecord(D->ev[3], s));
+  CK(cudaEventRecordWithFlags(D->ev[3], s, cudaEventRecordExternal));
   CK(cudaGetLastError());
 }
 

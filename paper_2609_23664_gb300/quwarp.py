@@ -268,6 +268,7 @@ class Plan:
                                     C.byref(h)))
         self.h = h
         self.n_tasks = workload.n
+        self._engine = engine  # the engine owns the device memory: keep it alive
 
     def execute(self, stream: Optional[int] = None):
         _check(lib().qw_execute(self.h, stream))
