@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Benchmark of the reuse hot path on GB300.
+
+Workload (per GPU): batched VQE sweep at 24 qubits, FP32 statevector with
+FP64 energy reductions -- 20-layer hardware-efficient shared prefix, 256
+tasks with U{1..4} suffix layers, 200-term random Pauli Hamiltonian, all
+suffixes in one persistent CUDA-graph-captured launch.
+
+A step = one execution of the whole planned workload (prefix once, every
+suffix, every energy).  `value` = tasks/s of the reuse+batched plan, timed
+with CUDA events on the stream the plan runs on, inputs resident on the
+device.  The same GPU also runs the per-task replay plan (same kernels, no
+reuse, one launch sequence per task) and the batched replay ablation;
+their tasks/s and the ratio are reported.  `e2e` runs the same workload
+through the public C ABI from host buffers (workload submission, planning,
+upload, execution, read-back of every energy) per step.
+
+Multi-GPU (torchrun): every rank runs its own seeded replica (tasks are
+independent: weak scaling, no collective on the data path); the step time
+is the max over ranks.  `--impl reference` times the CPU oracle (per-task
+rerun in complex128 on the host cores) on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2609_23664_gb300 import workloads as W  # noqa: E402
+
+METRIC = "workload tasks/s: reuse+batched vs per-task replay, same GB300; HBM % of peak"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--qubits", type=int, default=24)
+    ap.add_argument("--tasks", type=int, default=256)
+    ap.add_argument("--prefix-layers", type=int, default=20)
+    ap.add_argument("--terms", type=int, default=200)
+    ap.add_argument("--replay-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-replay", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-tasks", type=int, default=1)
+    return ap.parse_args()
+
+
+def workload_desc(a):
+    return ("vqe%d_fp32: %d qubits, %d-layer HEA shared prefix, %d tasks x U{1..4} HEA suffix "
+            "layers, %d-term random Pauli H" % (a.qubits, a.qubits, a.prefix_layers, a.tasks, a.terms))
+
+
+def make_tasks(a, rank):
+    return W.config2_vqe24(seed=W.BASE_SEED + 2 + 1000 * rank, n=a.qubits,
+                           prefix_layers=a.prefix_layers, n_tasks=a.tasks, n_terms=a.terms)
+
+
+# ---- clocks during the timed region -------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.lines = []
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.p:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.t.join(timeout=5)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---- helpers -------------------------------------------------------------------------
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel: str, workload_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if its source
+    hash matches the kernel source compiled now (else None)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2609_23664_gb300", "csrc")
+    h = hashlib.sha256()
+    for fn in ("sv_kernels.cu", "obs_kernels.cu", "qw_internal.h"):
+        with open(os.path.join(src, fn), "rb") as f:
+            h.update(f.read())
+    digest = h.hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload_key))
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m1 = re.search(r"source_sha16:\s*([0-9a-f]{16})", txt)
+    m2 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m1 or not m2 or m1.group(1) != digest:
+        return None
+    return float(m2.group(1))
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---- CPU oracle (reference arm and cpu_baseline) -------------------------------------
+
+def oracle_tasks_per_s(a, n_tasks: int):
+    from oracle import oracle as orc
+    tasks = make_tasks(a, 0)[:n_tasks]
+    t0 = time.perf_counter()
+    for t in tasks:
+        orc.run_task(t)
+    dt = time.perf_counter() - t0
+    return n_tasks / dt, dt, orc.num_threads()
+
+
+def run_reference(a):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    from oracle import oracle as orc
+    orc.build()
+    tasks = make_tasks(a, 0)
+    per = []
+    for s in range(a.warmup + a.steps):
+        t = tasks[s % len(tasks)]
+        t0 = time.perf_counter()
+        orc.run_task(t)
+        dt = time.perf_counter() - t0
+        if s >= a.warmup:
+            per.append(dt)
+    ms = 1000.0 * statistics.mean(per)
+    value = 1000.0 / ms
+    sample = "1 task per step (per-task rerun from |0>, complex128: %d gates + %d-term energy)" % (
+        tasks[0].n_gates, a.terms)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "tasks/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_desc(a), "global_batch": a.tasks,
+                                            "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": "tasks/s", "cores": orc.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- native arm ------------------------------------------------------------------------
+
+def run_native(a):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2609_23664_gb300 import quwarp as Q
+
+    eng = Q.Engine(local)
+    info = eng.info()
+    tasks = make_tasks(a, rank)
+    n_tasks = len(tasks)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+
+    wl = Q.Workload(tasks)
+    t0 = time.perf_counter()
+    plan = Q.Plan(eng, wl)
+    planning_ms = (time.perf_counter() - t0) * 1e3
+    ex = plan.explain()
+    for _ in range(max(1, a.warmup)):
+        plan.execute(sptr)
+        plan.wait()
+
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    recs = []
+    ev0.record(stream)
+    for _ in range(a.steps):
+        plan.execute(sptr)
+        plan.wait()
+        recs.append(plan.cost_record())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / a.steps
+    ms_max = max_over_ranks(ms, world)
+    value = world * n_tasks / (ms_max / 1e3)
+    cr = recs[-1]
+    launches = int(cr["kernel_launches"])
+    suffix_ms = statistics.mean(r["suffix_ms"] for r in recs)
+    energy_ms = statistics.mean(r["energy_ms"] for r in recs)
+    prefix_ms = statistics.mean(r["prefix_ms"] for r in recs)
+    # energies of the last step, checked for finiteness (parity lives in tests)
+    e_last = [plan.energy(i)[0] for i in range(n_tasks)]
+    assert all(np.isfinite(e_last))
+
+    peak, peak_src = load_peaks()
+    S = 8 << a.qubits
+    batch_alg_bytes = float(cr.get("batch_alg_bytes", 0.0))
+    energy_alg_bytes = float(cr.get("energy_alg_bytes", 0.0))
+    wkey = "vqe%d_%dtasks" % (a.qubits, a.tasks)
+    if energy_ms >= suffix_ms:
+        kern, dur, alg = "energy_kernel", energy_ms, energy_alg_bytes
+    else:
+        kern, dur, alg = "sv_batch_kernel", suffix_ms, batch_alg_bytes
+    achieved = alg / (dur * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src,
+                "traffic": profiled_traffic(kern, wkey),
+                "algorithmic_bytes_per_launch": alg, "launch_ms": dur,
+                "other_kernels_ms": {"sv_batch_kernel": suffix_ms, "energy": energy_ms,
+                                     "prefix_passes": prefix_ms}}
+
+    line = {"metric": METRIC, "value": value, "unit": "tasks/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(a), "global_batch": world * n_tasks,
+                       "qubits": a.qubits, "state_bytes": S,
+                       "l2": "inputs larger than L2 (task states %.1f GiB > L2 %.0f MB)" % (
+                           n_tasks * S / 2 ** 30, info["l2_bytes"] / 1e6),
+                       "parallelism": "replicas (one independent workload per GPU)"},
+            "gpu_launches": launches * a.steps,
+            "planning_ms": planning_ms, "artifacts": ex["artifacts"],
+            "estimated_speedup": ex["estimated_speedup"],
+            "engine_hbm_gbs": info["hbm_gbs"]}
+    if ck:
+        line["clocks"] = ck
+
+    # per-task replay and batched replay on the same GPU, same kernels
+    if not a.no_replay:
+        plan.close()
+        for key, opts in (("per_task_replay", dict(reuse=0, batched=0)),
+                          ("batched_replay", dict(reuse=0, batched=1))):
+            rp = Q.Plan(eng, wl, **opts)
+            rp.execute(sptr)
+            rp.wait()
+            barrier(world)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(a.replay_steps):
+                rp.execute(sptr)
+                rp.wait()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rms = max_over_ranks(e0.elapsed_time(e1) / a.replay_steps, world)
+            line[key] = {"value": world * n_tasks / (rms / 1e3), "unit": "tasks/s", "ms_per_step": rms}
+            rp.close()
+        line["speedup_vs_per_task_replay"] = value / line["per_task_replay"]["value"]
+        line["speedup_vs_batched_replay"] = value / line["batched_replay"]["value"]
+
+    # end to end through the C ABI from host buffers
+    if a.e2e_steps > 0:
+        plan.close()
+        e2e_ms, h2d, d2h = [], 0, 0
+        for _ in range(a.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            wl2 = Q.Workload(tasks)
+            p2 = Q.Plan(eng, wl2)
+            p2.execute(sptr)
+            p2.wait()
+            en = [p2.energy(i) for i in range(n_tasks)]
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            r2 = p2.cost_record()
+            h2d, d2h = int(r2["h2d_bytes"]), int(r2["d2h_bytes"])
+            p2.close()
+            wl2.close()
+            del en
+        em = max_over_ranks(statistics.mean(e2e_ms), world)
+        line["e2e"] = {"value": world * n_tasks / (em / 1e3), "unit": "tasks/s", "ms_per_step": em,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "includes": "workload submission, planning, device allocation, upload, "
+                                   "execution, read-back of all energies"}
+
+    line["roofline"] = roofline
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        from oracle import oracle as orc
+        orc.build()
+        v, dt, cores = oracle_tasks_per_s(a, a.cpu_sample_tasks)
+        line["cpu_baseline"] = {"value": v, "unit": "tasks/s", "cores": cores, "kind": "oracle",
+                                "sample": "%d of %d tasks, per-task rerun from |0> in complex128 "
+                                          "(%d gates each incl. shared prefix) + %d-term energy; "
+                                          "%.1f s" % (a.cpu_sample_tasks, a.tasks,
+                                                      tasks[0].n_gates, a.terms, dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_native(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -139,7 +139,11 @@ qw_status qw_workload_add_task(qw_workload *w, const qw_task *t, uint64_t *task_
     for (uint32_t s = 0; s < t->n_spans; s++) {
       const qw_gate_span &sp = t->spans[s];
       if (sp.n_gates && !sp.gates) fail(QW_ERR_INVALID_ARG, "span %u has NULL gates", s);
-      for (uint64_t i = 0; i < sp.n_gates; i++) validate_gate(sp.gates[i], t->mode, n, total + i);
+      const auto key = std::make_tuple(sp.gates, sp.n_gates, t->mode, n);
+      if (!w->validated.count(key)) {
+        for (uint64_t i = 0; i < sp.n_gates; i++) validate_gate(sp.gates[i], t->mode, n, total + i);
+        w->validated.insert(key);
+      }
       if (sp.n_gates) {
         d.spans.push_back({sp.gates, sp.n_gates});
         total += sp.n_gates;
@@ -305,11 +309,14 @@ qw_status qw_cost_record_json(const qw_plan *p, char *buf, size_t cap, size_t *n
       "\"estimated_plan_ms\":%.6f,\"estimated_speedup\":%.4f,\"executions\":%d,"
       "\"upload_ms\":%.6f,\"prefix_ms\":%.6f,\"suffix_ms\":%.6f,\"energy_ms\":%.6f,"
       "\"sampling_ms\":%.6f,\"tableau_tasks_ms\":%.6f,\"device_total_ms\":%.6f,"
+      "\"kernel_launches\":%llu,\"h2d_bytes\":%llu,\"d2h_bytes\":%llu,"
+      "\"batch_alg_bytes\":%.0f,\"energy_alg_bytes\":%.0f,"
       "\"artifacts\":%zu,\"artifact_bytes\":%llu,\"batch_ms\":[",
       p->planning_ns * 1e-6, p->est_direct_ns * 1e-6, p->est_plan_ns * 1e-6,
       p->est_plan_ns > 0 ? p->est_direct_ns / p->est_plan_ns : 1.0, p->timed, p->t_upload_ms,
       p->t_prefix_ms, p->t_suffix_ms, p->t_energy_ms, p->t_sample_ms, p->t_tab_ms, p->t_total_ms,
-      p->mats.size(), [&] {
+      (unsigned long long)p->n_launches, (unsigned long long)p->h2d_bytes,
+      (unsigned long long)p->d2h_bytes, p->batch_alg_bytes, p->energy_alg_bytes, p->mats.size(), [&] {
         unsigned long long b = 0;
         for (auto &m : p->mats) b += m.bytes;
         return b;

@@ -109,6 +109,7 @@ struct SvTableBuilder {
 // device allocation tracked for release
 struct DevArena {
   std::vector<void *> ptrs;
+  uint64_t h2d = 0;  // bytes uploaded from the host
   void *alloc(size_t bytes) {
     void *p = nullptr;
     if (bytes == 0) bytes = 16;
@@ -120,6 +121,7 @@ struct DevArena {
   T *upload(const std::vector<T> &v, cudaStream_t s) {
     T *p = (T *)alloc(v.size() * sizeof(T));
     if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    h2d += v.size() * sizeof(T);
     return p;
   }
   void release() {
@@ -398,6 +400,11 @@ static void prepare(qw_plan *P) {
       }
       max_smp_blocks = std::max<size_t>(max_smp_blocks, W.smp_blocks);
       max_src = std::max<size_t>(max_src, W.src.size());
+      // algorithmic bytes: every pass reads and writes its state once; the
+      // energy of a task reads every amplitude once per term class
+      for (const SvJob &j : W.jobs) P->batch_alg_bytes += 2.0 * (double)S;
+      for (const EnJob &j : W.en)
+        P->energy_alg_bytes += (double)j.n_classes * (double)sv_state_bytes(fp64, j.n);
       // device copies
       W.d_jobs = D->arena.upload(W.jobs, s);
       W.ctr_words = 2 + W.jobs.size();
@@ -505,6 +512,9 @@ static void prepare(qw_plan *P) {
   }
   for (auto &e : D->ev) CK(cudaEventCreate(&e));
   CK(cudaStreamSynchronize(s));
+  P->h2d_bytes = D->arena.h2d;
+  P->d2h_bytes = 16ull * nt + 8ull * P->sample_off[nt] +
+                 (any_tab ? (uint64_t)P->outs_off[nt] + P->outs_mat_off[P->mats.size()] : 0ull);
 }
 
 // ---------------------------------------------------------------------------
@@ -512,6 +522,7 @@ static void prepare(qw_plan *P) {
 // ---------------------------------------------------------------------------
 static void enqueue(qw_plan *P, cudaStream_t s) {
   DeviceState *D = P->dev;
+  uint64_t nl = 0;  // kernels launched by one execution
   CK(cudaEventRecordWithFlags(D->ev[0], s, cudaEventRecordExternal));
   // 1) shared prefixes (boundary states), in creation order (parents first)
   for (size_t m = 0; m < P->mats.size(); m++) {
@@ -525,18 +536,21 @@ static void enqueue(qw_plan *P, cudaStream_t s) {
       if (psrc) launch_copy(psrc, D->mat_buf[m], sv_state_bytes(fp64, M.n_eff), s);
       continue;
     }
+    nl += M.sv.passes.size();
     for (size_t p = 0; p < M.sv.passes.size(); p++) {
       launch_sv_pass(fp64, T, D->mat_pass0[m] + (uint32_t)p, (uint32_t)M.sv.passes[p].q.size(), M.n_eff,
                      p == 0 ? psrc : D->mat_buf[m], D->mat_buf[m], s);
     }
   }
   for (auto &L : D->tab_mat_launches) launch_tab(L.a, L.n_tasks, s);
+  nl += D->tab_mat_launches.size();
   CK(cudaEventRecordWithFlags(D->ev[1], s, cudaEventRecordExternal));
   // 2) task suffixes, observables
   size_t wi = 0;
   for (auto &W : D->waves) {
     const SvTables &T = W.fp64 ? D->t64 : D->t32;
     CK(cudaEventRecordWithFlags(D->wave_ev[4 * wi], s, cudaEventRecordExternal));
+    nl += W.converts.size();
     for (auto &c : W.converts) {
       const TaskPlan &tp = P->tasks[c.first];
       const size_t n = (size_t)1 << tp.n_eff;
@@ -548,8 +562,10 @@ static void enqueue(qw_plan *P, cudaStream_t s) {
         CK(cudaMemsetAsync(W.d_ctr, 0, W.ctr_words * sizeof(unsigned int), s));
         launch_sv_batch(W.fp64, T, W.d_jobs, (uint32_t)W.jobs.size(), W.total_items, W.k_max, W.d_ctr,
                         W.grid, s);
+        nl += 1;
       }
     } else {
+      nl += W.jobs.size();
       for (const SvJob &j : W.jobs) {
         const uint32_t k = j.n - (uint32_t)std::log2((double)j.n_tiles);
         launch_sv_pass(W.fp64, T, j.pass, k, j.n, j.src, j.dst, s);
@@ -558,6 +574,8 @@ static void enqueue(qw_plan *P, cudaStream_t s) {
     CK(cudaEventRecordWithFlags(D->wave_ev[4 * wi + 1], s, cudaEventRecordExternal));
     launch_energy(W.fp64, W.d_en, (uint32_t)W.en.size(), W.en_blocks, D->d_classes, D->d_terms,
                   D->d_partials, s);
+    if (!W.en.empty()) nl += 2;
+    if (!W.src.empty()) nl += W.shots.empty() ? 2 : 3;
     CK(cudaEventRecordWithFlags(D->wave_ev[4 * wi + 2], s, cudaEventRecordExternal));
     launch_sampling(W.fp64, W.d_src, (uint32_t)W.src.size(), W.smp_blocks, D->d_bsum, D->d_blast, D->d_boff,
                     D->d_lastnz, W.d_shots, (uint32_t)W.shots.size(), s);
@@ -567,7 +585,9 @@ static void enqueue(qw_plan *P, cudaStream_t s) {
   CK(cudaEventRecordWithFlags(D->ev[2], s, cudaEventRecordExternal));
   // 3) tableau tasks
   for (auto &L : D->tab_task_launches) launch_tab(L.a, L.n_tasks, s);
+  nl += D->tab_task_launches.size();
   CK(cudaEventRecordWithFlags(D->ev[3], s, cudaEventRecordExternal));
+  P->n_launches = nl;
   CK(cudaGetLastError());
 }
 

@@ -7,8 +7,13 @@
 
 #include "qw_internal.h"
 
+#include <set>
+#include <tuple>
+
 struct qw_workload {
   qw::Workload w;
+  // spans already validated for (mode, n): shared spans are checked once
+  std::set<std::tuple<const qw_gate *, uint64_t, uint32_t, uint32_t>> validated;
 };
 
 namespace qw {
@@ -169,4 +174,6 @@ struct qw_plan {
          t_tab_ms = 0, t_total_ms = 0;
   int timed = 0;
   std::vector<double> batch_ms;  // per wave: suffix launch(es) only
+  uint64_t n_launches = 0, h2d_bytes = 0, d2h_bytes = 0;
+  double batch_alg_bytes = 0, energy_alg_bytes = 0;
 };
