@@ -146,19 +146,39 @@ energy_kernel(const EnJob *__restrict__ jobs, uint32_t n_jobs, const EnClass *__
     }
     nrm += a[j].x * a[j].x + a[j].y * a[j].y;
   }
+  // x_j = base | j << 8 | tid: the three fields occupy disjoint bits, so the
+  // partner index, the sign parity and the skip test split into a per-term
+  // part and a compile-time part per j.
   typename AccOf<T>::t acc;
+  const uint32_t tid = threadIdx.x;
   for (uint32_t t = K.term_begin; t < K.term_end; t++) {
     const uint32_t xm = __ldg(&terms[t].xm), zm = __ldg(&terms[t].zm);
     const uint32_t skip = __ldg(&terms[t].skip), fl = __ldg(&terms[t].flags);
     const T coef = (T)__ldg(&terms[t].coef);
+    if ((base | tid) & skip) continue;  // pair counted from its other member
+    const uint32_t ks = (skip >> 8) & 7u;
+    const uint32_t pb = (base ^ (xm & ~2047u)) | (tid ^ (xm & 255u));
+    const uint32_t mj = (xm >> 8) & 7u, zj = (zm >> 8) & 7u;
+    // parity of (j & zj) for j = 0..7 as bits of an 8-bit mask, xor the
+    // parity of (base|tid) & zm
+    const uint32_t par = ((zj & 1u) ? 0xAAu : 0u) ^ ((zj & 2u) ? 0xCCu : 0u) ^ ((zj & 4u) ? 0xF0u : 0u) ^
+                         ((__popc((base | tid) & zm) & 1) ? 0xFFu : 0u);
     T s = 0;
+    if (fl) {
 #pragma unroll
-    for (int j = 0; j < EN_EPT; j++) {
-      const uint32_t x = xs[j];
-      if (x < dim && !(x & skip)) {
-        const C p = __ldg(psi + (x ^ xm));
-        const T v = fl ? (p.x * a[j].y - p.y * a[j].x) : (p.x * a[j].x + p.y * a[j].y);
-        s += (__popc(x & zm) & 1) ? -v : v;
+      for (int j = 0; j < EN_EPT; j++) {
+        if (((uint32_t)j & ks) || xs[j] >= dim) continue;
+        const C p = __ldg(psi + (pb | (((uint32_t)j ^ mj) << 8)));
+        const T v = p.x * a[j].y - p.y * a[j].x;
+        s += ((par >> j) & 1u) ? -v : v;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < EN_EPT; j++) {
+        if (((uint32_t)j & ks) || xs[j] >= dim) continue;
+        const C p = __ldg(psi + (pb | (((uint32_t)j ^ mj) << 8)));
+        const T v = p.x * a[j].x + p.y * a[j].y;
+        s += ((par >> j) & 1u) ? -v : v;
       }
     }
     acc.add(coef * s);

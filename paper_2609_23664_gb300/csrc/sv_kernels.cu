@@ -23,13 +23,25 @@ template <typename T> struct V2;
 template <> struct V2<float> { typedef float2 t; };
 template <> struct V2<double> { typedef double2 t; };
 
+// Shared-memory swizzle of the tile (amplitude index -> slot).  It XORs bits
+// of the index above the 16-byte unit into the unit index inside a 128-byte
+// row, so strided stage accesses spread over the banks, and it keeps every
+// 16-byte unit (two FP32 amplitudes / one FP64 amplitude) contiguous, so the
+// tile can be filled with 16-byte asynchronous copies.  It is linear over
+// GF(2): swz(a ^ b) = swz(a) ^ swz(b).
 template <typename T> __device__ __forceinline__ uint32_t swz(uint32_t l);
 template <> __device__ __forceinline__ uint32_t swz<float>(uint32_t l) {
-  return l ^ (((l >> 4) ^ (l >> 8) ^ (l >> 12)) & 15u);
+  return l ^ ((((l >> 4) ^ (l >> 7) ^ (l >> 10) ^ (l >> 13)) & 7u) << 1);
 }
 template <> __device__ __forceinline__ uint32_t swz<double>(uint32_t l) {
   return l ^ (((l >> 3) ^ (l >> 6) ^ (l >> 9) ^ (l >> 12)) & 7u);
 }
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ---- register operations on the 32 amplitudes of a stage group -------------
 template <typename C, typename T, int P>
@@ -115,11 +127,6 @@ __device__ __forceinline__ void apply_op(uint32_t code, const T (&m)[8], C (&a)[
   }
 }
 
-template <typename T>
-__device__ __forceinline__ typename V2<T>::t ld_amp(const typename V2<T>::t *p, bool cg) {
-  return cg ? __ldcg(p) : *p;
-}
-
 // Processes one tile of one pass.  src == nullptr starts from |0...0>.
 template <typename T>
 __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__restrict__ stages,
@@ -133,19 +140,31 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
   const uint32_t ntile = 1u << k, lomask = (1u << b) - 1u;
   const uint32_t nt = blockDim.x;
 
-  for (uint32_t l = threadIdx.x; l < ntile; l += nt) {
-    const uint32_t lh = l >> b;
-    const uint32_t g = base | __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) |
-                       (l & lomask);
-    C v;
-    if (src) {
-      v = ld_amp<T>(src + g, cg);
-    } else {
+  // 16-byte units: two FP32 amplitudes or one FP64 amplitude
+  constexpr uint32_t APU = (sizeof(T) == 4) ? 2u : 1u;
+  const uint32_t n_units = ntile / APU;
+  if (src) {
+#pragma unroll 4
+    for (uint32_t u = threadIdx.x; u < n_units; u += nt) {
+      const uint32_t l = u * APU;
+      const uint32_t lh = l >> b;
+      const uint32_t g = base | __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) |
+                         (l & lomask);
+      cp_async16(sm + swz<T>(l), src + g);
+    }
+    cp_async_wait_all();
+  } else {
+    for (uint32_t l = threadIdx.x; l < ntile; l += nt) {
+      const uint32_t lh = l >> b;
+      const uint32_t g = base | __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) |
+                         (l & lomask);
+      C v;
       v.x = (g == 0) ? T(1) : T(0);
       v.y = T(0);
+      sm[swz<T>(l)] = v;
     }
-    sm[swz<T>(l)] = v;
   }
+  (void)cg;
   __syncthreads();
 
   const uint32_t n_groups = 1u << (k - SV_G);
@@ -193,16 +212,18 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
     __syncthreads();
   }
 
-  for (uint32_t l = threadIdx.x; l < ntile; l += nt) {
+#pragma unroll 4
+  for (uint32_t u = threadIdx.x; u < n_units; u += nt) {
+    const uint32_t l = u * APU;
     const uint32_t lh = l >> b;
     const uint32_t g = base | __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) |
                        (l & lomask);
-    dst[g] = sm[swz<T>(l)];
+    *(float4 *)(dst + g) = *(const float4 *)(sm + swz<T>(l));
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 3 : 1))
 sv_pass_kernel(SvTables t, uint32_t pass, const typename V2<T>::t *src, typename V2<T>::t *dst) {
   extern __shared__ __align__(16) unsigned char smraw[];
   typedef typename V2<T>::t C;
@@ -224,7 +245,7 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per dependency wait
 
 template <typename T>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 3 : 1))
 sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, uint32_t n_jobs, uint32_t total,
                 unsigned int *ctr) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -271,9 +292,11 @@ sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, uint32_t n_jobs, uin
 }
 
 // ---- host launchers -----------------------------------------------------------
+// 128 threads: every thread owns at least two stage groups of a 2^13 tile,
+// and three CTAs fit on an SM (registers and shared memory).
 int sv_threads_for_k(uint32_t k) {
-  const uint32_t g = 1u << (k - SV_G);
-  return (int)(g < 32 ? 32 : (g > 256 ? 256 : g));
+  const uint32_t g = 1u << (k - SV_G - 1);
+  return (int)(g < 32 ? 32 : (g > 128 ? 128 : g));
 }
 size_t sv_smem_bytes(bool fp64, uint32_t k) { return (size_t)(fp64 ? 16 : 8) << k; }
 
