@@ -77,25 +77,31 @@ static int popc32(uint32_t v) { return __builtin_popcount(v); }
 // greedy cover of the remaining gates by groups of at most `cap` positions;
 // `forced` positions belong to every group.  Returns, per group, the gate
 // indices (into idx) and the position mask.
+// With `perm` given, a gate that is not a permutation (perm[i] == 0) is not
+// taken into a group after a permutation gate on one of its positions, so
+// every permutation gate of a group can be moved to the end of the group.
 static void greedy_groups(const std::vector<uint32_t> &masks, uint32_t n_pos, uint32_t cap,
                           uint32_t forced, std::vector<std::vector<uint32_t>> &groups,
-                          std::vector<uint32_t> &group_masks) {
+                          std::vector<uint32_t> &group_masks,
+                          const std::vector<uint8_t> *perm = nullptr) {
   const uint32_t full = (n_pos >= 32) ? 0xFFFFFFFFu : ((1u << n_pos) - 1);
   std::vector<uint32_t> rem(masks.size());
   for (uint32_t i = 0; i < rem.size(); i++) rem[i] = i;
   while (!rem.empty()) {
-    uint32_t Q = forced, blocked = 0;
+    uint32_t Q = forced, blocked = 0, permq = 0;
     std::vector<uint32_t> taken;
     std::vector<uint32_t> keep;
     keep.reserve(rem.size());
     size_t i = 0;
     for (; i < rem.size(); i++) {
       const uint32_t gi = rem[i], qs = masks[gi];
-      if (qs & blocked) {
+      const bool is_perm = perm && (*perm)[gi];
+      if ((qs & blocked) || (perm && !is_perm && (qs & permq))) {
         blocked |= qs;  // must stay after an earlier skipped gate on a shared qubit
         keep.push_back(gi);
       } else if ((uint32_t)popc32(Q | qs) <= cap) {
         Q |= qs;        // commutes past every skipped gate (disjoint qubits)
+        if (is_perm) permq |= qs;
         taken.push_back(gi);
       } else {
         blocked |= qs;
@@ -163,7 +169,12 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
     }
     std::vector<std::vector<uint32_t>> st_gates;
     std::vector<uint32_t> st_masks;
-    greedy_groups(lmask, k, SV_G, 0, st_gates, st_masks);
+    std::vector<uint8_t> lperm(pass_gates[p].size());
+    for (size_t i = 0; i < pass_gates[p].size(); i++) {
+      const uint32_t op = gates[pass_gates[p][i]].op;
+      lperm[i] = (op == QW_OP_CNOT || op == QW_OP_SWAP) ? 1 : 0;
+    }
+    greedy_groups(lmask, k, SV_G, 0, st_gates, st_masks, &lperm);
     for (size_t s = 0; s < st_gates.size(); s++) {
       HostStage hs;
       uint32_t P = st_masks[s];
@@ -214,6 +225,23 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
       // diagonal ops keep {d0, d1} in m[0..3]
       for (auto &o : hs.ops)
         if (o.kind == K_D1) { o.m[2] = o.m[6]; o.m[3] = o.m[7]; }
+      // the permutation gates (all movable to the end of the stage) become
+      // the linear index map A = E_last ... E_first; row j of A as a mask
+      uint8_t row[SV_G];
+      for (int t = 0; t < SV_G; t++) row[t] = (uint8_t)(1u << t);
+      std::vector<HostOp> kept;
+      for (const HostOp &o : hs.ops) {
+        if (o.kind == K_CX) { row[o.b] ^= row[o.a]; continue; }
+        if (o.kind == K_SWAP) { std::swap(row[o.a], row[o.b]); continue; }
+        kept.push_back(o);
+      }
+      hs.ops.swap(kept);
+      for (int c = 0; c < SV_G; c++) {
+        uint8_t m = 0;
+        for (int r = 0; r < SV_G; r++)
+          if ((row[r] >> c) & 1u) m |= (uint8_t)(1u << r);
+        hs.colmask[c] = m;
+      }
       hp.stages.push_back(std::move(hs));
     }
     prog.passes.push_back(std::move(hp));

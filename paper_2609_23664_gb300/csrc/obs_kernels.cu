@@ -102,6 +102,18 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// sum_j (-1)^{popc(j & Z)} v[j] with the signs resolved at compile time
+__host__ __device__ constexpr int parity3(int x) { return (x ^ (x >> 1) ^ (x >> 2)) & 1; }
+
+template <typename T, int Z>
+__device__ __forceinline__ T signed_sum(const T (&v)[EN_EPT]) {
+  static_assert(EN_EPT == 8, "the j-field is three bits wide");
+  T s = 0;
+#pragma unroll
+  for (int j = 0; j < EN_EPT; j++) s += parity3(j & Z) ? -v[j] : v[j];
+  return s;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(EN_THREADS)
 energy_kernel(const EnJob *__restrict__ jobs, uint32_t n_jobs, const EnClass *__restrict__ classes,
@@ -164,7 +176,28 @@ energy_kernel(const EnJob *__restrict__ jobs, uint32_t n_jobs, const EnClass *__
     const uint32_t par = ((zj & 1u) ? 0xAAu : 0u) ^ ((zj & 2u) ? 0xCCu : 0u) ^ ((zj & 4u) ? 0xF0u : 0u) ^
                          ((__popc((base | tid) & zm) & 1) ? 0xFFu : 0u);
     T s = 0;
-    if (fl) {
+    if (ks == 0 && dim >= 2048u) {
+      // common case: every j takes part; the sign of each j is a compile-time
+      // function of the three z bits of the j-field
+      const uint32_t pb2 = pb | (mj << 8);
+      T v[EN_EPT];
+#pragma unroll
+      for (int j = 0; j < EN_EPT; j++) {
+        const C p = __ldg(psi + (pb2 ^ ((uint32_t)j << 8)));
+        v[j] = fl ? (p.x * a[j].y - p.y * a[j].x) : (p.x * a[j].x + p.y * a[j].y);
+      }
+      switch (zj) {
+        case 0: s = signed_sum<T, 0>(v); break;
+        case 1: s = signed_sum<T, 1>(v); break;
+        case 2: s = signed_sum<T, 2>(v); break;
+        case 3: s = signed_sum<T, 3>(v); break;
+        case 4: s = signed_sum<T, 4>(v); break;
+        case 5: s = signed_sum<T, 5>(v); break;
+        case 6: s = signed_sum<T, 6>(v); break;
+        default: s = signed_sum<T, 7>(v); break;
+      }
+      if (__popc((base | tid) & zm) & 1) s = -s;
+    } else if (fl) {
 #pragma unroll
       for (int j = 0; j < EN_EPT; j++) {
         if (((uint32_t)j & ks) || xs[j] >= dim) continue;

@@ -80,6 +80,9 @@ struct HostOp {
 };
 struct HostStage {
   uint8_t pos[SV_G];  // local tile bit positions (distinct)
+  // trailing CNOT/SWAP chain of the stage as a GF(2)-linear map of the
+  // stage index: column k of the map = bits j with colmask[k] bit j set
+  uint8_t colmask[SV_G];
   std::vector<HostOp> ops;
 };
 struct HostPass {
@@ -109,7 +112,7 @@ struct SvPassDesc {
 };
 struct SvStageDesc {
   uint8_t pos[SV_G];
-  uint8_t pad;
+  uint8_t colmask[SV_G];
   uint16_t n_ops;
   uint32_t op_begin;
 };

@@ -171,11 +171,19 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
   const uint32_t n_st = pd->n_stages, st0 = pd->stage_begin;
   for (uint32_t s = 0; s < n_st; s++) {
     const SvStageDesc st = stages[st0 + s];
-    uint32_t pos[SV_G], sp[SV_G];
+    uint32_t pos[SV_G], sp[SV_G], ss[SV_G];
 #pragma unroll
     for (int j = 0; j < SV_G; j++) {
       pos[j] = st.pos[j];
       sp[j] = swz<T>(1u << pos[j]);
+    }
+    // the stage's trailing CNOT/SWAP chain maps register index i to the
+    // stage index A i: register i is stored at the offsets of A i
+#pragma unroll
+    for (int c = 0; c < SV_G; c++) {
+      const uint32_t cm = st.colmask[c];
+      ss[c] = ((cm & 1u) ? sp[0] : 0u) ^ ((cm & 2u) ? sp[1] : 0u) ^ ((cm & 4u) ? sp[2] : 0u) ^
+              ((cm & 8u) ? sp[3] : 0u) ^ ((cm & 16u) ? sp[4] : 0u);
     }
     for (uint32_t grp = threadIdx.x; grp < n_groups; grp += nt) {
       uint32_t bse = grp;
@@ -203,9 +211,9 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
       }
 #pragma unroll
       for (int i = 0; i < 32; i++) {
-        const uint32_t idx = sb ^ ((i & 1) ? sp[0] : 0u) ^ ((i & 2) ? sp[1] : 0u) ^
-                             ((i & 4) ? sp[2] : 0u) ^ ((i & 8) ? sp[3] : 0u) ^
-                             ((i & 16) ? sp[4] : 0u);
+        const uint32_t idx = sb ^ ((i & 1) ? ss[0] : 0u) ^ ((i & 2) ? ss[1] : 0u) ^
+                             ((i & 4) ? ss[2] : 0u) ^ ((i & 8) ? ss[3] : 0u) ^
+                             ((i & 16) ? ss[4] : 0u);
         sm[idx] = a[i];
       }
     }
