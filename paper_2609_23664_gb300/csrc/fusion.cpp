@@ -74,15 +74,16 @@ static uint32_t gate_mask(const qw_gate &g) {
 
 static int popc32(uint32_t v) { return __builtin_popcount(v); }
 
-// greedy cover of the remaining gates by groups of at most `cap` positions;
-// `forced` positions belong to every group.  Returns, per group, the gate
-// indices (into idx) and the position mask.
-// With `perm` given, a gate that is not a permutation (perm[i] == 0) is not
-// taken into a group after a permutation gate on one of its positions, so
-// every permutation gate of a group can be moved to the end of the group.
-static void greedy_groups(const std::vector<uint32_t> &masks, uint32_t n_pos, uint32_t cap,
-                          uint32_t forced, std::vector<std::vector<uint32_t>> &groups,
-                          std::vector<uint32_t> &group_masks,
+// Greedy cover of the gates (in order) by groups of at most `cap`
+// positions; `forced` positions belong to every group.  A gate joins the
+// current group when it touches no position blocked by an earlier skipped
+// gate (it then commutes past every skipped gate) and when the positions it
+// reserves, cap_masks[i] (a superset of masks[i]), still fit.  With `perm`
+// given, a non-permutation gate is not taken after a permutation gate on one
+// of its positions, so the permutations of a group can all move to its end.
+static void greedy_groups(const std::vector<uint32_t> &masks, const std::vector<uint32_t> *cap_masks,
+                          uint32_t n_pos, uint32_t cap, uint32_t forced,
+                          std::vector<std::vector<uint32_t>> &groups, std::vector<uint32_t> &group_masks,
                           const std::vector<uint8_t> *perm = nullptr) {
   const uint32_t full = (n_pos >= 32) ? 0xFFFFFFFFu : ((1u << n_pos) - 1);
   std::vector<uint32_t> rem(masks.size());
@@ -95,13 +96,17 @@ static void greedy_groups(const std::vector<uint32_t> &masks, uint32_t n_pos, ui
     size_t i = 0;
     for (; i < rem.size(); i++) {
       const uint32_t gi = rem[i], qs = masks[gi];
+      const uint32_t cs = cap_masks ? (qs | ((*cap_masks)[gi] & ~blocked)) : qs;
       const bool is_perm = perm && (*perm)[gi];
       if ((qs & blocked) || (perm && !is_perm && (qs & permq))) {
         blocked |= qs;  // must stay after an earlier skipped gate on a shared qubit
         keep.push_back(gi);
-      } else if ((uint32_t)popc32(Q | qs) <= cap) {
-        Q |= qs;        // commutes past every skipped gate (disjoint qubits)
+      } else if ((uint32_t)popc32(Q | cs) <= cap) {
+        Q |= cs;
         if (is_perm) permq |= qs;
+        taken.push_back(gi);
+      } else if ((uint32_t)popc32(Q | qs) <= cap && cs != qs && (qs & Q) == qs) {
+        if (is_perm) permq |= qs;  // fits without its reservation: positions already held
         taken.push_back(gi);
       } else {
         blocked |= qs;
@@ -116,6 +121,33 @@ static void greedy_groups(const std::vector<uint32_t> &masks, uint32_t n_pos, ui
     rem.swap(keep);
   }
 }
+
+namespace {
+// FP32 operations per amplitude pair of each register-op kind
+int kind_cost(uint8_t k) {
+  switch (k) {
+    case K_U1: return 16;
+    case K_D1: case K_R: case K_RX: return 8;
+    case K_P1: return 4;
+    default: return 16;
+  }
+}
+// cheapest kind that represents the 2x2 matrix m exactly
+uint8_t classify(const double m[8]) {
+  const bool off0 = m[2] == 0 && m[3] == 0 && m[4] == 0 && m[5] == 0;
+  if (off0) return (m[0] == 1.0 && m[1] == 0.0) ? K_P1 : K_D1;
+  if (m[1] == 0 && m[3] == 0 && m[5] == 0 && m[7] == 0) return K_R;
+  if (m[1] == 0 && m[7] == 0 && m[2] == 0 && m[4] == 0 && m[0] == m[6] && m[3] == m[5]) return K_RX;
+  return K_U1;
+}
+void scale(double m[8], cd g) {
+  for (int i = 0; i < 4; i++) {
+    const cd v = cd(m[2 * i], m[2 * i + 1]) * g;
+    m[2 * i] = v.real();
+    m[2 * i + 1] = v.imag();
+  }
+}
+}  // namespace
 
 static void mat_mul(const double a[8], const double b[8], double out[8]) {  // out = a * b
   cd A[4], B[4];
@@ -146,9 +178,10 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
     pass_gates.push_back(all);
     pass_masks.push_back((n_eff >= 32) ? 0xFFFFFFFFu : ((1u << n_eff) - 1));
   } else {
-    greedy_groups(masks, n_eff, k, forced, pass_gates, pass_masks);
+    greedy_groups(masks, nullptr, n_eff, k, forced, pass_gates, pass_masks);
   }
 
+  cd gphase(1.0, 0.0);  // global phase pulled out of diagonal gates
   for (size_t p = 0; p < pass_gates.size(); p++) {
     HostPass hp;
     uint32_t Q = pass_masks[p];
@@ -159,22 +192,36 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
       if (Q & (1u << q)) { loc[q] = (uint32_t)hp.q.size(); hp.q.push_back(q); }
     hp.b = b;
     hp.n_gates = (uint32_t)pass_gates[p].size();
-    // stages inside the pass (positions = local tile bits)
-    std::vector<uint32_t> lmask(pass_gates[p].size());
-    for (size_t i = 0; i < pass_gates[p].size(); i++) {
+    // stages inside the pass (positions = local tile bits).  A single-qubit
+    // gate reserves the positions of the next two-qubit gate on its qubit, so
+    // it lands in the same stage as that gate.
+    const size_t np = pass_gates[p].size();
+    std::vector<uint32_t> lmask(np), emask(np);
+    std::vector<uint8_t> lperm(np);
+    for (size_t i = 0; i < np; i++) {
       const qw_gate &g = gates[pass_gates[p][i]];
       uint32_t m = 1u << loc[g.q0];
       if (is_two_qubit_op(g.op)) m |= 1u << loc[g.q1];
       lmask[i] = m;
+      lperm[i] = (g.op == QW_OP_CNOT || g.op == QW_OP_SWAP || g.op == QW_OP_X) ? 1 : 0;
+    }
+    std::vector<int> next_on(32, -1);
+    for (size_t ii = np; ii-- > 0;) {
+      const qw_gate &g = gates[pass_gates[p][ii]];
+      const uint32_t a = loc[g.q0];
+      if (!is_two_qubit_op(g.op)) {
+        const int j = next_on[a];
+        emask[ii] = (j < 0) ? lmask[ii] : emask[j];
+        next_on[a] = (int)ii;
+      } else {
+        emask[ii] = lmask[ii];
+        next_on[a] = (int)ii;
+        next_on[loc[g.q1]] = (int)ii;
+      }
     }
     std::vector<std::vector<uint32_t>> st_gates;
     std::vector<uint32_t> st_masks;
-    std::vector<uint8_t> lperm(pass_gates[p].size());
-    for (size_t i = 0; i < pass_gates[p].size(); i++) {
-      const uint32_t op = gates[pass_gates[p][i]].op;
-      lperm[i] = (op == QW_OP_CNOT || op == QW_OP_SWAP) ? 1 : 0;
-    }
-    greedy_groups(lmask, k, SV_G, 0, st_gates, st_masks, &lperm);
+    greedy_groups(lmask, &emask, k, SV_G, 0, st_gates, st_masks, &lperm);
     for (size_t s = 0; s < st_gates.size(); s++) {
       HostStage hs;
       uint32_t P = st_masks[s];
@@ -185,22 +232,51 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
         if (P & (1u << q)) { hs.pos[j] = (uint8_t)q; rel[q] = j; j++; }
       int last1q[SV_G];
       for (int t = 0; t < SV_G; t++) last1q[t] = -1;
+      // affine index map of the stage's trailing permutations: row j of A
+      // as a mask, c = constant
+      uint8_t row[SV_G];
+      for (int t = 0; t < SV_G; t++) row[t] = (uint8_t)(1u << t);
+      uint8_t cvec = 0;
       for (uint32_t gi_local : st_gates[s]) {
         const qw_gate &g = gates[pass_gates[p][gi_local]];
         const int a = rel[loc[g.q0]];
+        if (g.op == QW_OP_X) { cvec ^= (uint8_t)(1u << a); continue; }
+        if (g.op == QW_OP_CNOT) {
+          const int t = rel[loc[g.q1]];
+          row[t] ^= row[a];
+          if ((cvec >> a) & 1u) cvec ^= (uint8_t)(1u << t);
+          continue;
+        }
+        if (g.op == QW_OP_SWAP) {
+          const int t = rel[loc[g.q1]];
+          std::swap(row[a], row[t]);
+          const uint8_t ba = (cvec >> a) & 1u, bt = (cvec >> t) & 1u;
+          if (ba != bt) cvec ^= (uint8_t)((1u << a) | (1u << t));
+          continue;
+        }
         HostOp op{};
         double m[8];
         bool diag = false;
         if (gate_matrix_1q(g, m, &diag)) {
+          if (diag && !(m[0] == 1.0 && m[1] == 0.0)) {  // diag(d0,d1) = d0 diag(1, d1/d0)
+            const cd d0(m[0], m[1]), d1(m[6], m[7]);
+            gphase *= d0;
+            const cd r = d1 / d0;
+            m[0] = 1; m[1] = 0; m[6] = r.real(); m[7] = r.imag();
+          }
+          const uint8_t kn = classify(m);
           if (last1q[a] >= 0) {
             HostOp &prev = hs.ops[last1q[a]];
             double out[8];
             mat_mul(m, prev.m, out);
-            std::memcpy(prev.m, out, sizeof(out));
-            prev.kind = (prev.kind == K_D1 && diag) ? K_D1 : K_U1;
-            continue;
+            const uint8_t km = classify(out);
+            if (kind_cost(km) <= kind_cost(prev.kind) + kind_cost(kn)) {
+              std::memcpy(prev.m, out, sizeof(out));
+              prev.kind = km;
+              continue;
+            }
           }
-          op.kind = diag ? K_D1 : K_U1;
+          op.kind = kn;
           op.a = (uint8_t)a;
           std::memcpy(op.m, m, sizeof(m));
           last1q[a] = (int)hs.ops.size();
@@ -208,44 +284,53 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
           continue;
         }
         const int bb = rel[loc[g.q1]];
-        op.a = (uint8_t)a;
-        op.b = (uint8_t)bb;
-        switch (g.op) {
-          case QW_OP_CNOT: op.kind = K_CX; break;
-          case QW_OP_CZ: op.kind = K_CD; op.m[0] = -1; op.m[1] = 0; break;
-          case QW_OP_CPHASE: op.kind = K_CD; op.m[0] = std::cos(g.theta); op.m[1] = std::sin(g.theta); break;
-          case QW_OP_SWAP: op.kind = K_SWAP; break;
-          default: fail(QW_ERR_INVALID_ARG, "fusion: unsupported statevector op %u", g.op);
-        }
-        if ((op.kind == K_CD || op.kind == K_SWAP) && op.a > op.b) std::swap(op.a, op.b);
+        op.a = (uint8_t)std::min(a, bb);
+        op.b = (uint8_t)std::max(a, bb);
+        op.kind = K_CD;
+        if (g.op == QW_OP_CZ) { op.m[0] = -1; op.m[1] = 0; }
+        else if (g.op == QW_OP_CPHASE) { op.m[0] = std::cos(g.theta); op.m[1] = std::sin(g.theta); }
+        else fail(QW_ERR_INVALID_ARG, "fusion: unsupported statevector op %u", g.op);
         last1q[a] = -1;
         last1q[bb] = -1;
         hs.ops.push_back(op);
       }
-      // diagonal ops keep {d0, d1} in m[0..3]
-      for (auto &o : hs.ops)
-        if (o.kind == K_D1) { o.m[2] = o.m[6]; o.m[3] = o.m[7]; }
-      // the permutation gates (all movable to the end of the stage) become
-      // the linear index map A = E_last ... E_first; row j of A as a mask
-      uint8_t row[SV_G];
-      for (int t = 0; t < SV_G; t++) row[t] = (uint8_t)(1u << t);
-      std::vector<HostOp> kept;
-      for (const HostOp &o : hs.ops) {
-        if (o.kind == K_CX) { row[o.b] ^= row[o.a]; continue; }
-        if (o.kind == K_SWAP) { std::swap(row[o.a], row[o.b]); continue; }
-        kept.push_back(o);
-      }
-      hs.ops.swap(kept);
       for (int c = 0; c < SV_G; c++) {
-        uint8_t m = 0;
+        uint8_t mk = 0;
         for (int r = 0; r < SV_G; r++)
-          if ((row[r] >> c) & 1u) m |= (uint8_t)(1u << r);
-        hs.colmask[c] = m;
+          if ((row[r] >> c) & 1u) mk |= (uint8_t)(1u << r);
+        hs.colmask[c] = mk;
       }
+      hs.xmask = cvec;
       hp.stages.push_back(std::move(hs));
     }
     prog.passes.push_back(std::move(hp));
   }
+  // fold the global phase into one single-qubit op (every amplitude is in
+  // exactly one of its pairs): the first general op if there is one, else
+  // the first single-qubit op of any kind
+  if (gphase != cd(1.0, 0.0)) {
+    HostOp *target = nullptr;
+    for (auto &ps : prog.passes)
+      for (auto &st : ps.stages)
+        for (auto &o : st.ops)
+          if (!target && o.kind == K_U1) target = &o;
+    for (auto &ps : prog.passes)
+      for (auto &st : ps.stages)
+        for (auto &o : st.ops)
+          if (!target && o.kind != K_CD) target = &o;
+    if (!target) fail(QW_ERR_INVALID_ARG, "fusion: global phase without a single-qubit op");
+    scale(target->m, gphase);
+    target->kind = classify(target->m);
+  }
+  // device layout of the diagonal kinds: D1 keeps {d0, d1} in m[0..3], P1 keeps
+  // p in m[0..1]; the other kinds keep the full matrix
+  for (auto &ps : prog.passes)
+    for (auto &st : ps.stages)
+      for (auto &o : st.ops) {
+        if (o.kind == K_D1) { o.m[2] = o.m[6]; o.m[3] = o.m[7]; }
+        if (o.kind == K_P1) { o.m[0] = o.m[6]; o.m[1] = o.m[7]; }
+        if (o.kind == K_RX) { o.m[1] = -o.m[3]; }  // m[0] = c, m[1] = s (matrix [[c,-is],[-is,c]])
+      }
   return prog;
 }
 

@@ -102,16 +102,26 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// sum_j (-1)^{popc(j & Z)} v[j] with the signs resolved at compile time
-__host__ __device__ constexpr int parity3(int x) { return (x ^ (x >> 1) ^ (x >> 2)) & 1; }
+__host__ __device__ constexpr int parity4(int x) { return (x ^ (x >> 1) ^ (x >> 2) ^ (x >> 3)) & 1; }
 
+// sum_j (-1)^{popc(j & Z)} v[j] with the signs resolved at compile time
 template <typename T, int Z>
 __device__ __forceinline__ T signed_sum(const T (&v)[EN_EPT]) {
-  static_assert(EN_EPT == 8, "the j-field is three bits wide");
+  static_assert(EN_EPT == 16, "the j-field is four bits wide");
   T s = 0;
 #pragma unroll
-  for (int j = 0; j < EN_EPT; j++) s += parity3(j & Z) ? -v[j] : v[j];
+  for (int j = 0; j < EN_EPT; j++) s += parity4(j & Z) ? -v[j] : v[j];
   return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T signed_sum_rt(const T (&v)[EN_EPT], uint32_t z) {
+  switch (z) {
+#define SS(Z) case Z: return signed_sum<T, Z>(v);
+    SS(0) SS(1) SS(2) SS(3) SS(4) SS(5) SS(6) SS(7) SS(8) SS(9) SS(10) SS(11) SS(12) SS(13) SS(14)
+#undef SS
+    default: return signed_sum<T, 15>(v);
+  }
 }
 
 template <typename T>
@@ -163,58 +173,46 @@ energy_kernel(const EnJob *__restrict__ jobs, uint32_t n_jobs, const EnClass *__
   // part and a compile-time part per j.
   typename AccOf<T>::t acc;
   const uint32_t tid = threadIdx.x;
+  constexpr uint32_t JM = EN_EPT - 1;  // j-field mask (bits 8..11 of x)
   for (uint32_t t = K.term_begin; t < K.term_end; t++) {
     const uint32_t xm = __ldg(&terms[t].xm), zm = __ldg(&terms[t].zm);
     const uint32_t skip = __ldg(&terms[t].skip), fl = __ldg(&terms[t].flags);
     const T coef = (T)__ldg(&terms[t].coef);
     if ((base | tid) & skip) continue;  // pair counted from its other member
-    const uint32_t ks = (skip >> 8) & 7u;
-    const uint32_t pb = (base ^ (xm & ~2047u)) | (tid ^ (xm & 255u));
-    const uint32_t mj = (xm >> 8) & 7u, zj = (zm >> 8) & 7u;
-    // parity of (j & zj) for j = 0..7 as bits of an 8-bit mask, xor the
-    // parity of (base|tid) & zm
-    const uint32_t par = ((zj & 1u) ? 0xAAu : 0u) ^ ((zj & 2u) ? 0xCCu : 0u) ^ ((zj & 4u) ? 0xF0u : 0u) ^
-                         ((__popc((base | tid) & zm) & 1) ? 0xFFu : 0u);
+    const uint32_t ks = (skip >> 8) & JM;
+    const uint32_t pb = (base ^ (xm & ~((1u << EN_BLOCK_BITS) - 1u))) | (tid ^ (xm & 255u));
+    const uint32_t mj = (xm >> 8) & JM, zj = (zm >> 8) & JM;
+    const bool neg = __popc((base | tid) & zm) & 1;
     T s = 0;
-    if (ks == 0 && dim >= 2048u) {
-      // common case: every j takes part; the sign of each j is a compile-time
-      // function of the three z bits of the j-field
+    if (ks == 0 && dim >= (1u << EN_BLOCK_BITS)) {
+      // common case: every j takes part, signs resolved at compile time
       const uint32_t pb2 = pb | (mj << 8);
       T v[EN_EPT];
+      if (fl) {
 #pragma unroll
-      for (int j = 0; j < EN_EPT; j++) {
-        const C p = __ldg(psi + (pb2 ^ ((uint32_t)j << 8)));
-        v[j] = fl ? (p.x * a[j].y - p.y * a[j].x) : (p.x * a[j].x + p.y * a[j].y);
-      }
-      switch (zj) {
-        case 0: s = signed_sum<T, 0>(v); break;
-        case 1: s = signed_sum<T, 1>(v); break;
-        case 2: s = signed_sum<T, 2>(v); break;
-        case 3: s = signed_sum<T, 3>(v); break;
-        case 4: s = signed_sum<T, 4>(v); break;
-        case 5: s = signed_sum<T, 5>(v); break;
-        case 6: s = signed_sum<T, 6>(v); break;
-        default: s = signed_sum<T, 7>(v); break;
-      }
-      if (__popc((base | tid) & zm) & 1) s = -s;
-    } else if (fl) {
+        for (int j = 0; j < EN_EPT; j++) {
+          const C p = __ldg(psi + (pb2 ^ ((uint32_t)j << 8)));
+          v[j] = p.x * a[j].y - p.y * a[j].x;
+        }
+      } else {
 #pragma unroll
-      for (int j = 0; j < EN_EPT; j++) {
-        if (((uint32_t)j & ks) || xs[j] >= dim) continue;
-        const C p = __ldg(psi + (pb | (((uint32_t)j ^ mj) << 8)));
-        const T v = p.x * a[j].y - p.y * a[j].x;
-        s += ((par >> j) & 1u) ? -v : v;
+        for (int j = 0; j < EN_EPT; j++) {
+          const C p = __ldg(psi + (pb2 ^ ((uint32_t)j << 8)));
+          v[j] = p.x * a[j].x + p.y * a[j].y;
+        }
       }
+      s = signed_sum_rt<T>(v, zj);
     } else {
+      // general case (small registers, skipped j): per-element tests
 #pragma unroll
       for (int j = 0; j < EN_EPT; j++) {
         if (((uint32_t)j & ks) || xs[j] >= dim) continue;
         const C p = __ldg(psi + (pb | (((uint32_t)j ^ mj) << 8)));
-        const T v = p.x * a[j].x + p.y * a[j].y;
-        s += ((par >> j) & 1u) ? -v : v;
+        const T v = fl ? (p.x * a[j].y - p.y * a[j].x) : (p.x * a[j].x + p.y * a[j].y);
+        s += (__popc((uint32_t)j & zj) & 1) ? -v : v;
       }
     }
-    acc.add(coef * s);
+    acc.add(coef * (neg ? -s : s));
   }
   double e = acc.value();
   double nn = (K.hb == 0xFFFFFFFFu) ? (double)nrm : 0.0;

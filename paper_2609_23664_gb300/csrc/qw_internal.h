@@ -66,9 +66,10 @@ bool is_barrier_op(uint32_t op);  // MEASURE / RESET
 enum SvKind : uint8_t {
   K_U1 = 1,    // general 2x2 on position a: m = {u00r,u00i,u01r,u01i,u10r,u10i,u11r,u11i}
   K_D1 = 2,    // diagonal on a: m = {d0r,d0i,d1r,d1i}
-  K_CX = 3,    // controlled-X, control a, target b
   K_CD = 4,    // multiply amplitudes with bits a and b set by m = {pr, pi}
-  K_SWAP = 5,  // swap positions a, b
+  K_P1 = 6,    // diag(1, p) on a: m = {pr, pi}
+  K_R = 7,     // real 2x2 on a: m = {r00, 0, r01, 0, r10, 0, r11, 0}
+  K_RX = 8,    // [[c, -is], [-is, c]] on a: m = {c, s}
 };
 constexpr int SV_G = 5;            // positions per stage (32 register amplitudes)
 constexpr int SV_MAX_TILE_FP32 = 14;
@@ -83,6 +84,7 @@ struct HostStage {
   // trailing CNOT/SWAP chain of the stage as a GF(2)-linear map of the
   // stage index: column k of the map = bits j with colmask[k] bit j set
   uint8_t colmask[SV_G];
+  uint8_t xmask = 0;  // constant part of the map (X gates)
   std::vector<HostOp> ops;
 };
 struct HostPass {
@@ -113,7 +115,10 @@ struct SvPassDesc {
 struct SvStageDesc {
   uint8_t pos[SV_G];
   uint8_t colmask[SV_G];
+  uint8_t xmask;
+  uint8_t pad;
   uint16_t n_ops;
+  uint16_t pad2;
   uint32_t op_begin;
 };
 template <typename T>
@@ -152,8 +157,8 @@ struct EnJob {
   uint32_t block_begin, n_blocks;  // global block range of this job
 };
 constexpr int EN_THREADS = 256;
-constexpr int EN_EPT = 8;  // amplitudes per thread
-constexpr int EN_BLOCK_BITS = 11;
+constexpr int EN_EPT = 16;  // amplitudes per thread
+constexpr int EN_BLOCK_BITS = 12;  // EN_THREADS * EN_EPT amplitudes per block
 
 // ---------------------------------------------------------------------------
 // sampling descriptors

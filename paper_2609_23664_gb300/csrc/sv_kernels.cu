@@ -68,17 +68,6 @@ __device__ __forceinline__ void op_d1(C (&a)[32], const T (&m)[8]) {
     a[i].y = dr * x.y + di * x.x;
   }
 }
-template <typename C, int CT, int TG>
-__device__ __forceinline__ void op_cx(C (&a)[32]) {
-#pragma unroll
-  for (int i = 0; i < 32; i++) {
-    if (!(i & (1 << CT)) || (i & (1 << TG))) continue;
-    const int j = i | (1 << TG);
-    const C t = a[i];
-    a[i] = a[j];
-    a[j] = t;
-  }
-}
 template <typename C, typename T, int A, int B>
 __device__ __forceinline__ void op_cd(C (&a)[32], const T (&m)[8]) {
 #pragma unroll
@@ -89,15 +78,43 @@ __device__ __forceinline__ void op_cd(C (&a)[32], const T (&m)[8]) {
     a[i].y = m[0] * x.y + m[1] * x.x;
   }
 }
-template <typename C, int A, int B>
-__device__ __forceinline__ void op_swap(C (&a)[32]) {
+// diag(1, p): only the amplitudes with bit P set change
+template <typename C, typename T, int P>
+__device__ __forceinline__ void op_p1(C (&a)[32], const T (&m)[8]) {
 #pragma unroll
   for (int i = 0; i < 32; i++) {
-    if (!(i & (1 << A)) || (i & (1 << B))) continue;
-    const int j = (i & ~(1 << A)) | (1 << B);
-    const C t = a[i];
-    a[i] = a[j];
-    a[j] = t;
+    if (!(i & (1 << P))) continue;
+    const C x = a[i];
+    a[i].x = m[0] * x.x - m[1] * x.y;
+    a[i].y = m[0] * x.y + m[1] * x.x;
+  }
+}
+// real 2x2 matrix {m0, m2; m4, m6}
+template <typename C, typename T, int P>
+__device__ __forceinline__ void op_r(C (&a)[32], const T (&m)[8]) {
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    if (i & (1 << P)) continue;
+    const int j = i | (1 << P);
+    const C x = a[i], y = a[j];
+    a[i].x = m[0] * x.x + m[2] * y.x;
+    a[i].y = m[0] * x.y + m[2] * y.y;
+    a[j].x = m[4] * x.x + m[6] * y.x;
+    a[j].y = m[4] * x.y + m[6] * y.y;
+  }
+}
+// [[c, -is], [-is, c]] with c = m0, s = m1
+template <typename C, typename T, int P>
+__device__ __forceinline__ void op_rx(C (&a)[32], const T (&m)[8]) {
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    if (i & (1 << P)) continue;
+    const int j = i | (1 << P);
+    const C x = a[i], y = a[j];
+    a[i].x = m[0] * x.x + m[1] * y.y;
+    a[i].y = m[0] * x.y - m[1] * y.x;
+    a[j].x = m[1] * x.y + m[0] * y.x;
+    a[j].y = m[0] * y.y - m[1] * x.x;
   }
 }
 
@@ -112,17 +129,18 @@ __device__ __forceinline__ void apply_op(uint32_t code, const T (&m)[8], C (&a)[
     D1(0) D1(1) D1(2) D1(3) D1(4)
 #undef U1
 #undef D1
-#define CX(c, t) case QW_CODE(K_CX, c, t): op_cx<C, c, t>(a); break;
-    CX(0, 1) CX(0, 2) CX(0, 3) CX(0, 4) CX(1, 0) CX(1, 2) CX(1, 3) CX(1, 4)
-    CX(2, 0) CX(2, 1) CX(2, 3) CX(2, 4) CX(3, 0) CX(3, 1) CX(3, 2) CX(3, 4)
-    CX(4, 0) CX(4, 1) CX(4, 2) CX(4, 3)
-#undef CX
+#define P1(P) case QW_CODE(K_P1, P, 0): op_p1<C, T, P>(a, m); break;
+#define RR(P) case QW_CODE(K_R, P, 0): op_r<C, T, P>(a, m); break;
+#define RX(P) case QW_CODE(K_RX, P, 0): op_rx<C, T, P>(a, m); break;
+    P1(0) P1(1) P1(2) P1(3) P1(4)
+    RR(0) RR(1) RR(2) RR(3) RR(4)
+    RX(0) RX(1) RX(2) RX(3) RX(4)
+#undef P1
+#undef RR
+#undef RX
 #define CD(x, y) case QW_CODE(K_CD, x, y): op_cd<C, T, x, y>(a, m); break;
-#define SW(x, y) case QW_CODE(K_SWAP, x, y): op_swap<C, x, y>(a); break;
     CD(0, 1) CD(0, 2) CD(0, 3) CD(0, 4) CD(1, 2) CD(1, 3) CD(1, 4) CD(2, 3) CD(2, 4) CD(3, 4)
-    SW(0, 1) SW(0, 2) SW(0, 3) SW(0, 4) SW(1, 2) SW(1, 3) SW(1, 4) SW(2, 3) SW(2, 4) SW(3, 4)
 #undef CD
-#undef SW
     default: break;
   }
 }
@@ -209,9 +227,13 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
         for (int t = 0; t < 8; t++) m[t] = __ldg(&op->m[t]);
         apply_op<C, T>(code, m, a);
       }
+      // constant part of the affine map (X gates of the stage)
+      const uint32_t xm = st.xmask;
+      const uint32_t sbs = sb ^ ((xm & 1u) ? sp[0] : 0u) ^ ((xm & 2u) ? sp[1] : 0u) ^
+                           ((xm & 4u) ? sp[2] : 0u) ^ ((xm & 8u) ? sp[3] : 0u) ^ ((xm & 16u) ? sp[4] : 0u);
 #pragma unroll
       for (int i = 0; i < 32; i++) {
-        const uint32_t idx = sb ^ ((i & 1) ? ss[0] : 0u) ^ ((i & 2) ? ss[1] : 0u) ^
+        const uint32_t idx = sbs ^ ((i & 1) ? ss[0] : 0u) ^ ((i & 2) ? ss[1] : 0u) ^
                              ((i & 4) ? ss[2] : 0u) ^ ((i & 8) ? ss[3] : 0u) ^
                              ((i & 16) ? ss[4] : 0u);
         sm[idx] = a[i];
