@@ -82,6 +82,7 @@ struct SvTableBuilder {
         SvStageDesc sd;
         memset(&sd, 0, sizeof(sd));
         for (int j = 0; j < SV_G; j++) { sd.pos[j] = hs.pos[j]; sd.colmask[j] = hs.colmask[j]; }
+        sd.xmask = hs.xmask;
         sd.n_ops = (uint16_t)hs.ops.size();
         sd.op_begin = (uint32_t)(fp64 ? ops64.size() : ops32.size());
         for (const HostOp &o : hs.ops) {
