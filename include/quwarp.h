@@ -355,6 +355,34 @@ qw_status qw_sv_sample_dev(qw_engine *e, uint32_t mode, uint32_t n, const void *
                            const double *uniforms, uint32_t shots, uint64_t *out,
                            void *stream);
 
+/* ---- energy without device allocation --------------------------------------
+ * The paper has no counterpart of this entry point; it exists for callers of
+ * this library that cannot allocate device memory: code issuing work while a
+ * CUDA graph is captured in global mode (cudaMalloc/cudaFree are not allowed
+ * there), programs whose device memory is owned by another allocator, and
+ * latency-bound loops that cannot pay the device synchronization of
+ * cudaFree.  It computes what qw_sv_energy_dev computes, with the same
+ * kernels, but needs no engine and allocates nothing: the term layout, the
+ * job record and the per-block partial sums live in one fixed device array
+ * of the library (about 1.2 MB, held by every GPU that loads the library
+ * until the process exits).
+ *   state : device, 2^n amplitudes (double2 for QW_MODE_SV_FP64, float2 for
+ *           QW_MODE_SV_FP32), n in [5, QW_NOALLOC_MAX_QUBITS].
+ *   terms : host, n_terms <= QW_NOALLOC_MAX_TERMS; masks within n bits.
+ *   out   : device, 2 doubles {energy, <psi|psi>}, written asynchronously on
+ *           `stream` (a cudaStream_t; NULL = legacy default stream).
+ * Larger n or n_terms return QW_ERR_BUDGET.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress), which loads the
+ * module; make that first call before any stream capture.  Every call uses
+ * the same array: calls whose work overlaps on the GPU (different streams,
+ * or host threads without ordering) race and corrupt each other's results;
+ * serialize them on one stream.  The array keeps the last call's contents. */
+#define QW_NOALLOC_MAX_QUBITS 26
+#define QW_NOALLOC_MAX_TERMS 1024
+qw_status qw_sv_energy_noalloc_dev(uint32_t mode, uint32_t n, const void *state,
+                                   const qw_pauli_term *terms, uint64_t n_terms, double *out,
+                                   void *stream);
+
 #ifdef __cplusplus
 }
 #endif

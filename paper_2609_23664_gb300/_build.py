@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libquwarp.so")
 SOURCES = ["sv_kernels.cu", "obs_kernels.cu", "tab_kernels.cu", "mlp_kernels.cu", "engine.cu",
-           "planner.cpp", "fusion.cpp", "capi.cpp"]
+           "noalloc.cu", "planner.cpp", "fusion.cpp", "capi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

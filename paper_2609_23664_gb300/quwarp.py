@@ -116,6 +116,7 @@ SIGNATURES = {
     "qw_sv_apply_dev": (_st, [_vp, _u32, _u32, _vp, _vp, _u64, _vp, _vp]),
     "qw_sv_energy_dev": (_st, [_vp, _u32, _u32, _vp, _vp, _u64, _vp, _vp, _vp]),
     "qw_sv_sample_dev": (_st, [_vp, _u32, _u32, _vp, _vp, _u32, _vp, _vp]),
+    "qw_sv_energy_noalloc_dev": (_st, [_u32, _u32, _vp, _vp, _u64, _vp, _vp]),
 }
 
 
@@ -407,3 +408,12 @@ def sv_sample_dev(engine: Engine, mode: int, n: int, state_ptr: int, uniforms: n
     _check(lib().qw_sv_sample_dev(engine.h, mode, n, state_ptr, _p(u) if len(u) else None, len(u),
                                   _p(out) if len(u) else None, stream or None))
     return out
+
+
+def sv_energy_noalloc_dev(mode: int, n: int, state_ptr: int, terms: np.ndarray, out_ptr: int,
+                          stream: int = 0):
+    """Energy into a caller-owned device buffer (2 doubles) without any device
+    allocation (see qw_sv_energy_noalloc_dev); asynchronous on `stream`."""
+    t = np.ascontiguousarray(terms, dtype=W.TERM_DTYPE)
+    _check(lib().qw_sv_energy_noalloc_dev(mode, n, state_ptr, _p(t) if len(t) else None, len(t),
+                                          out_ptr, stream or None))
