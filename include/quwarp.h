@@ -182,11 +182,17 @@ typedef struct qw_plan_opts {
   uint32_t low_qubits;        /* 0 = autotuned; contiguous low qubits in every tile */
   uint32_t window;            /* 0 = autotuned; tasks interleaved in the batch order */
   int32_t use_graph;          /* 1 = capture execution in a CUDA graph              */
+  int32_t fault_injection;    /* test only, default 0.  1 = the first tile of the
+                                 persistent suffix launch waits on a dependency that
+                                 never completes: its bounded wait runs out, the
+                                 launch ends early and qw_wait reports
+                                 QW_ERR_DEVICE_TIMEOUT (results are then invalid;
+                                 the device stays usable). */
 } qw_plan_opts;
 
 /* Fills the defaults: reuse=1, batched=1, legality=1, analytic costs,
  * delta_frac=0.10, min_group=2, min_prefix_gates=1, min_prefix_cost_ns=0,
- * autotuned tiles, use_graph=1. */
+ * autotuned tiles, use_graph=1, fault_injection=0. */
 void qw_plan_opts_default(qw_plan_opts *o);
 
 typedef struct qw_plan qw_plan;
@@ -327,9 +333,12 @@ qw_status qw_costmodel_set(qw_engine *e, const float *params, const float *feat_
  * by segment with CUDA events and appends one row per timed segment to the
  * caller's arrays (capacity cap rows); *n_rows receives the count.  Each row
  * is the 12 features the planner computes for that segment and log2 of the
- * measured nanoseconds. */
+ * measured nanoseconds; analytic_log2ns (nullable) receives log2 of the
+ * analytic model's estimate for the same segment (passes x (2 S / bandwidth
+ * + launch overhead)). */
 qw_status qw_costmodel_probe(qw_engine *e, const qw_workload *w, float *features,
-                             float *targets, uint64_t cap, uint64_t *n_rows);
+                             float *targets, float *analytic_log2ns, uint64_t cap,
+                             uint64_t *n_rows);
 /* Feature vector the planner uses for gates [gate_begin, gate_end) of task
  * `task` of workload `w` executed as one segment shared by n_sharing tasks. */
 qw_status qw_costmodel_features(const qw_engine *e, const qw_workload *w, uint64_t task,

@@ -18,7 +18,8 @@ void engine_release(Engine *E);
 void costmodel_train(Engine *E, const float *feat, const float *tgt, uint64_t n, uint32_t epochs,
                      uint32_t batch, float lr, uint64_t seed, float *final_loss);
 void costmodel_set(Engine *E, const float *params, const float *mean, const float *scale);
-void costmodel_probe(Engine *E, const Workload &W, float *feat, float *tgt, uint64_t cap, uint64_t *n_rows);
+void costmodel_probe(Engine *E, const Workload &W, float *feat, float *tgt, float *analytic, uint64_t cap,
+                     uint64_t *n_rows);
 qw_status sv_apply_dev(Engine *E, uint32_t mode, uint32_t n, void *state, const qw_gate *gates,
                        uint64_t n_gates, bool init, void *stream);
 qw_status sv_energy_dev(Engine *E, uint32_t mode, uint32_t n, const void *state, const qw_pauli_term *terms,
@@ -180,6 +181,7 @@ void qw_plan_opts_default(qw_plan_opts *o) {
   o->min_prefix_gates = 1;
   o->min_prefix_cost_ns = 0.0;
   o->use_graph = 1;
+  o->fault_injection = 0;
 }
 
 qw_status qw_plan_create(qw_engine *e, const qw_workload *w, const qw_plan_opts *o, qw_plan **out) {
@@ -437,10 +439,11 @@ qw_status qw_costmodel_set(qw_engine *e, const float *params, const float *feat_
 }
 
 qw_status qw_costmodel_probe(qw_engine *e, const qw_workload *w, float *features, float *targets,
+                             float *analytic_log2ns,
                              uint64_t cap, uint64_t *n_rows) {
   QW_GUARD({
     if (!e || !w || !features || !targets || !n_rows) fail(QW_ERR_INVALID_ARG, "NULL argument");
-    costmodel_probe(&e->e, w->w, features, targets, cap, n_rows);
+    costmodel_probe(&e->e, w->w, features, targets, analytic_log2ns, cap, n_rows);
   })
 }
 

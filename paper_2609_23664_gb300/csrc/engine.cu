@@ -406,9 +406,20 @@ static void prepare(qw_plan *P) {
       for (const SvJob &j : W.jobs) P->batch_alg_bytes += 2.0 * (double)S;
       for (const EnJob &j : W.en)
         P->energy_alg_bytes += (double)j.n_classes * (double)sv_state_bytes(fp64, j.n);
-      // device copies
-      W.d_jobs = D->arena.upload(W.jobs, s);
-      W.ctr_words = 2 + W.jobs.size();
+      // device copies.  With fault injection (tests only) the first job waits
+      // on an extra job that no CTA ever takes: its counter never reaches
+      // the one tile it needs, so the bounded wait runs out.
+      std::vector<SvJob> up = W.jobs;
+      if (P->opts.fault_injection && batched && !up.empty()) {
+        SvJob ph{};
+        ph.n_tiles = 1;
+        ph.dep = -1;
+        ph.item_begin = W.total_items;  // beyond every item: never taken
+        up[0].dep = (int32_t)up.size();
+        up.push_back(ph);
+      }
+      W.d_jobs = D->arena.upload(up, s);
+      W.ctr_words = 2 + up.size();
       W.d_ctr = (unsigned int *)D->arena.alloc(W.ctr_words * sizeof(unsigned int));
       CK(cudaMemsetAsync(W.d_ctr, 0, W.ctr_words * sizeof(unsigned int), s));
       W.d_en = D->arena.upload(W.en, s);
@@ -956,7 +967,8 @@ void costmodel_set(Engine *E, const float *params, const float *mean, const floa
 
 // timing probe: runs segments of the workload's statevector tasks on a
 // scratch state and records (features, log2 ns)
-void costmodel_probe(Engine *E, const Workload &W, float *feat, float *tgt, uint64_t cap, uint64_t *n_rows) {
+void costmodel_probe(Engine *E, const Workload &W, float *feat, float *tgt, float *analytic, uint64_t cap,
+                     uint64_t *n_rows) {
   CK(cudaSetDevice(E->device));
   cudaStream_t s = (cudaStream_t)E->stream;
   cudaEvent_t e0, e1;
@@ -1002,6 +1014,10 @@ void costmodel_probe(Engine *E, const Workload &W, float *feat, float *tgt, uint
       ar.release();
       features_for(T, sg.first, sg.second, 1, tc, 0.0, feat + rows * QW_MLP_IN);
       tgt[rows] = (float)std::log2(std::max(1.0, (double)best * 1e6));
+      if (analytic) {
+        const double ns = (double)pr.passes.size() * (2.0 * (double)S / E->hbm_gbs + E->launch_ns);
+        analytic[rows] = (float)std::log2(std::max(1.0, ns));
+      }
       rows++;
     }
   }

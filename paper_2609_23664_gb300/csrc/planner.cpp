@@ -445,7 +445,10 @@ struct PlanCtx {
     const uint32_t n_eff = std::max<uint32_t>(t.n, SV_G);
     TileConfig tc = tiles(n_eff, t.mode == QW_MODE_SV_FP64);
     float f[QW_MLP_IN];
-    features_for(t, b, e, sharing, tc, (double)store_used / std::max<double>(1.0, (double)store_budget), f);
+    // the probe measures segments run alone on an empty store, so the
+    // sharing and occupancy features are queried at those values
+    (void)sharing;
+    features_for(t, b, e, 1, tc, 0.0, f);
     for (int i = 0; i < QW_MLP_IN; i++)  // outside the training range: analytic fallback
       if (f[i] < E->cm.f_lo[i] - 1e-3f || f[i] > E->cm.f_hi[i] + 1e-3f) return false;
     float y;

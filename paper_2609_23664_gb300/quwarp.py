@@ -58,7 +58,7 @@ class qw_plan_opts(C.Structure):
                 ("cost_model", C.c_int32), ("delta_frac", C.c_double), ("min_group", C.c_uint32),
                 ("min_prefix_gates", C.c_uint32), ("min_prefix_cost_ns", C.c_double),
                 ("tile_qubits", C.c_uint32), ("low_qubits", C.c_uint32), ("window", C.c_uint32),
-                ("use_graph", C.c_int32)]
+                ("use_graph", C.c_int32), ("fault_injection", C.c_int32)]
 
 
 class qw_cost_tuple(C.Structure):
@@ -111,7 +111,7 @@ SIGNATURES = {
     "qw_costmodel_predict": (_st, [_vp, _vp, _u64, _vp]),
     "qw_costmodel_get": (_st, [_vp, _vp, _vp, _vp]),
     "qw_costmodel_set": (_st, [_vp, _vp, _vp, _vp]),
-    "qw_costmodel_probe": (_st, [_vp, _vp, _vp, _vp, _u64, _vp]),
+    "qw_costmodel_probe": (_st, [_vp, _vp, _vp, _vp, _vp, _u64, _vp]),
     "qw_costmodel_features": (_st, [_vp, _vp, _u64, _u64, _u64, _u32, _vp]),
     "qw_sv_apply_dev": (_st, [_vp, _u32, _u32, _vp, _vp, _u64, _vp, _vp]),
     "qw_sv_energy_dev": (_st, [_vp, _u32, _u32, _vp, _vp, _u64, _vp, _vp, _vp]),
@@ -205,11 +205,13 @@ class Engine:
         _check(lib().qw_costmodel_set(self.h, _p(p), _p(m), _p(s)))
 
     def costmodel_probe(self, workload: "Workload", cap: int):
+        """-> (features [rows, 12], measured log2 ns, analytic-model log2 ns)"""
         f = np.zeros((cap, MLP_IN), np.float32)
         t = np.zeros(cap, np.float32)
+        a = np.zeros(cap, np.float32)
         n = C.c_uint64()
-        _check(lib().qw_costmodel_probe(self.h, workload.h, _p(f), _p(t), cap, C.byref(n)))
-        return f[:n.value], t[:n.value]
+        _check(lib().qw_costmodel_probe(self.h, workload.h, _p(f), _p(t), _p(a), cap, C.byref(n)))
+        return f[:n.value], t[:n.value], a[:n.value]
 
 
 class Workload:

@@ -1,0 +1,72 @@
+"""Learned cost model (Eq. 2 costs): engine-measured timings -> GPU training
+-> planning.  Shows what the trained network gains over the analytic model
+on held-out engine timings, and that plans built with it stay exact."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2609_23664_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2609_23664_gb300 import quwarp as Q  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def trained():
+    eng = Q.Engine(0)
+    # timing corpus: the mixed family (shared prefixes and prefix-free
+    # circuits) at 12..20 qubits, a training and a held-out seed
+    tr = W.config5_mixed(seed=11, n_tasks=900, n_min=12, n_max=20)
+    te = W.config5_mixed(seed=12, n_tasks=200, n_min=12, n_max=20)
+    f_tr, y_tr, a_tr = eng.costmodel_probe(Q.Workload(tr), 3 * len(tr))
+    f_te, y_te, a_te = eng.costmodel_probe(Q.Workload(te), 3 * len(te))
+    loss = eng.costmodel_train(f_tr, y_tr, epochs=60, batch=256, lr=2e-3, seed=7)
+    return eng, (f_tr, y_tr, a_tr), (f_te, y_te, a_te), loss
+
+
+def test_probe_collects_engine_timings(trained):
+    eng, (f, y, a), _, _ = trained
+    assert len(y) >= 2000 and f.shape == (len(y), Q.MLP_IN)
+    assert np.all(np.isfinite(y)) and np.all(y > 8)      # > 256 ns per timed segment
+
+
+def test_training_beats_the_analytic_model_on_held_out_timings(trained):
+    eng, (f_tr, y_tr, _), (f, y, a), loss = trained
+    base = float(np.mean((y_tr - y_tr.mean()) ** 2))
+    assert loss < 0.25 * base                              # learned something
+    pred = eng.costmodel_predict(f)
+    err_mlp = float(np.mean(np.abs(pred - y)))             # mean |log2 error|
+    err_ana = float(np.mean(np.abs(a - y)))
+    print("held-out mean |log2 error|: mlp %.3f analytic %.3f" % (err_mlp, err_ana))
+    assert err_mlp < err_ana
+    assert err_mlp < 0.5                                   # within ~1.4x on average
+
+
+def test_parameters_roundtrip_and_forward_kernel_agree(trained):
+    eng, _, (f, y, a), _ = trained
+    p, m, s = eng.costmodel_get()
+    pred = eng.costmodel_predict(f[:50])
+    e2 = Q.Engine(0)
+    e2.costmodel_set(p, m, s)
+    assert np.array_equal(e2.costmodel_predict(f[:50]), pred)
+    e2.close()
+
+
+def test_planning_with_the_learned_model_stays_exact(trained):
+    eng = trained[0]
+    tasks = W.config5_mixed(seed=13, n_tasks=60, n_min=12, n_max=18)
+    wl = Q.Workload(tasks)
+    plan = Q.Plan(eng, wl, cost_model=Q.COST_MLP)
+    ex = plan.explain()
+    srcs = {d["cost_source"] for d in ex["decisions"]}
+    assert "MLP" in srcs
+    plan.run()
+    for i in range(0, len(tasks), 7):
+        ref = orc.run_task(tasks[i])
+        e, _ = plan.energy(i)
+        assert abs(e - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(tasks[i].terms["coef"])))

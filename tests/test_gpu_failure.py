@@ -1,0 +1,35 @@
+"""Failure detection without a GPU fault: the persistent suffix launch's
+dependency waits are bounded; a plan built with the test-only
+fault_injection option makes one wait run out (it waits on a job no CTA
+takes), and the host must see QW_ERR_DEVICE_TIMEOUT while the device stays
+usable for the next plan."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2609_23664_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2609_23664_gb300 import quwarp as Q  # noqa: E402
+
+
+def test_bounded_wait_reports_timeout_and_device_stays_usable():
+    eng = Q.Engine(0)
+    tasks = W.config2_vqe24(n=16, n_tasks=6, n_terms=10)
+    bad = Q.Plan(eng, Q.Workload(tasks), fault_injection=1)
+    bad.execute()
+    with pytest.raises(Q.QuwarpError) as ei:
+        bad.wait()
+    assert ei.value.status == -5   # QW_ERR_DEVICE_TIMEOUT
+    bad.close()
+    good = Q.Plan(eng, Q.Workload(tasks))
+    good.run()
+    ref = orc.run_task(tasks[0])
+    e, _ = good.energy(0)
+    assert abs(e - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(tasks[0].terms["coef"])))
+    eng.close()

@@ -1,0 +1,78 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py
+times (reuse + batched, graph-captured): the whole workload runs on the GPU,
+and sampled tasks are checked against the oracle one by one."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2609_23664_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2609_23664_gb300 import quwarp as Q  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def eng():
+    e = Q.Engine(0)
+    yield e
+    e.close()
+
+
+def test_config2_vqe24_full_size_sampled(eng):
+    tasks = W.config2_vqe24()                     # 24 qubits, 256 tasks, 200 terms
+    keep = 5
+    tasks[keep].want_state = True
+    plan = Q.Plan(eng, Q.Workload(tasks))
+    plan.run()
+    ex = plan.explain()
+    assert ex["artifacts"] == 1 and ex["tasks_reusing"] == 256
+    for i in (0, keep, 255):
+        ref = orc.run_task(tasks[i], want_state=(i == keep))
+        e, nr = plan.energy(i)
+        rel = abs(e - ref["energy"]) / abs(ref["energy"])
+        print("task %d energy %.10e ref %.10e rel %.2e" % (i, e, ref["energy"], rel))
+        assert abs(e - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(tasks[i].terms["coef"])))
+        assert abs(nr - 1) < 1e-5
+        if i == keep:
+            st = plan.state(i, 24, False).astype(np.complex128)
+            err = float(np.max(np.abs(st - ref["state"])))
+            print("task %d max-abs amplitude error %.2e" % (i, err))
+            assert err <= 1e-5
+
+
+def test_config3_noisy22_full_size_sampled(eng):
+    tasks = W.config3_noisy22()                   # 22 qubits, 1024 trajectories
+    plan = Q.Plan(eng, Q.Workload(tasks))
+    plan.run()
+    ex = plan.explain()
+    assert ex["tasks_reusing"] > 900
+    # earliest / latest error trajectories and error-free ones
+    n_gates = np.array([t.n_gates for t in tasks])
+    free = np.nonzero(n_gates == 400)[0]
+    noisy = np.nonzero(n_gates > 400)[0]
+    sample = [int(free[0]), int(free[-1]), int(noisy[0]), int(noisy[-1])]
+    for i in sample:
+        ref = orc.run_task(tasks[i], want_state=True)
+        got = plan.samples(i)
+        p = np.abs(ref["state"]) ** 2
+        F = np.cumsum(p / p.sum())
+        r = ref["samples"].astype(np.int64)
+        near = (np.abs(F[np.minimum(r, len(F) - 1)] - tasks[i].uniforms) < 1e-5) | \
+               (np.abs(F[np.maximum(r - 1, 0)] - tasks[i].uniforms) < 1e-5)
+        assert np.all((got == ref["samples"]) | near), i
+
+
+def test_config4_qec_d15_full_size_sampled(eng):
+    tasks = W.config4_qec()                       # 449 qubits, 100 + 5 rounds, 4096 tasks
+    plan = Q.Plan(eng, Q.Workload(tasks))
+    plan.run()
+    for i in (0, 1, 4095):
+        ref = orc.tab_run(tasks[i].n, tasks[i].gates)
+        got = plan.syndrome(i)
+        assert len(got) == 105 * 224
+        assert np.array_equal(got, ref), i
