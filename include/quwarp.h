@@ -143,7 +143,10 @@ typedef struct qw_engine_opts {
 } qw_engine_opts;
 
 /* Creates an engine on `opts->device` (NULL opts = defaults on device 0).
- * Owns the device memory it allocates and its internal streams. */
+ * Owns the device memory it allocates and its internal streams.  Destroying
+ * an engine also releases the device memory of the plans created on it;
+ * those plans keep their host results and EXPLAIN trace, but qw_execute and
+ * qw_get_state on them return QW_ERR_STATE. */
 qw_status qw_engine_create(const qw_engine_opts *opts, qw_engine **out);
 void qw_engine_destroy(qw_engine *e);
 /* Measured/assumed bandwidth (GB/s) and SM count the cost model uses. */

@@ -78,6 +78,12 @@ qw_status qw_engine_create(const qw_engine_opts *opts, qw_engine **out) {
 
 void qw_engine_destroy(qw_engine *e) {
   if (!e) return;
+  // plans still alive lose their device state and become host-only objects
+  for (qw_plan *p : e->e.plans) {
+    try { plan_release(p); } catch (...) {}
+    p->eng = nullptr;
+  }
+  e->e.plans.clear();
   try { engine_release(&e->e); } catch (...) {}
   delete e;
 }
@@ -200,12 +206,14 @@ qw_status qw_plan_create(qw_engine *e, const qw_workload *w, const qw_plan_opts 
       delete p;
       throw;
     }
+    if (p->eng) p->eng->plans.insert(p);
     *out = p;
   })
 }
 
 void qw_plan_destroy(qw_plan *p) {
   if (!p) return;
+  if (p->eng) p->eng->plans.erase(p);
   try { plan_release(p); } catch (...) {}
   delete p;
 }
@@ -280,6 +288,7 @@ qw_status qw_get_state(const qw_plan *p, uint64_t task, void *host_dst, size_t b
     const size_t want = es << tp.n;
     if (bytes != want) fail(QW_ERR_INVALID_ARG, "state of task %llu has %zu bytes", (unsigned long long)task, want);
     if (!host_dst) fail(QW_ERR_INVALID_ARG, "host_dst is NULL");
+    if (!p->eng || !plan_state_ptr(p, task)) fail(QW_ERR_STATE, "the plan's device memory was released");
     cudaSetDevice(p->eng->device);
     // padded qubits (n < 5) stay |0>: the state is the first 2^n amplitudes
     if (cudaMemcpy(host_dst, plan_state_ptr(p, task), want, cudaMemcpyDeviceToHost) != cudaSuccess)

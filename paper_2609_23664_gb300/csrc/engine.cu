@@ -605,7 +605,7 @@ static void enqueue(qw_plan *P, cudaStream_t s) {
 
 void plan_execute(qw_plan *P, void *stream) {
   Engine *E = P->eng;
-  if (!E) fail(QW_ERR_STATE, "plan was created without an engine");
+  if (!E) fail(QW_ERR_STATE, "plan has no engine (created without one, or its engine was destroyed)");
   CK(cudaSetDevice(E->device));
   const auto t0 = std::chrono::steady_clock::now();
   if (!P->dev) {
@@ -644,7 +644,7 @@ void plan_execute(qw_plan *P, void *stream) {
 
 void plan_wait(qw_plan *P) {
   DeviceState *D = P->dev;
-  if (!D) fail(QW_ERR_STATE, "qw_wait before qw_execute");
+  if (!D || !P->eng) fail(QW_ERR_STATE, "qw_wait before qw_execute, or the engine was destroyed");
   CK(cudaSetDevice(P->eng->device));
   CK(cudaEventSynchronize(D->ev[3]));
   CK(cudaGetLastError());

@@ -10,6 +10,8 @@
 #include <set>
 #include <tuple>
 
+struct qw_plan;
+
 struct qw_workload {
   qw::Workload w;
   // spans already validated for (mode, n): shared spans are checked once
@@ -133,6 +135,7 @@ struct Engine {
   // scratch for the *_dev entry points
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
+  std::set<qw_plan *> plans;  // live plans (released when the engine is destroyed)
   TileConfig tile_config(uint32_t n_eff, bool fp64);
   double predict_log2ns(const float *feat, uint32_t rows, float *out);
   void *ensure_scratch(size_t bytes);

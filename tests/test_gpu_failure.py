@@ -33,3 +33,18 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable():
     e, _ = good.energy(0)
     assert abs(e - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(tasks[0].terms["coef"])))
     eng.close()
+
+
+def test_destroying_the_engine_releases_its_plans():
+    eng = Q.Engine(0)
+    tasks = W.config1_vqe12(n_tasks=3)
+    plan = Q.Plan(eng, Q.Workload(tasks))
+    plan.run()
+    e_before, _ = plan.energy(1)
+    eng.close()                       # releases the plan's device memory
+    assert plan.explain()["artifacts"] == 1
+    assert plan.energy(1)[0] == e_before     # host results stay readable
+    with pytest.raises(Q.QuwarpError) as ei:
+        plan.execute()
+    assert ei.value.status == -6      # QW_ERR_STATE
+    plan.close()
