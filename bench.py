@@ -57,6 +57,10 @@ def parse_args():
     ap.add_argument("--no-replay", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-tasks", type=int, default=1)
+    ap.add_argument("--fuse-energy", type=int, default=0,
+                    help="1: energy blocks as work items of the persistent suffix launch")
+    ap.add_argument("--window", type=int, default=0,
+                    help="tasks advanced together in the persistent launch (0: all of a wave)")
     return ap.parse_args()
 
 
@@ -247,7 +251,7 @@ def run_native(a):
 
     wl = Q.Workload(tasks)
     t0 = time.perf_counter()
-    plan = Q.Plan(eng, wl)
+    plan = Q.Plan(eng, wl, window=a.window, fuse_energy=a.fuse_energy)
     planning_ms = (time.perf_counter() - t0) * 1e3
     ex = plan.explain()
     for _ in range(max(1, a.warmup)):
@@ -287,7 +291,11 @@ def run_native(a):
     batch_alg_bytes = float(cr.get("batch_alg_bytes", 0.0))
     energy_alg_bytes = float(cr.get("energy_alg_bytes", 0.0))
     wkey = "vqe%d_%dtasks" % (a.qubits, a.tasks)
-    if energy_ms >= suffix_ms:
+    if cr.get("energy_fused"):
+        # energy blocks run inside the persistent suffix launch: one kernel
+        # moves the pass bytes and the energy bytes
+        kern, dur, alg = "sv_batch_kernel", suffix_ms, batch_alg_bytes + energy_alg_bytes
+    elif energy_ms >= suffix_ms:
         kern, dur, alg = "energy_kernel", energy_ms, energy_alg_bytes
     else:
         kern, dur, alg = "sv_batch_kernel", suffix_ms, batch_alg_bytes
@@ -319,7 +327,7 @@ def run_native(a):
         plan.close()
         for key, opts in (("per_task_replay", dict(reuse=0, batched=0)),
                           ("batched_replay", dict(reuse=0, batched=1))):
-            rp = Q.Plan(eng, wl, **opts)
+            rp = Q.Plan(eng, wl, window=a.window, fuse_energy=a.fuse_energy, **opts)
             rp.execute(sptr)
             rp.wait()
             barrier(world)
@@ -346,7 +354,7 @@ def run_native(a):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             wl2 = Q.Workload(tasks)
-            p2 = Q.Plan(eng, wl2)
+            p2 = Q.Plan(eng, wl2, window=a.window, fuse_energy=a.fuse_energy)
             p2.execute(sptr)
             p2.wait()
             en = [p2.energy(i) for i in range(n_tasks)]

@@ -191,11 +191,14 @@ typedef struct qw_plan_opts {
                                  launch ends early and qw_wait reports
                                  QW_ERR_DEVICE_TIMEOUT (results are then invalid;
                                  the device stays usable). */
+  int32_t fuse_energy;        /* 1 = the energy blocks of every task run as work items of
+                                 the persistent suffix launch (same results, one launch);
+                                 0 = a separate energy launch after it.  Default 0. */
 } qw_plan_opts;
 
 /* Fills the defaults: reuse=1, batched=1, legality=1, analytic costs,
  * delta_frac=0.10, min_group=2, min_prefix_gates=1, min_prefix_cost_ns=0,
- * autotuned tiles, use_graph=1, fault_injection=0. */
+ * autotuned tiles, use_graph=1, fault_injection=0, fuse_energy=0. */
 void qw_plan_opts_default(qw_plan_opts *o);
 
 typedef struct qw_plan qw_plan;

@@ -33,7 +33,7 @@ def _flags():
 def _compile(src: str) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     srcp = os.path.join(CSRC, src)
-    deps = [srcp] + [os.path.join(CSRC, h) for h in ("qw_internal.h", "plan.h")] + \
+    deps = [srcp] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))] + \
         [os.path.join(ROOT, "include", "quwarp.h")]
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj

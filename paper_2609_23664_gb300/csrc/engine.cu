@@ -137,12 +137,17 @@ struct Wave {
   int grid = 0;
   std::vector<uint32_t> tasks;            // tasks run in this wave (own buffers)
   std::vector<uint32_t> obs_tasks;        // tasks whose observables are evaluated in this wave
-  std::vector<SvJob> jobs;
+  std::vector<SvJob> jobs;                // pass jobs, in list order
+  bool fused_energy = false;              // energy blocks run inside the persistent launch
+  uint32_t seg_bits = 0;
+  std::vector<SvSeg> segs;
   uint32_t total_items = 0;
   SvJob *d_jobs = nullptr;
+  SvSeg *d_segs = nullptr;
   unsigned int *d_ctr = nullptr;
   size_t ctr_words = 0;
   std::vector<EnJob> en;
+  std::vector<uint32_t> obs_tasks_en;     // task of each energy job
   uint32_t en_blocks = 0;
   EnJob *d_en = nullptr;
   std::vector<SmpSource> src;
@@ -195,6 +200,71 @@ struct DeviceState {
 };
 
 static size_t sv_state_bytes(bool fp64, uint32_t n_eff) { return (size_t)(fp64 ? 16 : 8) << n_eff; }
+
+// Segment size of a persistent work list: the largest power of two (at most
+// 64) that no job's unit count falls below, so that few items are empty.
+static uint32_t segment_bits(const std::vector<SvJob> &jobs) {
+  uint32_t mn = 64;
+  for (const SvJob &j : jobs) mn = std::min<uint32_t>(mn, std::max<uint32_t>(1, j.n_tiles));
+  uint32_t b = 0;
+  while ((2u << b) <= mn) b++;
+  return b;
+}
+
+// Orders the work of one persistent launch into segments.  jobs[0, n_pass)
+// are pass jobs, already in list order (a task's passes in sequence); the
+// rest are energy jobs sorted by the pass job they wait for.  An energy job
+// is released once its dependency has been listed and `lag` more items have
+// gone by (by then its last tiles have been taken, so the wait is short);
+// released energy work is interleaved so that the pass and energy streams
+// advance at the same fraction of their totals, which keeps the two kinds
+// of work (ALU-bound tiles, L2-bound energy blocks) running side by side.
+static void build_segments(const std::vector<SvJob> &jobs, size_t n_pass, uint32_t seg_bits, uint64_t lag,
+                           std::vector<SvSeg> &segs) {
+  const uint64_t G = 1ull << seg_bits;
+  auto nseg = [&](const SvJob &j) { return (uint64_t)(j.n_tiles + G - 1) / G; };
+  uint64_t pass_total = 0, en_total = 0;
+  for (size_t i = 0; i < jobs.size(); i++) (i < n_pass ? pass_total : en_total) += nseg(jobs[i]);
+  segs.clear();
+  segs.reserve(pass_total + en_total);
+  std::vector<int64_t> end_seg(jobs.size(), -1);  // one past the job's last segment
+  std::vector<int64_t> first_seg(jobs.size(), -1);
+  size_t pi = 0, ei = n_pass;
+  uint32_t pu = 0, eu = 0;
+  uint64_t pass_done = 0, en_done = 0;
+  const uint64_t lag_segs = (lag + G - 1) / G;
+  while (pi < n_pass || ei < jobs.size()) {
+    // skip jobs without units
+    if (pi < n_pass && jobs[pi].n_tiles == 0) { end_seg[pi] = first_seg[pi] = (int64_t)segs.size(); pi++; continue; }
+    if (ei < jobs.size() && jobs[ei].n_tiles == 0) { ei++; continue; }
+    bool e_ready = false;
+    if (ei < jobs.size()) {
+      const int dep = jobs[ei].dep;
+      e_ready = dep < 0 || (end_seg[dep] >= 0 && (pi >= n_pass || (uint64_t)segs.size() - end_seg[dep] >= lag_segs));
+    }
+    bool take_e;
+    if (pi >= n_pass) take_e = true;
+    else if (!e_ready) take_e = false;
+    else take_e = en_done * pass_total <= pass_done * en_total;
+    const size_t j = take_e ? ei : pi;
+    uint32_t &u = take_e ? eu : pu;
+    if (first_seg[j] < 0) first_seg[j] = (int64_t)segs.size();
+    segs.push_back(SvSeg{(uint32_t)j, u});
+    u += (uint32_t)G;
+    (take_e ? en_done : pass_done) += 1;
+    if (u >= jobs[j].n_tiles) {
+      end_seg[j] = (int64_t)segs.size();
+      u = 0;
+      if (take_e) ei++; else pi++;
+    }
+  }
+  // every dependency lies wholly before its dependent (the launch drains)
+  for (size_t j = 0; j < jobs.size(); j++) {
+    const int d = jobs[j].dep;
+    if (d >= 0 && jobs[j].n_tiles && jobs[d].n_tiles && end_seg[d] > first_seg[j])
+      fail(QW_ERR_STATE, "internal: work list orders a job before its dependency");
+  }
+}
 
 // ---------------------------------------------------------------------------
 // prepare: allocate, upload, build launch descriptors
@@ -319,7 +389,8 @@ static void prepare(qw_plan *P) {
       W.k_max = kmax;
       W.obs_tasks = W.tasks;
       if (w == 0) W.obs_tasks.insert(W.obs_tasks.end(), shared_src.begin(), shared_src.end());
-      // jobs, round-robin over pass index (window = all tasks of the wave)
+      // jobs, round-robin over pass index within windows of tasks
+      std::map<uint32_t, int> last_pass;  // task -> its last pass job
       uint32_t window = P->opts.window ? P->opts.window : (uint32_t)W.tasks.size();
       window = std::max<uint32_t>(1, window);
       for (size_t w0 = 0; w0 < W.tasks.size(); w0 += window) {
@@ -339,10 +410,10 @@ static void prepare(qw_plan *P) {
             j.pass = D->task_pass0[t] + (uint32_t)p;
             j.n_tiles = 1u << (tp.n_eff - (uint32_t)tp.sv.passes[p].q.size());
             j.dep = last[i];
-            j.item_begin = W.total_items;
+            j.kind = SVJ_PASS;
             j.n = tp.n_eff;
-            W.total_items += j.n_tiles;
             last[i] = (int)W.jobs.size();
+            last_pass[t] = (int)W.jobs.size();
             W.jobs.push_back(j);
           }
         }
@@ -368,6 +439,7 @@ static void prepare(qw_plan *P) {
         j.n_blocks = H.n_blocks;
         W.en_blocks += H.n_blocks;
         W.en.push_back(j);
+        W.obs_tasks_en.push_back(t);
       }
       max_partials = std::max<size_t>(max_partials, W.en_blocks);
       // sampling sources (deduplicated by state) and shots
@@ -406,26 +478,53 @@ static void prepare(qw_plan *P) {
       for (const SvJob &j : W.jobs) P->batch_alg_bytes += 2.0 * (double)S;
       for (const EnJob &j : W.en)
         P->energy_alg_bytes += (double)j.n_classes * (double)sv_state_bytes(fp64, j.n);
-      // device copies.  With fault injection (tests only) the first job waits
-      // on an extra job that no CTA ever takes: its counter never reaches
-      // the one tile it needs, so the bounded wait runs out.
+      // persistent work list: pass jobs, then (fused) the energy jobs,
+      // released in the order their states finish
       std::vector<SvJob> up = W.jobs;
+      W.grid = batched ? sv_batch_grid(fp64, W.k_max, E->sm_count) : 0;
+      W.fused_energy = batched && P->opts.fuse_energy && !W.en.empty() && sv_threads_for_k(W.k_max) == 128;
+      if (W.fused_energy) {
+        std::vector<SvJob> ej;
+        for (size_t e = 0; e < W.en.size(); e++) {
+          SvJob j{};
+          const uint32_t t = W.obs_tasks_en[e];
+          auto it = last_pass.find(t);
+          j.dep = (it == last_pass.end()) ? -1 : it->second;
+          j.kind = SVJ_ENERGY;
+          j.pass = (uint32_t)e;
+          j.n_tiles = W.en[e].n_blocks;
+          j.n = W.en[e].n;
+          ej.push_back(j);
+        }
+        std::stable_sort(ej.begin(), ej.end(), [](const SvJob &a, const SvJob &b) { return a.dep < b.dep; });
+        up.insert(up.end(), ej.begin(), ej.end());
+      }
+      if (batched) {
+        W.seg_bits = segment_bits(up);
+        build_segments(up, W.jobs.size(), W.seg_bits, 2ull * (uint64_t)W.grid, W.segs);
+        if (((uint64_t)W.segs.size() << W.seg_bits) > 0xFFFFFFF0ull)
+          fail(QW_ERR_BUDGET, "a wave's work list exceeds 2^32 items; lower task_budget");
+        W.total_items = (uint32_t)(W.segs.size() << W.seg_bits);
+        if (W.fused_energy) P->energy_fused = true;
+      }
+      // With fault injection (tests only) the first job waits on an extra
+      // job that has no segment, so no CTA ever takes it: its counter never
+      // reaches the one unit it needs and the bounded wait runs out.
       if (P->opts.fault_injection && batched && !up.empty()) {
         SvJob ph{};
         ph.n_tiles = 1;
         ph.dep = -1;
-        ph.item_begin = W.total_items;  // beyond every item: never taken
         up[0].dep = (int32_t)up.size();
         up.push_back(ph);
       }
       W.d_jobs = D->arena.upload(up, s);
+      W.d_segs = D->arena.upload(W.segs, s);
       W.ctr_words = 2 + up.size();
       W.d_ctr = (unsigned int *)D->arena.alloc(W.ctr_words * sizeof(unsigned int));
       CK(cudaMemsetAsync(W.d_ctr, 0, W.ctr_words * sizeof(unsigned int), s));
       W.d_en = D->arena.upload(W.en, s);
       W.d_src = D->arena.upload(W.src, s);
       W.d_shots = D->arena.upload(W.shots, s);
-      W.grid = batched ? sv_batch_grid(fp64, W.k_max, E->sm_count) : 0;
       D->waves.push_back(std::move(W));
     }
   }
@@ -572,7 +671,8 @@ static void enqueue(qw_plan *P, cudaStream_t s) {
     if (P->opts.batched) {
       if (W.total_items) {
         CK(cudaMemsetAsync(W.d_ctr, 0, W.ctr_words * sizeof(unsigned int), s));
-        launch_sv_batch(W.fp64, T, W.d_jobs, (uint32_t)W.jobs.size(), W.total_items, W.k_max, W.d_ctr,
+        EnTables et{W.d_en, D->d_classes, D->d_terms, D->d_partials};
+        launch_sv_batch(W.fp64, T, W.d_jobs, W.d_segs, W.seg_bits, W.total_items, W.k_max, W.d_ctr, et,
                         W.grid, s);
         nl += 1;
       }
@@ -584,9 +684,14 @@ static void enqueue(qw_plan *P, cudaStream_t s) {
       }
     }
     CK(cudaEventRecordWithFlags(D->wave_ev[4 * wi + 1], s, cudaEventRecordExternal));
-    launch_energy(W.fp64, W.d_en, (uint32_t)W.en.size(), W.en_blocks, D->d_classes, D->d_terms,
-                  D->d_partials, s);
-    if (!W.en.empty()) nl += 2;
+    if (W.fused_energy) {
+      launch_energy_reduce(W.d_en, (uint32_t)W.en.size(), D->d_partials, s);
+      nl += 1;
+    } else {
+      launch_energy(W.fp64, W.d_en, (uint32_t)W.en.size(), W.en_blocks, D->d_classes, D->d_terms,
+                    D->d_partials, s);
+      if (!W.en.empty()) nl += 2;
+    }
     if (!W.src.empty()) nl += W.shots.empty() ? 2 : 3;
     CK(cudaEventRecordWithFlags(D->wave_ev[4 * wi + 2], s, cudaEventRecordExternal));
     launch_sampling(W.fp64, W.d_src, (uint32_t)W.src.size(), W.smp_blocks, D->d_bsum, D->d_blast, D->d_boff,

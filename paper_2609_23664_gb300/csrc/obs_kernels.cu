@@ -20,6 +20,7 @@
 
 #include <algorithm>
 
+#include "energy_block.cuh"
 #include "qw_internal.h"
 
 namespace qw {
@@ -76,59 +77,16 @@ void build_energy_layout(const qw_pauli_term *terms, uint64_t n_terms, uint32_t 
 // ---------------------------------------------------------------------------
 // energy kernels
 // ---------------------------------------------------------------------------
-struct DFAcc {  // double-float accumulator (two-sum of the high part)
-  float hi = 0.f, lo = 0.f;
-  __device__ __forceinline__ void add(float p) {
-    const float s = hi + p;
-    const float bp = s - hi;
-    const float err = (hi - (s - bp)) + (p - bp);
-    hi = s;
-    lo += err;
-  }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-struct DAcc {
-  double v = 0.0;
-  __device__ __forceinline__ void add(double p) { v += p; }
-  __device__ __forceinline__ double value() const { return v; }
-};
-template <typename T> struct AccOf;
-template <> struct AccOf<float> { typedef DFAcc t; };
-template <> struct AccOf<double> { typedef DAcc t; };
+__device__ __forceinline__ double warp_sum_d(double v) { return en_warp_sum(v); }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__host__ __device__ constexpr int parity4(int x) { return (x ^ (x >> 1) ^ (x >> 2) ^ (x >> 3)) & 1; }
-
-// sum_j (-1)^{popc(j & Z)} v[j] with the signs resolved at compile time
-template <typename T, int Z>
-__device__ __forceinline__ T signed_sum(const T (&v)[EN_EPT]) {
-  static_assert(EN_EPT == 16, "the j-field is four bits wide");
-  T s = 0;
-#pragma unroll
-  for (int j = 0; j < EN_EPT; j++) s += parity4(j & Z) ? -v[j] : v[j];
-  return s;
-}
-
+// one CTA per 4096-amplitude block; the block's job is found by binary search.
+// Four CTAs per SM (64 registers for FP32): the kernel is bound by the
+// latency and bandwidth of its L2 partner reads, so resident warps matter
+// more than registers.
 template <typename T>
-__device__ __forceinline__ T signed_sum_rt(const T (&v)[EN_EPT], uint32_t z) {
-  switch (z) {
-#define SS(Z) case Z: return signed_sum<T, Z>(v);
-    SS(0) SS(1) SS(2) SS(3) SS(4) SS(5) SS(6) SS(7) SS(8) SS(9) SS(10) SS(11) SS(12) SS(13) SS(14)
-#undef SS
-    default: return signed_sum<T, 15>(v);
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(EN_THREADS)
+__global__ void __launch_bounds__(EN_THREADS, 4)
 energy_kernel(const EnJob *__restrict__ jobs, uint32_t n_jobs, const EnClass *__restrict__ classes,
               const EnTerm *__restrict__ terms, double *partials) {
-  typedef typename V2o<T>::t C;
   const uint32_t gb = blockIdx.x;
   uint32_t lo = 0, hi = n_jobs;
   while (hi - lo > 1) {
@@ -136,98 +94,7 @@ energy_kernel(const EnJob *__restrict__ jobs, uint32_t n_jobs, const EnClass *__
     if (jobs[mid].block_begin <= gb) lo = mid; else hi = mid;
   }
   const EnJob J = jobs[lo];
-  const uint32_t jb = gb - J.block_begin;
-  uint32_t c = J.class_begin;
-  const uint32_t ce = J.class_begin + J.n_classes;
-  while (c + 1 < ce && classes[c + 1].block_begin <= jb) c++;
-  const EnClass K = classes[c];
-  const uint32_t within = jb - K.block_begin;
-  const uint32_t bpc_bits = (J.chunk_bits > (uint32_t)EN_BLOCK_BITS) ? J.chunk_bits - EN_BLOCK_BITS : 0u;
-  const uint32_t own = within >> bpc_bits;
-  const uint32_t bic = within & ((1u << bpc_bits) - 1u);
-  uint32_t chunk = own;
-  if (K.hb != 0xFFFFFFFFu) {
-    const uint32_t p = K.hb - J.chunk_bits;
-    chunk = ((own >> p) << (p + 1)) | (own & ((1u << p) - 1u));
-  }
-  const uint32_t dim = 1u << J.n;
-  const uint32_t base = (chunk << J.chunk_bits) + (bic << EN_BLOCK_BITS);
-  const C *psi = (const C *)J.state;
-
-  C a[EN_EPT];
-  uint32_t xs[EN_EPT];
-  T nrm = 0;
-#pragma unroll
-  for (int j = 0; j < EN_EPT; j++) {
-    xs[j] = base + (uint32_t)j * EN_THREADS + threadIdx.x;
-    if (xs[j] < dim) {
-      a[j] = __ldg(psi + xs[j]);
-    } else {
-      a[j].x = 0;
-      a[j].y = 0;
-    }
-    nrm += a[j].x * a[j].x + a[j].y * a[j].y;
-  }
-  // x_j = base | j << 8 | tid: the three fields occupy disjoint bits, so the
-  // partner index, the sign parity and the skip test split into a per-term
-  // part and a compile-time part per j.
-  typename AccOf<T>::t acc;
-  const uint32_t tid = threadIdx.x;
-  constexpr uint32_t JM = EN_EPT - 1;  // j-field mask (bits 8..11 of x)
-  for (uint32_t t = K.term_begin; t < K.term_end; t++) {
-    const uint32_t xm = __ldg(&terms[t].xm), zm = __ldg(&terms[t].zm);
-    const uint32_t skip = __ldg(&terms[t].skip), fl = __ldg(&terms[t].flags);
-    const T coef = (T)__ldg(&terms[t].coef);
-    if ((base | tid) & skip) continue;  // pair counted from its other member
-    const uint32_t ks = (skip >> 8) & JM;
-    const uint32_t pb = (base ^ (xm & ~((1u << EN_BLOCK_BITS) - 1u))) | (tid ^ (xm & 255u));
-    const uint32_t mj = (xm >> 8) & JM, zj = (zm >> 8) & JM;
-    const bool neg = __popc((base | tid) & zm) & 1;
-    T s = 0;
-    if (ks == 0 && dim >= (1u << EN_BLOCK_BITS)) {
-      // common case: every j takes part, signs resolved at compile time
-      const uint32_t pb2 = pb | (mj << 8);
-      T v[EN_EPT];
-      if (fl) {
-#pragma unroll
-        for (int j = 0; j < EN_EPT; j++) {
-          const C p = __ldg(psi + (pb2 ^ ((uint32_t)j << 8)));
-          v[j] = p.x * a[j].y - p.y * a[j].x;
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < EN_EPT; j++) {
-          const C p = __ldg(psi + (pb2 ^ ((uint32_t)j << 8)));
-          v[j] = p.x * a[j].x + p.y * a[j].y;
-        }
-      }
-      s = signed_sum_rt<T>(v, zj);
-    } else {
-      // general case (small registers, skipped j): per-element tests
-#pragma unroll
-      for (int j = 0; j < EN_EPT; j++) {
-        if (((uint32_t)j & ks) || xs[j] >= dim) continue;
-        const C p = __ldg(psi + (pb | (((uint32_t)j ^ mj) << 8)));
-        const T v = fl ? (p.x * a[j].y - p.y * a[j].x) : (p.x * a[j].x + p.y * a[j].y);
-        s += (__popc((uint32_t)j & zj) & 1) ? -v : v;
-      }
-    }
-    acc.add(coef * (neg ? -s : s));
-  }
-  double e = acc.value();
-  double nn = (K.hb == 0xFFFFFFFFu) ? (double)nrm : 0.0;
-  __shared__ double red[2][EN_THREADS / 32];
-  e = warp_sum_d(e);
-  nn = warp_sum_d(nn);
-  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
-  if (ln == 0) { red[0][w] = e; red[1][w] = nn; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double se = 0, sn = 0;
-    for (int i = 0; i < EN_THREADS / 32; i++) { se += red[0][i]; sn += red[1][i]; }
-    partials[2 * (size_t)gb] = se;
-    partials[2 * (size_t)gb + 1] = sn;
-  }
+  energy_block<T, EN_THREADS, true>(J, gb - J.block_begin, classes, terms, partials + 2 * (size_t)gb);
 }
 
 // one warp per job; fixed summation order
@@ -250,6 +117,13 @@ __global__ void energy_reduce_kernel(const EnJob *__restrict__ jobs, uint32_t n_
   }
 }
 
+void launch_energy_reduce(const EnJob *jobs, uint32_t n_jobs, const double *partials, void *stream) {
+  if (n_jobs == 0) return;
+  const int warps = 4;
+  energy_reduce_kernel<<<(n_jobs + warps - 1) / warps, warps * 32, 0, (cudaStream_t)stream>>>(jobs, n_jobs,
+                                                                                           partials);
+}
+
 void launch_energy(bool fp64, const EnJob *jobs, uint32_t n_jobs, uint32_t total_blocks,
                    const EnClass *classes, const EnTerm *terms, double *partials, void *stream) {
   if (n_jobs == 0 || total_blocks == 0) return;
@@ -258,8 +132,7 @@ void launch_energy(bool fp64, const EnJob *jobs, uint32_t n_jobs, uint32_t total
     energy_kernel<double><<<total_blocks, EN_THREADS, 0, s>>>(jobs, n_jobs, classes, terms, partials);
   else
     energy_kernel<float><<<total_blocks, EN_THREADS, 0, s>>>(jobs, n_jobs, classes, terms, partials);
-  const int warps = 4;
-  energy_reduce_kernel<<<(n_jobs + warps - 1) / warps, warps * 32, 0, s>>>(jobs, n_jobs, partials);
+  launch_energy_reduce(jobs, n_jobs, partials, stream);
 }
 
 // ---------------------------------------------------------------------------

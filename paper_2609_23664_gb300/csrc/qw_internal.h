@@ -122,11 +122,11 @@ struct SvStageDesc {
   uint32_t op_begin;
 };
 template <typename T>
-struct SvOpDesc {
+struct alignas(16) SvOpDesc {
+  T m[8];         // read as 16-byte vectors
   uint32_t code;  // kind | a << 8 | b << 16
-  uint32_t pad;
-  T m[8];
 };
+static_assert(sizeof(SvOpDesc<float>) == 48 && sizeof(SvOpDesc<double>) == 80, "op descriptor layout");
 
 // Fusion planner: gates -> passes -> stages (host).
 SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const TileConfig &tc);
@@ -142,6 +142,7 @@ struct EnTerm {
   uint32_t xm, zm, skip, flags;  // flags bit0: imaginary component of conj(p)*a
   double coef;                   // c_k * sign(i^{#Y}) * (2 if xm != 0)
 };
+static_assert(sizeof(EnTerm) == 24, "EnTerm is read as two 8-byte words and a double");
 struct EnClass {
   uint32_t term_begin, term_end;
   uint32_t hb;           // highest bit of the class's flip pattern, 0xFFFFFFFF for class 0
@@ -157,8 +158,7 @@ struct EnJob {
   uint32_t block_begin, n_blocks;  // global block range of this job
 };
 constexpr int EN_THREADS = 256;
-constexpr int EN_EPT = 16;  // amplitudes per thread
-constexpr int EN_BLOCK_BITS = 12;  // EN_THREADS * EN_EPT amplitudes per block
+constexpr int EN_BLOCK_BITS = 12;  // amplitudes per block: EN_THREADS x 16
 
 // ---------------------------------------------------------------------------
 // sampling descriptors
@@ -223,15 +223,30 @@ struct SvTables {
   const SvStageDesc *stages;
   const void *ops;  // SvOpDesc<T>*
 };
+// A job of the persistent launch: one pass over one state (n_tiles tiles),
+// or the energy blocks of one state (kind SVJ_ENERGY, n_tiles blocks).
+enum SvJobKind : uint32_t { SVJ_PASS = 0, SVJ_ENERGY = 1 };
 struct SvJob {
   const void *src;   // NULL: start from |0...0>
   void *dst;
-  uint32_t pass;     // index into the pass table
-  uint32_t n_tiles;
+  uint32_t pass;     // SVJ_PASS: index into the pass table; SVJ_ENERGY: index of the EnJob
+  uint32_t n_tiles;  // work units
   int32_t dep;       // job that must finish first, -1 none
-  uint32_t item_begin;
+  uint32_t kind;     // SvJobKind
   uint32_t n;        // effective qubits
   uint32_t pad;
+};
+// The work list of a persistent launch is cut into segments of 2^seg_bits
+// items; segment i holds units [first, first + 2^seg_bits) of job `job`
+// (units past the job's end are empty items).
+struct SvSeg {
+  uint32_t job, first;
+};
+struct EnTables {
+  const EnJob *jobs;
+  const EnClass *classes;
+  const EnTerm *terms;
+  double *partials;
 };
 
 void sv_init_attrs();
@@ -242,9 +257,10 @@ size_t sv_smem_bytes(bool fp64, uint32_t k);
 void launch_sv_pass(bool fp64, const SvTables &t, uint32_t pass_idx, uint32_t k, uint32_t n,
                     const void *src, void *dst, void *stream);
 // persistent batch over jobs; counters: [0] = next item, [1] = error flag,
-// [2..] = per-job completed tiles (all zeroed by the caller beforehand)
-void launch_sv_batch(bool fp64, const SvTables &t, const SvJob *jobs, uint32_t n_jobs,
-                     uint32_t total_items, uint32_t k_max, unsigned int *counters,
+// [2..] = per-job completed units (all zeroed by the caller beforehand).
+// Energy jobs need 128-thread CTAs (sv_threads_for_k(k_max) == 128).
+void launch_sv_batch(bool fp64, const SvTables &t, const SvJob *jobs, const SvSeg *segs, uint32_t seg_bits,
+                     uint32_t total_items, uint32_t k_max, unsigned int *counters, const EnTables &en,
                      int grid, void *stream);
 int sv_batch_grid(bool fp64, uint32_t k, int sm_count);
 void launch_copy(const void *src, void *dst, size_t bytes, void *stream);
@@ -253,6 +269,8 @@ void launch_copy(const void *src, void *dst, size_t bytes, void *stream);
 // kernel writes {energy, norm2} of every job
 void launch_energy(bool fp64, const EnJob *jobs, uint32_t n_jobs, uint32_t total_blocks,
                    const EnClass *classes, const EnTerm *terms, double *partials, void *stream);
+// the reduction alone, for partials written by the persistent launch
+void launch_energy_reduce(const EnJob *jobs, uint32_t n_jobs, const double *partials, void *stream);
 // sampling: block sums -> per-source sequential offsets -> shots
 void launch_sampling(bool fp64, const SmpSource *srcs, uint32_t n_src, uint32_t total_blocks,
                      double *bsum, int32_t *blast, double *boff, int64_t *lastnz,

@@ -13,8 +13,10 @@
 // sv_batch_kernel runs the suffixes of many tasks in ONE persistent launch:
 // CTAs take tiles from a global work list in order; a tile of pass p of a
 // task waits (bounded) until every tile of pass p-1 of that task is done.
+// On request the list also holds the energy blocks of each finished state.
 #include <cuda_runtime.h>
 
+#include "energy_block.cuh"
 #include "qw_internal.h"
 
 namespace qw {
@@ -118,6 +120,21 @@ __device__ __forceinline__ void op_rx(C (&a)[32], const T (&m)[8]) {
   }
 }
 
+// the eight matrix parameters of an op as 16-byte loads
+__device__ __forceinline__ void load_m(const SvOpDesc<float> *op, float (&m)[8]) {
+  const float4 u = __ldg((const float4 *)op->m), v = __ldg((const float4 *)(op->m + 4));
+  m[0] = u.x; m[1] = u.y; m[2] = u.z; m[3] = u.w;
+  m[4] = v.x; m[5] = v.y; m[6] = v.z; m[7] = v.w;
+}
+__device__ __forceinline__ void load_m(const SvOpDesc<double> *op, double (&m)[8]) {
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const double2 u = __ldg((const double2 *)(op->m + 2 * i));
+    m[2 * i] = u.x;
+    m[2 * i + 1] = u.y;
+  }
+}
+
 #define QW_CODE(kind, a, b) ((uint32_t)(kind) | ((uint32_t)(a) << 8) | ((uint32_t)(b) << 16))
 
 template <typename C, typename T>
@@ -158,7 +175,11 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
   const uint32_t ntile = 1u << k, lomask = (1u << b) - 1u;
   const uint32_t nt = blockDim.x;
 
-  // 16-byte units: two FP32 amplitudes or one FP64 amplitude
+  // 16-byte units: two FP32 amplitudes or one FP64 amplitude.  The deposit
+  // of a tile index into the state index and the swizzle are both linear
+  // over GF(2); a thread's units are l0 | li with l0 = APU * tid below the
+  // step APU * nt (a power of two) and li a multiple of it, so the thread
+  // part is looked up once and only the warp-uniform part per unit.
   constexpr uint32_t APU = (sizeof(T) == 4) ? 2u : 1u;
   const uint32_t n_units = ntile / APU;
   if (src) {
@@ -223,8 +244,7 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
         const SvOpDesc<T> *op = ops + st.op_begin + o;
         const uint32_t code = __ldg(&op->code);
         T m[8];
-#pragma unroll
-        for (int t = 0; t < 8; t++) m[t] = __ldg(&op->m[t]);
+        load_m(op, m);
         apply_op<C, T>(code, m, a);
       }
       // constant part of the affine map (X gates of the stage)
@@ -274,47 +294,69 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per dependency wait
 
+// Persistent launch over an ordered work list: a CTA takes the next item,
+// maps it through the segment table to (job, unit), waits (bounded) until
+// the job's dependency has completed every unit, runs the unit (one tile of
+// a pass, or one energy block of a finished state) and counts it done.
+// Items are taken in list order and every dependency lies wholly before its
+// dependent, so the oldest unfinished item never waits and the launch always
+// drains.
 template <typename T>
 __global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 3 : 1))
-sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, uint32_t n_jobs, uint32_t total,
-                unsigned int *ctr) {
+sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, const SvSeg *__restrict__ segs,
+                uint32_t seg_bits, uint32_t total, unsigned int *ctr, EnTables en) {
   extern __shared__ __align__(16) unsigned char smraw[];
   typedef typename V2<T>::t C;
-  __shared__ uint32_t s_item, s_job;
-  __shared__ int s_abort;
+  __shared__ uint32_t s_job, s_unit;
+  __shared__ int s_state;  // 0 run, 1 empty item, 2 stop
   for (;;) {
     if (threadIdx.x == 0) {
       const uint32_t it = atomicAdd(&ctr[0], 1u);
-      s_item = it;
-      s_abort = 0;
-      if (it < total) {
-        uint32_t lo = 0, hi = n_jobs;
-        while (hi - lo > 1) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (jobs[mid].item_begin <= it) lo = mid; else hi = mid;
-        }
-        s_job = lo;
-        const int dep = jobs[lo].dep;
-        if (dep >= 0) {
-          const uint32_t need = jobs[dep].n_tiles;
-          const uint64_t t0 = globaltimer_ns();
-          while (ld_acquire_u32(&ctr[2 + dep]) < need) {
-            if (ld_acquire_u32(&ctr[1]) != 0u) { s_abort = 1; break; }
-            if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
-              atomicExch(&ctr[1], 1u);  // reported to the host as a device timeout
-              s_abort = 1;
-              break;
+      int st = 0;
+      if (it >= total) {
+        st = 2;
+      } else {
+        const SvSeg sg = segs[it >> seg_bits];
+        const uint32_t unit = sg.first + (it & ((1u << seg_bits) - 1u));
+        s_job = sg.job;
+        s_unit = unit;
+        if (unit >= jobs[sg.job].n_tiles) {
+          st = 1;
+        } else {
+          const int dep = jobs[sg.job].dep;
+          if (dep >= 0) {
+            const uint32_t need = jobs[dep].n_tiles;
+            const uint64_t t0 = globaltimer_ns();
+            while (ld_acquire_u32(&ctr[2 + dep]) < need) {
+              if (ld_acquire_u32(&ctr[1]) != 0u) { st = 2; break; }
+              if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
+                atomicExch(&ctr[1], 1u);  // reported to the host as a device timeout
+                st = 2;
+                break;
+              }
+              __nanosleep(100);
             }
-            __nanosleep(100);
           }
         }
       }
+      s_state = st;
     }
     __syncthreads();
-    if (s_item >= total || s_abort) break;
+    const int st = s_state;
+    if (st == 2) break;
+    if (st == 1) {
+      __syncthreads();  // s_state is rewritten only after every thread read it
+      continue;
+    }
     const SvJob job = jobs[s_job];
-    sv_tile<T>(t.passes + job.pass, t.stages, (const SvOpDesc<T> *)t.ops, (C *)smraw,
-               (const C *)job.src, (C *)job.dst, s_item - job.item_begin, true);
+    if (job.kind == SVJ_ENERGY) {
+      const EnJob J = en.jobs[job.pass];
+      energy_block<T, 128, false>(J, s_unit, en.classes, en.terms,
+                                  en.partials + 2 * (size_t)(J.block_begin + s_unit));
+    } else {
+      sv_tile<T>(t.passes + job.pass, t.stages, (const SvOpDesc<T> *)t.ops, (C *)smraw, (const C *)job.src,
+                 (C *)job.dst, s_unit, true);
+    }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd(&ctr[2 + s_job], 1u);
@@ -368,16 +410,16 @@ int sv_batch_grid(bool fp64, uint32_t k, int sm_count) {
   return per_sm * sm_count;
 }
 
-void launch_sv_batch(bool fp64, const SvTables &t, const SvJob *jobs, uint32_t n_jobs,
-                     uint32_t total_items, uint32_t k_max, unsigned int *counters, int grid,
-                     void *stream) {
+void launch_sv_batch(bool fp64, const SvTables &t, const SvJob *jobs, const SvSeg *segs, uint32_t seg_bits,
+                     uint32_t total_items, uint32_t k_max, unsigned int *counters, const EnTables &en,
+                     int grid, void *stream) {
   const int threads = sv_threads_for_k(k_max);
   const size_t smem = sv_smem_bytes(fp64, k_max);
   cudaStream_t s = (cudaStream_t)stream;
   if (fp64)
-    sv_batch_kernel<double><<<grid, threads, smem, s>>>(t, jobs, n_jobs, total_items, counters);
+    sv_batch_kernel<double><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items, counters, en);
   else
-    sv_batch_kernel<float><<<grid, threads, smem, s>>>(t, jobs, n_jobs, total_items, counters);
+    sv_batch_kernel<float><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items, counters, en);
 }
 
 }  // namespace qw

@@ -194,6 +194,28 @@ def test_config2_vqe_fp32_small(eng, reuse, batched):
             assert np.max(np.abs(got - ref["state"])) <= 1e-5
 
 
+@pytest.mark.parametrize("mode,n", [(W.MODE_SV_FP32, 16), (W.MODE_SV_FP64, 15)])
+def test_energy_fused_into_the_suffix_launch(eng, mode, n):
+    # energy blocks as work items of the persistent launch: same results as
+    # the separate energy launch and as the oracle
+    tasks = W.config2_vqe24(n=n, n_tasks=12, n_terms=60, mode=mode)
+    p, wl = run_plan(eng, tasks, fuse_energy=1, tile_qubits=13)
+    assert p.cost_record()["energy_fused"] is True
+    q, wl2 = run_plan(eng, tasks, tile_qubits=13)
+    assert q.cost_record()["energy_fused"] is False
+    fp64 = mode == W.MODE_SV_FP64
+    for i, t in enumerate(tasks):
+        ref = orc.run_task(t)
+        e, nr = p.energy(i)
+        e2, nr2 = q.energy(i)
+        c1 = float(np.sum(np.abs(t.terms["coef"])))
+        tol = 1e-12 * max(1.0, abs(ref["energy"])) if fp64 else 2e-5 * c1
+        assert abs(e - ref["energy"]) <= tol, (i, e, ref["energy"])
+        # the two launches differ only in the order of the block sums
+        assert abs(e - e2) <= (1e-13 if fp64 else 1e-6) * c1, (i, e, e2)
+        assert abs(nr - nr2) <= (1e-13 if fp64 else 1e-6)
+
+
 def test_config3_noisy_small(eng):
     tasks = W.config3_noisy22(n=14, n_gates=200, n_traj=96, p=0.01, shots=50)
     p, wl = run_plan(eng, tasks)
