@@ -86,7 +86,10 @@ struct SvTableBuilder {
         sd.n_ops = (uint16_t)hs.ops.size();
         sd.op_begin = (uint32_t)(fp64 ? ops64.size() : ops32.size());
         for (const HostOp &o : hs.ops) {
-          const uint32_t code = (uint32_t)o.kind | ((uint32_t)o.a << 8) | ((uint32_t)o.b << 16);
+          const uint32_t lo = std::min(o.a, o.b), hi = std::max(o.a, o.b);
+          const uint32_t code = o.kind == K_CD ? sv_op_index(o.kind, lo, hi) : sv_op_index(o.kind, o.a, 0);
+          if (code >= SV_N_OP_INDEX || o.a >= SV_G || (o.kind == K_CD && (hi >= SV_G || lo == hi)))
+            fail(QW_ERR_STATE, "internal: op outside the stage dispatch table");
           if (fp64) {
             SvOpDesc<double> od{};
             od.code = code;

@@ -72,6 +72,20 @@ enum SvKind : uint8_t {
   K_RX = 8,    // [[c, -is], [-is, c]] on a: m = {c, s}
 };
 constexpr int SV_G = 5;            // positions per stage (32 register amplitudes)
+
+// Dense index of an op for the kernels' jump table: each one-position kind
+// takes SV_G consecutive slots (its stage position), the controlled phase
+// the ten position pairs a < b.
+constexpr uint32_t SV_N_OP_INDEX = 35;
+__host__ __device__ constexpr uint32_t sv_op_index(uint32_t kind, uint32_t a, uint32_t b) {
+  return kind == K_U1   ? a
+         : kind == K_D1 ? 5 + a
+         : kind == K_P1 ? 10 + a
+         : kind == K_R  ? 15 + a
+         : kind == K_RX ? 20 + a
+         : kind == K_CD ? 25 + a * (9 - a) / 2 + (b - a - 1)
+                        : SV_N_OP_INDEX;
+}
 constexpr int SV_MAX_TILE_FP32 = 14;
 constexpr int SV_MAX_TILE_FP64 = 13;
 
@@ -124,7 +138,7 @@ struct SvStageDesc {
 template <typename T>
 struct alignas(16) SvOpDesc {
   T m[8];         // read as 16-byte vectors
-  uint32_t code;  // kind | a << 8 | b << 16
+  uint32_t code;  // sv_op_index(kind, a, b)
 };
 static_assert(sizeof(SvOpDesc<float>) == 48 && sizeof(SvOpDesc<double>) == 80, "op descriptor layout");
 

@@ -105,6 +105,33 @@ __device__ __forceinline__ void op_r(C (&a)[32], const T (&m)[8]) {
     a[j].y = m[4] * x.y + m[6] * y.y;
   }
 }
+// FP32 real matrix: both components of an amplitude in one packed op
+template <int P>
+__device__ __forceinline__ void op_r_f2(float2 (&a)[32], const float (&m)[8]) {
+  const float2 m0 = make_float2(m[0], m[0]), m2 = make_float2(m[2], m[2]);
+  const float2 m4 = make_float2(m[4], m[4]), m6 = make_float2(m[6], m[6]);
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    if (i & (1 << P)) continue;
+    const int j = i | (1 << P);
+    const float2 x = a[i], y = a[j];
+    a[i] = __ffma2_rn(m2, y, __fmul2_rn(m0, x));
+    a[j] = __ffma2_rn(m6, y, __fmul2_rn(m4, x));
+  }
+}
+template <typename C, typename T, int P>
+__device__ __forceinline__ void op_r_any(C (&a)[32], const T (&m)[8]) { op_r<C, T, P>(a, m); }
+template <>
+__device__ __forceinline__ void op_r_any<float2, float, 0>(float2 (&a)[32], const float (&m)[8]) { op_r_f2<0>(a, m); }
+template <>
+__device__ __forceinline__ void op_r_any<float2, float, 1>(float2 (&a)[32], const float (&m)[8]) { op_r_f2<1>(a, m); }
+template <>
+__device__ __forceinline__ void op_r_any<float2, float, 2>(float2 (&a)[32], const float (&m)[8]) { op_r_f2<2>(a, m); }
+template <>
+__device__ __forceinline__ void op_r_any<float2, float, 3>(float2 (&a)[32], const float (&m)[8]) { op_r_f2<3>(a, m); }
+template <>
+__device__ __forceinline__ void op_r_any<float2, float, 4>(float2 (&a)[32], const float (&m)[8]) { op_r_f2<4>(a, m); }
+
 // [[c, -is], [-is, c]] with c = m0, s = m1
 template <typename C, typename T, int P>
 __device__ __forceinline__ void op_rx(C (&a)[32], const T (&m)[8]) {
@@ -135,27 +162,26 @@ __device__ __forceinline__ void load_m(const SvOpDesc<double> *op, double (&m)[8
   }
 }
 
-#define QW_CODE(kind, a, b) ((uint32_t)(kind) | ((uint32_t)(a) << 8) | ((uint32_t)(b) << 16))
-
+// dispatch on the dense op index (a jump table)
 template <typename C, typename T>
 __device__ __forceinline__ void apply_op(uint32_t code, const T (&m)[8], C (&a)[32]) {
   switch (code) {
-#define U1(P) case QW_CODE(K_U1, P, 0): op_u1<C, T, P>(a, m); break;
-#define D1(P) case QW_CODE(K_D1, P, 0): op_d1<C, T, P>(a, m); break;
+#define U1(P) case sv_op_index(K_U1, P, 0): op_u1<C, T, P>(a, m); break;
+#define D1(P) case sv_op_index(K_D1, P, 0): op_d1<C, T, P>(a, m); break;
+#define P1(P) case sv_op_index(K_P1, P, 0): op_p1<C, T, P>(a, m); break;
+#define RR(P) case sv_op_index(K_R, P, 0): op_r_any<C, T, P>(a, m); break;
+#define RX(P) case sv_op_index(K_RX, P, 0): op_rx<C, T, P>(a, m); break;
     U1(0) U1(1) U1(2) U1(3) U1(4)
     D1(0) D1(1) D1(2) D1(3) D1(4)
-#undef U1
-#undef D1
-#define P1(P) case QW_CODE(K_P1, P, 0): op_p1<C, T, P>(a, m); break;
-#define RR(P) case QW_CODE(K_R, P, 0): op_r<C, T, P>(a, m); break;
-#define RX(P) case QW_CODE(K_RX, P, 0): op_rx<C, T, P>(a, m); break;
     P1(0) P1(1) P1(2) P1(3) P1(4)
     RR(0) RR(1) RR(2) RR(3) RR(4)
     RX(0) RX(1) RX(2) RX(3) RX(4)
+#undef U1
+#undef D1
 #undef P1
 #undef RR
 #undef RX
-#define CD(x, y) case QW_CODE(K_CD, x, y): op_cd<C, T, x, y>(a, m); break;
+#define CD(x, y) case sv_op_index(K_CD, x, y): op_cd<C, T, x, y>(a, m); break;
     CD(0, 1) CD(0, 2) CD(0, 3) CD(0, 4) CD(1, 2) CD(1, 3) CD(1, 4) CD(2, 3) CD(2, 4) CD(3, 4)
 #undef CD
     default: break;
@@ -240,12 +266,22 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
                              ((i & 16) ? sp[4] : 0u);
         a[i] = sm[idx];
       }
-      for (uint32_t o = 0; o < st.n_ops; o++) {
-        const SvOpDesc<T> *op = ops + st.op_begin + o;
-        const uint32_t code = __ldg(&op->code);
+      {
+        // the next op's parameters are loaded while the current op runs
+        const SvOpDesc<T> *op = ops + st.op_begin;
+        const uint32_t nops = st.n_ops;
+        uint32_t code = 0;
         T m[8];
-        load_m(op, m);
-        apply_op<C, T>(code, m, a);
+        if (nops) { code = __ldg(&op->code); load_m(op, m); }
+        for (uint32_t o = 0; o < nops; o++) {
+          uint32_t ncode = 0;
+          T nm[8];
+          if (o + 1 < nops) { ncode = __ldg(&op[o + 1].code); load_m(op + o + 1, nm); }
+          apply_op<C, T>(code, m, a);
+          code = ncode;
+#pragma unroll
+          for (int t = 0; t < 8; t++) m[t] = nm[t];
+        }
       }
       // constant part of the affine map (X gates of the stage)
       const uint32_t xm = st.xmask;
