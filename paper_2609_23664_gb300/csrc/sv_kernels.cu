@@ -201,11 +201,7 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
   const uint32_t ntile = 1u << k, lomask = (1u << b) - 1u;
   const uint32_t nt = blockDim.x;
 
-  // 16-byte units: two FP32 amplitudes or one FP64 amplitude.  The deposit
-  // of a tile index into the state index and the swizzle are both linear
-  // over GF(2); a thread's units are l0 | li with l0 = APU * tid below the
-  // step APU * nt (a power of two) and li a multiple of it, so the thread
-  // part is looked up once and only the warp-uniform part per unit.
+  // 16-byte units: two FP32 amplitudes or one FP64 amplitude
   constexpr uint32_t APU = (sizeof(T) == 4) ? 2u : 1u;
   const uint32_t n_units = ntile / APU;
   if (src) {
@@ -250,6 +246,12 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
       ss[c] = ((cm & 1u) ? sp[0] : 0u) ^ ((cm & 2u) ? sp[1] : 0u) ^ ((cm & 4u) ? sp[2] : 0u) ^
               ((cm & 8u) ? sp[3] : 0u) ^ ((cm & 16u) ? sp[4] : 0u);
     }
+    uint32_t spB[SV_G], ssB[SV_G];
+#pragma unroll
+    for (int j = 0; j < SV_G; j++) {
+      spB[j] = sp[j] * (uint32_t)sizeof(C);
+      ssB[j] = ss[j] * (uint32_t)sizeof(C);
+    }
     for (uint32_t grp = threadIdx.x; grp < n_groups; grp += nt) {
       uint32_t bse = grp;
 #pragma unroll
@@ -258,13 +260,17 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
         bse = ((bse >> p) << (p + 1)) | (bse & ((1u << p) - 1u));
       }
       const uint32_t sb = swz<T>(bse);
+      // byte offsets into the tile: one XOR per access, the base added by
+      // the load's addressing
+      const char *smc = (const char *)sm;
+      const uint32_t sbB = sb * (uint32_t)sizeof(C);
       C a[32];
 #pragma unroll
       for (int i = 0; i < 32; i++) {
-        const uint32_t idx = sb ^ ((i & 1) ? sp[0] : 0u) ^ ((i & 2) ? sp[1] : 0u) ^
-                             ((i & 4) ? sp[2] : 0u) ^ ((i & 8) ? sp[3] : 0u) ^
-                             ((i & 16) ? sp[4] : 0u);
-        a[i] = sm[idx];
+        const uint32_t off = sbB ^ ((i & 1) ? spB[0] : 0u) ^ ((i & 2) ? spB[1] : 0u) ^
+                             ((i & 4) ? spB[2] : 0u) ^ ((i & 8) ? spB[3] : 0u) ^
+                             ((i & 16) ? spB[4] : 0u);
+        a[i] = *(const C *)(smc + off);
       }
       {
         // the next op's parameters are loaded while the current op runs
@@ -285,14 +291,15 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
       }
       // constant part of the affine map (X gates of the stage)
       const uint32_t xm = st.xmask;
-      const uint32_t sbs = sb ^ ((xm & 1u) ? sp[0] : 0u) ^ ((xm & 2u) ? sp[1] : 0u) ^
-                           ((xm & 4u) ? sp[2] : 0u) ^ ((xm & 8u) ? sp[3] : 0u) ^ ((xm & 16u) ? sp[4] : 0u);
+      const uint32_t sbs = sbB ^ ((xm & 1u) ? spB[0] : 0u) ^ ((xm & 2u) ? spB[1] : 0u) ^
+                           ((xm & 4u) ? spB[2] : 0u) ^ ((xm & 8u) ? spB[3] : 0u) ^ ((xm & 16u) ? spB[4] : 0u);
+      char *smw = (char *)sm;
 #pragma unroll
       for (int i = 0; i < 32; i++) {
-        const uint32_t idx = sbs ^ ((i & 1) ? ss[0] : 0u) ^ ((i & 2) ? ss[1] : 0u) ^
-                             ((i & 4) ? ss[2] : 0u) ^ ((i & 8) ? ss[3] : 0u) ^
-                             ((i & 16) ? ss[4] : 0u);
-        sm[idx] = a[i];
+        const uint32_t off = sbs ^ ((i & 1) ? ssB[0] : 0u) ^ ((i & 2) ? ssB[1] : 0u) ^
+                             ((i & 4) ? ssB[2] : 0u) ^ ((i & 8) ? ssB[3] : 0u) ^
+                             ((i & 16) ? ssB[4] : 0u);
+        *(C *)(smw + off) = a[i];
       }
     }
     __syncthreads();
