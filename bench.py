@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--cpu-sample-tasks", type=int, default=1)
     ap.add_argument("--fuse-energy", type=int, default=0,
                     help="1: energy blocks as work items of the persistent suffix launch")
+    ap.add_argument("--tile-qubits", type=int, default=0, help="0: autotuned")
+    ap.add_argument("--low-qubits", type=int, default=0, help="0: autotuned")
     ap.add_argument("--window", type=int, default=0,
                     help="tasks advanced together in the persistent launch (0: all of a wave)")
     return ap.parse_args()
@@ -251,7 +253,7 @@ def run_native(a):
 
     wl = Q.Workload(tasks)
     t0 = time.perf_counter()
-    plan = Q.Plan(eng, wl, window=a.window, fuse_energy=a.fuse_energy)
+    plan = Q.Plan(eng, wl, **plan_opts(a))
     planning_ms = (time.perf_counter() - t0) * 1e3
     ex = plan.explain()
     for _ in range(max(1, a.warmup)):
@@ -317,6 +319,7 @@ def run_native(a):
                        "parallelism": "replicas (one independent workload per GPU)"},
             "gpu_launches": launches * a.steps,
             "planning_ms": planning_ms, "artifacts": ex["artifacts"],
+            "tiles": cr.get("wave_tiles"),
             "estimated_speedup": ex["estimated_speedup"],
             "engine_hbm_gbs": info["hbm_gbs"]}
     if ck:
@@ -327,7 +330,7 @@ def run_native(a):
         plan.close()
         for key, opts in (("per_task_replay", dict(reuse=0, batched=0)),
                           ("batched_replay", dict(reuse=0, batched=1))):
-            rp = Q.Plan(eng, wl, window=a.window, fuse_energy=a.fuse_energy, **opts)
+            rp = Q.Plan(eng, wl, **plan_opts(a), **opts)
             rp.execute(sptr)
             rp.wait()
             barrier(world)
@@ -354,7 +357,7 @@ def run_native(a):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             wl2 = Q.Workload(tasks)
-            p2 = Q.Plan(eng, wl2, window=a.window, fuse_energy=a.fuse_energy)
+            p2 = Q.Plan(eng, wl2, **plan_opts(a))
             p2.execute(sptr)
             p2.wait()
             en = [p2.energy(i) for i in range(n_tasks)]
@@ -387,6 +390,11 @@ def run_native(a):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def plan_opts(a):
+    return dict(window=a.window, fuse_energy=a.fuse_energy, tile_qubits=a.tile_qubits,
+                low_qubits=a.low_qubits)
 
 
 def main():

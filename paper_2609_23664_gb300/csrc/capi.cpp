@@ -335,6 +335,9 @@ qw_status qw_cost_record_json(const qw_plan *p, char *buf, size_t cap, size_t *n
         return b;
       }());
   for (size_t i = 0; i < p->batch_ms.size(); i++) s += strf(i ? ",%.6f" : "%.6f", p->batch_ms[i]);
+  s += "],\"wave_tiles\":[";
+  for (size_t i = 0; i < p->wave_tiles.size(); i++)
+    s += strf(i ? ",[%u,%u]" : "[%u,%u]", p->wave_tiles[i].first, p->wave_tiles[i].second);
   s += "]}";
   return put_json(s, buf, cap, needed);
 }

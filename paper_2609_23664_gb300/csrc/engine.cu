@@ -390,6 +390,12 @@ static void prepare(qw_plan *P) {
         for (const HostPass &hp : P->tasks[t].sv.passes) kmax = std::max<uint32_t>(kmax, (uint32_t)hp.q.size());
       }
       W.k_max = kmax;
+      {
+        uint32_t b_first = 0;
+        for (uint32_t t : W.tasks)
+          if (!P->tasks[t].sv.passes.empty()) { b_first = P->tasks[t].sv.passes[0].b; break; }
+        P->wave_tiles.push_back({kmax, b_first});
+      }
       W.obs_tasks = W.tasks;
       if (w == 0) W.obs_tasks.insert(W.obs_tasks.end(), shared_src.begin(), shared_src.end());
       // jobs, round-robin over pass index within windows of tasks

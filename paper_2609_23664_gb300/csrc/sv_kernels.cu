@@ -344,8 +344,11 @@ constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per dependency wait
 // Items are taken in list order and every dependency lies wholly before its
 // dependent, so the oldest unfinished item never waits and the launch always
 // drains.
-template <typename T>
-__global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 3 : 1))
+// MINB: CTAs per SM the registers are budgeted for.  Tiles of 2^13 FP32
+// amplitudes (64 KB) fit three CTAs per SM; smaller tiles fit four, which
+// the 128-register build (MINB 4) can use.
+template <typename T, int MINB>
+__global__ void __launch_bounds__(128, MINB)
 sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, const SvSeg *__restrict__ segs,
                 uint32_t seg_bits, uint32_t total, unsigned int *ctr, EnTables en) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -421,8 +424,9 @@ void sv_init_attrs() {
   const int bytes = 200 * 1024;
   cudaFuncSetAttribute((const void *)sv_pass_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   cudaFuncSetAttribute((const void *)sv_pass_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute((const void *)sv_batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute((const void *)sv_batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute((const void *)sv_batch_kernel<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute((const void *)sv_batch_kernel<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute((const void *)sv_batch_kernel<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 void launch_sv_pass(bool fp64, const SvTables &t, uint32_t pass_idx, uint32_t k, uint32_t n,
@@ -445,9 +449,11 @@ int sv_batch_grid(bool fp64, uint32_t k, int sm_count) {
   const size_t smem = sv_smem_bytes(fp64, k);
   int per_sm = 0;
   if (fp64) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<double>, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<double, 1>, threads, smem);
+  } else if (k <= 12) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float, 4>, threads, smem);
   } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float>, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float, 3>, threads, smem);
   }
   if (per_sm < 1) per_sm = 1;
   return per_sm * sm_count;
@@ -460,9 +466,11 @@ void launch_sv_batch(bool fp64, const SvTables &t, const SvJob *jobs, const SvSe
   const size_t smem = sv_smem_bytes(fp64, k_max);
   cudaStream_t s = (cudaStream_t)stream;
   if (fp64)
-    sv_batch_kernel<double><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items, counters, en);
+    sv_batch_kernel<double, 1><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items, counters, en);
+  else if (k_max <= 12)
+    sv_batch_kernel<float, 4><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items, counters, en);
   else
-    sv_batch_kernel<float><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items, counters, en);
+    sv_batch_kernel<float, 3><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items, counters, en);
 }
 
 }  // namespace qw
