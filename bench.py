@@ -149,7 +149,7 @@ def profiled_traffic(kernel: str, workload_key: str):
     import hashlib
     src = os.path.join(ROOT, "paper_2609_23664_gb300", "csrc")
     h = hashlib.sha256()
-    for fn in ("sv_kernels.cu", "obs_kernels.cu", "qw_internal.h"):
+    for fn in ("sv_kernels.cu", "obs_kernels.cu", "energy_block.cuh", "qw_internal.h"):
         with open(os.path.join(src, fn), "rb") as f:
             h.update(f.read())
     digest = h.hexdigest()[:16]
@@ -306,6 +306,12 @@ def run_native(a):
                 "frac": achieved / peak, "peak_source": peak_src,
                 "traffic": profiled_traffic(kern, wkey),
                 "algorithmic_bytes_per_launch": alg, "launch_ms": dur,
+                "algorithmic_bytes": {"sv_batch_kernel": batch_alg_bytes, "energy_kernel": energy_alg_bytes},
+                # the energy kernel's partner reads are served by L2: its
+                # L2->SM bytes and rate (no measured L2 peak to divide by)
+                "energy_l2": {"bytes": float(cr.get("energy_l2_bytes", 0.0)),
+                              "achieved_gbs": float(cr.get("energy_l2_bytes", 0.0)) / (energy_ms * 1e-3) / 1e9
+                              if energy_ms > 0 else None},
                 "other_kernels_ms": {"sv_batch_kernel": suffix_ms, "energy": energy_ms,
                                      "prefix_passes": prefix_ms}}
 

@@ -485,8 +485,17 @@ static void prepare(qw_plan *P) {
       // algorithmic bytes: every pass reads and writes its state once; the
       // energy of a task reads every amplitude once per term class
       for (const SvJob &j : W.jobs) P->batch_alg_bytes += 2.0 * (double)S;
-      for (const EnJob &j : W.en)
-        P->energy_alg_bytes += (double)j.n_classes * (double)sv_state_bytes(fp64, j.n);
+      for (size_t e = 0; e < W.en.size(); e++) {
+        const EnJob &j = W.en[e];
+        const double Sj = (double)sv_state_bytes(fp64, j.n);
+        P->energy_alg_bytes += (double)j.n_classes * Sj;
+        // L2 -> SM reads: own amplitudes once per class, and half the state
+        // per flipping term (each pair is read from one side)
+        const HamLayout &H = P->hams[P->tasks[W.obs_tasks_en[e]].ham];
+        size_t flipping = 0;
+        for (const EnTerm &t : H.terms) flipping += (t.xm != 0);
+        P->energy_l2_bytes += (double)j.n_classes * Sj + 0.5 * Sj * (double)flipping;
+      }
       // persistent work list: pass jobs, then (fused) the energy jobs,
       // released in the order their states finish
       std::vector<SvJob> up = W.jobs;
