@@ -133,10 +133,7 @@ void sha256(const void *data, size_t len, uint8_t out[32]) {
 
 // Eq. 1: SHA256(layout || g_1 || ... || g_l) with layout = {u32 n, u32 mode}
 // and g_i the 24-byte little-endian gate records.
-void fingerprint(uint32_t n, uint32_t mode, const TaskData &t, uint64_t b, uint64_t e, uint8_t out[32]) {
-  Sha256 s;
-  const uint32_t layout[2] = {n, mode};
-  s.update(layout, sizeof(layout));
+static void hash_gates(Sha256 &s, const TaskData &t, uint64_t b, uint64_t e) {
   uint64_t i = b;
   while (i < e) {
     const size_t k = std::upper_bound(t.span_end.begin(), t.span_end.end(), i) - t.span_end.begin();
@@ -145,6 +142,17 @@ void fingerprint(uint32_t n, uint32_t mode, const TaskData &t, uint64_t b, uint6
     s.update(t.spans[k].g + (i - start), take * sizeof(qw_gate));
     i += take;
   }
+}
+
+static void hash_layout(Sha256 &s, uint32_t n, uint32_t mode) {
+  const uint32_t layout[2] = {n, mode};
+  s.update(layout, sizeof(layout));
+}
+
+void fingerprint(uint32_t n, uint32_t mode, const TaskData &t, uint64_t b, uint64_t e, uint8_t out[32]) {
+  Sha256 s;
+  hash_layout(s, n, mode);
+  hash_gates(s, t, b, e);
   s.final(out);
 }
 
@@ -390,6 +398,9 @@ struct PlanCtx {
   uint64_t store_budget = 0;
   double bw_gbs = 6000, launch_ns = 4000;
   std::map<uint64_t, double> gpp;  // gates per pass per (n_eff, fp64)
+  // per materialized node: SHA-256 state after its layout and gates [0, end),
+  // so a nested node's fingerprint continues from its parent's
+  std::vector<Sha256> mat_sha;
   PlanCtx(qw_plan *p, Engine *e, const Workload &w) : P(p), E(e), W(w), B(w) {}
 
   TileConfig tiles(uint32_t n_eff, bool fp64) {
@@ -569,7 +580,20 @@ static void decide(PlanCtx &C) {
           M.n = V.n;
           M.n_eff = (pm == QW_MODE_TABLEAU) ? V.n : std::max<uint32_t>(V.n, SV_G);
           M.bytes = (uint64_t)S;
-          fingerprint(V.n, pm, rep, 0, M.end, M.provenance);
+          // Eq. 1 over [0, end): continued from the parent's state (the
+          // tasks below V share the parent's gates [0, parent end))
+          Sha256 sh;
+          if (pmat >= 0 && P->mats[pmat].n == V.n) {
+            sh = C.mat_sha[pmat];
+            hash_gates(sh, rep, P->mats[pmat].end, M.end);
+          } else {
+            hash_layout(sh, V.n, pm);
+            hash_gates(sh, rep, 0, M.end);
+          }
+          {
+            Sha256 fin = sh;
+            fin.final(M.provenance);
+          }
           qw_artifact_desc A{};
           A.kind = (pm == QW_MODE_TABLEAU) ? QW_KIND_TABLEAU : QW_KIND_STATEVECTOR;
           A.exactness = QW_EXACT;
@@ -602,6 +626,7 @@ static void decide(PlanCtx &C) {
             D.reason = D.refusals.empty() ? "REUSE" : "REUSE_WITH_REFUSALS";
             D.mat = (int)P->mats.size();
             P->mats.push_back(M);
+            C.mat_sha.push_back(sh);
             C.store_used += M.bytes;
             mat = D.mat;
           } else {
@@ -615,6 +640,114 @@ static void decide(PlanCtx &C) {
       C.mat_at[it.node] = mat;
       for (auto k = V.kids.rbegin(); k != V.kids.rend(); ++k) st.push_back({*k, mat});
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pauli frames: stabilizer tasks on one boundary whose suffixes agree once
+// their Pauli gates (X, Y, Z) are removed share that reference suffix; each
+// task becomes a set of Pauli events (slot in the reference, qubit, X/Z
+// bits).  Only groups of two or more tasks on a materialized boundary are
+// converted; the per-task tableau launch stays in the plan as the fallback
+// for a reference with random outcomes (decided on the device).
+// ---------------------------------------------------------------------------
+static bool is_pauli_op(uint32_t op) { return op == QW_OP_X || op == QW_OP_Y || op == QW_OP_Z; }
+
+static bool same_ref_gate(const qw_gate &a, const qw_gate &b) {
+  if (a.op != b.op || a.q0 != b.q0) return false;
+  if (is_two_qubit_op(a.op) && a.q1 != b.q1) return false;
+  if (is_barrier_op(a.op) && a.theta != b.theta) return false;  // the random outcome bit
+  return true;
+}
+
+template <typename F>
+static void for_each_gate(const TaskData &T, uint64_t b, uint64_t e, F &&f) {
+  uint64_t i = b;
+  while (i < e) {
+    const size_t s = std::upper_bound(T.span_end.begin(), T.span_end.end(), i) - T.span_end.begin();
+    const uint64_t start = s ? T.span_end[s - 1] : 0;
+    const uint64_t take = std::min(e, T.span_end[s]) - i;
+    const qw_gate *g = T.spans[s].g + (i - start);
+    for (uint64_t j = 0; j < take; j++)
+      if (!f(g[j])) return;
+    i += take;
+  }
+}
+
+static void build_frame_groups(qw_plan *P, const Workload &W) {
+  const uint32_t nt = (uint32_t)P->tasks.size();
+  P->task_frame_group.assign(nt, -1);
+  if (!P->opts.pauli_frames) return;
+  std::map<std::pair<int, uint32_t>, std::vector<uint32_t>> cand;
+  for (uint32_t t = 0; t < nt; t++)
+    if (P->tasks[t].mode == QW_MODE_TABLEAU && P->tasks[t].src >= 0)
+      cand[{P->tasks[t].src, P->tasks[t].n}].push_back(t);
+  for (auto &c : cand) {
+    const std::vector<uint32_t> &tasks = c.second;
+    if (tasks.size() < 2) continue;
+    FrameGroup G;
+    G.src = c.first.first;
+    G.n = c.first.second;
+    // per task: (slot, qubit) -> X bit | Z bit << 1
+    std::vector<std::map<std::pair<uint64_t, uint32_t>, uint8_t>> ev(tasks.size());
+    bool ok = true;
+    for (size_t k = 0; k < tasks.size() && ok; k++) {
+      const TaskData &T = W.tasks[tasks[k]];
+      uint64_t slot = 0;
+      for_each_gate(T, P->tasks[tasks[k]].begin, T.n_gates, [&](const qw_gate &g) {
+        if (is_pauli_op(g.op)) {
+          const uint8_t b = (uint8_t)((g.op != QW_OP_Z ? 1 : 0) | (g.op != QW_OP_X ? 2 : 0));
+          ev[k][{slot, g.q0}] ^= b;
+          return true;
+        }
+        if (k == 0) {
+          G.ref.push_back(g);
+        } else if (slot >= G.ref.size() || !same_ref_gate(G.ref[slot], g)) {
+          ok = false;
+          return false;
+        }
+        slot++;
+        return true;
+      });
+      if (ok && k > 0 && slot != G.ref.size()) ok = false;
+    }
+    if (!ok) continue;
+    std::map<std::pair<uint64_t, uint32_t>, uint32_t> index;
+    for (auto &m : ev)
+      for (auto &kv : m)
+        if (kv.second) index.emplace(kv.first, 0u);
+    std::vector<std::pair<uint64_t, uint32_t>> events;
+    for (auto &kv : index) {
+      kv.second = (uint32_t)events.size();
+      events.push_back(kv.first);
+    }
+    G.tasks = tasks;
+    G.n_events = (uint32_t)events.size();
+    G.n_words = (uint32_t)((tasks.size() + 31) / 32);
+    G.ev_x.assign((size_t)G.n_events * G.n_words, 0u);
+    G.ev_z.assign((size_t)G.n_events * G.n_words, 0u);
+    for (size_t k = 0; k < tasks.size(); k++)
+      for (auto &kv : ev[k]) {
+        if (!kv.second) continue;
+        const size_t e = index[kv.first];
+        const uint32_t bit = 1u << (k & 31);
+        if (kv.second & 1) G.ev_x[e * G.n_words + k / 32] |= bit;
+        if (kv.second & 2) G.ev_z[e * G.n_words + k / 32] |= bit;
+      }
+    G.prog = compile_frames(G.ref.data(), G.ref.size(), G.n, events);
+    TabHostProgram hp = compile_tab(G.ref.data(), G.ref.size(), G.n);
+    const uint32_t bit_base = (uint32_t)P->tab_bits.size();
+    for (const qw_gate &g : G.ref)
+      if (is_barrier_op(g.op)) P->tab_bits.push_back(g.theta != 0.0 ? 1 : 0);
+    G.n_outs = hp.n_outs;
+    P->tab_progs.push_back(std::move(hp));
+    G.ref_segs.push_back({(uint32_t)P->tab_progs.size() - 1, bit_base});
+    bool outs_ok = true;
+    for (uint32_t t : tasks) outs_ok = outs_ok && P->tasks[t].tab_outs == G.n_outs;
+    if (!outs_ok) fail(QW_ERR_STATE, "internal: frame reference and task outcome counts differ");
+    const int gi = (int)P->frame_groups.size();
+    for (uint32_t t : tasks) P->task_frame_group[t] = gi;
+    P->frame_groups.push_back(std::move(G));
   }
 }
 
@@ -763,6 +896,8 @@ void build_plan(qw_plan *P, Engine *E, const Workload &W) {
     }
   }
 
+  build_frame_groups(P, W);
+
   // plan-level estimates (Table IV "Est." column analog: direct / planned)
   double direct = 0, planned = 0;
   for (uint32_t t = 0; t < nt; t++) {
@@ -785,16 +920,24 @@ void build_plan(qw_plan *P, Engine *E, const Workload &W) {
   s += strf("\"tasks\":%u,\"groups\":%zu,\"total_gates\":%llu,", nt, C.B.roots.size(),
             (unsigned long long)P->total_gates);
   s += strf("\"options\":{\"reuse\":%d,\"batched\":%d,\"legality\":%d,\"cost_model\":\"%s\","
-            "\"delta_frac\":%.6g,\"min_group\":%u,\"min_prefix_gates\":%u},",
+            "\"delta_frac\":%.6g,\"min_group\":%u,\"min_prefix_gates\":%u,\"pauli_frames\":%d},",
             P->opts.reuse, P->opts.batched, P->opts.legality,
             P->opts.cost_model == QW_COST_MLP ? "MLP" : "ANALYTIC", P->opts.delta_frac,
-            P->opts.min_group, P->opts.min_prefix_gates);
+            P->opts.min_group, P->opts.min_prefix_gates, P->opts.pauli_frames);
   s += strf("\"fast_path\":%s,\"planning_ns\":%.0f,\"estimated_direct_ns\":%.1f,"
             "\"estimated_plan_ns\":%.1f,\"estimated_speedup\":%.4f,",
             P->fast_path ? "true" : "false", P->planning_ns, direct, planned,
             planned > 0 ? direct / planned : 1.0);
   s += strf("\"tasks_reusing\":%u,\"tasks_refused\":%u,\"artifacts\":%zu,", n_reuse_tasks, n_ref,
             P->mats.size());
+  s += "\"pauli_frames\":[";
+  for (size_t g = 0; g < P->frame_groups.size(); g++) {
+    const FrameGroup &G = P->frame_groups[g];
+    s += strf("%s{\"artifact\":%d,\"tasks\":%zu,\"reference_gates\":%zu,\"events\":%u,"
+              "\"layers\":%zu,\"outcomes_per_task\":%u}",
+              g ? "," : "", G.src, G.tasks.size(), G.ref.size(), G.n_events, G.prog.layers.size(), G.n_outs);
+  }
+  s += "],";
   s += "\"decisions\":[";
   for (size_t i = 0; i < P->decisions.size(); i++) {
     const Decision &D = P->decisions[i];
