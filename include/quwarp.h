@@ -194,11 +194,16 @@ typedef struct qw_plan_opts {
   int32_t fuse_energy;        /* 1 = the energy blocks of every task run as work items of
                                  the persistent suffix launch (same results, one launch);
                                  0 = a separate energy launch after it.  Default 0. */
+  int32_t pauli_frames;       /* 1 = stabilizer tasks on one boundary whose suffixes differ
+                                 only by Pauli gates run the shared reference once on the
+                                 tableau and the tasks as Pauli frames (same outcomes; the
+                                 per-task tableau runs instead when a reference outcome is
+                                 random); 0 = every task on its own tableau.  Default 1. */
 } qw_plan_opts;
 
 /* Fills the defaults: reuse=1, batched=1, legality=1, analytic costs,
  * delta_frac=0.10, min_group=2, min_prefix_gates=1, min_prefix_cost_ns=0,
- * autotuned tiles, use_graph=1, fault_injection=0, fuse_energy=0. */
+ * autotuned tiles, use_graph=1, fault_injection=0, fuse_energy=0, pauli_frames=1. */
 void qw_plan_opts_default(qw_plan_opts *o);
 
 typedef struct qw_plan qw_plan;

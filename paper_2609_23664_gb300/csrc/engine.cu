@@ -187,8 +187,14 @@ struct DeviceState {
   struct TabLaunch {
     TabArgs a;
     uint32_t n_tasks;
+    int frame;  // >= 0: preceded by the reference run and the frame launch of this frame group
   };
   std::vector<TabLaunch> tab_mat_launches, tab_task_launches;
+  struct FrameLaunch {
+    TabArgs ref;  // the reference suffix on the tableau (one CTA), outcomes and random flag
+    FrameArgs fa;
+  };
+  std::vector<FrameLaunch> frame_launches;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaEvent_t ev[8] = {nullptr};
@@ -600,7 +606,7 @@ static void prepare(qw_plan *P) {
       a.slots = D->d_slots;
       a.bits = D->d_bits;
       a.outs = outs;
-      dst.push_back({a, (uint32_t)descs.size()});
+      dst.push_back({a, (uint32_t)descs.size(), -1});
     };
     for (size_t m = 0; m < P->mats.size(); m++) {
       const MatNode &M = P->mats[m];
@@ -637,6 +643,46 @@ static void prepare(qw_plan *P) {
       add_launch(D->tab_task_launches, g.first.second,
                  g.first.first >= 0 ? D->mat_buf[g.first.first] : nullptr, nullptr, descs, segs,
                  D->d_outs);
+      const int fg = P->task_frame_group[g.second[0]];
+      if (fg >= 0) {
+        // Pauli frames: the reference suffix once on the tableau, then the
+        // frame launch; the per-task launch above runs only if a reference
+        // outcome was random (decided on the device, no host round trip)
+        const FrameGroup &G = P->frame_groups[fg];
+        if (G.tasks != g.second) fail(QW_ERR_STATE, "internal: frame group and tableau group differ");
+        uint8_t *ref_out = (uint8_t *)D->arena.alloc(std::max<uint32_t>(1, G.n_outs));
+        uint32_t *rand = (uint32_t *)D->arena.alloc(sizeof(uint32_t));
+        std::vector<TabSegment> rsegs;
+        uint32_t oo = 0;
+        for (auto &sg : G.ref_segs) {
+          rsegs.push_back({sg.first, sg.second, oo, 0});
+          oo += P->tab_progs[sg.first].n_outs;
+        }
+        std::vector<TabTaskDesc> rd{{0, (uint32_t)rsegs.size(), 0, 0}};
+        std::vector<DeviceState::TabLaunch> tmp;
+        add_launch(tmp, G.n, D->mat_buf[G.src], nullptr, rd, rsegs, ref_out);
+        DeviceState::FrameLaunch fl{};
+        fl.ref = tmp[0].a;
+        fl.ref.rand_any = rand;
+        FrameArgs &fa = fl.fa;
+        fa.n = G.n;
+        fa.n_tasks = (uint32_t)G.tasks.size();
+        fa.n_words = G.n_words;
+        fa.n_layers = (uint32_t)G.prog.layers.size();
+        fa.layers = D->arena.upload(G.prog.layers, s);
+        fa.ops = D->arena.upload(G.prog.ops, s);
+        fa.ev_x = D->arena.upload(G.ev_x, s);
+        fa.ev_z = D->arena.upload(G.ev_z, s);
+        fa.ref_out = ref_out;
+        fa.rand_any = rand;
+        std::vector<uint32_t> ob;
+        for (uint32_t t : G.tasks) ob.push_back(P->outs_off[t]);
+        fa.out_base = D->arena.upload(ob, s);
+        fa.outs = D->d_outs;
+        D->tab_task_launches.back().a.run_if = rand;
+        D->tab_task_launches.back().frame = (int)D->frame_launches.size();
+        D->frame_launches.push_back(fl);
+      }
     }
   }
   for (auto &e : D->ev) CK(cudaEventCreate(&e));
@@ -649,10 +695,14 @@ static void prepare(qw_plan *P) {
 // ---------------------------------------------------------------------------
 // launch sequence of a prepared plan (captured once into a graph)
 // ---------------------------------------------------------------------------
-static void enqueue(qw_plan *P, cudaStream_t s) {
+static void enqueue(qw_plan *P, cudaStream_t s, bool capturing) {
   DeviceState *D = P->dev;
   uint64_t nl = 0;  // kernels launched by one execution
-  CK(cudaEventRecordWithFlags(D->ev[0], s, cudaEventRecordExternal));
+  // timing events: inside a capture they become external event-record nodes
+  auto rec = [&](cudaEvent_t e) {
+    return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+  };
+  CK(rec(D->ev[0]));
   // 1) shared prefixes (boundary states), in creation order (parents first)
   for (size_t m = 0; m < P->mats.size(); m++) {
     const MatNode &M = P->mats[m];
@@ -673,12 +723,12 @@ static void enqueue(qw_plan *P, cudaStream_t s) {
   }
   for (auto &L : D->tab_mat_launches) launch_tab(L.a, L.n_tasks, s);
   nl += D->tab_mat_launches.size();
-  CK(cudaEventRecordWithFlags(D->ev[1], s, cudaEventRecordExternal));
+  CK(rec(D->ev[1]));
   // 2) task suffixes, observables
   size_t wi = 0;
   for (auto &W : D->waves) {
     const SvTables &T = W.fp64 ? D->t64 : D->t32;
-    CK(cudaEventRecordWithFlags(D->wave_ev[4 * wi], s, cudaEventRecordExternal));
+    CK(rec(D->wave_ev[4 * wi]));
     nl += W.converts.size();
     for (auto &c : W.converts) {
       const TaskPlan &tp = P->tasks[c.first];
@@ -701,7 +751,7 @@ static void enqueue(qw_plan *P, cudaStream_t s) {
         launch_sv_pass(W.fp64, T, j.pass, k, j.n, j.src, j.dst, s);
       }
     }
-    CK(cudaEventRecordWithFlags(D->wave_ev[4 * wi + 1], s, cudaEventRecordExternal));
+    CK(rec(D->wave_ev[4 * wi + 1]));
     if (W.fused_energy) {
       launch_energy_reduce(W.d_en, (uint32_t)W.en.size(), D->d_partials, s);
       nl += 1;
@@ -711,17 +761,25 @@ static void enqueue(qw_plan *P, cudaStream_t s) {
       if (!W.en.empty()) nl += 2;
     }
     if (!W.src.empty()) nl += W.shots.empty() ? 2 : 3;
-    CK(cudaEventRecordWithFlags(D->wave_ev[4 * wi + 2], s, cudaEventRecordExternal));
+    CK(rec(D->wave_ev[4 * wi + 2]));
     launch_sampling(W.fp64, W.d_src, (uint32_t)W.src.size(), W.smp_blocks, D->d_bsum, D->d_blast, D->d_boff,
                     D->d_lastnz, W.d_shots, (uint32_t)W.shots.size(), s);
-    CK(cudaEventRecordWithFlags(D->wave_ev[4 * wi + 3], s, cudaEventRecordExternal));
+    CK(rec(D->wave_ev[4 * wi + 3]));
     wi++;
   }
-  CK(cudaEventRecordWithFlags(D->ev[2], s, cudaEventRecordExternal));
+  CK(rec(D->ev[2]));
   // 3) tableau tasks
-  for (auto &L : D->tab_task_launches) launch_tab(L.a, L.n_tasks, s);
+  for (auto &L : D->tab_task_launches) {
+    if (L.frame >= 0) {
+      const DeviceState::FrameLaunch &F = D->frame_launches[L.frame];
+      launch_tab(F.ref, 1, s);
+      launch_frames(F.fa, s);
+      nl += 2;
+    }
+    launch_tab(L.a, L.n_tasks, s);
+  }
   nl += D->tab_task_launches.size();
-  CK(cudaEventRecordWithFlags(D->ev[3], s, cudaEventRecordExternal));
+  CK(rec(D->ev[3]));
   P->n_launches = nl;
   CK(cudaGetLastError());
 }
@@ -748,7 +806,7 @@ void plan_execute(qw_plan *P, void *stream) {
       cudaStream_t cs = D->stream;
       CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
       try {
-        enqueue(P, cs);
+        enqueue(P, cs, true);
       } catch (...) {
         cudaGraph_t g = nullptr;
         if (cudaStreamEndCapture(cs, &g) == cudaSuccess && g) cudaGraphDestroy(g);
@@ -760,7 +818,7 @@ void plan_execute(qw_plan *P, void *stream) {
     }
     CK(cudaGraphLaunch(D->gexec, s));
   } else {
-    enqueue(P, s);
+    enqueue(P, s, false);
   }
   P->executed = true;
 }
@@ -879,8 +937,9 @@ void engine_init(Engine *E, const qw_engine_opts *o) {
     cudaFree(b);
   }
   // kernel attributes are set before any capture
-  sv_init_attrs();
-  tab_init_attrs();
+  CK(sv_init_attrs());
+  CK(tab_init_attrs());
+  CK(frame_init_attrs());
   CK(cudaGetLastError());
 }
 

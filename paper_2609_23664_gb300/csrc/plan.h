@@ -101,6 +101,20 @@ struct TaskPlan {
   uint32_t total_outs = 0;  // all MEASURE outcomes of the task
 };
 
+// Stabilizer tasks on one boundary whose suffixes agree once Pauli gates
+// are removed: the reference runs once, the tasks as Pauli frames.
+struct FrameGroup {
+  int src = -1;
+  uint32_t n = 0;
+  std::vector<uint32_t> tasks;                          // task ids, in group order
+  std::vector<qw_gate> ref;                             // reference suffix (Pauli gates removed)
+  std::vector<std::pair<uint32_t, uint32_t>> ref_segs;  // compiled tableau program (prog, bit base)
+  uint32_t n_outs = 0;
+  qw::FrameHostProgram prog;
+  uint32_t n_events = 0, n_words = 0;
+  std::vector<uint32_t> ev_x, ev_z;                     // [event * n_words + word]
+};
+
 struct HamLayout {
   uint32_t n_eff = 0, chunk_bits = 0, n_blocks = 0;
   std::vector<EnClass> classes;
@@ -156,6 +170,8 @@ struct qw_plan {
   std::vector<qw::HamLayout> hams;
   std::vector<qw::TabHostProgram> tab_progs;
   std::vector<uint8_t> tab_bits;  // random bits of every compiled tableau program instance
+  std::vector<qw::FrameGroup> frame_groups;
+  std::vector<int> task_frame_group;  // per task: frame group, -1 none
   std::string explain, cost;
   double planning_ns = 0;
   double est_direct_ns = 0, est_plan_ns = 0;

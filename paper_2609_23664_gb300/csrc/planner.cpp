@@ -473,6 +473,55 @@ static const char *cut_kind_name(int k) {
   return k == 0 ? "LARGEST_COMMON_PREFIX" : (k == 1 ? "CLIFFORD_SAFE_PREFIX" : "COARSE_BARRIER");
 }
 
+static bool is_pauli_op(uint32_t op) { return op == QW_OP_X || op == QW_OP_Y || op == QW_OP_Z; }
+
+static bool same_ref_gate(const qw_gate &a, const qw_gate &b) {
+  if (a.op != b.op || a.q0 != b.q0) return false;
+  if (is_two_qubit_op(a.op) && a.q1 != b.q1) return false;
+  if (is_barrier_op(a.op) && a.theta != b.theta) return false;  // the random outcome bit
+  return true;
+}
+
+template <typename F>
+static void for_each_gate(const TaskData &T, uint64_t b, uint64_t e, F &&f) {
+  uint64_t i = b;
+  while (i < e) {
+    const size_t s = std::upper_bound(T.span_end.begin(), T.span_end.end(), i) - T.span_end.begin();
+    const uint64_t start = s ? T.span_end[s - 1] : 0;
+    const uint64_t take = std::min(e, T.span_end[s]) - i;
+    const qw_gate *g = T.spans[s].g + (i - start);
+    for (uint64_t j = 0; j < take; j++)
+      if (!f(g[j])) return;
+    i += take;
+  }
+}
+
+// True when every (non-refused) task continues from gate `from` with the
+// same gate list once Pauli gates are removed (the Pauli-frame condition).
+static bool pauli_equivalent(const Workload &W, const std::vector<uint32_t> &tasks,
+                             const std::vector<uint8_t> &refused, uint64_t from) {
+  std::vector<const qw_gate *> ref;
+  bool first = true, ok = true;
+  for (uint32_t t : tasks) {
+    if (refused[t] || W.tasks[t].mode != QW_MODE_TABLEAU) continue;
+    size_t slot = 0;
+    for_each_gate(W.tasks[t], from, W.tasks[t].n_gates, [&](const qw_gate &g) {
+      if (is_pauli_op(g.op)) return true;
+      if (first) {
+        ref.push_back(&g);
+      } else if (slot >= ref.size() || !same_ref_gate(*ref[slot], g)) {
+        ok = false;
+        return false;
+      }
+      slot++;
+      return true;
+    });
+    if (!ok || (!first && slot != ref.size())) return false;
+    first = false;
+  }
+  return !first;
+}
+
 static void decide(PlanCtx &C) {
   qw_plan *P = C.P;
   const Workload &W = C.W;
@@ -481,17 +530,20 @@ static void decide(PlanCtx &C) {
   C.refused.assign(W.tasks.size(), 0);
   C.bypass.assign(W.tasks.size(), 0);
   const bool reuse = P->opts.reuse != 0;
-  // preorder traversal with the nearest materialized ancestor
-  struct Item { int node; int mat; };
+  // preorder traversal with the nearest materialized ancestor.  A subtree
+  // whose tasks all continue from one tableau boundary as Pauli frames is
+  // frozen: deeper boundaries would only split the frame group.
+  struct Item { int node; int mat; bool frozen; };
   for (auto &r : C.B.roots) {
-    std::vector<Item> st{{r.second, -1}};
+    std::vector<Item> st{{r.second, -1, false}};
     while (!st.empty()) {
       Item it = st.back();
       st.pop_back();
       const TNode &V = nodes[it.node];
       int mat = it.mat;
+      bool frozen = it.frozen;
       const uint32_t consumers = (uint32_t)(V.kids.size() + V.ending.size());
-      if (reuse && V.parent >= 0 && consumers >= 2 && V.below >= 2) {
+      if (!frozen && reuse && V.parent >= 0 && consumers >= 2 && V.below >= 2) {
         Decision D;
         D.node = it.node;
         D.n = V.n;
@@ -629,6 +681,8 @@ static void decide(PlanCtx &C) {
             C.mat_sha.push_back(sh);
             C.store_used += M.bytes;
             mat = D.mat;
+            if (pm == QW_MODE_TABLEAU && P->opts.pauli_frames)
+              frozen = pauli_equivalent(W, below_tasks, C.refused, M.end);
           } else {
             D.decision = D.refusals.empty() ? 1 : 2;
             D.reason = D.refusals.empty() ? "NOT_PROFITABLE" : "REFUSED_HANDOFF";
@@ -638,7 +692,7 @@ static void decide(PlanCtx &C) {
         P->decisions.push_back(D);
       }
       C.mat_at[it.node] = mat;
-      for (auto k = V.kids.rbegin(); k != V.kids.rend(); ++k) st.push_back({*k, mat});
+      for (auto k = V.kids.rbegin(); k != V.kids.rend(); ++k) st.push_back({*k, mat, frozen});
     }
   }
 }
@@ -651,29 +705,6 @@ static void decide(PlanCtx &C) {
 // converted; the per-task tableau launch stays in the plan as the fallback
 // for a reference with random outcomes (decided on the device).
 // ---------------------------------------------------------------------------
-static bool is_pauli_op(uint32_t op) { return op == QW_OP_X || op == QW_OP_Y || op == QW_OP_Z; }
-
-static bool same_ref_gate(const qw_gate &a, const qw_gate &b) {
-  if (a.op != b.op || a.q0 != b.q0) return false;
-  if (is_two_qubit_op(a.op) && a.q1 != b.q1) return false;
-  if (is_barrier_op(a.op) && a.theta != b.theta) return false;  // the random outcome bit
-  return true;
-}
-
-template <typename F>
-static void for_each_gate(const TaskData &T, uint64_t b, uint64_t e, F &&f) {
-  uint64_t i = b;
-  while (i < e) {
-    const size_t s = std::upper_bound(T.span_end.begin(), T.span_end.end(), i) - T.span_end.begin();
-    const uint64_t start = s ? T.span_end[s - 1] : 0;
-    const uint64_t take = std::min(e, T.span_end[s]) - i;
-    const qw_gate *g = T.spans[s].g + (i - start);
-    for (uint64_t j = 0; j < take; j++)
-      if (!f(g[j])) return;
-    i += take;
-  }
-}
-
 static void build_frame_groups(qw_plan *P, const Workload &W) {
   const uint32_t nt = (uint32_t)P->tasks.size();
   P->task_frame_group.assign(nt, -1);

@@ -263,8 +263,9 @@ struct EnTables {
   double *partials;
 };
 
-void sv_init_attrs();
-void tab_init_attrs();
+// kernel attributes (dynamic shared memory limits); the first failure is returned
+cudaError_t sv_init_attrs();
+cudaError_t tab_init_attrs();
 int sv_threads_for_k(uint32_t k);
 size_t sv_smem_bytes(bool fp64, uint32_t k);
 // one pass over one state (grid = tiles)
@@ -304,9 +305,59 @@ struct TabArgs {
   const TabSlot *slots;
   const uint8_t *bits;
   uint8_t *outs;
+  uint32_t *rand_any;          // when non-NULL: set to 1 if any outcome was random, else 0
+  const uint32_t *run_if;      // when non-NULL: the launch does nothing unless *run_if != 0
 };
 size_t tab_smem_bytes(uint32_t n);
 void launch_tab(const TabArgs &a, uint32_t n_tasks, void *stream);
+
+// Pauli frames (stabilizer tasks that differ from a shared reference only
+// by Pauli gates): the reference is run once on the tableau; every task's
+// deviation is a Pauli frame F, propagated through the reference's Clifford
+// gates 32 tasks per 32-bit word.  A Z measurement of the task returns the
+// reference outcome XOR the X bit of F on the measured qubit, which is exact
+// when the reference outcome is deterministic (F|psi> has the same
+// stabilizers up to sign).
+enum FrameKind : uint8_t {
+  F_H = 1,      // swap X, Z
+  F_S = 2,      // Z ^= X  (S and S^dagger)
+  F_CX = 3,     // X_b ^= X_a, Z_a ^= Z_b  (control a, target b)
+  F_CZ = 4,     // Z_a ^= X_b, Z_b ^= X_a
+  F_SWAP = 5,
+  F_RESET = 6,  // X = Z = 0
+  F_EVENT = 7,  // X ^= ev_x[aux], Z ^= ev_z[aux]  (the tasks' own Pauli gates)
+  F_MEAS = 8,   // outcome aux = reference outcome aux XOR X
+};
+struct FrameOp {
+  uint8_t kind, pad;
+  uint16_t a, b, pad2;
+  uint32_t aux;
+};
+struct FrameLayer {
+  uint32_t op_begin, n_ops;  // ops on distinct qubits; F_MEAS ops last
+  uint32_t n_meas, pad;
+};
+struct FrameHostProgram {
+  std::vector<FrameLayer> layers;
+  std::vector<FrameOp> ops;
+};
+// Builds the frame program of a reference gate list with Pauli events
+// inserted: events[i] = (slot, qubit) means "before reference gate slot";
+// event i becomes F_EVENT with aux = i.  Layers follow qubit dependencies.
+FrameHostProgram compile_frames(const qw_gate *ref, uint64_t n_ref, uint32_t n,
+                                const std::vector<std::pair<uint64_t, uint32_t>> &events);
+struct FrameArgs {
+  uint32_t n, n_tasks, n_words, n_layers;
+  const FrameLayer *layers;
+  const FrameOp *ops;
+  const uint32_t *ev_x, *ev_z;  // [event * n_words + word]
+  const uint8_t *ref_out;       // reference outcomes
+  const uint32_t *rand_any;     // nonzero: some reference outcome was random; frames do not apply
+  const uint32_t *out_base;     // per task of the group: first suffix outcome in outs
+  uint8_t *outs;
+};
+cudaError_t frame_init_attrs();
+void launch_frames(const FrameArgs &a, void *stream);
 
 // learned cost model
 void launch_mlp_forward(const float *params, const float *x, float *y, uint32_t batch, void *stream);

@@ -420,13 +420,16 @@ size_t sv_smem_bytes(bool fp64, uint32_t k) { return (size_t)(fp64 ? 16 : 8) << 
 
 // Kernel attributes are set once, before any stream capture (a capture
 // fails on attribute changes).
-void sv_init_attrs() {
+cudaError_t sv_init_attrs() {
   const int bytes = 200 * 1024;
-  cudaFuncSetAttribute((const void *)sv_pass_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute((const void *)sv_pass_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute((const void *)sv_batch_kernel<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute((const void *)sv_batch_kernel<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute((const void *)sv_batch_kernel<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const void *k[5] = {(const void *)sv_pass_kernel<float>, (const void *)sv_pass_kernel<double>,
+                      (const void *)sv_batch_kernel<float, 3>, (const void *)sv_batch_kernel<float, 4>,
+                      (const void *)sv_batch_kernel<double, 1>};
+  for (const void *f : k) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 void launch_sv_pass(bool fp64, const SvTables &t, uint32_t pass_idx, uint32_t k, uint32_t n,

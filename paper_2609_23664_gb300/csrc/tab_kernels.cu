@@ -30,6 +30,7 @@ struct TabSm {
   uint8_t *sign;   // rows
   uint8_t *pending;
   uint64_t *xs;    // W words (collapse scratch)
+  uint32_t *any_random;
 };
 
 __device__ __forceinline__ int getb(const uint64_t *row, uint32_t q) {
@@ -67,6 +68,7 @@ __device__ void tab_collapse(const TabArgs &A, TabSm &S, const TabSlot &sl, uint
   }
   const uint32_t p = (uint32_t)first;
   (void)n;
+  if (tid == 0) *S.any_random = 1u;
   // 1) CNOT(p -> q) for every other q in the X part of T(Z_a)
   for (uint32_t r = tid; r < rows; r += nt) {
     uint64_t *x = S.R + (size_t)r * 2 * W, *z = x + W;
@@ -200,8 +202,12 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
 
 __global__ void __launch_bounds__(256) tab_kernel(TabArgs A) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ uint32_t s_any_random;
+  if (A.run_if && *A.run_if == 0u) return;  // uniform over the grid
   const uint32_t W = A.W, rows = A.rows;
   TabSm S;
+  S.any_random = &s_any_random;
+  if (threadIdx.x == 0) s_any_random = 0u;
   S.R = (uint64_t *)smraw;
   S.sign = (uint8_t *)(S.R + (size_t)rows * 2 * W);
   S.pending = S.sign + ((rows + 15) & ~15u);
@@ -232,6 +238,8 @@ __global__ void __launch_bounds__(256) tab_kernel(TabArgs A) {
     const TabProgram P = A.progs[sg.prog];
     tab_run_program(A, S, P, sg.bit_base, T.out_base + sg.out_base);
   }
+  __syncthreads();
+  if (A.rand_any && threadIdx.x == 0) A.rand_any[blockIdx.x] = s_any_random;
   if (A.out_rows) {
     uint64_t *o = A.out_rows + (size_t)blockIdx.x * nwords;
     for (size_t i = threadIdx.x; i < nwords; i += blockDim.x) o[i] = S.R[i];
@@ -245,8 +253,11 @@ size_t tab_smem_bytes(uint32_t n) {
   return (size_t)rows * 2 * W * 8 + ((rows + 15) & ~15u) + ((n + 15) & ~15u) + (size_t)W * 8 + 16;
 }
 
-void tab_init_attrs() {
-  cudaFuncSetAttribute((const void *)tab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+// the largest tableau (QW_TABLEAU_MAX_QUBITS) fits below the 227 KB opt-in
+// limit together with the kernel's static shared memory
+cudaError_t tab_init_attrs() {
+  return cudaFuncSetAttribute((const void *)tab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tab_smem_bytes(QW_TABLEAU_MAX_QUBITS));
 }
 
 void launch_tab(const TabArgs &a, uint32_t n_tasks, void *stream) {

@@ -175,12 +175,12 @@ def test_config1_vqe12_fp64_full(eng):
             assert np.max(np.abs(got - ref["state"])) <= 1e-12
 
 
-@pytest.mark.parametrize("reuse,batched", [(1, 1), (0, 0), (0, 1), (1, 0)])
-def test_config2_vqe_fp32_small(eng, reuse, batched):
+@pytest.mark.parametrize("reuse,batched,graph", [(1, 1, 1), (0, 0, 1), (0, 1, 1), (1, 0, 1), (1, 1, 0)])
+def test_config2_vqe_fp32_small(eng, reuse, batched, graph):
     tasks = W.config2_vqe24(n=16, n_tasks=24, n_terms=40)
     for t in tasks[:2]:
         t.want_state = True
-    p, wl = run_plan(eng, tasks, reuse=reuse, batched=batched)
+    p, wl = run_plan(eng, tasks, reuse=reuse, batched=batched, use_graph=graph)
     ex = p.explain()
     assert ex["artifacts"] == (1 if reuse else 0)
     for i, t in enumerate(tasks):
@@ -237,6 +237,45 @@ def test_config4_qec_small_bit_exact(eng):
         ref = orc.tab_run(t.n, t.gates)
         got = p.syndrome(i)
         assert np.array_equal(got, ref), i
+
+
+@pytest.mark.parametrize("frames,graph", [(1, 1), (0, 1), (1, 0)])
+def test_config4_qec_frames_and_tableau_agree_bit_exact(eng, frames, graph):
+    # Pauli frames over the shared 3-round reference vs every task on its
+    # own tableau, with and without graph capture: identical syndromes,
+    # equal to the oracle's
+    tasks = W.config4_qec(d=5, shared_rounds=6, task_rounds=3, n_tasks=80, p=0.02)
+    p, wl = run_plan(eng, tasks, pauli_frames=frames, use_graph=graph)
+    ex = p.explain()
+    assert len(ex["pauli_frames"]) == frames
+    if frames:
+        assert ex["pauli_frames"][0]["tasks"] == 80 and ex["artifacts"] == 1
+    for i, t in enumerate(tasks):
+        assert np.array_equal(p.syndrome(i), orc.tab_run(t.n, t.gates)), (frames, i)
+
+
+def test_pauli_frames_fall_back_when_a_reference_outcome_is_random(eng):
+    # the shared reference measures a qubit in superposition: its outcome is
+    # random, so frames do not apply; the per-task tableau launch (gated on
+    # the device by the reference run) must produce the oracle's outcomes
+    rng = np.random.default_rng(77)
+    n = 7
+    pre = W.gates_from_list([(W.OP_H, 0, 0), (W.OP_CNOT, 0, 1), (W.OP_CNOT, 1, 2), (W.OP_H, 5, 0),
+                             (W.OP_MEASURE, 2, 0, 1.0), (W.OP_S, 1, 0), (W.OP_CZ, 1, 3)])
+    suf = W.gates_from_list([(W.OP_H, 4, 0), (W.OP_MEASURE, 4, 0, 1.0), (W.OP_CNOT, 0, 6),
+                             (W.OP_MEASURE, 6, 0, 0.0), (W.OP_H, 3, 0), (W.OP_MEASURE, 3, 0, 1.0),
+                             (W.OP_RESET, 4, 0, 0.0), (W.OP_MEASURE, 0, 0, 0.0)])
+    tasks = []
+    for i in range(40):
+        errs = [(int(rng.choice([W.OP_X, W.OP_Y, W.OP_Z])), int(rng.integers(0, n)), 0)
+                for _ in range(int(rng.integers(0, 3)))]
+        spans = [pre] + ([W.gates_from_list(errs)] if errs else []) + [suf]
+        tasks.append(W.Task(mode=W.MODE_TABLEAU, n=n, spans=spans))
+    p, wl = run_plan(eng, tasks, min_prefix_gates=1)
+    ex = p.explain()
+    assert ex["pauli_frames"] and ex["pauli_frames"][0]["tasks"] >= 2
+    for i, t in enumerate(tasks):
+        assert np.array_equal(p.syndrome(i), orc.tab_run(t.n, t.gates)), i
 
 
 def test_config4_qec_replay_bit_exact(eng):

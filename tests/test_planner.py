@@ -237,11 +237,48 @@ def test_tableau_workload_shares_the_prefix_span():
 
 
 def test_full_size_qec_planning_is_fast():
-    tasks = W.config4_qec(n_tasks=512)       # 449 qubits, 100 + 5 rounds
+    tasks = W.config4_qec()                  # 449 qubits, 100 + 5 rounds, 4096 tasks
     t0 = time.perf_counter()
-    p, ex, wl = host_plan(tasks)
+    p, ex, wl = host_plan(tasks, pauli_frames=0)
     dt = time.perf_counter() - t0
-    assert ex["artifacts"] >= 1 and dt < 20.0, dt
+    assert ex["artifacts"] >= 1 and dt < 10.0, dt
+
+
+def test_qec_tasks_become_one_pauli_frame_group():
+    # the tasks differ only by data errors (Pauli gates): one boundary after
+    # the shared rounds, every task a frame over the 5-round reference
+    tasks = W.config4_qec(d=5, shared_rounds=6, n_tasks=96, p=0.02)
+    p, ex, wl = host_plan(tasks)
+    assert ex["artifacts"] == 1 and ex["options"]["pauli_frames"] == 1
+    (fr,) = ex["pauli_frames"]
+    n_anc = 24
+    assert fr["tasks"] == 96 and fr["outcomes_per_task"] == 5 * n_anc
+    # reference = the suffix without its Pauli gates: 5 identical rounds
+    n_round = len(tasks[0].spans[-1])       # every task ends with a syndrome round
+    assert fr["reference_gates"] == 5 * n_round
+    # one event per distinct (position, qubit) carrying an error in some task
+    keys = set()
+    for t in tasks:
+        slot = 0
+        for sp in t.spans[1:]:
+            for g in sp:
+                if g["op"] in (W.OP_X, W.OP_Y, W.OP_Z):
+                    keys.add((slot, int(g["q0"])))
+                else:
+                    slot += 1
+    assert fr["events"] == len(keys) > 0
+    # without frames the trie nests boundaries at the error positions
+    _, ex0, _ = host_plan(tasks, pauli_frames=0)
+    assert ex0["pauli_frames"] == [] and ex0["artifacts"] >= 1
+
+
+def test_structural_differences_prevent_frames():
+    # a non-Pauli gate that differs between tasks after the boundary
+    tasks = W.config4_qec(d=3, shared_rounds=4, n_tasks=6, p=0.0)
+    extra = W.gates_from_list([(W.OP_H, 0, 0)])
+    tasks[3].spans = tasks[3].spans + [extra]
+    p, ex, wl = host_plan(tasks)
+    assert all(f["tasks"] < 6 for f in ex["pauli_frames"])
 
 
 @pytest.mark.parametrize("bad,code", [
