@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--no-replay", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-tasks", type=int, default=1)
+    ap.add_argument("--qec-steps", type=int, default=5,
+                    help="also time the QEC family (d=15, 4096 tasks, stabilizer); 0 = skip")
     ap.add_argument("--fuse-energy", type=int, default=0,
                     help="1: energy blocks as work items of the persistent suffix launch")
     ap.add_argument("--tile-qubits", type=int, default=0, help="0: autotuned")
@@ -379,6 +381,35 @@ def run_native(a):
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "includes": "workload submission, planning, device allocation, upload, "
                                    "execution, read-back of all energies"}
+
+    # the stabilizer family (QEC d=15, 4096 tasks): Pauli frames over the
+    # shared reference vs every task on its own tableau, same GPU
+    if a.qec_steps > 0 and world == 1:
+        qt = W.config4_qec()
+        qwl = Q.Workload(qt)
+        qec = {"workload": "qec_d15: rotated surface code, 449 qubits, 100 shared + 5 task rounds, "
+                           "4096 tasks, data X/Z errors p=1e-3"}
+        for key, opts in (("pauli_frames", dict(pauli_frames=1)), ("per_task_tableau", dict(pauli_frames=0))):
+            qp = Q.Plan(eng, qwl, **opts)
+            qp.execute(sptr)
+            qp.wait()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(a.qec_steps):
+                qp.execute(sptr)
+                qp.wait()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            qms = e0.elapsed_time(e1) / a.qec_steps
+            qcr = qp.cost_record()
+            qec[key] = {"value": len(qt) / (qms / 1e3), "unit": "tasks/s", "ms_per_step": qms,
+                        "prefix_ms": qcr["prefix_ms"], "tasks_ms": qcr["tableau_tasks_ms"],
+                        "kernel_launches": qcr["kernel_launches"], "artifacts": qcr["artifacts"]}
+            qp.close()
+        line["qec"] = qec
+        qwl.close()
 
     line["roofline"] = roofline
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
