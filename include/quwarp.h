@@ -199,11 +199,19 @@ typedef struct qw_plan_opts {
                                  tableau and the tasks as Pauli frames (same outcomes; the
                                  per-task tableau runs instead when a reference outcome is
                                  random); 0 = every task on its own tableau.  Default 1. */
+  int32_t handoff;            /* 1 = statevector tasks (n <= QW_SV_MAX_QUBITS) may continue
+                                 from a tableau boundary exported to a statevector (Table II
+                                 STAB -> SV), and an all-Clifford shared prefix may be run on
+                                 the tableau for them when Eq. 2 estimates it cheaper; the
+                                 exported state's global phase is fixed by a positive real
+                                 amplitude on the first basis state of its support.
+                                 0 = never.  Default 1. */
 } qw_plan_opts;
 
 /* Fills the defaults: reuse=1, batched=1, legality=1, analytic costs,
  * delta_frac=0.10, min_group=2, min_prefix_gates=1, min_prefix_cost_ns=0,
- * autotuned tiles, use_graph=1, fault_injection=0, fuse_energy=0, pauli_frames=1. */
+ * autotuned tiles, use_graph=1, fault_injection=0, fuse_energy=0, pauli_frames=1,
+ * handoff=1. */
 void qw_plan_opts_default(qw_plan_opts *o);
 
 typedef struct qw_plan qw_plan;

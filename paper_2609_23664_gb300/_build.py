@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libquwarp.so")
-SOURCES = ["sv_kernels.cu", "obs_kernels.cu", "tab_kernels.cu", "frames.cu", "mlp_kernels.cu", "engine.cu",
+SOURCES = ["sv_kernels.cu", "obs_kernels.cu", "tab_kernels.cu", "frames.cu", "handoff.cu", "mlp_kernels.cu", "engine.cu",
            "noalloc.cu", "planner.cpp", "fusion.cpp", "capi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -167,6 +167,9 @@ struct DeviceState {
   SvTables t32{}, t64{};
   std::vector<uint32_t> mat_pass0, task_pass0;
   std::vector<void *> mat_buf;
+  std::vector<void *> mat_export[2];   // per mode (FP64, FP32): statevector exported from a tableau node
+  std::vector<StabBasis *> mat_basis;  // scratch of each exporting tableau node
+  std::vector<int> tab_launch_of_mat;  // index into tab_mat_launches, -1 none
   std::vector<void *> task_state;  // state a task's observables read
   std::vector<Wave> waves;
   EnClass *d_classes = nullptr;
@@ -309,15 +312,33 @@ static void prepare(qw_plan *P) {
 
   // boundary store (budget was enforced by the planner)
   D->mat_buf.assign(P->mats.size(), nullptr);
+  D->mat_export[0].assign(P->mats.size(), nullptr);
+  D->mat_export[1].assign(P->mats.size(), nullptr);
+  D->mat_basis.assign(P->mats.size(), nullptr);
   for (size_t m = 0; m < P->mats.size(); m++) {
     const MatNode &M = P->mats[m];
     if (M.mode == QW_MODE_TABLEAU) {
       const uint32_t W = (M.n + 63) / 64;
       D->mat_buf[m] = D->arena.alloc((size_t)2 * M.n * 2 * W * 8 + 2 * M.n + 64);
+      if (M.export_modes) {
+        if (M.n > QW_SV_MAX_QUBITS) fail(QW_ERR_STATE, "internal: tableau export above the statevector cap");
+        D->mat_basis[m] = (StabBasis *)D->arena.alloc(sizeof(StabBasis));
+        const uint32_t n_eff = std::max<uint32_t>(M.n, SV_G);
+        for (uint32_t md = 0; md < 2; md++)
+          if ((M.export_modes >> md) & 1u)
+            D->mat_export[md][m] = D->arena.alloc(sv_state_bytes(md == QW_MODE_SV_FP64, n_eff));
+      }
     } else {
       D->mat_buf[m] = D->arena.alloc(sv_state_bytes(M.mode == QW_MODE_SV_FP64, M.n_eff));
     }
   }
+  // the state a statevector consumer of node m reads (the node itself, or its export)
+  auto sv_source = [&](int m, uint32_t mode) -> void * {
+    return P->mats[m].mode == QW_MODE_TABLEAU ? D->mat_export[mode][m] : D->mat_buf[m];
+  };
+  auto needs_convert = [&](const TaskPlan &tp) {
+    return tp.src >= 0 && P->mats[tp.src].mode != QW_MODE_TABLEAU && P->mats[tp.src].mode != tp.mode;
+  };
 
   // Hamiltonians
   std::vector<EnClass> cls;
@@ -358,9 +379,9 @@ static void prepare(qw_plan *P) {
     std::vector<uint32_t> own, shared_src;
     for (uint32_t t : g.second) {
       const TaskPlan &tp = P->tasks[t];
-      const bool convert = tp.src >= 0 && P->mats[tp.src].mode != tp.mode;
+      const bool convert = needs_convert(tp);
       if (!tp.sv.passes.empty() || convert) own.push_back(t);
-      else { shared_src.push_back(t); D->task_state[t] = D->mat_buf[tp.src]; }
+      else { shared_src.push_back(t); D->task_state[t] = sv_source(tp.src, tp.mode); }
     }
     // KEEP_STATE tasks get dedicated buffers; the others share a pool
     size_t per_wave = batched ? std::max<size_t>(1, E->task_budget / std::max<size_t>(S, 1)) : 1;
@@ -419,8 +440,8 @@ static void prepare(qw_plan *P) {
             const TaskPlan &tp = P->tasks[t];
             if (p >= tp.sv.passes.size()) continue;
             SvJob j{};
-            const bool convert = tp.src >= 0 && P->mats[tp.src].mode != tp.mode;
-            j.src = (p == 0 && !convert) ? (tp.src >= 0 ? D->mat_buf[tp.src] : nullptr) : D->task_state[t];
+            const bool convert = needs_convert(tp);
+            j.src = (p == 0 && !convert) ? (tp.src >= 0 ? sv_source(tp.src, tp.mode) : nullptr) : D->task_state[t];
             j.dst = D->task_state[t];
             j.pass = D->task_pass0[t] + (uint32_t)p;
             j.n_tiles = 1u << (tp.n_eff - (uint32_t)tp.sv.passes[p].q.size());
@@ -435,8 +456,7 @@ static void prepare(qw_plan *P) {
       }
       for (uint32_t t : W.tasks) {
         const TaskPlan &tp = P->tasks[t];
-        if (tp.src >= 0 && P->mats[tp.src].mode != tp.mode)
-          W.converts.push_back({t, {D->mat_buf[tp.src], D->task_state[t]}});
+        if (needs_convert(tp)) W.converts.push_back({t, {D->mat_buf[tp.src], D->task_state[t]}});
       }
       // energy jobs
       for (uint32_t t : W.obs_tasks) {
@@ -608,9 +628,11 @@ static void prepare(qw_plan *P) {
       a.outs = outs;
       dst.push_back({a, (uint32_t)descs.size(), -1});
     };
+    D->tab_launch_of_mat.assign(P->mats.size(), -1);
     for (size_t m = 0; m < P->mats.size(); m++) {
       const MatNode &M = P->mats[m];
       if (M.mode != QW_MODE_TABLEAU) continue;
+      D->tab_launch_of_mat[m] = (int)D->tab_mat_launches.size();
       std::vector<TabSegment> segs;
       uint32_t oo = 0;
       for (auto &sg : M.tab_segs) {
@@ -706,11 +728,27 @@ static void enqueue(qw_plan *P, cudaStream_t s, bool capturing) {
   // 1) shared prefixes (boundary states), in creation order (parents first)
   for (size_t m = 0; m < P->mats.size(); m++) {
     const MatNode &M = P->mats[m];
-    if (M.mode == QW_MODE_TABLEAU) continue;
+    if (M.mode == QW_MODE_TABLEAU) {
+      const DeviceState::TabLaunch &L = D->tab_mat_launches[D->tab_launch_of_mat[m]];
+      launch_tab(L.a, L.n_tasks, s);
+      nl += 1;
+      // Table II STAB -> SV: the statevectors its consumers continue from
+      for (uint32_t md = 0; md < 2; md++)
+        if (D->mat_export[md][m]) {
+          launch_stab_export(D->mat_buf[m], M.n, D->mat_basis[m], md == QW_MODE_SV_FP64,
+                             std::max<uint32_t>(M.n, SV_G), D->mat_export[md][m], P->eng->sm_count, s);
+          nl += 2;
+        }
+      continue;
+    }
     const bool fp64 = M.mode == QW_MODE_SV_FP64;
     const SvTables &T = fp64 ? D->t64 : D->t32;
-    const void *psrc = (M.parent >= 0) ? D->mat_buf[M.parent] : nullptr;
-    if (M.parent >= 0 && P->mats[M.parent].mode != M.mode) psrc = nullptr;  // never crosses families
+    const void *psrc = nullptr;
+    if (M.parent >= 0) {
+      const MatNode &PM = P->mats[M.parent];
+      if (PM.mode == M.mode) psrc = D->mat_buf[M.parent];
+      else if (PM.mode == QW_MODE_TABLEAU) psrc = D->mat_export[M.mode][M.parent];
+    }
     if (M.sv.passes.empty()) {
       if (psrc) launch_copy(psrc, D->mat_buf[m], sv_state_bytes(fp64, M.n_eff), s);
       continue;
@@ -721,8 +759,6 @@ static void enqueue(qw_plan *P, cudaStream_t s, bool capturing) {
                      p == 0 ? psrc : D->mat_buf[m], D->mat_buf[m], s);
     }
   }
-  for (auto &L : D->tab_mat_launches) launch_tab(L.a, L.n_tasks, s);
-  nl += D->tab_mat_launches.size();
   CK(rec(D->ev[1]));
   // 2) task suffixes, observables
   size_t wi = 0;

@@ -45,7 +45,7 @@ struct TNode {
 
 struct Candidate {
   uint64_t cut = 0;   // gate index (absolute) of the boundary
-  int kind = 0;       // 0 LCP, 1 Clifford transition, 2 barrier / checkpoint
+  int kind = 0;       // 0 LCP, 1 Clifford transition, 2 barrier / checkpoint, 3 tableau handoff
   uint32_t n_tasks = 0;
   double c_prefix = 0, c_mat = 0, c_reload = 0, c_handoff = 0, delta = 0, lhs = 0, rhs = 0;
   bool holds = false;
@@ -66,7 +66,7 @@ struct Decision {
   std::vector<Candidate> cands;
   int chosen = -1;
   int mat = -1;
-  double est_direct = 0, est_reuse = 0;
+  double est_direct = 0, est_reuse = 0, est_handoff = -1;  // est_handoff < 0: not applicable
   std::vector<RefusalRec> refusals;
   bool cost_from_mlp = false;
 };
@@ -84,6 +84,9 @@ struct MatNode {
   std::vector<std::pair<uint32_t, uint32_t>> tab_segs;  // (program, bit_base)
   uint32_t tab_outs = 0;    // outcomes this segment produces
   uint32_t out_offset = 0;  // cumulative outcomes from the root to the start of this node
+  // tableau node exported to statevectors (bit 1 << mode per precision that
+  // statevector consumers need; Table II STAB -> SV)
+  uint32_t export_modes = 0;
 };
 
 struct TaskPlan {

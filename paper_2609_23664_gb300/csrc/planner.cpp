@@ -224,9 +224,9 @@ bool legality(const qw_artifact_desc &a, uint32_t tb, const uint8_t *expected, q
                  a.kind, tk, a.backend, tb);
     return false;
   }
-  if (a.kind == QW_KIND_TABLEAU && tk == QW_KIND_STATEVECTOR) {
+  if (a.kind == QW_KIND_TABLEAU && tk == QW_KIND_STATEVECTOR && a.n_qubits > QW_SV_MAX_QUBITS) {
     fill_refusal(out, "UNSUPPORTED_CONVERSION",
-                 "exact tableau-to-statevector export is legal but not implemented by this engine",
+                 "exact tableau-to-statevector export is limited to the statevector qubit cap",
                  a.kind, tk, a.backend, tb);
     return false;
   }
@@ -386,6 +386,8 @@ struct Builder {
 
 }  // namespace
 
+static bool is_handoff_op(uint32_t op);
+
 struct PlanCtx {
   qw_plan *P;
   Engine *E;
@@ -401,7 +403,24 @@ struct PlanCtx {
   // per materialized node: SHA-256 state after its layout and gates [0, end),
   // so a nested node's fingerprint continues from its parent's
   std::vector<Sha256> mat_sha;
+  std::vector<int64_t> handoff_run;  // per task: leading gates a tableau can run (-1 = not yet known)
   PlanCtx(qw_plan *p, Engine *e, const Workload &w) : P(p), E(e), W(w), B(w) {}
+
+  uint64_t handoff_len(uint32_t t) {
+    if (handoff_run.empty()) handoff_run.assign(W.tasks.size(), -1);
+    if (handoff_run[t] < 0) {
+      const TaskData &T = W.tasks[t];
+      uint64_t len = 0;
+      bool go = true;
+      for (size_t k = 0; k < T.spans.size() && go; k++)
+        for (uint64_t j = 0; j < T.spans[k].n; j++) {
+          if (!is_handoff_op(T.spans[k].g[j].op)) { go = false; break; }
+          len++;
+        }
+      handoff_run[t] = (int64_t)len;
+    }
+    return (uint64_t)handoff_run[t];
+  }
 
   TileConfig tiles(uint32_t n_eff, bool fp64) {
     TileConfig tc;
@@ -470,7 +489,17 @@ struct PlanCtx {
 };
 
 static const char *cut_kind_name(int k) {
-  return k == 0 ? "LARGEST_COMMON_PREFIX" : (k == 1 ? "CLIFFORD_SAFE_PREFIX" : "COARSE_BARRIER");
+  return k == 0 ? "LARGEST_COMMON_PREFIX"
+                : (k == 1 ? "CLIFFORD_SAFE_PREFIX" : (k == 2 ? "COARSE_BARRIER" : "TABLEAU_HANDOFF"));
+}
+
+// gates a tableau can run ahead of a statevector handoff (unitary Cliffords)
+static bool is_handoff_op(uint32_t op) {
+  switch (op) {
+    case QW_OP_H: case QW_OP_S: case QW_OP_SDG: case QW_OP_X: case QW_OP_Y: case QW_OP_Z:
+    case QW_OP_CNOT: case QW_OP_CZ: case QW_OP_SWAP: return true;
+    default: return false;
+  }
 }
 
 static bool is_pauli_op(uint32_t op) { return op == QW_OP_X || op == QW_OP_Y || op == QW_OP_Z; }
@@ -556,7 +585,10 @@ static void decide(PlanCtx &C) {
         // the boundary this candidate would continue from must be of the
         // producer's own family (no cross-family continuation)
         int pmat = mat;
-        while (pmat >= 0 && P->mats[pmat].mode != pm) pmat = P->mats[pmat].parent;
+        auto same_family = [&](int m) {
+          return P->mats[m].mode == pm || (pm != QW_MODE_TABLEAU && ((P->mats[m].export_modes >> pm) & 1u));
+        };
+        while (pmat >= 0 && !same_family(pmat)) pmat = P->mats[pmat].parent;
         const uint64_t base = (pmat >= 0) ? P->mats[pmat].end : 0;
         const uint64_t lo = std::max<uint64_t>(base, nodes[V.parent].depth);
         // candidate cut points (<= 3), all on the edge into V
@@ -613,10 +645,47 @@ static void decide(PlanCtx &C) {
             D.est_reuse = cp + (double)V.below * c_suffix;
           }
         }
+        // Table II STAB -> SV: run an all-Clifford prefix on the tableau and
+        // export it once as the statevector the suffixes continue from.  In
+        // Eq. 2 terms: C_prefix is the statevector prefix every task would
+        // otherwise run, C_mat the tableau run plus the export minus the one
+        // statevector run that (N-1) C_prefix already leaves out.
+        const double S_sv = S;
+        if (P->opts.handoff && pm != QW_MODE_TABLEAU && V.n <= QW_SV_MAX_QUBITS && pmat < 0) {
+          const uint64_t hc = std::min<uint64_t>(V.depth, C.handoff_len(V.rep));
+          if (hc > 0) {
+            Candidate cd;
+            cd.cut = hc;
+            cd.kind = 3;
+            cd.n_tasks = V.below;
+            const double c_sv = C.seg_cost(rep, pm, 0, hc);
+            const double c_tab = C.seg_cost(rep, QW_MODE_TABLEAU, 0, hc);
+            const double c_exp = S_sv / C.bw_gbs + 2.0 * C.launch_ns;
+            cd.c_prefix = c_sv;
+            cd.c_mat = c_tab + c_exp - c_sv;
+            cd.c_reload = 0.0;
+            cd.c_handoff = 0.0;
+            const double c_suffix = C.seg_cost(rep, pm, hc, V.depth) + c_rest;
+            const double direct = (double)V.below * (c_sv + c_suffix);
+            cd.delta = P->opts.delta_frac * direct;
+            cd.lhs = ((double)V.below - 1.0) * cd.c_prefix;
+            cd.rhs = cd.c_mat + cd.delta;
+            cd.holds = cd.lhs > cd.rhs;
+            if (V.below < P->opts.min_group || hc < P->opts.min_prefix_gates || c_sv < P->opts.min_prefix_cost_ns)
+              cd.holds = false;
+            D.cands.push_back(cd);
+            D.est_handoff = c_tab + c_exp + (double)V.below * c_suffix;
+            const double net = cd.lhs - cd.rhs;
+            if (cd.holds && net > best_net) { best_net = net; D.chosen = (int)D.cands.size() - 1; }
+          }
+        }
+        const bool handoff = D.chosen >= 0 && D.cands[D.chosen].kind == 3;
+        const uint32_t prod = handoff ? (uint32_t)QW_MODE_TABLEAU : pm;
+        const double S_store = handoff ? PlanCtx::state_bytes(QW_MODE_TABLEAU, V.n) + S_sv : S;
         if (D.chosen < 0) {
           D.decision = 1;
           D.reason = (V.below < P->opts.min_group) ? "EARLY_FILTER_GROUP_SIZE" : "NOT_PROFITABLE";
-        } else if (C.store_used + (uint64_t)S > C.store_budget) {
+        } else if (C.store_used + (uint64_t)S_store > C.store_budget) {
           D.decision = 1;
           D.reason = "STORE_BUDGET";
           D.chosen = -1;
@@ -628,18 +697,19 @@ static void decide(PlanCtx &C) {
           M.begin = base;
           M.end = D.cands[D.chosen].cut;
           M.rep = V.rep;
-          M.mode = pm;
+          M.mode = prod;
           M.n = V.n;
-          M.n_eff = (pm == QW_MODE_TABLEAU) ? V.n : std::max<uint32_t>(V.n, SV_G);
-          M.bytes = (uint64_t)S;
+          M.n_eff = (prod == QW_MODE_TABLEAU) ? V.n : std::max<uint32_t>(V.n, SV_G);
+          M.bytes = (uint64_t)S_store;
+          if (handoff) M.export_modes = 1u << pm;
           // Eq. 1 over [0, end): continued from the parent's state (the
           // tasks below V share the parent's gates [0, parent end))
           Sha256 sh;
-          if (pmat >= 0 && P->mats[pmat].n == V.n) {
+          if (pmat >= 0 && P->mats[pmat].n == V.n && P->mats[pmat].mode == prod) {
             sh = C.mat_sha[pmat];
             hash_gates(sh, rep, P->mats[pmat].end, M.end);
           } else {
-            hash_layout(sh, V.n, pm);
+            hash_layout(sh, V.n, prod);
             hash_gates(sh, rep, 0, M.end);
           }
           {
@@ -647,9 +717,9 @@ static void decide(PlanCtx &C) {
             fin.final(M.provenance);
           }
           qw_artifact_desc A{};
-          A.kind = (pm == QW_MODE_TABLEAU) ? QW_KIND_TABLEAU : QW_KIND_STATEVECTOR;
+          A.kind = (prod == QW_MODE_TABLEAU) ? QW_KIND_TABLEAU : QW_KIND_STATEVECTOR;
           A.exactness = QW_EXACT;
-          A.backend = backend_of_mode(pm);
+          A.backend = backend_of_mode(prod);
           A.n_qubits = V.n;
           memcpy(A.provenance, M.provenance, 32);
           // consumers: every task below V
@@ -668,7 +738,7 @@ static void decide(PlanCtx &C) {
             qw_refusal rf;
             const uint32_t tb = backend_of_mode(W.tasks[t].mode);
             if (legality(A, tb, A.provenance, &rf)) { legal_count++; continue; }
-            const bool sv_both = W.tasks[t].mode != QW_MODE_TABLEAU && pm != QW_MODE_TABLEAU;
+            const bool sv_both = W.tasks[t].mode != QW_MODE_TABLEAU && prod != QW_MODE_TABLEAU;
             if (!P->opts.legality && sv_both) { C.bypass[t] = 1; legal_count++; continue; }
             C.refused[t] = 1;
             D.refusals.push_back({t, rf});
@@ -681,7 +751,7 @@ static void decide(PlanCtx &C) {
             C.mat_sha.push_back(sh);
             C.store_used += M.bytes;
             mat = D.mat;
-            if (pm == QW_MODE_TABLEAU && P->opts.pauli_frames)
+            if (prod == QW_MODE_TABLEAU && !handoff && P->opts.pauli_frames)
               frozen = pauli_equivalent(W, below_tasks, C.refused, M.end);
           } else {
             D.decision = D.refusals.empty() ? 1 : 2;
@@ -837,10 +907,18 @@ void build_plan(qw_plan *P, Engine *E, const Workload &W) {
     tp.legality_bypassed = C.bypass[t] != 0;
     int src = C.mat_at[C.B.end_node[t]];
     if (tp.refused) src = -1;
-    // an artifact of another mode is usable only through the bypass
-    while (src >= 0 && P->mats[src].mode != T.mode && !tp.legality_bypassed) src = P->mats[src].parent;
+    // an artifact of another mode is usable only through the bypass, or as
+    // a tableau boundary exported to the task's statevector (Table II)
+    auto usable = [&](int m) {
+      if (P->mats[m].mode == T.mode || tp.legality_bypassed) return true;
+      return T.mode != QW_MODE_TABLEAU && P->mats[m].mode == QW_MODE_TABLEAU && T.n <= QW_SV_MAX_QUBITS &&
+             P->opts.handoff;
+    };
+    while (src >= 0 && !usable(src)) src = P->mats[src].parent;
     tp.src = src;
     tp.begin = (src >= 0) ? P->mats[src].end : 0;
+    if (src >= 0 && P->mats[src].mode == QW_MODE_TABLEAU && T.mode != QW_MODE_TABLEAU)
+      P->mats[src].export_modes |= 1u << T.mode;
   }
 
   // Hamiltonian layouts (deduplicated by content)
@@ -991,18 +1069,31 @@ void build_plan(qw_plan *P, Engine *E, const Workload &W) {
                 cd.holds ? "true" : "false", (int)c == D.chosen ? "true" : "false");
     }
     s += "],";
+    const bool ho = D.chosen >= 0 && D.cands[D.chosen].kind == 3;
     s += strf("\"alternatives\":[{\"plan\":\"BASELINE\",\"est_ns\":%.1f,\"chosen\":%s},"
-              "{\"plan\":\"SAME_FAMILY_REUSE\",\"est_ns\":%.1f,\"chosen\":%s},"
-              "{\"plan\":\"CROSS_BACKEND_HANDOFF\",\"status\":\"NOT_APPLICABLE\"}],",
+              "{\"plan\":\"SAME_FAMILY_REUSE\",\"est_ns\":%.1f,\"chosen\":%s},",
               D.est_direct, D.decision == 0 ? "false" : "true", D.est_reuse,
-              D.decision == 0 ? "true" : "false");
+              (D.decision == 0 && !ho) ? "true" : "false");
+    if (D.est_handoff >= 0)
+      s += strf("{\"plan\":\"CROSS_BACKEND_HANDOFF\",\"est_ns\":%.1f,\"chosen\":%s}],", D.est_handoff,
+                (D.decision == 0 && ho) ? "true" : "false");
+    else
+      s += "{\"plan\":\"CROSS_BACKEND_HANDOFF\",\"status\":\"NOT_APPLICABLE\"}],";
     if (D.mat >= 0) {
       const MatNode &M = P->mats[D.mat];
       s += strf("\"artifact\":{\"kind\":\"%s\",\"exactness\":\"EXACT\",\"provenance_sha256\":\"%s\","
-                "\"backend\":\"%s\",\"bytes\":%llu,\"qubits\":%u,\"prefix_gates\":%llu},",
+                "\"backend\":\"%s\",\"bytes\":%llu,\"qubits\":%u,\"prefix_gates\":%llu,",
                 kind_name(M.mode == QW_MODE_TABLEAU ? QW_KIND_TABLEAU : QW_KIND_STATEVECTOR),
                 hex32(M.provenance).c_str(), backend_name(backend_of_mode(M.mode)),
                 (unsigned long long)M.bytes, M.n, (unsigned long long)M.end);
+      s += "\"exported_to\":[";
+      bool first_e = true;
+      for (uint32_t md = 0; md < 2; md++)
+        if ((M.export_modes >> md) & 1u) {
+          s += strf("%s\"%s\"", first_e ? "" : ",", backend_name(backend_of_mode(md)));
+          first_e = false;
+        }
+      s += "]},";
     } else {
       s += "\"artifact\":null,";
     }

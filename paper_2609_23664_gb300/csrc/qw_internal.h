@@ -359,6 +359,19 @@ struct FrameArgs {
 cudaError_t frame_init_attrs();
 void launch_frames(const FrameArgs &a, void *stream);
 
+// tableau -> statevector export (n <= QW_SV_MAX_QUBITS): echelon stabilizer
+// basis of the state, then one pass writing every amplitude
+struct StabBasis {
+  uint32_t n, k, err, pad;  // err != 0: the tableau did not describe a valid state
+  uint64_t x0;              // a basis state in the support
+  uint64_t gx[QW_SV_MAX_QUBITS], gz[QW_SV_MAX_QUBITS];  // echelon generators i^ge X^gx Z^gz
+  uint32_t ge[QW_SV_MAX_QUBITS];
+  uint8_t piv[QW_SV_MAX_QUBITS];                        // pivot bit of each generator
+};
+// tableau: 2n rows of (x, z) words followed by 2n sign bytes (n <= 30)
+void launch_stab_export(const void *tableau, uint32_t n, StabBasis *basis, bool fp64, uint32_t n_eff, void *dst,
+                        int sm_count, void *stream);
+
 // learned cost model
 void launch_mlp_forward(const float *params, const float *x, float *y, uint32_t batch, void *stream);
 void launch_mlp_loss_grad(const float *params, const float *x, const float *target, uint32_t batch,

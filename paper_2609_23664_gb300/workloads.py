@@ -155,6 +155,42 @@ def random_circuit(rng: np.random.Generator, n: int, n_gates: int) -> np.ndarray
     return gates_from_list(g)
 
 
+def random_clifford_layers(rng: np.random.Generator, n: int, depth: int) -> np.ndarray:
+    """`depth` layers: a 1q Clifford uniform over {H, S, SDG, X, Y, Z} on
+    every qubit, then CNOT or CZ (equal odds) on a random perfect matching
+    of the qubits (one qubit idle when n is odd)."""
+    ones = (OP_H, OP_S, OP_SDG, OP_X, OP_Y, OP_Z)
+    g = []
+    for _ in range(depth):
+        for q in range(n):
+            g.append((ones[int(rng.integers(0, 6))], q, 0, 0.0))
+        perm = rng.permutation(n)
+        for i in range(0, n - 1, 2):
+            op = OP_CNOT if rng.random() < 0.5 else OP_CZ
+            g.append((op, int(perm[i]), int(perm[i + 1]), 0.0))
+    return gates_from_list(g)
+
+
+def handoff_family(seed: int = BASE_SEED + 6, n: int = 16, clifford_depth: int = 200,
+                   n_tasks: int = 32, suffix_gates: int = 60, n_terms: int = 40,
+                   mode: int = MODE_SV_FP32) -> List[Task]:
+    """Statevector tasks sharing a deep all-Clifford prefix (random Clifford
+    layers, the stabilizer rounds of an error-correction experiment) followed
+    by each task's own non-Clifford suffix (random circuit with rotations),
+    each with an energy: the tableau-to-statevector handoff family."""
+    rng = np.random.default_rng(seed)
+    prefix = random_clifford_layers(rng, n, clifford_depth)
+    terms = random_pauli_hamiltonian(rng, n, n_terms)
+    tasks = []
+    for _ in range(n_tasks):
+        suf = random_circuit(rng, n, suffix_gates)
+        # the suffix starts with a rotation, so the shared Clifford run ends
+        # exactly at the prefix
+        rot = gates_from_list([(OP_RY, int(rng.integers(0, n)), 0, float(rng.uniform(0.1, 3.0)))])
+        tasks.append(Task(mode=mode, n=n, spans=[prefix, rot, suf], terms=terms))
+    return tasks
+
+
 _PAULI_OPS = (None, OP_X, OP_Y, OP_Z)
 
 

@@ -278,6 +278,68 @@ def test_pauli_frames_fall_back_when_a_reference_outcome_is_random(eng):
         assert np.array_equal(p.syndrome(i), orc.tab_run(t.n, t.gates)), i
 
 
+def phase_aligned_error(got, ref):
+    # exported states carry a canonical global phase: align it, then compare
+    k = int(np.argmax(np.abs(ref)))
+    ph = ref[k] / got[k]
+    return float(np.max(np.abs(got * ph / abs(ph) - ref)))
+
+
+@pytest.mark.parametrize("mode,n", [(W.MODE_SV_FP64, 16), (W.MODE_SV_FP32, 18)])
+def test_tableau_handoff_to_statevector(eng, mode, n):
+    # deep Clifford prefix on the tableau, exported once (Table II STAB -> SV),
+    # non-Clifford suffixes on the statevector: energies and states vs oracle
+    tasks = W.handoff_family(n=n, clifford_depth=200, n_tasks=5, suffix_gates=40, mode=mode)
+    for t in tasks[:2]:
+        t.want_state = True
+    p, wl = run_plan(eng, tasks)
+    d = p.explain()["decisions"][0]
+    alt = {a["plan"]: a for a in d["alternatives"]}
+    assert alt["CROSS_BACKEND_HANDOFF"]["est_ns"] < alt["SAME_FAMILY_REUSE"]["est_ns"]
+    assert d["artifact"]["kind"] == "TABLEAU_BOUNDARY_STATE" and d["artifact"]["exported_to"]
+    fp64 = mode == W.MODE_SV_FP64
+    for i, t in enumerate(tasks):
+        ref = orc.run_task(t, want_state=i < 2)
+        e, nr = p.energy(i)
+        c1 = float(np.sum(np.abs(t.terms["coef"])))
+        assert abs(e - ref["energy"]) <= (1e-12 * max(1.0, abs(ref["energy"])) if fp64 else 2e-5 * c1), i
+        assert abs(nr - 1.0) < (1e-12 if fp64 else 1e-5)
+        if i < 2:
+            got = p.state(i, n, fp64).astype(np.complex128)
+            assert phase_aligned_error(got, ref["state"]) <= (1e-12 if fp64 else 1e-5)
+    # the same workload without the handoff (statevector prefix) agrees
+    q, wl2 = run_plan(eng, tasks, handoff=0)
+    assert q.explain()["decisions"][0]["artifact"]["kind"] == "STATEVECTOR_BOUNDARY_STATE"
+    for i in range(len(tasks)):
+        assert abs(p.energy(i)[0] - q.energy(i)[0]) <= (1e-12 if fp64 else 1e-5)
+
+
+def test_tableau_boundary_serves_stabilizer_and_statevector_tasks(eng):
+    # a Clifford prefix shared by tableau tasks (majority) and statevector
+    # tasks: one tableau boundary, exported for the statevector consumers
+    rng = np.random.default_rng(5)
+    n = 10
+    pre = W.random_clifford_layers(rng, n, 30)
+    terms = W.random_pauli_hamiltonian(rng, n, 20)
+    tasks = []
+    for i in range(6):
+        suf = W.gates_from_list([(W.OP_H, i, 0), (W.OP_CNOT, i, (i + 1) % n),
+                                 (W.OP_MEASURE, i, 0, float(i & 1)), (W.OP_MEASURE, (i + 3) % n, 0, 0.0)])
+        tasks.append(W.Task(mode=W.MODE_TABLEAU, n=n, spans=[pre, suf]))
+    for i in range(3):
+        suf = W.random_circuit(rng, n, 25)
+        tasks.append(W.Task(mode=W.MODE_SV_FP64, n=n, spans=[pre, suf], terms=terms))
+    p, wl = run_plan(eng, tasks)
+    arts = [d["artifact"] for d in p.explain()["decisions"] if d["artifact"]]
+    assert any(a["kind"] == "TABLEAU_BOUNDARY_STATE" and "GPU_SV_FP64" in a["exported_to"] for a in arts)
+    for i, t in enumerate(tasks):
+        if t.mode == W.MODE_TABLEAU:
+            assert np.array_equal(p.syndrome(i), orc.tab_run(t.n, t.gates)), i
+        else:
+            ref = orc.run_task(t)
+            assert abs(p.energy(i)[0] - ref["energy"]) <= 1e-12 * max(1.0, abs(ref["energy"])), i
+
+
 def test_config4_qec_replay_bit_exact(eng):
     tasks = W.config4_qec(d=3, shared_rounds=4, task_rounds=2, n_tasks=16, p=0.05)
     p, wl = run_plan(eng, tasks, reuse=0)

@@ -69,15 +69,15 @@ def test_legality_matrix_table2():
     prov = hashlib.sha256(b"prefix").digest()
     for row in gold["rows"]:
         exact = 1 if row.get("exactness") == "FORBIDDEN" else 0
-        ok, ref = Q.legality_check(KIND[row["kind"]], exact, BK[row["source_backend"]], 7, prov,
-                                   BK[row["target_backend"]], prov)
+        ok, ref = Q.legality_check(KIND[row["kind"]], exact, BK[row["source_backend"]],
+                                   row.get("n_qubits", 7), prov, BK[row["target_backend"]], prov)
         if row["outcome"] == "EXACT":
             assert ok and ref["reason"] == "", row
         else:
             assert not ok, row
             assert ref["reason"], row
             assert set(ref) == set(gold["refusal_fields"])
-            if row["outcome"] == "EXACT_NOT_IMPLEMENTED":
+            if "cap" in row["case"]:
                 assert ref["reason"] == "UNSUPPORTED_CONVERSION"
     # the paper's example reason for a forbidden statevector handoff
     ok, ref = Q.legality_check(0, 0, BK["GPU_SV_FP32"], 7, prov, BK["GPU_TABLEAU"], prov)
@@ -234,6 +234,33 @@ def test_tableau_workload_shares_the_prefix_span():
     assert top["decision"] == "REUSE"
     assert top["artifact"]["kind"] == "TABLEAU_BOUNDARY_STATE"
     assert top["branch_gate"] >= len(tasks[0].spans[0])
+
+
+def test_clifford_prefix_is_run_on_the_tableau_and_exported():
+    # Table II STAB -> SV: statevector tasks sharing a deep Clifford prefix
+    tasks = W.handoff_family(n=16, clifford_depth=200, n_tasks=16)
+    p, ex, wl = host_plan(tasks)
+    (d,) = ex["decisions"]
+    assert d["decision"] == "REUSE"
+    art = d["artifact"]
+    assert art["kind"] == "TABLEAU_BOUNDARY_STATE" and art["exported_to"] == ["GPU_SV_FP32"]
+    assert art["prefix_gates"] == len(tasks[0].spans[0])     # the whole Clifford run
+    chosen = [c for c in d["candidates"] if c["chosen"]]
+    assert chosen[0]["boundary"] == "TABLEAU_HANDOFF" and chosen[0]["inequality_holds"]
+    alt = {a["plan"]: a for a in d["alternatives"]}
+    assert alt["CROSS_BACKEND_HANDOFF"]["chosen"]
+    assert alt["CROSS_BACKEND_HANDOFF"]["est_ns"] < alt["SAME_FAMILY_REUSE"]["est_ns"]
+    # switched off: the same prefix as a statevector boundary
+    _, ex0, _ = host_plan(tasks, handoff=0)
+    assert ex0["decisions"][0]["artifact"]["kind"] == "STATEVECTOR_BOUNDARY_STATE"
+    # a non-Clifford gate inside the shared prefix: no handoff
+    t2 = W.handoff_family(n=16, clifford_depth=40, n_tasks=8)
+    rot = W.gates_from_list([(W.OP_T, 3, 0)])
+    for t in t2:
+        t.spans = [t.spans[0][:100], rot, t.spans[0][100:]] + t.spans[1:]
+    _, ex2, _ = host_plan(t2)
+    assert all(c["boundary"] != "TABLEAU_HANDOFF" or c["cut_gate"] <= 100
+               for d in ex2["decisions"] for c in d["candidates"])
 
 
 def test_full_size_qec_planning_is_fast():
