@@ -1086,6 +1086,7 @@ void build_plan(qw_plan *P, Engine *E, const Workload &W) {
                 kind_name(M.mode == QW_MODE_TABLEAU ? QW_KIND_TABLEAU : QW_KIND_STATEVECTOR),
                 hex32(M.provenance).c_str(), backend_name(backend_of_mode(M.mode)),
                 (unsigned long long)M.bytes, M.n, (unsigned long long)M.end);
+      s += strf("\"id\":%d,\"parent\":%d,\"first_gate\":%llu,", D.mat, M.parent, (unsigned long long)M.begin);
       s += "\"exported_to\":[";
       bool first_e = true;
       for (uint32_t md = 0; md < 2; md++)

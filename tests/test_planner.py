@@ -263,6 +263,20 @@ def test_clifford_prefix_is_run_on_the_tableau_and_exported():
                for d in ex2["decisions"] for c in d["candidates"])
 
 
+def test_noisy_trajectories_reuse_nested_boundaries():
+    # multi-level reuse: trajectories share the error-free chain, then
+    # sub-groups share mid-segments up to later branch points; every nested
+    # boundary continues from its parent's (first_gate = parent's end)
+    tasks = W.config3_noisy22(n=10, n_gates=120, n_traj=64, p=0.02, shots=4)
+    p, ex, wl = host_plan(tasks)
+    arts = {d["artifact"]["id"]: d["artifact"] for d in ex["decisions"] if d["artifact"]}
+    nested = [a for a in arts.values() if a["parent"] >= 0]
+    assert len(arts) >= 3 and nested
+    for a in nested:
+        assert a["first_gate"] == arts[a["parent"]]["prefix_gates"]
+        assert a["prefix_gates"] > a["first_gate"]
+
+
 def test_full_size_qec_planning_is_fast():
     tasks = W.config4_qec()                  # 449 qubits, 100 + 5 rounds, 4096 tasks
     t0 = time.perf_counter()
