@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
+from paper_2609_23664_gb300 import replicas as R  # noqa: E402
 from paper_2609_23664_gb300 import workloads as W  # noqa: E402
 
 METRIC = "workload tasks/s: reuse+batched vs per-task replay, same GB300; HBM % of peak"
@@ -57,8 +58,8 @@ def parse_args():
     ap.add_argument("--no-replay", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-tasks", type=int, default=1)
-    ap.add_argument("--qec-steps", type=int, default=5,
-                    help="also time the QEC family (d=15, 4096 tasks, stabilizer); 0 = skip")
+    ap.add_argument("--qec-steps", type=int, default=3,
+                    help="also time the QEC, noisy and small-VQE families (steps each); 0 = skip")
     ap.add_argument("--fuse-energy", type=int, default=0,
                     help="1: energy blocks as work items of the persistent suffix launch")
     ap.add_argument("--tile-qubits", type=int, default=0, help="0: autotuned")
@@ -74,7 +75,7 @@ def workload_desc(a):
 
 
 def make_tasks(a, rank):
-    return W.config2_vqe24(seed=W.BASE_SEED + 2 + 1000 * rank, n=a.qubits,
+    return W.config2_vqe24(seed=R.rank_seed(W.BASE_SEED + 2, rank), n=a.qubits,
                            prefix_layers=a.prefix_layers, n_tasks=a.tasks, n_terms=a.terms)
 
 
@@ -168,26 +169,15 @@ def profiled_traffic(kernel: str, workload_key: str):
 
 
 def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    return R.env_ranks()
 
 
 def max_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return R.max_over_ranks(x, world, "cuda")
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    R.barrier(world)
 
 
 # ---- CPU oracle (reference arm and cpu_baseline) -------------------------------------
@@ -240,9 +230,8 @@ def run_native(a):
     import torch
     world, rank, local = dist_setup()
     if world > 1:
-        import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        R.init(world, "nccl", device=torch.device("cuda", local))
     torch.cuda.set_device(local)
     from paper_2609_23664_gb300 import quwarp as Q
 
@@ -280,7 +269,7 @@ def run_native(a):
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1) / a.steps
     ms_max = max_over_ranks(ms, world)
-    value = world * n_tasks / (ms_max / 1e3)
+    value = R.whole_job_rate(n_tasks, world, ms_max)
     cr = recs[-1]
     launches = int(cr["kernel_launches"])
     suffix_ms = statistics.mean(r["suffix_ms"] for r in recs)
@@ -382,34 +371,48 @@ def run_native(a):
                        "includes": "workload submission, planning, device allocation, upload, "
                                    "execution, read-back of all energies"}
 
-    # the stabilizer family (QEC d=15, 4096 tasks): Pauli frames over the
-    # shared reference vs every task on its own tableau, same GPU
+    # the other workload families of the paper's evaluation, same GPU:
+    # the planned execution vs a comparison plan (same kernels)
     if a.qec_steps > 0 and world == 1:
-        qt = W.config4_qec()
-        qwl = Q.Workload(qt)
-        qec = {"workload": "qec_d15: rotated surface code, 449 qubits, 100 shared + 5 task rounds, "
-                           "4096 tasks, data X/Z errors p=1e-3"}
-        for key, opts in (("pauli_frames", dict(pauli_frames=1)), ("per_task_tableau", dict(pauli_frames=0))):
-            qp = Q.Plan(eng, qwl, **opts)
-            qp.execute(sptr)
-            qp.wait()
+        fams = line["families"] = {}
+
+        def time_plan(wl, units, opts):
+            fp = Q.Plan(eng, wl, **opts)
+            fp.execute(sptr)
+            fp.wait()
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(a.qec_steps):
-                qp.execute(sptr)
-                qp.wait()
+                fp.execute(sptr)
+                fp.wait()
             e1.record(stream)
             torch.cuda.synchronize()
-            qms = e0.elapsed_time(e1) / a.qec_steps
-            qcr = qp.cost_record()
-            qec[key] = {"value": len(qt) / (qms / 1e3), "unit": "tasks/s", "ms_per_step": qms,
-                        "prefix_ms": qcr["prefix_ms"], "tasks_ms": qcr["tableau_tasks_ms"],
-                        "kernel_launches": qcr["kernel_launches"], "artifacts": qcr["artifacts"]}
-            qp.close()
-        line["qec"] = qec
-        qwl.close()
+            fms = e0.elapsed_time(e1) / a.qec_steps
+            fcr = fp.cost_record()
+            fp.close()
+            return {"value": units / (fms / 1e3), "unit": "tasks/s", "ms_per_step": fms,
+                    "kernel_launches": fcr["kernel_launches"], "artifacts": fcr["artifacts"]}
+
+        for key, desc, gen, plans in (
+                ("qec_d15", "rotated surface code, 449 qubits, 100 shared + 5 task rounds, 4096 tasks, "
+                            "data X/Z errors p=1e-3 (stabilizer)", W.config4_qec,
+                 (("pauli_frames", dict(pauli_frames=1)), ("per_task_tableau", dict(pauli_frames=0)))),
+                ("noisy22", "22 qubits, 400-gate random circuit, 1024 Pauli-noise trajectories "
+                            "(p=1e-3), 100 shots each (FP32)", W.config3_noisy22,
+                 (("reuse", {}), ("per_task_replay", dict(reuse=0, batched=0)))),
+                ("vqe12_fp64", "12 qubits, 6-layer HEA prefix, 16 tasks x final RY+RZ layer, 20-term "
+                               "energy (FP64)", W.config1_vqe12,
+                 (("reuse", {}), ("per_task_replay", dict(reuse=0, batched=0))))):
+            ft = gen()
+            fwl = Q.Workload(ft)
+            fams[key] = {"workload": desc}
+            for pk, opts in plans:
+                fams[key][pk] = time_plan(fwl, len(ft), opts)
+            ks = [pk for pk, _ in plans]
+            fams[key]["speedup"] = fams[key][ks[0]]["value"] / fams[key][ks[1]]["value"]
+            fwl.close()
 
     line["roofline"] = roofline
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -423,9 +426,7 @@ def run_native(a):
                                                       tasks[0].n_gates, a.terms, dt)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    R.finish(world)
     return 0
 
 
