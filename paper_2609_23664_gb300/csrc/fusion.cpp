@@ -123,12 +123,13 @@ static void greedy_groups(const std::vector<uint32_t> &masks, const std::vector<
 }
 
 namespace {
-// FP32 operations per amplitude pair of each register-op kind
+// FP32 instructions per amplitude pair of each register-op kind (a real
+// rotation uses packed two-lane FMAs)
 int kind_cost(uint8_t k) {
   switch (k) {
     case K_U1: return 16;
-    case K_D1: case K_R: case K_RX: return 8;
-    case K_P1: return 4;
+    case K_D1: case K_RX: case K_RP: return 8;
+    case K_R: case K_P1: return 4;
     default: return 16;
   }
 }
@@ -265,6 +266,19 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
             m[0] = 1; m[1] = 0; m[6] = r.real(); m[7] = r.imag();
           }
           const uint8_t kn = classify(m);
+          if (last1q[a] >= 0 && hs.ops[last1q[a]].kind == K_R && kn == K_P1) {
+            // diag(1, p) after a real rotation: one op, its factors kept exact
+            HostOp &prev = hs.ops[last1q[a]];
+            double out[8];
+            mat_mul(m, prev.m, out);
+            prev.x[0] = prev.m[4];
+            prev.x[1] = prev.m[6];
+            prev.x[2] = m[6];
+            prev.x[3] = m[7];
+            std::memcpy(prev.m, out, sizeof(out));
+            prev.kind = K_RP;
+            continue;
+          }
           if (last1q[a] >= 0) {
             HostOp &prev = hs.ops[last1q[a]];
             double out[8];
@@ -330,6 +344,12 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
         if (o.kind == K_D1) { o.m[2] = o.m[6]; o.m[3] = o.m[7]; }
         if (o.kind == K_P1) { o.m[0] = o.m[6]; o.m[1] = o.m[7]; }
         if (o.kind == K_RX) { o.m[1] = -o.m[3]; }  // m[0] = c, m[1] = s (matrix [[c,-is],[-is,c]])
+        if (o.kind == K_RP) {  // {r00, r01, r10, r11, pr, pi}
+          const double r00 = o.m[0], r01 = o.m[2];
+          o.m[0] = r00; o.m[1] = r01;
+          o.m[2] = o.x[0]; o.m[3] = o.x[1]; o.m[4] = o.x[2]; o.m[5] = o.x[3];
+          o.m[6] = 0; o.m[7] = 0;
+        }
       }
   return prog;
 }

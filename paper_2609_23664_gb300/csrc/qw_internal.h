@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "quwarp.h"
 
 #ifdef __CUDACC__
@@ -70,13 +72,14 @@ enum SvKind : uint8_t {
   K_P1 = 6,    // diag(1, p) on a: m = {pr, pi}
   K_R = 7,     // real 2x2 on a: m = {r00, 0, r01, 0, r10, 0, r11, 0}
   K_RX = 8,    // [[c, -is], [-is, c]] on a: m = {c, s}
+  K_RP = 9,    // diag(1, p) after a real 2x2 on a: m = {r00, r01, r10, r11, pr, pi}
 };
 constexpr int SV_G = 5;            // positions per stage (32 register amplitudes)
 
 // Dense index of an op for the kernels' jump table: each one-position kind
 // takes SV_G consecutive slots (its stage position), the controlled phase
 // the ten position pairs a < b.
-constexpr uint32_t SV_N_OP_INDEX = 35;
+constexpr uint32_t SV_N_OP_INDEX = 40;
 __host__ __device__ constexpr uint32_t sv_op_index(uint32_t kind, uint32_t a, uint32_t b) {
   return kind == K_U1   ? a
          : kind == K_D1 ? 5 + a
@@ -84,6 +87,7 @@ __host__ __device__ constexpr uint32_t sv_op_index(uint32_t kind, uint32_t a, ui
          : kind == K_R  ? 15 + a
          : kind == K_RX ? 20 + a
          : kind == K_CD ? 25 + a * (9 - a) / 2 + (b - a - 1)
+         : kind == K_RP ? 35 + a
                         : SV_N_OP_INDEX;
 }
 constexpr int SV_MAX_TILE_FP32 = 14;
@@ -92,6 +96,7 @@ constexpr int SV_MAX_TILE_FP64 = 13;
 struct HostOp {
   uint8_t kind, a, b;
   double m[8];
+  double x[4] = {0, 0, 0, 0};  // K_RP: r10, r11, pr, pi (exact factors of row 1 of m)
 };
 struct HostStage {
   uint8_t pos[SV_G];  // local tile bit positions (distinct)

@@ -132,6 +132,49 @@ __device__ __forceinline__ void op_r_any<float2, float, 3>(float2 (&a)[32], cons
 template <>
 __device__ __forceinline__ void op_r_any<float2, float, 4>(float2 (&a)[32], const float (&m)[8]) { op_r_f2<4>(a, m); }
 
+// diag(1, p) after the real 2x2 {r00, r01; r10, r11}: m = {r00, r01, r10, r11, pr, pi}
+template <typename C, typename T, int P>
+__device__ __forceinline__ void op_rp(C (&a)[32], const T (&m)[8]) {
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    if (i & (1 << P)) continue;
+    const int j = i | (1 << P);
+    const C x = a[i], y = a[j];
+    a[i].x = m[0] * x.x + m[1] * y.x;
+    a[i].y = m[0] * x.y + m[1] * y.y;
+    const T tx = m[2] * x.x + m[3] * y.x, ty = m[2] * x.y + m[3] * y.y;
+    a[j].x = m[4] * tx - m[5] * ty;
+    a[j].y = m[4] * ty + m[5] * tx;
+  }
+}
+template <int P>
+__device__ __forceinline__ void op_rp_f2(float2 (&a)[32], const float (&m)[8]) {
+  const float2 m0 = make_float2(m[0], m[0]), m1 = make_float2(m[1], m[1]);
+  const float2 m2 = make_float2(m[2], m[2]), m3 = make_float2(m[3], m[3]);
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    if (i & (1 << P)) continue;
+    const int j = i | (1 << P);
+    const float2 x = a[i], y = a[j];
+    a[i] = __ffma2_rn(m1, y, __fmul2_rn(m0, x));
+    const float2 t = __ffma2_rn(m3, y, __fmul2_rn(m2, x));
+    a[j].x = m[4] * t.x - m[5] * t.y;
+    a[j].y = m[4] * t.y + m[5] * t.x;
+  }
+}
+template <typename C, typename T, int P>
+__device__ __forceinline__ void op_rp_any(C (&a)[32], const T (&m)[8]) { op_rp<C, T, P>(a, m); }
+template <>
+__device__ __forceinline__ void op_rp_any<float2, float, 0>(float2 (&a)[32], const float (&m)[8]) { op_rp_f2<0>(a, m); }
+template <>
+__device__ __forceinline__ void op_rp_any<float2, float, 1>(float2 (&a)[32], const float (&m)[8]) { op_rp_f2<1>(a, m); }
+template <>
+__device__ __forceinline__ void op_rp_any<float2, float, 2>(float2 (&a)[32], const float (&m)[8]) { op_rp_f2<2>(a, m); }
+template <>
+__device__ __forceinline__ void op_rp_any<float2, float, 3>(float2 (&a)[32], const float (&m)[8]) { op_rp_f2<3>(a, m); }
+template <>
+__device__ __forceinline__ void op_rp_any<float2, float, 4>(float2 (&a)[32], const float (&m)[8]) { op_rp_f2<4>(a, m); }
+
 // [[c, -is], [-is, c]] with c = m0, s = m1
 template <typename C, typename T, int P>
 __device__ __forceinline__ void op_rx(C (&a)[32], const T (&m)[8]) {
@@ -184,6 +227,9 @@ __device__ __forceinline__ void apply_op(uint32_t code, const T (&m)[8], C (&a)[
 #define CD(x, y) case sv_op_index(K_CD, x, y): op_cd<C, T, x, y>(a, m); break;
     CD(0, 1) CD(0, 2) CD(0, 3) CD(0, 4) CD(1, 2) CD(1, 3) CD(1, 4) CD(2, 3) CD(2, 4) CD(3, 4)
 #undef CD
+#define RP(P) case sv_op_index(K_RP, P, 0): op_rp_any<C, T, P>(a, m); break;
+    RP(0) RP(1) RP(2) RP(3) RP(4)
+#undef RP
     default: break;
   }
 }
