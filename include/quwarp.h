@@ -206,12 +206,19 @@ typedef struct qw_plan_opts {
                                  exported state's global phase is fixed by a positive real
                                  amplitude on the first basis state of its support.
                                  0 = never.  Default 1. */
+  int32_t prefix_fp64;        /* 1 = a shared prefix of FP32 statevector tasks (up to 28
+                                 qubits) is evolved in FP64 and rounded once to FP32 for
+                                 them: the boundary's error then does not grow with the
+                                 prefix length (an FP64 artifact is exact for an FP32
+                                 consumer up to that one rounding), at the cost of FP64
+                                 arithmetic for the prefix.  0 = the prefix runs in FP32.
+                                 Default 0. */
 } qw_plan_opts;
 
 /* Fills the defaults: reuse=1, batched=1, legality=1, analytic costs,
  * delta_frac=0.10, min_group=2, min_prefix_gates=1, min_prefix_cost_ns=0,
  * autotuned tiles, use_graph=1, fault_injection=0, fuse_energy=0, pauli_frames=1,
- * handoff=1. */
+ * handoff=1, prefix_fp64=0. */
 void qw_plan_opts_default(qw_plan_opts *o);
 
 typedef struct qw_plan qw_plan;

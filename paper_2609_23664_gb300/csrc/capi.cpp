@@ -191,6 +191,7 @@ void qw_plan_opts_default(qw_plan_opts *o) {
   o->fuse_energy = 0;
   o->pauli_frames = 1;
   o->handoff = 1;
+  o->prefix_fp64 = 0;
 }
 
 qw_status qw_plan_create(qw_engine *e, const qw_workload *w, const qw_plan_opts *o, qw_plan **out) {

@@ -330,14 +330,21 @@ static void prepare(qw_plan *P) {
       }
     } else {
       D->mat_buf[m] = D->arena.alloc(sv_state_bytes(M.mode == QW_MODE_SV_FP64, M.n_eff));
+      // lower-precision copy for the consumers of another precision
+      for (uint32_t md = 0; md < 2; md++)
+        if (md != M.mode && ((M.export_modes >> md) & 1u))
+          D->mat_export[md][m] = D->arena.alloc(sv_state_bytes(md == QW_MODE_SV_FP64, M.n_eff));
     }
   }
-  // the state a statevector consumer of node m reads (the node itself, or its export)
+  // the state a statevector consumer of node m reads (the node itself, or its
+  // export into the consumer's precision)
   auto sv_source = [&](int m, uint32_t mode) -> void * {
-    return P->mats[m].mode == QW_MODE_TABLEAU ? D->mat_export[mode][m] : D->mat_buf[m];
+    if (P->mats[m].mode == mode) return D->mat_buf[m];
+    return D->mat_export[mode][m] ? D->mat_export[mode][m] : D->mat_buf[m];
   };
   auto needs_convert = [&](const TaskPlan &tp) {
-    return tp.src >= 0 && P->mats[tp.src].mode != QW_MODE_TABLEAU && P->mats[tp.src].mode != tp.mode;
+    return tp.src >= 0 && P->mats[tp.src].mode != QW_MODE_TABLEAU && P->mats[tp.src].mode != tp.mode &&
+           !D->mat_export[tp.mode][tp.src];
   };
 
   // Hamiltonians
@@ -747,17 +754,25 @@ static void enqueue(qw_plan *P, cudaStream_t s, bool capturing) {
     if (M.parent >= 0) {
       const MatNode &PM = P->mats[M.parent];
       if (PM.mode == M.mode) psrc = D->mat_buf[M.parent];
-      else if (PM.mode == QW_MODE_TABLEAU) psrc = D->mat_export[M.mode][M.parent];
+      else psrc = D->mat_export[M.mode][M.parent];
     }
     if (M.sv.passes.empty()) {
       if (psrc) launch_copy(psrc, D->mat_buf[m], sv_state_bytes(fp64, M.n_eff), s);
-      continue;
+    } else {
+      nl += M.sv.passes.size();
+      for (size_t p = 0; p < M.sv.passes.size(); p++) {
+        launch_sv_pass(fp64, T, D->mat_pass0[m] + (uint32_t)p, (uint32_t)M.sv.passes[p].q.size(), M.n_eff,
+                       p == 0 ? psrc : D->mat_buf[m], D->mat_buf[m], s);
+      }
     }
-    nl += M.sv.passes.size();
-    for (size_t p = 0; p < M.sv.passes.size(); p++) {
-      launch_sv_pass(fp64, T, D->mat_pass0[m] + (uint32_t)p, (uint32_t)M.sv.passes[p].q.size(), M.n_eff,
-                     p == 0 ? psrc : D->mat_buf[m], D->mat_buf[m], s);
-    }
+    // the boundary rounded once into the other precision its consumers use
+    for (uint32_t md = 0; md < 2; md++)
+      if (md != M.mode && D->mat_export[md][m]) {
+        const size_t n = (size_t)1 << M.n_eff;
+        convert_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(D->mat_buf[m], fp64, D->mat_export[md][m],
+                                                                  md == QW_MODE_SV_FP64, n);
+        nl += 1;
+      }
   }
   CK(rec(D->ev[1]));
   // 2) task suffixes, observables

@@ -230,7 +230,10 @@ bool legality(const qw_artifact_desc &a, uint32_t tb, const uint8_t *expected, q
                  a.kind, tk, a.backend, tb);
     return false;
   }
-  if (a.kind == QW_KIND_STATEVECTOR && a.backend != tb) {
+  // a higher-precision statevector serves a lower-precision consumer (it is
+  // rounded once to the consumer's precision); the reverse is not exact
+  if (a.kind == QW_KIND_STATEVECTOR && a.backend != tb &&
+      !(a.backend == QW_BACKEND_GPU_SV_FP64 && tb == QW_BACKEND_GPU_SV_FP32)) {
     fill_refusal(out, "FORBIDDEN_CONVERSION",
                  "statevector precision differs: the artifact is not exact for the consuming precision",
                  a.kind, tk, a.backend, tb);
@@ -680,8 +683,17 @@ static void decide(PlanCtx &C) {
           }
         }
         const bool handoff = D.chosen >= 0 && D.cands[D.chosen].kind == 3;
-        const uint32_t prod = handoff ? (uint32_t)QW_MODE_TABLEAU : pm;
-        const double S_store = handoff ? PlanCtx::state_bytes(QW_MODE_TABLEAU, V.n) + S_sv : S;
+        // shared prefixes of FP32 tasks are evolved in FP64 and rounded once
+        // (their error no longer grows with the prefix length)
+        // Up to 28 qubits (a 4 GiB FP64 boundary plus its 2 GiB copy), and
+        // only where both fit the store budget; larger registers keep FP32
+        // boundaries, whose memory decides how many the store admits.
+        bool up64 = !handoff && pm == QW_MODE_SV_FP32 && P->opts.prefix_fp64 && V.n <= 28;
+        if (up64 && C.store_used + (uint64_t)(PlanCtx::state_bytes(QW_MODE_SV_FP64, V.n) + S) > C.store_budget)
+          up64 = false;
+        const uint32_t prod = handoff ? (uint32_t)QW_MODE_TABLEAU : (up64 ? (uint32_t)QW_MODE_SV_FP64 : pm);
+        const double S_store = handoff ? PlanCtx::state_bytes(QW_MODE_TABLEAU, V.n) + S_sv
+                                       : (up64 ? PlanCtx::state_bytes(QW_MODE_SV_FP64, V.n) + S : S);
         if (D.chosen < 0) {
           D.decision = 1;
           D.reason = (V.below < P->opts.min_group) ? "EARLY_FILTER_GROUP_SIZE" : "NOT_PROFITABLE";
@@ -701,7 +713,7 @@ static void decide(PlanCtx &C) {
           M.n = V.n;
           M.n_eff = (prod == QW_MODE_TABLEAU) ? V.n : std::max<uint32_t>(V.n, SV_G);
           M.bytes = (uint64_t)S_store;
-          if (handoff) M.export_modes = 1u << pm;
+          if (handoff || up64) M.export_modes = 1u << pm;
           // Eq. 1 over [0, end): continued from the parent's state (the
           // tasks below V share the parent's gates [0, parent end))
           Sha256 sh;
@@ -910,14 +922,15 @@ void build_plan(qw_plan *P, Engine *E, const Workload &W) {
     // an artifact of another mode is usable only through the bypass, or as
     // a tableau boundary exported to the task's statevector (Table II)
     auto usable = [&](int m) {
-      if (P->mats[m].mode == T.mode || tp.legality_bypassed) return true;
-      return T.mode != QW_MODE_TABLEAU && P->mats[m].mode == QW_MODE_TABLEAU && T.n <= QW_SV_MAX_QUBITS &&
-             P->opts.handoff;
+      const uint32_t mm = P->mats[m].mode;
+      if (mm == T.mode || tp.legality_bypassed) return true;
+      if (T.mode == QW_MODE_SV_FP32 && mm == QW_MODE_SV_FP64) return true;  // rounded once
+      return T.mode != QW_MODE_TABLEAU && mm == QW_MODE_TABLEAU && T.n <= QW_SV_MAX_QUBITS && P->opts.handoff;
     };
     while (src >= 0 && !usable(src)) src = P->mats[src].parent;
     tp.src = src;
     tp.begin = (src >= 0) ? P->mats[src].end : 0;
-    if (src >= 0 && P->mats[src].mode == QW_MODE_TABLEAU && T.mode != QW_MODE_TABLEAU)
+    if (src >= 0 && P->mats[src].mode != T.mode && T.mode != QW_MODE_TABLEAU && !tp.legality_bypassed)
       P->mats[src].export_modes |= 1u << T.mode;
   }
 

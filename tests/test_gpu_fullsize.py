@@ -23,26 +23,42 @@ def eng():
     e.close()
 
 
-def test_config2_vqe24_full_size_sampled(eng):
+@pytest.mark.parametrize("prefix_fp64", [0, 1])
+def test_config2_vqe24_full_size_sampled(eng, prefix_fp64):
+    # the bench's configuration (FP32 throughout), and the same workload
+    # with the shared prefix in FP64, rounded once for the FP32 suffixes
     tasks = W.config2_vqe24()                     # 24 qubits, 256 tasks, 200 terms
     keep = 5
     tasks[keep].want_state = True
-    plan = Q.Plan(eng, Q.Workload(tasks))
+    plan = Q.Plan(eng, Q.Workload(tasks), prefix_fp64=prefix_fp64)
     plan.run()
     ex = plan.explain()
     assert ex["artifacts"] == 1 and ex["tasks_reusing"] == 256
     for i in (0, keep, 255):
-        ref = orc.run_task(tasks[i], want_state=(i == keep))
+        ref = _oracle(tasks, i, i == keep)
         e, nr = plan.energy(i)
         rel = abs(e - ref["energy"]) / abs(ref["energy"])
-        print("task %d energy %.10e ref %.10e rel %.2e" % (i, e, ref["energy"], rel))
+        print("prefix_fp64 %d task %d energy %.10e ref %.10e rel %.2e" % (prefix_fp64, i, e, ref["energy"], rel))
         assert abs(e - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(tasks[i].terms["coef"])))
+        if prefix_fp64:
+            assert rel <= 1e-6                        # FP32 relative energy tolerance
         assert abs(nr - 1) < 1e-5
         if i == keep:
             st = plan.state(i, 24, False).astype(np.complex128)
             err = float(np.max(np.abs(st - ref["state"])))
             print("task %d max-abs amplitude error %.2e" % (i, err))
             assert err <= 1e-5
+
+
+_ORACLE = {}
+
+
+def _oracle(tasks, i, want_state):
+    # the default 24-qubit workload is the same in both parametrizations
+    key = (i, want_state)
+    if key not in _ORACLE:
+        _ORACLE[key] = orc.run_task(tasks[i], want_state=want_state)
+    return _ORACLE[key]
 
 
 def test_config3_noisy22_full_size_sampled(eng):

@@ -388,6 +388,7 @@ def test_legality_refusal_keeps_exactness_and_disabled_guard_does_not(eng):
         tasks.append(W.Task(mode=mode, n=n, spans=[prefix, rand_gates(rng, n, 10)], terms=ham,
                             want_state=(i == 5)))
     ref = orc.run_task(tasks[5], want_state=True)
+    # FP32 boundary (prefix in the majority's precision): the FP64 task is refused
     p, wl = run_plan(eng, tasks)
     ex = p.explain()
     refs = [r for d in ex["decisions"] for r in d["refusals"]]
@@ -397,6 +398,10 @@ def test_legality_refusal_keeps_exactness_and_disabled_guard_does_not(eng):
     p2, wl2 = run_plan(eng, tasks, legality=0)
     err = np.max(np.abs(p2.state(5, n, True) - ref["state"]))
     assert err > 1e-9   # the unsafe continuation is measurably not exact
+    # FP64 boundary rounded once for the FP32 tasks: the FP64 task reuses it exactly
+    p3, wl3 = run_plan(eng, tasks, prefix_fp64=1)
+    assert [r for d in p3.explain()["decisions"] for r in d["refusals"]] == []
+    assert np.max(np.abs(p3.state(5, n, True) - ref["state"])) <= 1e-12
 
 
 def test_mlp_forward_and_grad_vs_oracle(eng):

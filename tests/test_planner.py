@@ -214,12 +214,19 @@ def test_mixed_precision_group_refuses_minority():
     pre = W.random_circuit(rng, 8, 40)
     tasks = [W.Task(mode=W.MODE_SV_FP32 if i < 3 else W.MODE_SV_FP64, n=8,
                     spans=[pre, W.random_circuit(rng, 8, 5)]) for i in range(4)]
+    # FP32 boundary (prefix in the tasks' precision): the FP64 task is refused
     _, ex, _ = host_plan(tasks)
     d = ex["decisions"][0]
     assert d["decision"] == "REUSE" and d["reason"] == "REUSE_WITH_REFUSALS"
+    assert d["artifact"]["backend"] == "GPU_SV_FP32"
     (r,) = d["refusals"]
     assert r["task"] == 3 and r["reason"] == "FORBIDDEN_CONVERSION" and r["fallback"] == "FULL_RERUN"
     assert ex["tasks_refused"] == 1
+    # FP64 boundary rounded once for the FP32 tasks: every task reuses it
+    _, ex, _ = host_plan(tasks, prefix_fp64=1)
+    d = ex["decisions"][0]
+    assert d["decision"] == "REUSE" and d["refusals"] == [] and ex["tasks_reusing"] == 4
+    assert d["artifact"]["backend"] == "GPU_SV_FP64" and d["artifact"]["exported_to"] == ["GPU_SV_FP32"]
 
 
 def test_reuse_off_plans_per_task_replay():
