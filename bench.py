@@ -146,7 +146,7 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def profiled_traffic(kernel: str, workload_key: str):
+def profiled_traffic(kernel: str, workload_key: str, field: str = "dram"):
     """DRAM bytes per launch from the committed ncu summary, if its source
     hash matches the kernel source compiled now (else None)."""
     import hashlib
@@ -165,6 +165,9 @@ def profiled_traffic(kernel: str, workload_key: str):
     m2 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     if not m1 or not m2 or m1.group(1) != digest:
         return None
+    if field == "lts_pct":
+        m3 = re.search(r"lts__throughput\.avg\.pct_of_peak_sustained_elapsed \| ([0-9.]+)", txt)
+        return float(m3.group(1)) if m3 else None
     return float(m2.group(1))
 
 
@@ -302,7 +305,8 @@ def run_native(a):
                 # L2->SM bytes and rate (no measured L2 peak to divide by)
                 "energy_l2": {"bytes": float(cr.get("energy_l2_bytes", 0.0)),
                               "achieved_gbs": float(cr.get("energy_l2_bytes", 0.0)) / (energy_ms * 1e-3) / 1e9
-                              if energy_ms > 0 else None},
+                              if energy_ms > 0 else None,
+                              "ncu_lts_throughput_pct": profiled_traffic("energy_kernel", wkey, "lts_pct")},
                 "other_kernels_ms": {"sv_batch_kernel": suffix_ms, "energy": energy_ms,
                                      "prefix_passes": prefix_ms}}
 
