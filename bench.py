@@ -186,13 +186,14 @@ def barrier(world):
 # ---- CPU oracle (reference arm and cpu_baseline) -------------------------------------
 
 def oracle_tasks_per_s(a, n_tasks: int):
+    """Times the oracle on the first tasks; returns (tasks/s, seconds,
+    threads, the oracle's energies)."""
     from oracle import oracle as orc
     tasks = make_tasks(a, 0)[:n_tasks]
     t0 = time.perf_counter()
-    for t in tasks:
-        orc.run_task(t)
+    energies = [orc.run_task(t)["energy"] for t in tasks]
     dt = time.perf_counter() - t0
-    return n_tasks / dt, dt, orc.num_threads()
+    return n_tasks / dt, dt, orc.num_threads(), energies
 
 
 def run_reference(a):
@@ -422,7 +423,11 @@ def run_native(a):
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         from oracle import oracle as orc
         orc.build()
-        v, dt, cores = oracle_tasks_per_s(a, a.cpu_sample_tasks)
+        v, dt, cores, e_ref = oracle_tasks_per_s(a, a.cpu_sample_tasks)
+        # the timed tasks double as a parity sample of the timed plan
+        line["parity_sample"] = [{"task": i, "energy": e_last[i], "oracle_energy": e_ref[i],
+                                  "rel_error": abs(e_last[i] - e_ref[i]) / abs(e_ref[i])}
+                                 for i in range(len(e_ref))]
         line["cpu_baseline"] = {"value": v, "unit": "tasks/s", "cores": cores, "kind": "oracle",
                                 "sample": "%d of %d tasks, per-task rerun from |0> in complex128 "
                                           "(%d gates each incl. shared prefix) + %d-term energy; "
