@@ -64,6 +64,8 @@ class Task:
     @property
     def gates(self) -> np.ndarray:
         parts = [s for s in self.spans if len(s)]
+        if not parts:
+            return np.zeros(0, dtype=GATE_DTYPE)
         if len(parts) == 1:
             return parts[0]
         return concat(*parts)
