@@ -15,9 +15,9 @@
 // x = base | j << TB | t.  The three fields are disjoint bit ranges, so for
 // a term (m, z) the partner of element j is pb | (j ^ mj) << TB with pb the
 // partner of element 0, and its sign is (-1)^{popc((base|t) & z)} times
-// (-1)^{popc(j & zj)}.  Both j-dependent parts are resolved at compile time
-// by a switch over (mj, flags) and over zj: a partner load is one load with
-// an immediate offset and the signed sum is plain adds.
+// (-1)^{popc(j & zj)}.  The partner offsets are resolved at compile time by
+// a switch over (mj, flags), so a partner load is one load with an immediate
+// offset; the signs are applied by a branch-free butterfly.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -65,25 +65,19 @@ __device__ __forceinline__ C en_ld(const C *p) {
   return __ldcg(p);
 }
 
-__host__ __device__ constexpr int en_parity4(int x) { return (x ^ (x >> 1) ^ (x >> 2) ^ (x >> 3)) & 1; }
-
-// sum_j (-1)^{popc(j & Z)} v[j], signs resolved at compile time
-template <typename T, int Z>
-__device__ __forceinline__ T en_signed16(const T (&v)[16]) {
-  T s = 0;
-#pragma unroll
-  for (int j = 0; j < 16; j++) s += en_parity4(j & Z) ? -v[j] : v[j];
-  return s;
-}
+// sum_j (-1)^{popc(j & z)} v[j] as a butterfly over the four bits of j with
+// runtime signs: 15 fused multiply-adds by +-1 (exact products), no branch
 template <typename T>
-__device__ __forceinline__ T en_signed16_rt(const T (&v)[16], uint32_t z) {
-  switch (z & 15u) {
-#define QW_SS(Z) case Z: return en_signed16<T, Z>(v);
-    QW_SS(0) QW_SS(1) QW_SS(2) QW_SS(3) QW_SS(4) QW_SS(5) QW_SS(6) QW_SS(7)
-    QW_SS(8) QW_SS(9) QW_SS(10) QW_SS(11) QW_SS(12) QW_SS(13) QW_SS(14)
-#undef QW_SS
-    default: return en_signed16<T, 15>(v);
-  }
+__device__ __forceinline__ T en_signed16_bf(const T (&v)[16], uint32_t z) {
+  const T s0 = (z & 1u) ? T(-1) : T(1), s1 = (z & 2u) ? T(-1) : T(1);
+  const T s2 = (z & 4u) ? T(-1) : T(1), s3 = (z & 8u) ? T(-1) : T(1);
+  T u[8], w[4];
+#pragma unroll
+  for (int k = 0; k < 8; k++) u[k] = fma(s0, v[2 * k + 1], v[2 * k]);
+#pragma unroll
+  for (int k = 0; k < 4; k++) w[k] = fma(s1, u[2 * k + 1], u[2 * k]);
+  const T x0 = fma(s2, w[1], w[0]), x1 = fma(s2, w[3], w[2]);
+  return fma(s3, x1, x0);
 }
 
 // v[j] = Re or Im part of conj(partner_j) a[j], partner_j = q[(j ^ MJ) << TB]
@@ -146,7 +140,7 @@ __device__ __forceinline__ void energy_sub(const typename EnC<T>::t *__restrict_
     if (ks == 0 && full) {
       T v[16];
       en_prod_rt<T, TB, NC>(psi + pb, a, v, mj | (fl << 4));
-      s = en_signed16_rt<T>(v, zj);
+      s = en_signed16_bf<T>(v, zj);
     } else {
       // a skipped bit inside the j-field, or a register smaller than the
       // sub-block: per-element tests
