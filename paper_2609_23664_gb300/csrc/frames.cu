@@ -125,10 +125,22 @@ __global__ void __launch_bounds__(FR_WARPS * 32) frame_kernel(FrameArgs A) {
       }
     }
     __syncwarp();
-    if (L.n_meas && has_task) {
-      for (uint32_t i = n_gate; i < L.n_ops; i++) {
-        const FrameOp op = A.ops[L.op_begin + i];
-        A.outs[ob + op.aux] = (uint8_t)(A.ref_out[op.aux] ^ ((X[op.a] >> lane) & 1u));
+    // measurements, 32 at a time: lane i loads op i of the batch and its
+    // reference outcome, then every lane writes its task's outcome of each
+    for (uint32_t b0 = n_gate; b0 < L.n_ops; b0 += 32) {
+      const uint32_t cnt = min(32u, L.n_ops - b0);
+      uint32_t q = 0, aux = 0, ref = 0;
+      if (lane < cnt) {
+        const FrameOp op = A.ops[L.op_begin + b0 + lane];
+        q = op.a;
+        aux = op.aux;
+        ref = A.ref_out[op.aux];
+      }
+      for (uint32_t i = 0; i < cnt; i++) {
+        const uint32_t qi = __shfl_sync(0xffffffffu, q, i);
+        const uint32_t ai = __shfl_sync(0xffffffffu, aux, i);
+        const uint32_t ri = __shfl_sync(0xffffffffu, ref, i);
+        if (has_task) A.outs[ob + ai] = (uint8_t)(ri ^ ((X[qi] >> lane) & 1u));
       }
     }
     __syncwarp();

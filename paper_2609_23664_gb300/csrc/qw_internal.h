@@ -212,6 +212,7 @@ struct TabSlot {
   uint32_t aux;      // T_MEAS: random-bit index (segment relative)
   uint32_t aux2;     // T_MEAS: outcome index (segment relative) or 0xFFFFFFFF
 };
+static_assert(sizeof(TabSlot) == 16, "slot layout");
 struct TabLayer {
   uint32_t slot_begin, n_slots, is_measure, pad;
 };

@@ -25,11 +25,15 @@
 
 namespace qw {
 
+constexpr uint32_t TAB_SLOT_STAGE = 1024;  // slots of a layer staged in shared memory at a time
+constexpr int TAB_THREADS = 512;
+
 struct TabSm {
   uint64_t *R;     // rows * 2W words
   uint8_t *sign;   // rows
   uint8_t *pending;
   uint64_t *xs;    // W words (collapse scratch)
+  TabSlot *sl;     // TAB_SLOT_STAGE staged slots
   uint32_t *any_random;
 };
 
@@ -126,11 +130,17 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
   for (uint32_t li = 0; li < P.n_layers; li++) {
     const TabLayer L = A.layers[P.layer_begin + li];
     if (!L.is_measure) {
-      for (uint32_t sb = warp * gpw; sb < L.n_slots; sb += nwarps * gpw) {
+      // the layer's slots are staged in shared memory (one coalesced read
+      // instead of a dependent global load per slot group)
+      for (uint32_t c0 = 0; c0 < L.n_slots; c0 += TAB_SLOT_STAGE) {
+      const uint32_t cn = min(TAB_SLOT_STAGE, L.n_slots - c0);
+      for (uint32_t i = threadIdx.x; i < cn; i += blockDim.x) S.sl[i] = A.slots[L.slot_begin + c0 + i];
+      __syncthreads();
+      for (uint32_t sb = warp * gpw; sb < cn; sb += nwarps * gpw) {
         const uint32_t si = sb + ln / lpp;
-        const bool act = si < L.n_slots;
+        const bool act = si < cn;
         TabSlot sl{};
-        if (act) sl = A.slots[L.slot_begin + si];
+        if (act) sl = S.sl[si];
         int t = 0;
         if (act && sl.kind == T_PROD) {
           if (w < W) {
@@ -166,13 +176,18 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
         }
       }
       __syncthreads();
+      }
     } else {
+      // a measurement layer holds at most one slot per qubit (<= 640), so
+      // all of its slots fit the staging buffer
+      for (uint32_t i = threadIdx.x; i < L.n_slots; i += blockDim.x) S.sl[i] = A.slots[L.slot_begin + i];
+      __syncthreads();
       // phase 1: deterministic outcomes in parallel, random ones flagged
       for (uint32_t sb = warp * gpw; sb < L.n_slots; sb += nwarps * gpw) {
         const uint32_t si = sb + ln / lpp;
         const bool act = si < L.n_slots;
         TabSlot sl{};
-        if (act) sl = A.slots[L.slot_begin + si];
+        if (act) sl = S.sl[si];
         uint64_t v = 0;
         if (act && w < W) v = S.R[(size_t)sl.dst * 2 * W + w];
         for (uint32_t o = lpp >> 1; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o, lpp);
@@ -191,7 +206,7 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
       // phase 2: random outcomes one at a time, in program order
       for (uint32_t si = 0; si < L.n_slots; si++) {
         if (S.pending[si]) {
-          const TabSlot sl = A.slots[L.slot_begin + si];
+          const TabSlot sl = S.sl[si];
           tab_collapse(A, S, sl, bits_base, out_base);
         }
       }
@@ -200,7 +215,7 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
   }
 }
 
-__global__ void __launch_bounds__(256) tab_kernel(TabArgs A) {
+__global__ void __launch_bounds__(TAB_THREADS) tab_kernel(TabArgs A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ uint32_t s_any_random;
   if (A.run_if && *A.run_if == 0u) return;  // uniform over the grid
@@ -212,6 +227,7 @@ __global__ void __launch_bounds__(256) tab_kernel(TabArgs A) {
   S.sign = (uint8_t *)(S.R + (size_t)rows * 2 * W);
   S.pending = S.sign + ((rows + 15) & ~15u);
   S.xs = (uint64_t *)(S.pending + ((A.n + 15) & ~15u));
+  S.sl = (TabSlot *)(S.xs + ((W + 1) & ~1u));
   const size_t nwords = (size_t)rows * 2 * W;
   const TabTaskDesc T = A.tasks[blockIdx.x];
   if (A.init_rows) {
@@ -250,7 +266,8 @@ __global__ void __launch_bounds__(256) tab_kernel(TabArgs A) {
 
 size_t tab_smem_bytes(uint32_t n) {
   const uint32_t W = (n + 63) / 64, rows = 2 * n;
-  return (size_t)rows * 2 * W * 8 + ((rows + 15) & ~15u) + ((n + 15) & ~15u) + (size_t)W * 8 + 16;
+  return (size_t)rows * 2 * W * 8 + ((rows + 15) & ~15u) + ((n + 15) & ~15u) + (size_t)((W + 1) & ~1u) * 8 +
+         (size_t)TAB_SLOT_STAGE * sizeof(TabSlot) + 16;
 }
 
 // the largest tableau (QW_TABLEAU_MAX_QUBITS) fits below the 227 KB opt-in
@@ -262,7 +279,7 @@ cudaError_t tab_init_attrs() {
 
 void launch_tab(const TabArgs &a, uint32_t n_tasks, void *stream) {
   if (n_tasks == 0) return;
-  tab_kernel<<<n_tasks, 256, tab_smem_bytes(a.n), (cudaStream_t)stream>>>(a);
+  tab_kernel<<<n_tasks, TAB_THREADS, tab_smem_bytes(a.n), (cudaStream_t)stream>>>(a);
 }
 
 }  // namespace qw
