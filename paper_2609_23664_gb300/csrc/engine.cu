@@ -170,6 +170,18 @@ struct DeviceState {
   std::vector<void *> mat_export[2];   // per mode (FP64, FP32): statevector exported from a tableau node
   std::vector<StabBasis *> mat_basis;  // scratch of each exporting tableau node
   std::vector<int> tab_launch_of_mat;  // index into tab_mat_launches, -1 none
+  // statevector boundaries of one precision in one persistent launch (a
+  // boundary's first pass waits for its parent's last); empty = per-pass launches
+  struct MatBatch {
+    bool fp64 = false;
+    uint32_t k_max = 5, seg_bits = 0, total_items = 0;
+    int grid = 0;
+    size_t n_jobs = 0, ctr_words = 0;
+    SvJob *d_jobs = nullptr;
+    SvSeg *d_segs = nullptr;
+    unsigned int *d_ctr = nullptr;
+  };
+  std::vector<MatBatch> mat_batches;
   std::vector<void *> task_state;  // state a task's observables read
   std::vector<Wave> waves;
   EnClass *d_classes = nullptr;
@@ -346,6 +358,76 @@ static void prepare(qw_plan *P) {
     return tp.src >= 0 && P->mats[tp.src].mode != QW_MODE_TABLEAU && P->mats[tp.src].mode != tp.mode &&
            !D->mat_export[tp.mode][tp.src];
   };
+
+  // ---- statevector boundaries: one persistent launch per precision --------
+  // Used when every boundary has passes and continues from |0...0> or from a
+  // statevector boundary of its own precision (no export or conversion in
+  // between); a boundary's first pass then waits for its parent's last, and
+  // sibling boundaries run side by side.  Otherwise: pass by pass.
+  {
+    bool ok = P->opts.batched != 0;
+    size_t n_sv = 0;
+    for (const MatNode &M : P->mats) {
+      if (M.mode == QW_MODE_TABLEAU) continue;
+      n_sv++;
+      if (M.sv.passes.empty()) ok = false;
+      if (M.parent >= 0 && P->mats[M.parent].mode != M.mode) ok = false;
+    }
+    // a single boundary is a chain of dependent passes: separate launches
+    // serve it as well, without CTAs waiting on the previous pass
+    if (ok && n_sv > 1) {
+      std::vector<uint32_t> level(P->mats.size(), 0);
+      uint32_t max_level = 0;
+      size_t max_p = 0;
+      for (size_t m = 0; m < P->mats.size(); m++) {  // parents precede their children
+        const MatNode &M = P->mats[m];
+        if (M.mode == QW_MODE_TABLEAU) continue;
+        level[m] = (M.parent >= 0) ? level[M.parent] + 1 : 0;
+        max_level = std::max(max_level, level[m]);
+        max_p = std::max(max_p, M.sv.passes.size());
+      }
+      for (uint32_t prec : {(uint32_t)QW_MODE_SV_FP32, (uint32_t)QW_MODE_SV_FP64}) {
+        std::vector<SvJob> jobs;
+        std::vector<int> last_job(P->mats.size(), -1);
+        uint32_t kmax = 5;
+        for (uint32_t L = 0; L <= max_level; L++)
+          for (size_t pi = 0; pi < max_p; pi++)
+            for (size_t m = 0; m < P->mats.size(); m++) {
+              const MatNode &M = P->mats[m];
+              if (M.mode != prec || level[m] != L || pi >= M.sv.passes.size()) continue;
+              const uint32_t k = (uint32_t)M.sv.passes[pi].q.size();
+              SvJob j{};
+              j.src = (pi == 0) ? (M.parent >= 0 ? D->mat_buf[M.parent] : nullptr) : D->mat_buf[m];
+              j.dst = D->mat_buf[m];
+              j.pass = D->mat_pass0[m] + (uint32_t)pi;
+              j.n_tiles = 1u << (M.n_eff - k);
+              j.dep = (pi == 0) ? (M.parent >= 0 ? last_job[M.parent] : -1) : last_job[m];
+              j.kind = SVJ_PASS;
+              j.n = M.n_eff;
+              last_job[m] = (int)jobs.size();
+              jobs.push_back(j);
+              kmax = std::max(kmax, k);
+            }
+        if (jobs.empty()) continue;
+        DeviceState::MatBatch B;
+        B.fp64 = prec == QW_MODE_SV_FP64;
+        B.k_max = kmax;
+        B.grid = sv_batch_grid(B.fp64, kmax, E->sm_count);
+        B.seg_bits = segment_bits(jobs);
+        std::vector<SvSeg> segs;
+        build_segments(jobs, jobs.size(), B.seg_bits, 2ull * (uint64_t)B.grid, segs);
+        if (((uint64_t)segs.size() << B.seg_bits) > 0xFFFFFFF0ull)
+          fail(QW_ERR_BUDGET, "the boundaries' work list exceeds 2^32 items");
+        B.total_items = (uint32_t)(segs.size() << B.seg_bits);
+        B.n_jobs = jobs.size();
+        B.d_jobs = D->arena.upload(jobs, s);
+        B.d_segs = D->arena.upload(segs, s);
+        B.ctr_words = 2 + jobs.size();
+        B.d_ctr = (unsigned int *)D->arena.alloc(B.ctr_words * sizeof(unsigned int));
+        D->mat_batches.push_back(B);
+      }
+    }
+  }
 
   // Hamiltonians
   std::vector<EnClass> cls;
@@ -748,6 +830,7 @@ static void enqueue(qw_plan *P, cudaStream_t s, bool capturing) {
         }
       continue;
     }
+    if (!D->mat_batches.empty()) continue;  // statevector boundaries run in the batches below
     const bool fp64 = M.mode == QW_MODE_SV_FP64;
     const SvTables &T = fp64 ? D->t64 : D->t32;
     const void *psrc = nullptr;
@@ -773,6 +856,26 @@ static void enqueue(qw_plan *P, cudaStream_t s, bool capturing) {
                                                                   md == QW_MODE_SV_FP64, n);
         nl += 1;
       }
+  }
+  if (!D->mat_batches.empty()) {
+    for (const DeviceState::MatBatch &B : D->mat_batches) {
+      CK(cudaMemsetAsync(B.d_ctr, 0, B.ctr_words * sizeof(unsigned int), s));
+      launch_sv_batch(B.fp64, B.fp64 ? D->t64 : D->t32, B.d_jobs, B.d_segs, B.seg_bits, B.total_items, B.k_max,
+                      B.d_ctr, EnTables{}, B.grid, s);
+      nl += 1;
+    }
+    // each boundary rounded once into the other precision its consumers use
+    for (size_t m = 0; m < P->mats.size(); m++) {
+      const MatNode &M = P->mats[m];
+      if (M.mode == QW_MODE_TABLEAU) continue;
+      for (uint32_t md = 0; md < 2; md++)
+        if (md != M.mode && D->mat_export[md][m]) {
+          const size_t n = (size_t)1 << M.n_eff;
+          convert_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+              D->mat_buf[m], M.mode == QW_MODE_SV_FP64, D->mat_export[md][m], md == QW_MODE_SV_FP64, n);
+          nl += 1;
+        }
+    }
   }
   CK(rec(D->ev[1]));
   // 2) task suffixes, observables
@@ -887,6 +990,11 @@ void plan_wait(qw_plan *P) {
     unsigned int flag = 0;
     CK(cudaMemcpy(&flag, W.d_ctr + 1, sizeof(flag), cudaMemcpyDeviceToHost));
     if (flag) fail(QW_ERR_DEVICE_TIMEOUT, "a bounded dependency wait of the persistent batch expired");
+  }
+  for (const DeviceState::MatBatch &B : D->mat_batches) {
+    unsigned int flag = 0;
+    CK(cudaMemcpy(&flag, B.d_ctr + 1, sizeof(flag), cudaMemcpyDeviceToHost));
+    if (flag) fail(QW_ERR_DEVICE_TIMEOUT, "a bounded dependency wait of the boundaries' launch expired");
   }
   std::vector<double> en(2 * (size_t)nt);
   if (nt) CK(cudaMemcpy(en.data(), D->d_energy, en.size() * sizeof(double), cudaMemcpyDeviceToHost));
