@@ -112,13 +112,16 @@ struct SvTableBuilder {
 
 // device allocation tracked for release
 struct DevArena {
-  std::vector<void *> ptrs;
+  Engine *eng = nullptr;  // when set, blocks come from and return to the engine's cache
+  std::vector<std::pair<void *, size_t>> blocks;
   uint64_t h2d = 0;  // bytes uploaded from the host
   void *alloc(size_t bytes) {
     void *p = nullptr;
     if (bytes == 0) bytes = 16;
-    CK(cudaMalloc(&p, bytes));
-    ptrs.push_back(p);
+    size_t got = bytes;
+    if (eng) p = eng->dev_alloc(bytes, &got);
+    else CK(cudaMalloc(&p, bytes));
+    blocks.push_back({p, got});
     return p;
   }
   template <typename T>
@@ -129,8 +132,11 @@ struct DevArena {
     return p;
   }
   void release() {
-    for (void *p : ptrs) cudaFree(p);
-    ptrs.clear();
+    for (auto &b : blocks) {
+      if (eng) eng->dev_free(b.first, b.second);
+      else cudaFree(b.first);
+    }
+    blocks.clear();
   }
 };
 
@@ -296,6 +302,7 @@ static void build_segments(const std::vector<SvJob> &jobs, size_t n_pass, uint32
 static void prepare(qw_plan *P) {
   Engine *E = P->eng;
   DeviceState *D = new DeviceState();
+  D->arena.eng = E;
   P->dev = D;
   D->stream = (cudaStream_t)E->stream;
   cudaStream_t s = D->stream;
@@ -1036,7 +1043,9 @@ void plan_wait(qw_plan *P) {
 void plan_release(qw_plan *P) {
   if (P->dev) {
     if (P->eng) cudaSetDevice(P->eng->device);
-    cudaStreamSynchronize(P->dev->stream);
+    // the plan may have run on a caller's stream: its blocks go back to the
+    // engine's cache only once the device has finished with them
+    cudaDeviceSynchronize();
     delete P->dev;
     P->dev = nullptr;
   }
@@ -1102,8 +1111,48 @@ void engine_init(Engine *E, const qw_engine_opts *o) {
   CK(cudaGetLastError());
 }
 
+void *Engine::dev_alloc(size_t bytes, size_t *got) {
+  const size_t want = (bytes + 511) & ~(size_t)511;
+  auto it = free_blocks.lower_bound(want);
+  if (it != free_blocks.end() && it->first <= want + want / 4 + 4096) {
+    void *p = it->second;
+    *got = it->first;
+    cached_bytes -= it->first;
+    free_blocks.erase(it);
+    return p;
+  }
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) {  // give the cached blocks back and try once more
+    cudaGetLastError();
+    trim_cache();
+    e = cudaMalloc(&p, want);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(QW_ERR_OOM, "device allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+  }
+  *got = want;
+  return p;
+}
+
+void Engine::dev_free(void *p, size_t bytes) {
+  free_blocks.insert({bytes, p});
+  cached_bytes += bytes;
+}
+
+void Engine::trim_cache() {
+  if (free_blocks.empty()) return;
+  cudaSetDevice(device);
+  cudaDeviceSynchronize();
+  for (auto &b : free_blocks) cudaFree(b.second);
+  free_blocks.clear();
+  cached_bytes = 0;
+}
+
 void engine_release(Engine *E) {
   cudaSetDevice(E->device);
+  E->trim_cache();
   if (E->scratch) cudaFree(E->scratch);
   if (E->d_mlp) cudaFree(E->d_mlp);
   if (E->stream) cudaStreamDestroy((cudaStream_t)E->stream);

@@ -152,6 +152,14 @@ struct Engine {
   // scratch for the *_dev entry points
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
+  // Device-memory cache: blocks a plan releases are kept (by size) for the
+  // next plans, so planning and executing a workload again allocates and
+  // frees nothing; dropped when an allocation fails and on destruction.
+  std::multimap<size_t, void *> free_blocks;
+  size_t cached_bytes = 0;
+  void *dev_alloc(size_t bytes, size_t *got);
+  void dev_free(void *p, size_t bytes);
+  void trim_cache();
   std::set<qw_plan *> plans;  // live plans (released when the engine is destroyed)
   TileConfig tile_config(uint32_t n_eff, bool fp64);
   double predict_log2ns(const float *feat, uint32_t rows, float *out);
