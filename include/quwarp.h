@@ -418,6 +418,60 @@ qw_status qw_sv_energy_noalloc_dev(uint32_t mode, uint32_t n, const void *state,
                                    const qw_pauli_term *terms, uint64_t n_terms, double *out,
                                    void *stream);
 
+
+/* ---- dense blocks: fused k-qubit unitaries ----------------------------------
+ * A dense block is a 2^k x 2^k unitary (k in [1, 5]) on qubits q[0..k-1]:
+ * bit j of the block-local index is qubit q[j]; for every assignment of the
+ * other n-k bits it maps the 2^k amplitudes by the matrix.  A gate list is
+ * fused into blocks of at most kmax qubits (greedy: a gate joins the blocks
+ * that hold its qubits while their union fits, the largest of them is
+ * closed otherwise; disjoint blocks commute and are packed together), each
+ * block's matrix being the product of its gates' matrices in double
+ * precision.  A program applies its blocks in order, one pass over the state
+ * per block.  It is the statevector backend's gate application (Sec. III-A
+ * "Execution on the bounded Qrack surface", Sec. V-B "Backend surface") in
+ * fused-block form; the paper does not fix how gates are applied, and the
+ * pass kernels of qw_sv_apply_dev stay the path that plans use.
+ *   QW_DENSE_TENSOR: tcgen05 tensor cores.  FP32 states only, n in
+ *     [12, QW_SV_MAX_QUBITS]; each FP32 operand is split into two TF32
+ *     parts and three products are accumulated in FP32 (3xTF32); nacc in
+ *     {1, 2, 4} spreads the 8 K-steps over that many tensor-memory
+ *     accumulators, added on the CUDA cores (more accurate, more readback).
+ *     Blocks of fewer than 5 qubits are widened with identity on the
+ *     highest qubits they do not touch.
+ *   QW_DENSE_SIMT: CUDA cores in the state's precision (FP32 or FP64),
+ *     n >= k (nacc ignored).
+ * Gates: the unitary ops of qw_gate (MEASURE/RESET -> QW_ERR_UNSUPPORTED). */
+#define QW_DENSE_TENSOR 0u
+#define QW_DENSE_SIMT 1u
+typedef struct qw_dense_prog qw_dense_prog;
+
+/* Host only (no engine, no GPU): the blocks a program would apply, before
+ * widening.  k[i], qubits[5 i + j] (j < k[i]), u[2048 i ..] = the 32 x 32
+ * complex matrix (re, im interleaved, row-major over the 2^k x 2^k block,
+ * the rest zero).  With cap = 0 only *n_blocks is written. */
+qw_status qw_dense_fuse(const qw_gate *gates, uint64_t n_gates, uint32_t n, uint32_t kmax,
+                        uint32_t *k, uint32_t *qubits, double *u, uint64_t cap,
+                        uint64_t *n_blocks);
+/* Fuses `gates` (host) and uploads the blocks' operands (synchronous). */
+qw_status qw_dense_prog_create(qw_engine *e, uint32_t mode, uint32_t n, const qw_gate *gates,
+                               uint64_t n_gates, uint32_t kmax, uint32_t engine, uint32_t nacc,
+                               qw_dense_prog **out);
+/* One explicit block: u = 2^k x 2^k complex doubles (re, im interleaved,
+ * row-major, output index first) on qubits[0..k-1] (distinct, < n).  The
+ * matrix is used as given (it is not checked for unitarity). */
+qw_status qw_dense_prog_create_block(qw_engine *e, uint32_t mode, uint32_t n,
+                                     const uint32_t *qubits, uint32_t k, const double *u,
+                                     uint32_t engine, uint32_t nacc, qw_dense_prog **out);
+qw_status qw_dense_prog_info(const qw_dense_prog *p, uint64_t *n_blocks, uint64_t *n_gates);
+/* Applies the blocks in place to the device state (2^n float2 or double2)
+ * on `stream`, asynchronously. */
+qw_status qw_dense_prog_run(qw_dense_prog *p, void *state, void *stream);
+/* Synchronizes the last run's stream; QW_ERR_DEVICE_TIMEOUT if a bounded
+ * wait for the tensor core ran out (the state is then undefined). */
+qw_status qw_dense_prog_check(qw_dense_prog *p);
+void qw_dense_prog_destroy(qw_dense_prog *p);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,6 +90,33 @@ def sv_run(n: int, gates: np.ndarray) -> np.ndarray:
     return sv_apply(n, sv_zero(n), gates)
 
 
+def apply_matrix(n: int, psi: np.ndarray, qubits, u: np.ndarray) -> np.ndarray:
+    """A k-qubit operator on the listed qubits, by definition: bit j of the
+    block-local index is qubits[j], and for every basis index x
+        psi'[x] = sum_p u[loc(x), p] * psi[(x with its block bits set to p)],
+    where loc(x) is x's own block-local index.  This is how any gate (or
+    product of gates) on k qubits acts on the statevector that the
+    statevector backend evolves (Sec. III-A "Execution on the bounded Qrack
+    surface"); it is the reference for fused dense blocks.  Returns a new
+    array (complex128)."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    u = np.asarray(u, dtype=np.complex128)
+    k = len(qubits)
+    assert u.shape == (1 << k, 1 << k) and psi.size == 1 << n
+    x = np.arange(1 << n, dtype=np.int64)
+    mask = 0
+    loc = np.zeros_like(x)
+    for j, q in enumerate(qubits):
+        loc |= ((x >> q) & 1) << j
+        mask |= 1 << q
+    base = x & ~mask
+    out = np.zeros_like(psi)
+    for p in range(1 << k):
+        off = sum(((p >> j) & 1) << q for j, q in enumerate(qubits))
+        out += u[loc, p] * psi[base | off]
+    return out
+
+
 def norm2(n: int, psi: np.ndarray) -> float:
     return float(lib().orc_sv_norm2(n, _ptr(psi)))
 

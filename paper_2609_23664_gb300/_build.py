@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libquwarp.so")
 SOURCES = ["sv_kernels.cu", "obs_kernels.cu", "tab_kernels.cu", "frames.cu", "handoff.cu", "mlp_kernels.cu", "engine.cu",
-           "noalloc.cu", "planner.cpp", "fusion.cpp", "capi.cpp"]
+           "noalloc.cu", "dense_kernels.cu", "dense_host.cpp", "planner.cpp", "fusion.cpp", "capi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -5,9 +5,17 @@
 #include <algorithm>
 #include <cmath>
 
+#include "dense.h"
 #include "plan.h"
 
 namespace qw {
+qw_dense_prog *dense_prog_create(Engine *E, uint32_t mode, uint32_t n, std::vector<DenseBlock> blocks,
+                                 uint64_t n_gates, uint32_t engine, uint32_t nacc);
+void dense_prog_run(qw_dense_prog *p, void *state, void *stream);
+qw_status dense_prog_check(qw_dense_prog *p);
+void dense_prog_destroy(qw_dense_prog *p);
+uint64_t dense_prog_blocks(const qw_dense_prog *p);
+uint64_t dense_prog_gates(const qw_dense_prog *p);
 void build_plan(qw_plan *P, Engine *E, const Workload &W);
 void plan_execute(qw_plan *P, void *stream);
 void plan_wait(qw_plan *P);
@@ -522,6 +530,111 @@ qw_status qw_sv_sample_dev(qw_engine *e, uint32_t mode, uint32_t n, const void *
     qw_status st = sv_sample_dev(&e->e, mode, n, state, uniforms, shots, out, stream);
     if (st != QW_OK) return st;
   })
+}
+
+// ---- dense blocks ------------------------------------------------------------
+static void check_dense_target(uint32_t mode, uint32_t n, uint32_t engine, uint32_t nacc) {
+  if (mode > QW_MODE_SV_FP32) fail(QW_ERR_INVALID_ARG, "statevector modes only");
+  if (engine == QW_DENSE_TENSOR) {
+    if (mode != QW_MODE_SV_FP32) fail(QW_ERR_UNSUPPORTED, "tensor-core dense blocks need an FP32 state");
+    if (n < DENSE_TC_MIN_QUBITS || n > QW_SV_MAX_QUBITS)
+      fail(QW_ERR_UNSUPPORTED, "tensor-core dense blocks need n in [%u, %d]", DENSE_TC_MIN_QUBITS, QW_SV_MAX_QUBITS);
+    if (nacc != 1 && nacc != 2 && nacc != 4) fail(QW_ERR_INVALID_ARG, "nacc must be 1, 2 or 4");
+  } else if (engine == QW_DENSE_SIMT) {
+    if (n < 1 || n > QW_SV_MAX_QUBITS) fail(QW_ERR_INVALID_ARG, "n must be in [1, %d]", QW_SV_MAX_QUBITS);
+  } else {
+    fail(QW_ERR_INVALID_ARG, "unknown dense engine %u", engine);
+  }
+}
+
+qw_status qw_dense_fuse(const qw_gate *gates, uint64_t n_gates, uint32_t n, uint32_t kmax, uint32_t *k,
+                        uint32_t *qubits, double *u, uint64_t cap, uint64_t *n_blocks) {
+  QW_GUARD({
+    if ((n_gates && !gates) || !n_blocks || (cap && (!k || !qubits || !u))) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    if (n < 1 || n > QW_SV_MAX_QUBITS) fail(QW_ERR_INVALID_ARG, "n must be in [1, %d]", QW_SV_MAX_QUBITS);
+    for (uint64_t i = 0; i < n_gates; i++) validate_gate(gates[i], QW_MODE_SV_FP64, n, i);
+    std::vector<DenseBlock> b = fuse_dense(gates, n_gates, kmax);
+    *n_blocks = b.size();
+    if (cap == 0) return QW_OK;
+    if (cap < b.size()) fail(QW_ERR_BUFFER_TOO_SMALL, "%zu blocks, capacity %llu", b.size(), (unsigned long long)cap);
+    for (size_t i = 0; i < b.size(); i++) {
+      k[i] = b[i].k;
+      const uint32_t d = 1u << b[i].k;
+      for (uint32_t j = 0; j < DENSE_MAX_QUBITS; j++) qubits[5 * i + j] = j < b[i].k ? b[i].q[j] : 0;
+      double *ui = u + 2048 * i;
+      std::fill(ui, ui + 2048, 0.0);
+      for (uint32_t r = 0; r < d; r++)
+        for (uint32_t c = 0; c < d; c++) {
+          ui[2 * (r * d + c)] = b[i].u[r * d + c].real();
+          ui[2 * (r * d + c) + 1] = b[i].u[r * d + c].imag();
+        }
+    }
+  })
+}
+
+qw_status qw_dense_prog_create(qw_engine *e, uint32_t mode, uint32_t n, const qw_gate *gates, uint64_t n_gates,
+                               uint32_t kmax, uint32_t engine, uint32_t nacc, qw_dense_prog **out) {
+  QW_GUARD({
+    if (!e || !out || (n_gates && !gates)) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    check_dense_target(mode, n, engine, nacc);
+    for (uint64_t i = 0; i < n_gates; i++) validate_gate(gates[i], mode, n, i);
+    *out = dense_prog_create(&e->e, mode, n, fuse_dense(gates, n_gates, kmax), n_gates, engine, nacc);
+  })
+}
+
+qw_status qw_dense_prog_create_block(qw_engine *e, uint32_t mode, uint32_t n, const uint32_t *qubits, uint32_t k,
+                                     const double *u, uint32_t engine, uint32_t nacc, qw_dense_prog **out) {
+  QW_GUARD({
+    if (!e || !out || !qubits || !u) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    check_dense_target(mode, n, engine, nacc);
+    if (k < 1 || k > DENSE_MAX_QUBITS || k > n) fail(QW_ERR_INVALID_ARG, "k must be in [1, min(5, n)]");
+    DenseBlock b;
+    b.k = k;
+    uint32_t seen = 0;
+    for (uint32_t j = 0; j < k; j++) {
+      if (qubits[j] >= n || (seen >> qubits[j] & 1)) fail(QW_ERR_INVALID_ARG, "qubit %u repeated or out of range", qubits[j]);
+      seen |= 1u << qubits[j];
+      b.q[j] = qubits[j];
+    }
+    const uint32_t d = 1u << k;
+    b.u.resize((size_t)d * d);
+    for (size_t i = 0; i < b.u.size(); i++) {
+      if (!std::isfinite(u[2 * i]) || !std::isfinite(u[2 * i + 1])) fail(QW_ERR_INVALID_ARG, "non-finite matrix entry");
+      b.u[i] = std::complex<double>(u[2 * i], u[2 * i + 1]);
+    }
+    *out = dense_prog_create(&e->e, mode, n, std::vector<DenseBlock>{b}, 0, engine, nacc);
+  })
+}
+
+qw_status qw_dense_prog_info(const qw_dense_prog *p, uint64_t *n_blocks, uint64_t *n_gates) {
+  QW_GUARD({
+    if (!p) fail(QW_ERR_INVALID_ARG, "NULL program");
+    if (n_blocks) *n_blocks = dense_prog_blocks(p);
+    if (n_gates) *n_gates = dense_prog_gates(p);
+  })
+}
+
+qw_status qw_dense_prog_run(qw_dense_prog *p, void *state, void *stream) {
+  QW_GUARD({
+    if (!p || !state) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    dense_prog_run(p, state, stream);
+  })
+}
+
+qw_status qw_dense_prog_check(qw_dense_prog *p) {
+  QW_GUARD({
+    if (!p) fail(QW_ERR_INVALID_ARG, "NULL program");
+    dense_prog_check(p);
+  })
+}
+
+void qw_dense_prog_destroy(qw_dense_prog *p) {
+  try {
+    dense_prog_destroy(p);
+  } catch (...) {
+  }
 }
 
 }  // extern "C"

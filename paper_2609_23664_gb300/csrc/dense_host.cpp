@@ -1,0 +1,256 @@
+// Dense blocks on the host: greedy fusion of a gate list into blocks of at
+// most 5 qubits, the blocks' unitaries (products of the gate matrices in
+// double precision), and the device program that applies them in order.
+#include <algorithm>
+#include <cmath>
+
+#include "dense.h"
+#include "plan.h"
+
+namespace qw {
+
+using cd = std::complex<double>;
+
+bool gate_matrix_1q(const qw_gate &g, double m[8], bool *diagonal);
+bool is_two_qubit_op(uint32_t op);
+bool is_barrier_op(uint32_t op);
+
+#define DCK(x)                                                                              \
+  do {                                                                                      \
+    cudaError_t e_ = (x);                                                                   \
+    if (e_ != cudaSuccess)                                                                  \
+      fail(e_ == cudaErrorMemoryAllocation ? QW_ERR_OOM : QW_ERR_CUDA, "%s: %s", #x,       \
+           cudaGetErrorString(e_));                                                         \
+  } while (0)
+
+// U <- G U for gate g acting on block-local bits a (and b for 2-qubit gates).
+static void left_multiply(std::vector<cd> &U, uint32_t dim, const qw_gate &g, uint32_t a, uint32_t b) {
+  const uint32_t ma = 1u << a, mb = 1u << b;
+  auto rows = [&](uint32_t i, uint32_t j, const cd m[4]) {
+    for (uint32_t c = 0; c < dim; c++) {
+      const cd x = U[i * dim + c], y = U[j * dim + c];
+      U[i * dim + c] = m[0] * x + m[1] * y;
+      U[j * dim + c] = m[2] * x + m[3] * y;
+    }
+  };
+  if (!is_two_qubit_op(g.op)) {
+    double m8[8];
+    if (!gate_matrix_1q(g, m8, nullptr)) fail(QW_ERR_INVALID_ARG, "gate op %u has no matrix", g.op);
+    const cd m[4] = {{m8[0], m8[1]}, {m8[2], m8[3]}, {m8[4], m8[5]}, {m8[6], m8[7]}};
+    for (uint32_t i = 0; i < dim; i++)
+      if (!(i & ma)) rows(i, i | ma, m);
+    return;
+  }
+  switch (g.op) {
+    case QW_OP_CNOT:  // control a, target b
+      for (uint32_t i = 0; i < dim; i++)
+        if ((i & ma) && !(i & mb))
+          for (uint32_t c = 0; c < dim; c++) std::swap(U[i * dim + c], U[(i | mb) * dim + c]);
+      break;
+    case QW_OP_CZ:
+      for (uint32_t i = 0; i < dim; i++)
+        if ((i & ma) && (i & mb))
+          for (uint32_t c = 0; c < dim; c++) U[i * dim + c] = -U[i * dim + c];
+      break;
+    case QW_OP_CPHASE: {
+      const cd ph = std::polar(1.0, g.theta);
+      for (uint32_t i = 0; i < dim; i++)
+        if ((i & ma) && (i & mb))
+          for (uint32_t c = 0; c < dim; c++) U[i * dim + c] *= ph;
+      break;
+    }
+    case QW_OP_SWAP:
+      for (uint32_t i = 0; i < dim; i++)
+        if ((i & ma) && !(i & mb))
+          for (uint32_t c = 0; c < dim; c++) std::swap(U[i * dim + c], U[((i & ~ma) | mb) * dim + c]);
+      break;
+    default:
+      fail(QW_ERR_INVALID_ARG, "gate op %u has no matrix", g.op);
+  }
+}
+
+static DenseBlock make_block(const qw_gate *gates, uint32_t mask, const std::vector<uint64_t> &gi) {
+  DenseBlock b;
+  uint32_t local[32] = {};
+  for (uint32_t q = 0; q < 32; q++)
+    if (mask >> q & 1) {
+      local[q] = b.k;
+      b.q[b.k++] = q;
+    }
+  const uint32_t dim = 1u << b.k;
+  b.u.assign((size_t)dim * dim, 0.0);
+  for (uint32_t i = 0; i < dim; i++) b.u[i * dim + i] = 1.0;
+  for (uint64_t i : gi) {
+    const qw_gate &g = gates[i];
+    left_multiply(b.u, dim, g, local[g.q0], is_two_qubit_op(g.op) ? local[g.q1] : 0);
+  }
+  b.n_gates = (uint32_t)gi.size();
+  return b;
+}
+
+std::vector<DenseBlock> fuse_dense(const qw_gate *gates, uint64_t n_gates, uint32_t kmax) {
+  if (kmax < 2 || kmax > DENSE_MAX_QUBITS) fail(QW_ERR_INVALID_ARG, "kmax must be in [2, %u]", DENSE_MAX_QUBITS);
+  struct Open {
+    uint32_t mask;
+    std::vector<uint64_t> gi;
+  };
+  std::vector<Open> open;  // pairwise disjoint qubit sets
+  std::vector<DenseBlock> out;
+  auto close = [&](size_t b) {
+    out.push_back(make_block(gates, open[b].mask, open[b].gi));
+    open.erase(open.begin() + (ptrdiff_t)b);
+  };
+  for (uint64_t i = 0; i < n_gates; i++) {
+    const qw_gate &g = gates[i];
+    if (is_barrier_op(g.op)) fail(QW_ERR_UNSUPPORTED, "gate %llu: measurement or reset in a dense block", (unsigned long long)i);
+    uint32_t qm = 1u << g.q0;
+    if (is_two_qubit_op(g.op)) qm |= 1u << g.q1;
+    for (;;) {
+      uint32_t um = qm;
+      for (const Open &o : open)
+        if (o.mask & qm) um |= o.mask;
+      if ((uint32_t)__builtin_popcount(um) <= kmax) break;
+      // close the largest touching block (ties: the oldest) and retry
+      size_t best = open.size();
+      for (size_t b = 0; b < open.size(); b++)
+        if ((open[b].mask & qm) &&
+            (best == open.size() || __builtin_popcount(open[b].mask) > __builtin_popcount(open[best].mask)))
+          best = b;
+      close(best);
+    }
+    // merge every touching block, in order, and append the gate
+    Open m{qm, {}};
+    for (size_t b = 0; b < open.size();) {
+      if (open[b].mask & qm) {
+        m.mask |= open[b].mask;
+        m.gi.insert(m.gi.end(), open[b].gi.begin(), open[b].gi.end());
+        open.erase(open.begin() + (ptrdiff_t)b);
+      } else {
+        b++;
+      }
+    }
+    m.gi.push_back(i);
+    open.push_back(std::move(m));
+  }
+  // pack what is left (disjoint blocks commute): first fit, largest first
+  std::stable_sort(open.begin(), open.end(), [](const Open &a, const Open &b) {
+    return __builtin_popcount(a.mask) > __builtin_popcount(b.mask);
+  });
+  std::vector<Open> packed;
+  for (Open &o : open) {
+    bool placed = false;
+    for (Open &p : packed)
+      if ((uint32_t)__builtin_popcount(p.mask | o.mask) <= kmax) {
+        p.mask |= o.mask;
+        p.gi.insert(p.gi.end(), o.gi.begin(), o.gi.end());
+        placed = true;
+        break;
+      }
+    if (!placed) packed.push_back(std::move(o));
+  }
+  for (Open &p : packed) out.push_back(make_block(gates, p.mask, p.gi));
+  return out;
+}
+
+}  // namespace qw
+
+// ---------------------------------------------------------------------------
+// device program
+// ---------------------------------------------------------------------------
+struct qw_dense_prog {
+  qw::Engine *eng = nullptr;
+  uint32_t mode = 0, n = 0, engine = 0, nacc = 1;
+  uint64_t n_gates = 0;
+  std::vector<qw::DenseBlock> blocks;  // as applied (padded to 5 qubits on the tensor cores)
+  void *d_ops = nullptr;               // per block: 8192 floats (tensor) or 2 * 4^k values (CUDA cores)
+  std::vector<size_t> op_offset;       // byte offset of each block's operand
+  int *d_err = nullptr;
+  void *last_stream = nullptr;
+};
+
+namespace qw {
+
+qw_dense_prog *dense_prog_create(Engine *E, uint32_t mode, uint32_t n, std::vector<DenseBlock> blocks,
+                                 uint64_t n_gates, uint32_t engine, uint32_t nacc) {
+  DCK(cudaSetDevice(E->device));
+  std::unique_ptr<qw_dense_prog> p(new qw_dense_prog());
+  p->eng = E;
+  p->mode = mode;
+  p->n = n;
+  p->engine = engine;
+  p->nacc = nacc;
+  p->n_gates = n_gates;
+  const bool fp64 = mode == QW_MODE_SV_FP64;
+  std::vector<uint8_t> host;
+  for (DenseBlock &b : blocks) {
+    p->op_offset.push_back(host.size());
+    if (engine == QW_DENSE_TENSOR) {
+      b = pad_block(b, n);
+      host.resize(host.size() + 8192 * sizeof(float));
+      dense_tc_operands(b, reinterpret_cast<float *>(host.data() + p->op_offset.back()));
+    } else {
+      const size_t cnt = 2 * b.u.size();
+      const size_t bytes = cnt * (fp64 ? sizeof(double) : sizeof(float));
+      host.resize(host.size() + ((bytes + 15) & ~(size_t)15));
+      uint8_t *dst = host.data() + p->op_offset.back();
+      for (size_t i = 0; i < b.u.size(); i++) {
+        if (fp64) {
+          reinterpret_cast<double *>(dst)[2 * i] = b.u[i].real();
+          reinterpret_cast<double *>(dst)[2 * i + 1] = b.u[i].imag();
+        } else {
+          reinterpret_cast<float *>(dst)[2 * i] = (float)b.u[i].real();
+          reinterpret_cast<float *>(dst)[2 * i + 1] = (float)b.u[i].imag();
+        }
+      }
+    }
+  }
+  p->blocks = std::move(blocks);
+  DCK(cudaMalloc(&p->d_err, sizeof(int)));
+  DCK(cudaMemset(p->d_err, 0, sizeof(int)));
+  if (!host.empty()) {
+    DCK(cudaMalloc(&p->d_ops, host.size()));
+    DCK(cudaMemcpy(p->d_ops, host.data(), host.size(), cudaMemcpyHostToDevice));
+  }
+  return p.release();
+}
+
+void dense_prog_run(qw_dense_prog *p, void *state, void *stream) {
+  DCK(cudaSetDevice(p->eng->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  for (size_t i = 0; i < p->blocks.size(); i++) {
+    const uint8_t *op = static_cast<const uint8_t *>(p->d_ops) + p->op_offset[i];
+    if (p->engine == QW_DENSE_TENSOR)
+      launch_dense_tc((float2 *)state, p->n, p->blocks[i], reinterpret_cast<const float *>(op), (int)p->nacc,
+                      p->d_err, p->eng->sm_count, s);
+    else
+      launch_dense_simt(p->mode == QW_MODE_SV_FP64, state, p->n, p->blocks[i], op, p->eng->sm_count, s);
+  }
+  DCK(cudaGetLastError());
+  p->last_stream = stream;
+}
+
+qw_status dense_prog_check(qw_dense_prog *p) {
+  DCK(cudaSetDevice(p->eng->device));
+  DCK(cudaStreamSynchronize((cudaStream_t)p->last_stream));
+  int err = 0;
+  DCK(cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    DCK(cudaMemset(p->d_err, 0, sizeof(int)));
+    fail(QW_ERR_DEVICE_TIMEOUT, "a tensor-core wait of a dense block ran out; the state is undefined");
+  }
+  return QW_OK;
+}
+
+uint64_t dense_prog_blocks(const qw_dense_prog *p) { return p->blocks.size(); }
+uint64_t dense_prog_gates(const qw_dense_prog *p) { return p->n_gates; }
+
+void dense_prog_destroy(qw_dense_prog *p) {
+  if (!p) return;
+  cudaSetDevice(p->eng->device);
+  cudaStreamSynchronize((cudaStream_t)p->last_stream);
+  cudaFree(p->d_ops);
+  cudaFree(p->d_err);
+  delete p;
+}
+
+}  // namespace qw

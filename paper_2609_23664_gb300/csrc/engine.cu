@@ -10,6 +10,7 @@
 #include <map>
 #include <random>
 
+#include "dense.h"
 #include "plan.h"
 
 namespace qw {
@@ -1107,6 +1108,7 @@ void engine_init(Engine *E, const qw_engine_opts *o) {
   // kernel attributes are set before any capture
   CK(sv_init_attrs());
   CK(tab_init_attrs());
+  CK(dense_init_attrs());
   CK(frame_init_attrs());
   CK(cudaGetLastError());
 }

@@ -119,7 +119,16 @@ SIGNATURES = {
     "qw_sv_energy_dev": (_st, [_vp, _u32, _u32, _vp, _vp, _u64, _vp, _vp, _vp]),
     "qw_sv_sample_dev": (_st, [_vp, _u32, _u32, _vp, _vp, _u32, _vp, _vp]),
     "qw_sv_energy_noalloc_dev": (_st, [_u32, _u32, _vp, _vp, _u64, _vp, _vp]),
+    "qw_dense_fuse": (_st, [_vp, _u64, _u32, _u32, _vp, _vp, _vp, _u64, _vp]),
+    "qw_dense_prog_create": (_st, [_vp, _u32, _u32, _vp, _u64, _u32, _u32, _u32, _vp]),
+    "qw_dense_prog_create_block": (_st, [_vp, _u32, _u32, _vp, _u32, _vp, _u32, _u32, _vp]),
+    "qw_dense_prog_info": (_st, [_vp, _vp, _vp]),
+    "qw_dense_prog_run": (_st, [_vp, _vp, _vp]),
+    "qw_dense_prog_check": (_st, [_vp]),
+    "qw_dense_prog_destroy": (None, [_vp]),
 }
+
+DENSE_TENSOR, DENSE_SIMT = 0, 1
 
 
 def library_path() -> str:
@@ -421,3 +430,68 @@ def sv_energy_noalloc_dev(mode: int, n: int, state_ptr: int, terms: np.ndarray, 
     t = np.ascontiguousarray(terms, dtype=W.TERM_DTYPE)
     _check(lib().qw_sv_energy_noalloc_dev(mode, n, state_ptr, _p(t) if len(t) else None, len(t),
                                           out_ptr, stream or None))
+
+
+def dense_fuse(gates: np.ndarray, n: int, kmax: int = 5):
+    """Host only: the dense blocks a program would apply, as a list of
+    (qubits, u) with u the 2^k x 2^k complex matrix (see qw_dense_fuse)."""
+    g = np.ascontiguousarray(gates, dtype=W.GATE_DTYPE)
+    nb = C.c_uint64()
+    _check(lib().qw_dense_fuse(_p(g) if len(g) else None, len(g), n, kmax, None, None, None, 0,
+                               C.byref(nb)))
+    cap = max(1, nb.value)
+    k = np.zeros(cap, dtype=np.uint32)
+    q = np.zeros(5 * cap, dtype=np.uint32)
+    u = np.zeros(2048 * cap, dtype=np.float64)
+    _check(lib().qw_dense_fuse(_p(g) if len(g) else None, len(g), n, kmax, _p(k), _p(q), _p(u), cap,
+                               C.byref(nb)))
+    out = []
+    for i in range(nb.value):
+        d = 1 << int(k[i])
+        m = u[2048 * i:2048 * i + 2 * d * d].view(np.complex128).reshape(d, d).copy()
+        out.append((tuple(int(x) for x in q[5 * i:5 * i + k[i]]), m))
+    return out
+
+
+class DenseProgram:
+    """Fused dense blocks applied to a caller's device state (see the dense
+    block section of include/quwarp.h).  Built from a gate list, or from one
+    explicit block (qubits, u)."""
+
+    def __init__(self, engine: Engine, mode: int, n: int, gates: Optional[np.ndarray] = None,
+                 kmax: int = 5, engine_kind: int = DENSE_TENSOR, nacc: int = 1,
+                 block: Optional[tuple] = None):
+        self.h = C.c_void_p()
+        self.engine = engine
+        if block is not None:
+            qubits, u = block
+            qa = np.ascontiguousarray(qubits, dtype=np.uint32)
+            ua = np.ascontiguousarray(np.asarray(u, dtype=np.complex128)).view(np.float64)
+            _check(lib().qw_dense_prog_create_block(engine.h, mode, n, _p(qa), len(qa), _p(ua),
+                                                    engine_kind, nacc, C.byref(self.h)))
+        else:
+            g = np.ascontiguousarray(gates, dtype=W.GATE_DTYPE)
+            _check(lib().qw_dense_prog_create(engine.h, mode, n, _p(g) if len(g) else None, len(g),
+                                              kmax, engine_kind, nacc, C.byref(self.h)))
+
+    def info(self):
+        nb, ng = C.c_uint64(), C.c_uint64()
+        _check(lib().qw_dense_prog_info(self.h, C.byref(nb), C.byref(ng)))
+        return {"blocks": nb.value, "gates": ng.value}
+
+    def run(self, state_ptr: int, stream: int = 0):
+        _check(lib().qw_dense_prog_run(self.h, state_ptr, stream or None))
+
+    def check(self):
+        _check(lib().qw_dense_prog_check(self.h))
+
+    def close(self):
+        if self.h:
+            lib().qw_dense_prog_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

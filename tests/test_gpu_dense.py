@@ -1,0 +1,151 @@
+"""Dense blocks on the GPU against the oracle: single explicit blocks (random
+unitaries on arbitrary qubits, 1 to 5 qubits), fused gate lists, and the
+24-qubit hardware-efficient suffix shape, on the tensor cores (3xTF32 with
+1, 2 or 4 accumulators) and on the CUDA cores (FP32 and FP64)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2609_23664_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2609_23664_gb300 import quwarp as Q  # noqa: E402
+
+T, S = Q.DENSE_TENSOR, Q.DENSE_SIMT
+FP32, FP64 = W.MODE_SV_FP32, W.MODE_SV_FP64
+# Relative 2-norm error of one block application, FP32 state.  3xTF32 drops
+# the lo*lo product (2^-22 relative) and the tensor core accumulates the 24
+# partial products of a 64-term dot product in FP32 with its own rounding;
+# spreading the K-steps over more accumulators that the CUDA cores add in
+# round-to-nearest lowers the error.  The bounds are a few times the errors
+# measured on GB300 (random unitaries and states).
+REL_TOL = {(T, 1): 4e-6, (T, 2): 3e-6, (T, 4): 2e-6, (S, 0): 1e-6}
+
+
+@pytest.fixture(scope="module")
+def eng():
+    e = Q.Engine(0)
+    yield e
+    e.close()
+
+
+def random_state(rng, n):
+    v = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    return v / np.linalg.norm(v)
+
+
+def random_unitary(rng, d):
+    z = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def run_prog(prog, psi, mode):
+    st = torch.tensor(psi, dtype=torch.complex128 if mode == FP64 else torch.complex64, device="cuda")
+    prog.run(st.data_ptr())
+    prog.check()
+    return st.cpu().numpy().astype(np.complex128)
+
+
+def rounded(psi, mode):
+    return psi if mode == FP64 else psi.astype(np.complex64).astype(np.complex128)
+
+
+@pytest.mark.parametrize("engine,nacc", [(T, 1), (T, 2), (T, 4), (S, 0)])
+@pytest.mark.parametrize("n,qubits", [(12, [0, 1, 2, 3, 4]), (13, [12, 0, 7, 3, 9]), (16, [15, 14, 13, 12, 11]),
+                                      (16, [2, 9]), (20, [19, 0, 10]), (14, [5]), (17, [3, 4, 5, 6])])
+def test_single_block_matches_oracle(eng, engine, nacc, n, qubits):
+    rng = np.random.default_rng(n * 31 + len(qubits))
+    u = random_unitary(rng, 1 << len(qubits))
+    psi = rounded(random_state(rng, n), FP32)
+    prog = Q.DenseProgram(eng, FP32, n, engine_kind=engine, nacc=max(nacc, 1), block=(qubits, u))
+    got = run_prog(prog, psi, FP32)
+    want = orc.apply_matrix(n, psi, qubits, u)
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert np.max(np.abs(got - want)) <= 1e-5
+    assert rel <= REL_TOL[(engine, nacc)], rel
+    prog.close()
+
+
+@pytest.mark.parametrize("n,k", [(5, 5), (10, 3), (14, 5), (9, 1)])
+def test_fp64_block_on_cuda_cores_matches_oracle(eng, n, k):
+    rng = np.random.default_rng(7 * n + k)
+    qubits = list(rng.permutation(n)[:k])
+    u = random_unitary(rng, 1 << k)
+    psi = random_state(rng, n)
+    prog = Q.DenseProgram(eng, FP64, n, engine_kind=S, block=(qubits, u))
+    got = run_prog(prog, psi, FP64)
+    assert np.max(np.abs(got - orc.apply_matrix(n, psi, qubits, u))) <= 1e-12
+
+
+def random_gate_list(rng, n, count):
+    one = [W.OP_H, W.OP_X, W.OP_Y, W.OP_Z, W.OP_S, W.OP_SDG, W.OP_T, W.OP_TDG, W.OP_RX, W.OP_RY, W.OP_RZ,
+           W.OP_PHASE]
+    ops = []
+    for _ in range(count):
+        if rng.random() < 0.35:
+            a, b = rng.choice(n, 2, replace=False)
+            ops.append((int(rng.choice([W.OP_CNOT, W.OP_CZ, W.OP_SWAP, W.OP_CPHASE])), int(a), int(b),
+                        float(rng.uniform(-3, 3))))
+        else:
+            ops.append((int(rng.choice(one)), int(rng.integers(n)), 0, float(rng.uniform(-3, 3))))
+    return W.gates_from_list(ops)
+
+
+@pytest.mark.parametrize("mode,engine,nacc", [(FP32, T, 1), (FP32, T, 4), (FP32, S, 1), (FP64, S, 1)])
+@pytest.mark.parametrize("n,kmax,seed", [(12, 5, 0), (13, 4, 1), (16, 5, 2), (15, 3, 3)])
+def test_fused_gate_list_matches_oracle(eng, mode, engine, nacc, n, kmax, seed):
+    rng = np.random.default_rng(500 + seed)
+    g = random_gate_list(rng, n, 150)
+    psi = rounded(random_state(rng, n), mode)
+    prog = Q.DenseProgram(eng, mode, n, gates=g, kmax=kmax, engine_kind=engine, nacc=nacc)
+    info = prog.info()
+    assert info["gates"] == len(g) and 0 < info["blocks"] < len(g)
+    got = run_prog(prog, psi, mode)
+    want = orc.sv_apply(n, psi.copy(), g)
+    if mode == FP64:
+        assert np.max(np.abs(got - want)) <= 1e-12
+    else:
+        assert np.max(np.abs(got - want)) <= 1e-5
+        assert np.linalg.norm(got - want) <= 2e-5
+
+
+@pytest.mark.parametrize("nacc", [1, 4])
+def test_hardware_efficient_suffix_at_24_qubits(eng, nacc):
+    # the statevector suffix shape of the 24-qubit VQE sweep: 4 layers of RY,
+    # RZ on every qubit and a CNOT chain, from a random FP32 state
+    n = 24
+    rng = np.random.default_rng(24)
+    g = W.hea_circuit(rng, n, 4)
+    psi = rounded(random_state(rng, n), FP32)
+    prog = Q.DenseProgram(eng, FP32, n, gates=g, kmax=5, engine_kind=T, nacc=nacc)
+    assert prog.info()["blocks"] == 24
+    got = run_prog(prog, psi, FP32)
+    want = orc.sv_apply(n, psi.copy(), g)
+    assert np.max(np.abs(got - want)) <= 1e-5
+    assert np.linalg.norm(got - want) <= (1.5e-5 if nacc == 1 else 1e-5)
+    # the pass kernels on the same input agree to FP32 rounding as well
+    st = torch.tensor(psi, dtype=torch.complex64, device="cuda")
+    Q.sv_apply_dev(eng, FP32, n, st.data_ptr(), g)
+    assert np.linalg.norm(st.cpu().numpy().astype(np.complex128) - want) <= 1e-5
+
+
+def test_invalid_dense_requests_are_refused(eng):
+    u = np.eye(4, dtype=np.complex128)
+    with pytest.raises(Q.QuwarpError) as e:      # tensor cores take FP32 states only
+        Q.DenseProgram(eng, FP64, 14, engine_kind=T, block=([0, 1], u))
+    assert e.value.status == -9
+    with pytest.raises(Q.QuwarpError) as e:      # 5 block bits + 7 row bits at least
+        Q.DenseProgram(eng, FP32, 11, engine_kind=T, block=([0, 1], u))
+    assert e.value.status == -9
+    with pytest.raises(Q.QuwarpError) as e:
+        Q.DenseProgram(eng, FP32, 14, engine_kind=T, block=([3, 3], u))
+    assert e.value.status == -1
+    with pytest.raises(Q.QuwarpError) as e:
+        Q.DenseProgram(eng, FP32, 14, engine_kind=T, nacc=3, block=([0, 1], u))
+    assert e.value.status == -1
