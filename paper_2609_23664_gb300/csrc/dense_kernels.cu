@@ -1,5 +1,6 @@
 // Dense-block kernels: the tensor-core form (tcgen05 kind::tf32, operands in
 // shared memory, accumulators in tensor memory) and the CUDA-core form.
+#include <algorithm>
 #include <cstring>
 
 #include "dense.h"
@@ -30,7 +31,25 @@ struct DenseTcArgs {
   uint64_t n_tiles;
   uint32_t other_mask;
   DensePos pos;
+  // staged layout only: for bit b of the tile index (the 12 tile qubits in
+  // ascending order), its offset in the state (tx) and its byte offset in
+  // the [position][row] staging array (ts)
+  uint32_t tx[12], ts[12];
 };
+
+// A block holding most of the lowest qubits leaves the rows of a warp far
+// apart in memory (the 32 rows of a warp span 32 x 128 bytes or more, which
+// thrashes the L1 left beside 2 x 96 KB of shared memory), so its tiles are
+// staged: loaded in memory order with 16-byte accesses into a
+// [position][row] array in shared memory (the A_lo area, free between MMAs),
+// read back per row, and written out the same way.  Row r of position p sits in slot
+// p * 128 + (r ^ (p >> 1)): a warp reading one position of 32 rows stays
+// in one aligned 32-slot group, and a warp moving memory-order indices whose
+// low bits are block bits spreads over all banks.
+// Stage when at least 4 of qubits 0-4 are block qubits (measured on GB300
+// at 28 qubits: staged 3.9-4.2 TB/s for such blocks against 1.8-3.1 TB/s
+// direct; direct 4.2-5.4 TB/s for every other block against 3.2-4.2 staged).
+constexpr int DT_STAGE_LOW_BITS = 4;
 
 }  // namespace
 
@@ -48,7 +67,7 @@ __device__ __forceinline__ uint64_t dense_deposit(uint64_t g, uint32_t mask) {
 // from tensor memory (lane quarter = warp % 4, columns 16h.. and 32+16h..)
 // and stores them where it loaded them, so the update is in place.  The next
 // tile's loads are issued while the tensor core works on the current one.
-template <int NACC>
+template <int NACC, bool STAGED>
 __global__ void __launch_bounds__(DT_THREADS, 2) dense_tc_kernel(const DenseTcArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const int t = threadIdx.x, w = t >> 5;
@@ -81,16 +100,53 @@ __global__ void __launch_bounds__(DT_THREADS, 2) dense_tc_kernel(const DenseTcAr
   const uint32_t idesc = idesc_tf32(128, 64);
   const uint32_t lane_addr = tm + ((uint32_t)(32 * (w & 3)) << 16) + 16u * (uint32_t)h;
 
+  // staged layout: thread t moves tile indices 2t + 512m (+1), m < 8; the
+  // state offsets add up, the staging slots combine by XOR (swizzle)
+  uint32_t sx0 = 0, ss0 = 0, sx[8], ss[8];
+  if (STAGED) {
+#pragma unroll
+    for (int b = 1; b < 9; b++)
+      if ((t >> (b - 1)) & 1) {
+        sx0 += a.tx[b];
+        ss0 ^= a.ts[b];
+      }
+#pragma unroll
+    for (int m = 0; m < 8; m++) {
+      sx[m] = sx0 + ((m & 1) ? a.tx[9] : 0) + ((m & 2) ? a.tx[10] : 0) + ((m & 4) ? a.tx[11] : 0);
+      ss[m] = ss0 ^ ((m & 1) ? a.ts[9] : 0) ^ ((m & 2) ? a.ts[10] : 0) ^ ((m & 4) ? a.ts[11] : 0);
+    }
+  }
+  const uint32_t ss1 = a.ts[0];
+  float2 *stage = reinterpret_cast<float2 *>(sm + DT_OFF_ALO);
+
   uint32_t phase = 0;
   bool failed = false;
   float2 v[16];
+  float4 raw[8];
   uint64_t tile = blockIdx.x, xb = 0;
   if (tile < a.n_tiles) {
-    xb = dense_deposit(tile << 7, a.other_mask) | dr;
+    if (STAGED) {
+      xb = dense_deposit(tile << 7, a.other_mask);
 #pragma unroll
-    for (int j = 0; j < 16; j++) v[j] = __ldcs(a.state + xb + po[j]);
+      for (int m = 0; m < 8; m++) raw[m] = __ldcs(reinterpret_cast<const float4 *>(a.state + xb + sx[m]));
+    } else {
+      xb = dense_deposit(tile << 7, a.other_mask) | dr;
+#pragma unroll
+      for (int j = 0; j < 16; j++) v[j] = __ldcs(a.state + xb + po[j]);
+    }
   }
   for (; tile < a.n_tiles; tile += gridDim.x) {
+    if (STAGED) {
+#pragma unroll
+      for (int m = 0; m < 8; m++) {
+        *reinterpret_cast<float2 *>(sm + DT_OFF_ALO + ss[m]) = make_float2(raw[m].x, raw[m].y);
+        *reinterpret_cast<float2 *>(sm + DT_OFF_ALO + (ss[m] ^ ss1)) = make_float2(raw[m].z, raw[m].w);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < 16; j++) v[j] = stage[(16 * h + j) * 128 + (r ^ ((16 * h + j) >> 1))];
+      __syncthreads();
+    }
 #pragma unroll
     for (int c = 0; c < 4; c++) {
       float rh[4], rl[4], ih[4], il[4];
@@ -132,9 +188,15 @@ __global__ void __launch_bounds__(DT_THREADS, 2) dense_tc_kernel(const DenseTcAr
     }
     const uint64_t xcur = xb, nt = tile + gridDim.x;
     if (nt < a.n_tiles) {
-      xb = dense_deposit(nt << 7, a.other_mask) | dr;
+      if (STAGED) {
+        xb = dense_deposit(nt << 7, a.other_mask);
 #pragma unroll
-      for (int j = 0; j < 16; j++) v[j] = __ldcs(a.state + xb + po[j]);
+        for (int m = 0; m < 8; m++) raw[m] = __ldcs(reinterpret_cast<const float4 *>(a.state + xb + sx[m]));
+      } else {
+        xb = dense_deposit(nt << 7, a.other_mask) | dr;
+#pragma unroll
+        for (int j = 0; j < 16; j++) v[j] = __ldcs(a.state + xb + po[j]);
+      }
     }
     const bool ok = mbar_wait_bounded(bar, phase, DT_WAIT_NS);
     if (__syncthreads_or(!ok)) {
@@ -155,8 +217,20 @@ __global__ void __launch_bounds__(DT_THREADS, 2) dense_tc_kernel(const DenseTcAr
         im[j] += im2[j];
       }
     }
+    if (STAGED) {
 #pragma unroll
-    for (int j = 0; j < 16; j++) __stcs(a.state + xcur + po[j], make_float2(re[j], im[j]));
+      for (int j = 0; j < 16; j++) stage[(16 * h + j) * 128 + (r ^ ((16 * h + j) >> 1))] = make_float2(re[j], im[j]);
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < 8; m++) {
+        const float2 lo = *reinterpret_cast<const float2 *>(sm + DT_OFF_ALO + ss[m]);
+        const float2 hi = *reinterpret_cast<const float2 *>(sm + DT_OFF_ALO + (ss[m] ^ ss1));
+        __stcs(reinterpret_cast<float4 *>(a.state + xcur + sx[m]), make_float4(lo.x, lo.y, hi.x, hi.y));
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; j++) __stcs(a.state + xcur + po[j], make_float2(re[j], im[j]));
+    }
     tc_fence_before();
     __syncthreads();
   }
@@ -209,13 +283,17 @@ __global__ void __launch_bounds__(128) dense_simt_kernel(T2 *state, const T *u, 
   }
 }
 
+template <int NACC, bool STAGED>
+static cudaError_t dense_attr() {
+  return cudaFuncSetAttribute(dense_tc_kernel<NACC, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize, DT_SMEM);
+}
+
 cudaError_t dense_init_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(dense_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, DT_SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(dense_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, DT_SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(dense_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, DT_SMEM);
-  return e;
+  const cudaError_t e[6] = {dense_attr<1, false>(), dense_attr<2, false>(), dense_attr<4, false>(),
+                            dense_attr<1, true>(),  dense_attr<2, true>(),  dense_attr<4, true>()};
+  for (cudaError_t x : e)
+    if (x != cudaSuccess) return x;
+  return cudaSuccess;
 }
 
 void launch_dense_tc(float2 *state, uint32_t n, const DenseBlock &b5, const float *bops, int nacc, int *err,
@@ -230,11 +308,34 @@ void launch_dense_tc(float2 *state, uint32_t n, const DenseBlock &b5, const floa
   a.n_tiles = 1ull << (n - DENSE_TC_MIN_QUBITS);
   a.other_mask = dense_other_mask(b5, n);
   a.pos = dense_positions(b5);
+  // tile bits in ascending order: the block's 5 and the 7 lowest others
+  uint32_t tmask = ~a.other_mask & ((1u << n) - 1);
+  for (uint32_t m = a.other_mask, c = 0; m && c < 7; m &= m - 1, c++) tmask |= m & (~m + 1u);
+  for (uint32_t b = 0, m = tmask; b < 12; b++, m &= m - 1) {
+    const uint32_t q = (uint32_t)__builtin_ctz(m);
+    a.tx[b] = 1u << q;
+    uint32_t j = 0;
+    while (j < 5 && b5.q[j] != q) j++;
+    // byte offset of the staging slot, XOR-linear in the tile-index bits
+    if (j < 5) {
+      a.ts[b] = (((1u << j) << 7) ^ ((1u << j) >> 1)) * 8;  // position bit j (and its swizzle)
+    } else {
+      const uint32_t rho = (uint32_t)__builtin_popcount(a.other_mask & ((1u << q) - 1));
+      a.ts[b] = (1u << rho) * 8;  // row bit rho
+    }
+  }
+  const bool staged = __builtin_popcount(~a.other_mask & 31u) >= DT_STAGE_LOW_BITS;
   const int grid = (int)std::min<uint64_t>(a.n_tiles, (uint64_t)(2 * sm_count));
-  if (nacc == 4) dense_tc_kernel<4><<<grid, DT_THREADS, DT_SMEM, s>>>(a);
-  else if (nacc == 2) dense_tc_kernel<2><<<grid, DT_THREADS, DT_SMEM, s>>>(a);
-  else if (nacc == 1) dense_tc_kernel<1><<<grid, DT_THREADS, DT_SMEM, s>>>(a);
-  else fail(QW_ERR_INVALID_ARG, "nacc must be 1, 2 or 4");
+  if (nacc != 1 && nacc != 2 && nacc != 4) fail(QW_ERR_INVALID_ARG, "nacc must be 1, 2 or 4");
+  if (staged) {
+    if (nacc == 4) dense_tc_kernel<4, true><<<grid, DT_THREADS, DT_SMEM, s>>>(a);
+    else if (nacc == 2) dense_tc_kernel<2, true><<<grid, DT_THREADS, DT_SMEM, s>>>(a);
+    else dense_tc_kernel<1, true><<<grid, DT_THREADS, DT_SMEM, s>>>(a);
+  } else {
+    if (nacc == 4) dense_tc_kernel<4, false><<<grid, DT_THREADS, DT_SMEM, s>>>(a);
+    else if (nacc == 2) dense_tc_kernel<2, false><<<grid, DT_THREADS, DT_SMEM, s>>>(a);
+    else dense_tc_kernel<1, false><<<grid, DT_THREADS, DT_SMEM, s>>>(a);
+  }
 }
 
 void launch_dense_simt(bool fp64, void *state, uint32_t n, const DenseBlock &b, const void *u, int sm_count,

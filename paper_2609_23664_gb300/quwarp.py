@@ -459,7 +459,7 @@ class DenseProgram:
     explicit block (qubits, u)."""
 
     def __init__(self, engine: Engine, mode: int, n: int, gates: Optional[np.ndarray] = None,
-                 kmax: int = 5, engine_kind: int = DENSE_TENSOR, nacc: int = 1,
+                 kmax: int = 5, engine_kind: int = DENSE_TENSOR, nacc: int = 4,
                  block: Optional[tuple] = None):
         self.h = C.c_void_p()
         self.engine = engine

@@ -58,7 +58,8 @@ def rounded(psi, mode):
 
 @pytest.mark.parametrize("engine,nacc", [(T, 1), (T, 2), (T, 4), (S, 0)])
 @pytest.mark.parametrize("n,qubits", [(12, [0, 1, 2, 3, 4]), (13, [12, 0, 7, 3, 9]), (16, [15, 14, 13, 12, 11]),
-                                      (16, [2, 9]), (20, [19, 0, 10]), (14, [5]), (17, [3, 4, 5, 6])])
+                                      (16, [2, 9]), (20, [19, 0, 10]), (14, [5]), (17, [3, 4, 5, 6]),
+                                      (15, [1, 6, 3]), (16, [3, 1, 4, 2]), (20, [4, 3, 0, 1, 19])])
 def test_single_block_matches_oracle(eng, engine, nacc, n, qubits):
     rng = np.random.default_rng(n * 31 + len(qubits))
     u = random_unitary(rng, 1 << len(qubits))
