@@ -64,6 +64,10 @@ def parse_args():
                     help="1: energy blocks as work items of the persistent suffix launch")
     ap.add_argument("--tile-qubits", type=int, default=0, help="0: autotuned")
     ap.add_argument("--low-qubits", type=int, default=0, help="0: autotuned")
+    ap.add_argument("--dense-qubits", type=int, default=28,
+                    help="register of the tensor-core dense-block family (0: skip it)")
+    ap.add_argument("--dense-only", action="store_true",
+                    help="run only the dense-block family (one JSON line)")
     ap.add_argument("--window", type=int, default=0,
                     help="tasks advanced together in the persistent launch (0: all of a wave)")
     return ap.parse_args()
@@ -241,6 +245,13 @@ def run_native(a):
 
     eng = Q.Engine(local)
     info = eng.info()
+    if a.dense_only:
+        peak, peak_src = load_peaks()
+        if rank == 0:
+            print(json.dumps({"dense_tc": dense_family(a, eng, torch.cuda.current_stream(), peak),
+                              "peak_gbs": peak, "peak_source": peak_src}), flush=True)
+        R.finish(world)
+        return 0
     tasks = make_tasks(a, rank)
     n_tasks = len(tasks)
     stream = torch.cuda.current_stream()
@@ -419,6 +430,9 @@ def run_native(a):
             fams[key]["speedup"] = fams[key][ks[0]]["value"] / fams[key][ks[1]]["value"]
             fwl.close()
 
+    if a.dense_qubits > 0 and world == 1:
+        line.setdefault("families", {})["dense_tc"] = dense_family(a, eng, stream, peak)
+
     line["roofline"] = roofline
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         from oracle import oracle as orc
@@ -437,6 +451,71 @@ def run_native(a):
         print(json.dumps(line), flush=True)
     R.finish(world)
     return 0
+
+
+def gpu_ms(stream, fn, reps):
+    """Mean device time of fn() over reps calls, CUDA events on `stream`.  A
+    short device sleep is queued before the start event so that host-side
+    preparation inside fn (fusion, uploads) overlaps it and is not timed."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        torch.cuda._sleep(50_000_000)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def dense_family(a, eng, stream, peak_gbs):
+    """Fused dense blocks on the tensor cores (tcgen05, 3xTF32): one random
+    5-qubit unitary per pass over an FP32 state larger than L2, in the direct
+    and the staged layout and on the CUDA cores; and the 4-layer
+    hardware-efficient suffix at 24 qubits as 24 fused blocks against the
+    pass kernels that plans use."""
+    import torch
+    from paper_2609_23664_gb300 import quwarp as Q
+    n = a.dense_qubits
+    rng = np.random.default_rng(20260923)
+    st = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
+    st[0] = 1
+    sp = stream.cuda_stream
+    out = {"workload": "%d-qubit FP32 state (%.1f GiB, larger than L2): one random 5-qubit unitary per "
+                       "pass; 24-qubit 4-layer HEA suffix as fused 5-qubit blocks" % (n, (8 << n) / 2**30)}
+    state_bytes = 8 << n
+    for key, qubits, kind in (("block_pass", [5, 6, 7, 8, 9], Q.DENSE_TENSOR),
+                              ("block_pass_low_qubits", [0, 1, 2, 3, 4], Q.DENSE_TENSOR),
+                              ("block_pass_cuda_cores", [5, 6, 7, 8, 9], Q.DENSE_SIMT)):
+        z = rng.normal(size=(32, 32)) + 1j * rng.normal(size=(32, 32))
+        u, _ = np.linalg.qr(z)
+        prog = Q.DenseProgram(eng, W.MODE_SV_FP32, n, engine_kind=kind, nacc=4, block=(qubits, u))
+        ms = gpu_ms(stream, lambda: prog.run(st.data_ptr(), sp), 5)
+        prog.check()
+        prog.close()
+        gbs = 2 * state_bytes / (ms * 1e-3) / 1e9
+        out[key] = {"qubits": qubits, "engine": "tensor" if kind == Q.DENSE_TENSOR else "cuda_cores",
+                    "ms": ms, "gbs": gbs, "frac_of_measured_hbm": gbs / peak_gbs}
+    del st
+    torch.cuda.empty_cache()
+    n2 = 24
+    g = W.hea_circuit(np.random.default_rng(24), n2, 4)
+    s2 = torch.zeros(1 << n2, dtype=torch.complex64, device="cuda")
+    s2[0] = 1
+    prog = Q.DenseProgram(eng, W.MODE_SV_FP32, n2, gates=g, kmax=5, engine_kind=Q.DENSE_TENSOR, nacc=4)
+    t_dense = gpu_ms(stream, lambda: prog.run(s2.data_ptr(), sp), 5)
+    prog.check()
+    nb = prog.info()["blocks"]
+    prog.close()
+    t_pass = gpu_ms(stream, lambda: Q.sv_apply_dev(eng, W.MODE_SV_FP32, n2, s2.data_ptr(), g, stream=sp), 5)
+    out["hea_suffix_24q"] = {"gates": int(len(g)), "dense_blocks": nb, "tensor_blocks_ms": t_dense,
+                             "pass_kernels_ms": t_pass, "pass_kernels_speedup": t_dense / t_pass}
+    return out
 
 
 def plan_opts(a):
