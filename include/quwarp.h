@@ -152,6 +152,14 @@ void qw_engine_destroy(qw_engine *e);
 /* Measured/assumed bandwidth (GB/s) and SM count the cost model uses. */
 qw_status qw_engine_info(const qw_engine *e, double *hbm_gbs, int32_t *sm_count,
                          uint64_t *l2_bytes);
+/* Measures the L2 read bandwidth (GB/s) for the access pattern of the
+ * energy step: independent 64 KB blocks of an L2-resident buffer (half the
+ * L2, at most 64 MB) in hashed order, 16 loads of 16 bytes in flight per
+ * thread.  The energy of random Pauli strings reads each term's partner
+ * amplitudes from L2 (Sec. V workload families: repeated expectation
+ * evaluation), so this, not the HBM bandwidth, bounds it.  Synchronous;
+ * allocates and frees its buffer. */
+qw_status qw_engine_probe_l2(qw_engine *e, double *l2_read_gbs);
 
 /* Message of the last error on the calling thread ("" if none).  Valid until
  * the next qw_* call on this thread. */

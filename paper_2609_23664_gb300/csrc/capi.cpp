@@ -23,6 +23,7 @@ void plan_release(qw_plan *P);
 void *plan_state_ptr(const qw_plan *P, uint64_t t);
 void engine_init(Engine *E, const qw_engine_opts *o);
 void engine_release(Engine *E);
+double engine_probe_l2(Engine *E);
 void costmodel_train(Engine *E, const float *feat, const float *tgt, uint64_t n, uint32_t epochs,
                      uint32_t batch, float lr, uint64_t seed, float *final_loss);
 void costmodel_set(Engine *E, const float *params, const float *mean, const float *scale);
@@ -492,6 +493,13 @@ qw_status qw_costmodel_features(const qw_engine *e, const qw_workload *w, uint64
 }
 
 // ---- statevector kernels on caller buffers ----------------------------------------
+qw_status qw_engine_probe_l2(qw_engine *e, double *l2_read_gbs) {
+  QW_GUARD({
+    if (!e || !l2_read_gbs) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    *l2_read_gbs = engine_probe_l2(&e->e);
+  })
+}
+
 qw_status qw_sv_apply_dev(qw_engine *e, uint32_t mode, uint32_t n, void *state, const qw_gate *gates,
                           uint64_t n_gates, const int32_t *init, void *stream) {
   QW_GUARD({

@@ -1064,6 +1064,57 @@ __global__ void bw_probe_kernel(const float4 *a, float4 *b, size_t n) {
     b[i] = a[i];
 }
 
+// L2 read probe: 64 KB blocks of an L2-resident buffer in hashed order (the
+// access pattern of the energy kernel's partner reads: independent blocks
+// at scattered places), 16 independent 16-byte loads per thread per block.
+// Every block index is reduced modulo the block count, so all loads stay in
+// the buffer.
+__global__ void l2_probe_kernel(const float4 *__restrict__ buf, uint64_t n_blocks, int iters, float *sink) {
+  float acc = 0.f;
+  for (int it = 0; it < iters; it++) {
+    const uint64_t b = ((((uint64_t)blockIdx.x * iters + it) * 0x9E3779B97F4A7C15ull) >> 20) % n_blocks;
+    float4 v[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) v[j] = __ldg(buf + b * 4096 + j * 256 + threadIdx.x);
+#pragma unroll
+    for (int j = 0; j < 16; j++) acc += (v[j].x + v[j].y) + (v[j].z + v[j].w);
+  }
+  if (acc == 1.5e30f) sink[0] = acc;  // keeps the loads; the buffer holds zeros
+}
+
+double engine_probe_l2(Engine *E) {
+  CK(cudaSetDevice(E->device));
+  cudaStream_t s = (cudaStream_t)E->stream;
+  const size_t bytes = std::min<size_t>((size_t)64 << 20, (size_t)(E->l2_bytes / 2) & ~(size_t)0xFFFF);
+  if (bytes < ((size_t)1 << 20)) fail(QW_ERR_UNSUPPORTED, "L2 of %llu bytes is too small to probe", (unsigned long long)E->l2_bytes);
+  float4 *buf = nullptr;
+  float *sink = nullptr;
+  CK(cudaMalloc(&buf, bytes));
+  CK(cudaMalloc(&sink, sizeof(float)));
+  CK(cudaMemsetAsync(buf, 0, bytes, s));
+  const int grid = E->sm_count * 8, iters = 64;
+  const uint64_t nb = bytes / (size_t)65536;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int r = 0; r < 4; r++) {
+    CK(cudaEventRecord(e0, s));
+    l2_probe_kernel<<<grid, 256, 0, s>>>(buf, nb, iters, sink);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (r) best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  cudaFree(sink);
+  CK(cudaGetLastError());
+  return (double)grid * iters * 65536.0 / (best * 1e-3) / 1e9;
+}
+
 void engine_init(Engine *E, const qw_engine_opts *o) {
   E->device = o ? o->device : 0;
   CK(cudaSetDevice(E->device));

@@ -87,6 +87,7 @@ SIGNATURES = {
     "qw_engine_create": (_st, [_vp, _vp]),
     "qw_engine_destroy": (None, [_vp]),
     "qw_engine_info": (_st, [_vp, _vp, _vp, _vp]),
+    "qw_engine_probe_l2": (_st, [_vp, _vp]),
     "qw_last_error": (C.c_char_p, []),
     "qw_workload_create": (_st, [_vp]),
     "qw_workload_add_task": (_st, [_vp, _vp, _vp]),
@@ -174,6 +175,12 @@ class Engine:
         bw, sm, l2 = C.c_double(), C.c_int32(), C.c_uint64()
         _check(lib().qw_engine_info(self.h, C.byref(bw), C.byref(sm), C.byref(l2)))
         return {"hbm_gbs": bw.value, "sm_count": sm.value, "l2_bytes": l2.value}
+
+    def probe_l2(self) -> float:
+        """Measured L2 read bandwidth (GB/s) for the energy step's access pattern."""
+        v = C.c_double()
+        _check(lib().qw_engine_probe_l2(self.h, C.byref(v)))
+        return v.value
 
     def close(self):
         if getattr(self, "h", None):

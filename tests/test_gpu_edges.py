@@ -160,3 +160,12 @@ def test_largest_tableau_ghz_and_noiseless_surface_code(eng):
         s = p.syndrome(i).reshape(4, len(anc))
         assert np.all(s[:, zpos] == 0)
         assert np.array_equal(s[1:, xpos], np.repeat(s[:1, xpos], 3, axis=0))
+
+
+def test_l2_read_probe_exceeds_hbm_bandwidth(eng):
+    # the energy step's L2 read bandwidth (hashed 64 KB blocks of an
+    # L2-resident buffer) must come out above the HBM copy bandwidth the
+    # engine measured at start-up
+    l2 = eng.probe_l2()
+    hbm = eng.info()["hbm_gbs"]
+    assert np.isfinite(l2) and l2 > hbm, (l2, hbm)
