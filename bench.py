@@ -439,6 +439,16 @@ def run_native(a):
         line.setdefault("families", {})["dense_tc"] = dense_family(a, eng, stream, peak)
 
     line["roofline"] = roofline
+    # every task of the default workload against the oracle's stored energies
+    # (tests/golden/make_vqe24_energies.py, complex128)
+    gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "vqe24_256_energies.json")
+    if (rank == 0 and os.path.exists(gold) and (a.qubits, a.tasks, a.prefix_layers, a.terms) == (24, 256, 20, 200)):
+        ref = np.array([t["energy"] for t in json.load(open(gold))["tasks"]])
+        rel = np.abs(np.array(e_last) - ref) / np.abs(ref)
+        line["parity_all_tasks"] = {"tasks": int(len(rel)), "max_rel_energy_error": float(rel.max()),
+                                    "median_rel_energy_error": float(np.median(rel)),
+                                    "tasks_above_1e-6": int(np.sum(rel > 1e-6)),
+                                    "reference": "oracle energies, complex128, tests/golden/vqe24_256_energies.json"}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         from oracle import oracle as orc
         orc.build()
