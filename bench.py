@@ -444,10 +444,16 @@ def run_native(a):
     gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "vqe24_256_energies.json")
     if (rank == 0 and os.path.exists(gold) and (a.qubits, a.tasks, a.prefix_layers, a.terms) == (24, 256, 20, 200)):
         ref = np.array([t["energy"] for t in json.load(open(gold))["tasks"]])
-        rel = np.abs(np.array(e_last) - ref) / np.abs(ref)
-        line["parity_all_tasks"] = {"tasks": int(len(rel)), "max_rel_energy_error": float(rel.max()),
+        err = np.abs(np.array(e_last) - ref)
+        rel = err / np.abs(ref)
+        coef = tasks[0].terms["coef"]
+        e_typ = float(np.sqrt(np.sum(coef ** 2))) * 2.0 ** (-a.qubits / 2)
+        normed = err / np.maximum(np.abs(ref), e_typ)
+        line["parity_all_tasks"] = {"tasks": int(len(rel)), "max_abs_energy_error": float(err.max()),
+                                    "max_rel_energy_error": float(rel.max()),
                                     "median_rel_energy_error": float(np.median(rel)),
-                                    "tasks_above_1e-6": int(np.sum(rel > 1e-6)),
+                                    "tasks_rel_above_1e-6": int(np.sum(rel > 1e-6)),
+                                    "e_typ": e_typ, "max_error_over_max_absE_etyp": float(normed.max()),
                                     "reference": "oracle energies, complex128, tests/golden/vqe24_256_energies.json"}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         from oracle import oracle as orc

@@ -19,12 +19,17 @@ if not torch.cuda.is_available():
 from paper_2609_23664_gb300 import quwarp as Q  # noqa: E402
 
 
-# Relative energy error bounds over all 256 tasks of the 24-qubit sweep
-# (|E| ~ 3e-3 against sum |c_k| ~ 160: the energy is a near-cancellation, so
-# the FP32 state's rounding shows up at the 1e-6 level): FP32 throughout,
-# and with the shared prefix in FP64.  Set a little above the maxima
-# measured on GB300.
-REL_BOUND = {0: 1e-5, 1: 1e-5}
+# Energy error bounds over all 256 tasks of the 24-qubit sweep, FP32
+# throughout (0) and with the shared prefix in FP64 (1).  The energy of a
+# random-like 24-qubit state is a near-cancellation: its typical size is
+# E_typ = ||c||_2 2^(-n/2) = 3.6e-3 against sum |c_k| = 166, and 1 % of the
+# tasks have |E| < 0.006 E_typ, where any relative error diverges.  So the
+# bound is on the error normalized by max(|E_ref|, E_typ), plus the median
+# relative error; both a little above the values measured on GB300 (FP32:
+# normalized max 4.8e-6, median relative 1.24e-6; FP64 prefix: 1.45e-6 and
+# 3.9e-7).
+NORM_BOUND = {0: 1e-5, 1: 3e-6}
+MEDIAN_REL_BOUND = {0: 2e-6, 1: 6e-7}
 
 
 @pytest.fixture(scope="module")
@@ -78,9 +83,13 @@ def test_config2_vqe24_every_task_against_stored_oracle(eng, prefix_fp64):
     rel = np.abs(e - ref) / np.abs(ref)
     print("prefix_fp64 %d: relative energy error over %d tasks: max %.2e median %.2e, above 1e-6: %d"
           % (prefix_fp64, len(rel), rel.max(), np.median(rel), int(np.sum(rel > 1e-6))))
-    csum = float(np.sum(np.abs(tasks[0].terms["coef"])))
-    assert np.all(np.abs(e - ref) <= 2e-5 * csum)
-    assert rel.max() <= REL_BOUND[prefix_fp64], rel.max()
+    c = tasks[0].terms["coef"]
+    e_typ = float(np.sqrt(np.sum(c ** 2))) * 2.0 ** (-24 / 2)
+    normed = np.abs(e - ref) / np.maximum(np.abs(ref), e_typ)
+    print("  error / max(|E_ref|, E_typ): max %.2e median %.2e" % (normed.max(), np.median(normed)))
+    assert np.all(np.abs(e - ref) <= 2e-5 * float(np.sum(np.abs(c))))
+    assert normed.max() <= NORM_BOUND[prefix_fp64], normed.max()
+    assert np.median(rel) <= MEDIAN_REL_BOUND[prefix_fp64], np.median(rel)
 
 
 _ORACLE = {}
