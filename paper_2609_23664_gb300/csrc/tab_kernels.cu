@@ -127,15 +127,45 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, ln = threadIdx.x & 31;
   const uint32_t gpw = 32 / lpp;  // slot groups per warp
   const uint32_t w = ln % lpp;
+  // The first TAB_SLOT_STAGE slots of the next layer (and its descriptor)
+  // are loaded into registers while the current layer runs, so staging a
+  // layer costs a shared-memory store instead of a dependent global load.
+  constexpr int PRE = TAB_SLOT_STAGE / TAB_THREADS;
+  static_assert(PRE * TAB_THREADS == TAB_SLOT_STAGE, "slot prefetch shape");
+  TabSlot pre[PRE];
+  TabLayer L = {};
+  auto prefetch = [&](uint32_t li) {
+    if (li >= P.n_layers) return;
+    L = A.layers[P.layer_begin + li];
+    const uint32_t cn = min(TAB_SLOT_STAGE, L.n_slots);
+#pragma unroll
+    for (int k = 0; k < PRE; k++) {
+      const uint32_t i = threadIdx.x + (uint32_t)k * TAB_THREADS;
+      if (i < cn) pre[k] = A.slots[L.slot_begin + i];
+    }
+  };
+  prefetch(0);
   for (uint32_t li = 0; li < P.n_layers; li++) {
-    const TabLayer L = A.layers[P.layer_begin + li];
-    if (!L.is_measure) {
+    const TabLayer cur = L;
+    {
+      const uint32_t cn = min(TAB_SLOT_STAGE, cur.n_slots);
+#pragma unroll
+      for (int k = 0; k < PRE; k++) {
+        const uint32_t i = threadIdx.x + (uint32_t)k * TAB_THREADS;
+        if (i < cn) S.sl[i] = pre[k];
+      }
+    }
+    __syncthreads();
+    if (cur.n_slots <= TAB_SLOT_STAGE) prefetch(li + 1);
+    if (!cur.is_measure) {
       // the layer's slots are staged in shared memory (one coalesced read
       // instead of a dependent global load per slot group)
-      for (uint32_t c0 = 0; c0 < L.n_slots; c0 += TAB_SLOT_STAGE) {
-      const uint32_t cn = min(TAB_SLOT_STAGE, L.n_slots - c0);
-      for (uint32_t i = threadIdx.x; i < cn; i += blockDim.x) S.sl[i] = A.slots[L.slot_begin + c0 + i];
-      __syncthreads();
+      for (uint32_t c0 = 0; c0 < cur.n_slots; c0 += TAB_SLOT_STAGE) {
+      const uint32_t cn = min(TAB_SLOT_STAGE, cur.n_slots - c0);
+      if (c0 > 0) {
+        for (uint32_t i = threadIdx.x; i < cn; i += blockDim.x) S.sl[i] = A.slots[cur.slot_begin + c0 + i];
+        __syncthreads();
+      }
       for (uint32_t sb = warp * gpw; sb < cn; sb += nwarps * gpw) {
         const uint32_t si = sb + ln / lpp;
         const bool act = si < cn;
@@ -177,15 +207,15 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
       }
       __syncthreads();
       }
+      if (cur.n_slots > TAB_SLOT_STAGE) prefetch(li + 1);
     } else {
       // a measurement layer holds at most one slot per qubit (<= 640), so
-      // all of its slots fit the staging buffer
-      for (uint32_t i = threadIdx.x; i < L.n_slots; i += blockDim.x) S.sl[i] = A.slots[L.slot_begin + i];
-      __syncthreads();
+      // all of its slots are in the staging buffer already
       // phase 1: deterministic outcomes in parallel, random ones flagged
-      for (uint32_t sb = warp * gpw; sb < L.n_slots; sb += nwarps * gpw) {
+      int my_pending = 0;
+      for (uint32_t sb = warp * gpw; sb < cur.n_slots; sb += nwarps * gpw) {
         const uint32_t si = sb + ln / lpp;
-        const bool act = si < L.n_slots;
+        const bool act = si < cur.n_slots;
         TabSlot sl{};
         if (act) sl = S.sl[si];
         uint64_t v = 0;
@@ -199,18 +229,21 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
             S.pending[si] = 0;
           } else {
             S.pending[si] = 1;
+            my_pending = 1;
           }
         }
       }
-      __syncthreads();
-      // phase 2: random outcomes one at a time, in program order
-      for (uint32_t si = 0; si < L.n_slots; si++) {
-        if (S.pending[si]) {
-          const TabSlot sl = S.sl[si];
-          tab_collapse(A, S, sl, bits_base, out_base);
+      // phase 2 (only when some outcome is random): one at a time, in
+      // program order
+      if (__syncthreads_or(my_pending)) {
+        for (uint32_t si = 0; si < cur.n_slots; si++) {
+          if (S.pending[si]) {
+            const TabSlot sl = S.sl[si];
+            tab_collapse(A, S, sl, bits_base, out_base);
+          }
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
 }
