@@ -35,26 +35,41 @@ struct TabSm {
   uint64_t *xs;    // W words (collapse scratch)
   TabSlot *sl;     // TAB_SLOT_STAGE staged slots
   uint32_t *any_random;
+  uint32_t W, W2;  // words per half row, per row
+  uint32_t swz;    // word swizzle mask (2W - 1 when 2W is a power of two <= 16, else 0)
 };
 
-__device__ __forceinline__ int getb(const uint64_t *row, uint32_t q) {
-  return (int)((row[q >> 6] >> (q & 63)) & 1ull);
+// Word c of row r (x words 0..W-1, then z words W..2W-1).  When a row is a
+// power-of-two number of words, word c is stored at position c ^ (r mod 2W)
+// of its row, so that 32 threads reading word c of 32 different rows
+// spread over the shared-memory banks instead of all hitting one.
+__device__ __forceinline__ uint64_t &tw(const TabSm &S, uint32_t r, uint32_t c) {
+  return S.R[(size_t)r * S.W2 + (c ^ (r & S.swz))];
 }
-__device__ __forceinline__ void flipb(uint64_t *row, uint32_t q) { row[q >> 6] ^= 1ull << (q & 63); }
+__device__ __forceinline__ int getx(const TabSm &S, uint32_t r, uint32_t q) {
+  return (int)((tw(S, r, q >> 6) >> (q & 63)) & 1ull);
+}
+__device__ __forceinline__ int getz(const TabSm &S, uint32_t r, uint32_t q) {
+  return (int)((tw(S, r, S.W + (q >> 6)) >> (q & 63)) & 1ull);
+}
+__device__ __forceinline__ void flipx(const TabSm &S, uint32_t r, uint32_t q) { tw(S, r, q >> 6) ^= 1ull << (q & 63); }
+__device__ __forceinline__ void flipz(const TabSm &S, uint32_t r, uint32_t q) {
+  tw(S, r, S.W + (q >> 6)) ^= 1ull << (q & 63);
+}
 
-// column op in the initial frame: CNOT(c -> t) conjugation of one row
-__device__ __forceinline__ void col_cnot(uint64_t *x, uint64_t *z, uint8_t *r, uint32_t c, uint32_t t) {
-  const int xc = getb(x, c), zc = getb(z, c), xt = getb(x, t), zt = getb(z, t);
-  *r ^= (uint8_t)(xc & zt & (xt ^ zc ^ 1));
-  if (xc) flipb(x, t);
-  if (zt) flipb(z, c);
+// column op in the initial frame: CNOT(c -> t) conjugation of row r
+__device__ __forceinline__ void col_cnot(const TabSm &S, uint32_t r, uint8_t *sg, uint32_t c, uint32_t t) {
+  const int xc = getx(S, r, c), zc = getz(S, r, c), xt = getx(S, r, t), zt = getz(S, r, t);
+  *sg ^= (uint8_t)(xc & zt & (xt ^ zc ^ 1));
+  if (xc) flipx(S, r, t);
+  if (zt) flipz(S, r, c);
 }
 
 __device__ void tab_collapse(const TabArgs &A, TabSm &S, const TabSlot &sl, uint32_t bits_base,
                              uint32_t out_base) {
   const uint32_t n = A.n, W = A.W, rows = A.rows, row = sl.dst;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid < (int)W) S.xs[tid] = S.R[(size_t)row * 2 * W + tid];
+  if (tid < (int)W) S.xs[tid] = tw(S, row, (uint32_t)tid);
   __syncthreads();
   int first = -1;
   for (uint32_t w = 0; w < W; w++)
@@ -75,7 +90,6 @@ __device__ void tab_collapse(const TabArgs &A, TabSm &S, const TabSlot &sl, uint
   if (tid == 0) *S.any_random = 1u;
   // 1) CNOT(p -> q) for every other q in the X part of T(Z_a)
   for (uint32_t r = tid; r < rows; r += nt) {
-    uint64_t *x = S.R + (size_t)r * 2 * W, *z = x + W;
     uint8_t sg = S.sign[r];
     for (uint32_t w = 0; w < W; w++) {
       uint64_t bitsw = S.xs[w];
@@ -83,21 +97,20 @@ __device__ void tab_collapse(const TabArgs &A, TabSm &S, const TabSlot &sl, uint
       while (bitsw) {
         const uint32_t q = w * 64 + __ffsll((long long)bitsw) - 1;
         bitsw &= bitsw - 1;
-        col_cnot(x, z, &sg, p, q);
+        col_cnot(S, r, &sg, p, q);
       }
     }
     S.sign[r] = sg;
   }
   __syncthreads();
   // 2) Y -> X at p by S^dagger conjugation when T(Z_a) has Z at p
-  const int zp = getb(S.R + (size_t)row * 2 * W + W, p);
+  const int zp = getz(S, row, p);
   __syncthreads();
   if (zp) {
     for (uint32_t r = tid; r < rows; r += nt) {
-      uint64_t *x = S.R + (size_t)r * 2 * W, *z = x + W;
-      const int xb = getb(x, p), zb = getb(z, p);
+      const int xb = getx(S, r, p), zb = getz(S, r, p);
       S.sign[r] ^= (uint8_t)(xb & (zb ^ 1));
-      if (xb) flipb(z, p);
+      if (xb) flipz(S, r, p);
     }
     __syncthreads();
   }
@@ -106,10 +119,9 @@ __device__ void tab_collapse(const TabArgs &A, TabSm &S, const TabSlot &sl, uint
   __syncthreads();
   const int bb = (int)(m ^ s);
   for (uint32_t r = tid; r < rows; r += nt) {
-    uint64_t *x = S.R + (size_t)r * 2 * W, *z = x + W;
-    const int xb = getb(x, p), zb = getb(z, p);
+    const int xb = getx(S, r, p), zb = getz(S, r, p);
     uint8_t sg = S.sign[r] ^ (uint8_t)(xb & zb);
-    if (xb != zb) { flipb(x, p); flipb(z, p); }
+    if (xb != zb) { flipx(S, r, p); flipz(S, r, p); }
     if (bb) sg ^= (uint8_t)xb;  // new z bit at p equals the old x bit
     S.sign[r] = sg;
   }
@@ -166,6 +178,38 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
         for (uint32_t i = threadIdx.x; i < cn; i += blockDim.x) S.sl[i] = A.slots[cur.slot_begin + c0 + i];
         __syncthreads();
       }
+      if (S.swz) {
+        // one thread per slot over all the row's words (swizzled rows keep
+        // the 32 rows of a warp on different banks)
+        for (uint32_t i = threadIdx.x; i < cn; i += blockDim.x) {
+          const TabSlot sl = S.sl[i];
+          if (sl.kind == T_PROD) {
+            int t = 0;
+            for (uint32_t c = 0; c < W; c++) {
+              const uint64_t x1 = tw(S, sl.s1, c), z1 = tw(S, sl.s1, W + c);
+              const uint64_t x2 = tw(S, sl.s2, c), z2 = tw(S, sl.s2, W + c);
+              const uint64_t x3 = x1 ^ x2, z3 = z1 ^ z2;
+              t += __popcll(x1 & z1) + __popcll(x2 & z2) - __popcll(x3 & z3) + 2 * __popcll(z1 & x2);
+              tw(S, sl.dst, c) = x3;
+              tw(S, sl.dst, W + c) = z3;
+            }
+            S.sign[sl.dst] = S.sign[sl.s1] ^ S.sign[sl.s2] ^ (uint8_t)((((t + sl.flags) & 3) >> 1) & 1);
+          } else if (sl.kind == T_SWAP2) {
+            for (uint32_t c = 0; c < 2 * W; c++) {
+              const uint64_t a0 = tw(S, sl.dst, c);
+              tw(S, sl.dst, c) = tw(S, sl.s2, c);
+              tw(S, sl.s2, c) = a0;
+            }
+            const uint8_t tmp = S.sign[sl.dst];
+            S.sign[sl.dst] = S.sign[sl.s2];
+            S.sign[sl.s2] = tmp;
+          } else if (sl.kind == T_SIGN) {
+            S.sign[sl.dst] ^= 1;
+          }
+        }
+        __syncthreads();
+        continue;
+      }
       for (uint32_t sb = warp * gpw; sb < cn; sb += nwarps * gpw) {
         const uint32_t si = sb + ln / lpp;
         const bool act = si < cn;
@@ -174,22 +218,20 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
         int t = 0;
         if (act && sl.kind == T_PROD) {
           if (w < W) {
-            uint64_t *d = S.R + (size_t)sl.dst * 2 * W;
-            const uint64_t *p1 = S.R + (size_t)sl.s1 * 2 * W, *p2 = S.R + (size_t)sl.s2 * 2 * W;
-            const uint64_t x1 = p1[w], z1 = p1[W + w], x2 = p2[w], z2 = p2[W + w];
+            const uint64_t x1 = tw(S, sl.s1, w), z1 = tw(S, sl.s1, W + w);
+            const uint64_t x2 = tw(S, sl.s2, w), z2 = tw(S, sl.s2, W + w);
             const uint64_t x3 = x1 ^ x2, z3 = z1 ^ z2;
             t = __popcll(x1 & z1) + __popcll(x2 & z2) - __popcll(x3 & z3) + 2 * __popcll(z1 & x2);
-            d[w] = x3;
-            d[W + w] = z3;
+            tw(S, sl.dst, w) = x3;
+            tw(S, sl.dst, W + w) = z3;
           }
         } else if (act && sl.kind == T_SWAP2) {
           if (w < W) {
-            uint64_t *r1 = S.R + (size_t)sl.dst * 2 * W, *r2 = S.R + (size_t)sl.s2 * 2 * W;
-            uint64_t a0 = r1[w], a1 = r1[W + w];
-            r1[w] = r2[w];
-            r1[W + w] = r2[W + w];
-            r2[w] = a0;
-            r2[W + w] = a1;
+            const uint64_t a0 = tw(S, sl.dst, w), a1 = tw(S, sl.dst, W + w);
+            tw(S, sl.dst, w) = tw(S, sl.s2, w);
+            tw(S, sl.dst, W + w) = tw(S, sl.s2, W + w);
+            tw(S, sl.s2, w) = a0;
+            tw(S, sl.s2, W + w) = a1;
           }
         }
         for (uint32_t o = lpp >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o, lpp);
@@ -219,7 +261,7 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
         TabSlot sl{};
         if (act) sl = S.sl[si];
         uint64_t v = 0;
-        if (act && w < W) v = S.R[(size_t)sl.dst * 2 * W + w];
+        if (act && w < W) v = tw(S, sl.dst, w);
         for (uint32_t o = lpp >> 1; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o, lpp);
         if (act && w == 0) {
           if (v == 0) {
@@ -261,10 +303,14 @@ __global__ void __launch_bounds__(TAB_THREADS) tab_kernel(TabArgs A) {
   S.pending = S.sign + ((rows + 15) & ~15u);
   S.xs = (uint64_t *)(S.pending + ((A.n + 15) & ~15u));
   S.sl = (TabSlot *)(S.xs + ((W + 1) & ~1u));
+  S.W = W;
+  S.W2 = 2 * W;
+  S.swz = (W == 1 || W == 2 || W == 4 || W == 8) ? 2 * W - 1 : 0u;
   const size_t nwords = (size_t)rows * 2 * W;
   const TabTaskDesc T = A.tasks[blockIdx.x];
   if (A.init_rows) {
-    for (size_t i = threadIdx.x; i < nwords; i += blockDim.x) S.R[i] = __ldg(A.init_rows + i);
+    for (size_t i = threadIdx.x; i < nwords; i += blockDim.x)
+      tw(S, (uint32_t)(i / (2 * W)), (uint32_t)(i % (2 * W))) = __ldg(A.init_rows + i);
     for (uint32_t i = threadIdx.x; i < rows; i += blockDim.x) S.sign[i] = __ldg(A.init_sign + i);
   } else {
     for (size_t i = threadIdx.x; i < nwords; i += blockDim.x) {
@@ -277,7 +323,7 @@ __global__ void __launch_bounds__(TAB_THREADS) tab_kernel(TabArgs A) {
         const uint32_t q = r - A.n;
         if (c >= W && (q >> 6) == c - W) v = 1ull << (q & 63);
       }
-      S.R[i] = v;
+      tw(S, r, c) = v;
     }
     for (uint32_t i = threadIdx.x; i < rows; i += blockDim.x) S.sign[i] = 0;
   }
@@ -291,7 +337,8 @@ __global__ void __launch_bounds__(TAB_THREADS) tab_kernel(TabArgs A) {
   if (A.rand_any && threadIdx.x == 0) A.rand_any[blockIdx.x] = s_any_random;
   if (A.out_rows) {
     uint64_t *o = A.out_rows + (size_t)blockIdx.x * nwords;
-    for (size_t i = threadIdx.x; i < nwords; i += blockDim.x) o[i] = S.R[i];
+    for (size_t i = threadIdx.x; i < nwords; i += blockDim.x)
+      o[i] = tw(S, (uint32_t)(i / (2 * W)), (uint32_t)(i % (2 * W)));
     uint8_t *os = A.out_sign + (size_t)blockIdx.x * rows;
     for (uint32_t i = threadIdx.x; i < rows; i += blockDim.x) os[i] = S.sign[i];
   }
