@@ -255,15 +255,11 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
       // all of its slots are in the staging buffer already
       // phase 1: deterministic outcomes in parallel, random ones flagged
       int my_pending = 0;
-      for (uint32_t sb = warp * gpw; sb < cur.n_slots; sb += nwarps * gpw) {
-        const uint32_t si = sb + ln / lpp;
-        const bool act = si < cur.n_slots;
-        TabSlot sl{};
-        if (act) sl = S.sl[si];
-        uint64_t v = 0;
-        if (act && w < W) v = tw(S, sl.dst, w);
-        for (uint32_t o = lpp >> 1; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o, lpp);
-        if (act && w == 0) {
+      if (S.swz) {  // one thread per slot (swizzled rows)
+        for (uint32_t si = threadIdx.x; si < cur.n_slots; si += blockDim.x) {
+          const TabSlot sl = S.sl[si];
+          uint64_t v = 0;
+          for (uint32_t c = 0; c < W; c++) v |= tw(S, sl.dst, c);
           if (v == 0) {
             const uint8_t oc = S.sign[sl.dst];
             if (sl.aux2 != 0xFFFFFFFFu) A.outs[out_base + sl.aux2] = oc;
@@ -272,6 +268,27 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
           } else {
             S.pending[si] = 1;
             my_pending = 1;
+          }
+        }
+      } else {
+        for (uint32_t sb = warp * gpw; sb < cur.n_slots; sb += nwarps * gpw) {
+          const uint32_t si = sb + ln / lpp;
+          const bool act = si < cur.n_slots;
+          TabSlot sl{};
+          if (act) sl = S.sl[si];
+          uint64_t v = 0;
+          if (act && w < W) v = tw(S, sl.dst, w);
+          for (uint32_t o = lpp >> 1; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o, lpp);
+          if (act && w == 0) {
+            if (v == 0) {
+              const uint8_t oc = S.sign[sl.dst];
+              if (sl.aux2 != 0xFFFFFFFFu) A.outs[out_base + sl.aux2] = oc;
+              if ((sl.flags & 1) && oc) S.sign[sl.dst] ^= 1;
+              S.pending[si] = 0;
+            } else {
+              S.pending[si] = 1;
+              my_pending = 1;
+            }
           }
         }
       }
