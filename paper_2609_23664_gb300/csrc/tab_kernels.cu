@@ -139,26 +139,36 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, ln = threadIdx.x & 31;
   const uint32_t gpw = 32 / lpp;  // slot groups per warp
   const uint32_t w = ln % lpp;
-  // The first TAB_SLOT_STAGE slots of the next layer (and its descriptor)
-  // are loaded into registers while the current layer runs, so staging a
-  // layer costs a shared-memory store instead of a dependent global load.
+  // The first TAB_SLOT_STAGE slots of the next layer are loaded into
+  // registers while the current layer runs, and the descriptor of the layer
+  // after it as well, so that neither staging a layer nor starting its
+  // prefetch waits on a dependent global load.
   constexpr int PRE = TAB_SLOT_STAGE / TAB_THREADS;
   static_assert(PRE * TAB_THREADS == TAB_SLOT_STAGE, "slot prefetch shape");
   TabSlot pre[PRE];
-  TabLayer L = {};
+  TabLayer Lnext = {}, Lafter = {};
+  auto desc = [&](uint32_t li) {
+    TabLayer d = {};
+    if (li < P.n_layers) d = A.layers[P.layer_begin + li];
+    return d;
+  };
+  // slots of layer li (descriptor Lnext) into pre[], descriptor of li + 1
+  // into Lafter
   auto prefetch = [&](uint32_t li) {
     if (li >= P.n_layers) return;
-    L = A.layers[P.layer_begin + li];
-    const uint32_t cn = min(TAB_SLOT_STAGE, L.n_slots);
+    const uint32_t cn = min(TAB_SLOT_STAGE, Lnext.n_slots);
 #pragma unroll
     for (int k = 0; k < PRE; k++) {
       const uint32_t i = threadIdx.x + (uint32_t)k * TAB_THREADS;
-      if (i < cn) pre[k] = A.slots[L.slot_begin + i];
+      if (i < cn) pre[k] = A.slots[Lnext.slot_begin + i];
     }
+    Lafter = desc(li + 1);
   };
+  Lnext = desc(0);
   prefetch(0);
   for (uint32_t li = 0; li < P.n_layers; li++) {
-    const TabLayer cur = L;
+    const TabLayer cur = Lnext;
+    Lnext = Lafter;
     {
       const uint32_t cn = min(TAB_SLOT_STAGE, cur.n_slots);
 #pragma unroll
