@@ -65,6 +65,44 @@ __device__ __forceinline__ void col_cnot(const TabSm &S, uint32_t r, uint8_t *sg
   if (zt) flipz(S, r, c);
 }
 
+// One unitary slot by one thread, W a power of two (swizzled rows): the
+// row bases and swizzles are computed once, the word loop is unrolled.
+template <uint32_t W>
+__device__ __forceinline__ void tab_slot(const TabSm &S, const TabSlot &sl) {
+  constexpr uint32_t M = 2 * W - 1;
+  uint64_t *rd = S.R + (size_t)sl.dst * (2 * W);
+  const uint32_t kd = sl.dst & M;
+  if (sl.kind == T_PROD) {
+    const uint64_t *r1 = S.R + (size_t)sl.s1 * (2 * W), *r2 = S.R + (size_t)sl.s2 * (2 * W);
+    const uint32_t k1 = sl.s1 & M, k2 = sl.s2 & M;
+    int t = 0;
+#pragma unroll
+    for (uint32_t c = 0; c < W; c++) {
+      const uint64_t x1 = r1[c ^ k1], z1 = r1[(W + c) ^ k1];
+      const uint64_t x2 = r2[c ^ k2], z2 = r2[(W + c) ^ k2];
+      const uint64_t x3 = x1 ^ x2, z3 = z1 ^ z2;
+      t += __popcll(x1 & z1) + __popcll(x2 & z2) - __popcll(x3 & z3) + 2 * __popcll(z1 & x2);
+      rd[c ^ kd] = x3;
+      rd[(W + c) ^ kd] = z3;
+    }
+    S.sign[sl.dst] = S.sign[sl.s1] ^ S.sign[sl.s2] ^ (uint8_t)((((t + sl.flags) & 3) >> 1) & 1);
+  } else if (sl.kind == T_SWAP2) {
+    uint64_t *r2 = S.R + (size_t)sl.s2 * (2 * W);
+    const uint32_t k2 = sl.s2 & M;
+#pragma unroll
+    for (uint32_t c = 0; c < 2 * W; c++) {
+      const uint64_t a0 = rd[c ^ kd];
+      rd[c ^ kd] = r2[c ^ k2];
+      r2[c ^ k2] = a0;
+    }
+    const uint8_t tmp = S.sign[sl.dst];
+    S.sign[sl.dst] = S.sign[sl.s2];
+    S.sign[sl.s2] = tmp;
+  } else if (sl.kind == T_SIGN) {
+    S.sign[sl.dst] ^= 1;
+  }
+}
+
 __device__ void tab_collapse(const TabArgs &A, TabSm &S, const TabSlot &sl, uint32_t bits_base,
                              uint32_t out_base) {
   const uint32_t n = A.n, W = A.W, rows = A.rows, row = sl.dst;
@@ -193,28 +231,11 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
         // the 32 rows of a warp on different banks)
         for (uint32_t i = threadIdx.x; i < cn; i += blockDim.x) {
           const TabSlot sl = S.sl[i];
-          if (sl.kind == T_PROD) {
-            int t = 0;
-            for (uint32_t c = 0; c < W; c++) {
-              const uint64_t x1 = tw(S, sl.s1, c), z1 = tw(S, sl.s1, W + c);
-              const uint64_t x2 = tw(S, sl.s2, c), z2 = tw(S, sl.s2, W + c);
-              const uint64_t x3 = x1 ^ x2, z3 = z1 ^ z2;
-              t += __popcll(x1 & z1) + __popcll(x2 & z2) - __popcll(x3 & z3) + 2 * __popcll(z1 & x2);
-              tw(S, sl.dst, c) = x3;
-              tw(S, sl.dst, W + c) = z3;
-            }
-            S.sign[sl.dst] = S.sign[sl.s1] ^ S.sign[sl.s2] ^ (uint8_t)((((t + sl.flags) & 3) >> 1) & 1);
-          } else if (sl.kind == T_SWAP2) {
-            for (uint32_t c = 0; c < 2 * W; c++) {
-              const uint64_t a0 = tw(S, sl.dst, c);
-              tw(S, sl.dst, c) = tw(S, sl.s2, c);
-              tw(S, sl.s2, c) = a0;
-            }
-            const uint8_t tmp = S.sign[sl.dst];
-            S.sign[sl.dst] = S.sign[sl.s2];
-            S.sign[sl.s2] = tmp;
-          } else if (sl.kind == T_SIGN) {
-            S.sign[sl.dst] ^= 1;
+          switch (W) {
+            case 8: tab_slot<8>(S, sl); break;
+            case 4: tab_slot<4>(S, sl); break;
+            case 2: tab_slot<2>(S, sl); break;
+            default: tab_slot<1>(S, sl); break;
           }
         }
         __syncthreads();
@@ -268,8 +289,10 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
       if (S.swz) {  // one thread per slot (swizzled rows)
         for (uint32_t si = threadIdx.x; si < cur.n_slots; si += blockDim.x) {
           const TabSlot sl = S.sl[si];
+          const uint64_t *rr = S.R + (size_t)sl.dst * S.W2;
+          const uint32_t kr = sl.dst & S.swz;
           uint64_t v = 0;
-          for (uint32_t c = 0; c < W; c++) v |= tw(S, sl.dst, c);
+          for (uint32_t c = 0; c < W; c++) v |= rr[c ^ kr];
           if (v == 0) {
             const uint8_t oc = S.sign[sl.dst];
             if (sl.aux2 != 0xFFFFFFFFu) A.outs[out_base + sl.aux2] = oc;
