@@ -534,8 +534,15 @@ def dense_family(a, eng, stream, peak_gbs):
     nb = prog.info()["blocks"]
     prog.close()
     t_pass = gpu_ms(stream, lambda: Q.sv_apply_dev(eng, W.MODE_SV_FP32, n2, s2.data_ptr(), g, stream=sp), 5)
+    auto = Q.DenseProgram(eng, W.MODE_SV_FP32, n2, gates=g, kmax=0, engine_kind=Q.DENSE_AUTO)
+    cfg = auto.config()
+    t_auto = gpu_ms(stream, lambda: auto.run(s2.data_ptr(), sp), 5)
+    auto.close()
     out["hea_suffix_24q"] = {"gates": int(len(g)), "dense_blocks": nb, "tensor_blocks_ms": t_dense,
-                             "pass_kernels_ms": t_pass, "pass_kernels_speedup": t_dense / t_pass}
+                             "pass_kernels_ms": t_pass, "pass_kernels_speedup": t_dense / t_pass,
+                             "autotuned": {"engine": "tensor" if cfg["engine"] == Q.DENSE_TENSOR else "cuda_cores",
+                                           "fusion_width": cfg["kmax"], "estimated_ms": cfg["estimated_ms"],
+                                           "ms": t_auto}}
     return out
 
 

@@ -452,6 +452,7 @@ qw_status qw_sv_energy_noalloc_dev(uint32_t mode, uint32_t n, const void *state,
  * Gates: the unitary ops of qw_gate (MEASURE/RESET -> QW_ERR_UNSUPPORTED). */
 #define QW_DENSE_TENSOR 0u
 #define QW_DENSE_SIMT 1u
+#define QW_DENSE_AUTO 2u  /* qw_dense_prog_create only: the autotuner picks the engine */
 typedef struct qw_dense_prog qw_dense_prog;
 
 /* Host only (no engine, no GPU): the blocks a program would apply, before
@@ -461,7 +462,13 @@ typedef struct qw_dense_prog qw_dense_prog;
 qw_status qw_dense_fuse(const qw_gate *gates, uint64_t n_gates, uint32_t n, uint32_t kmax,
                         uint32_t *k, uint32_t *qubits, double *u, uint64_t cap,
                         uint64_t *n_blocks);
-/* Fuses `gates` (host) and uploads the blocks' operands (synchronous). */
+/* Fuses `gates` (host) and uploads the blocks' operands (synchronous).
+ * Autotuning: kmax = 0 tries the fusion widths 2..5, engine = QW_DENSE_AUTO
+ * both engines (the tensor cores only for FP32 states with n >= 12); each
+ * candidate's time is the sum of its blocks' pass times, measured once per
+ * (n, precision, engine, width, layout) on a scratch state of the engine and
+ * cached in it; the fastest candidate is built (4 accumulators on the tensor
+ * cores).  qw_dense_prog_config reports the choice. */
 qw_status qw_dense_prog_create(qw_engine *e, uint32_t mode, uint32_t n, const qw_gate *gates,
                                uint64_t n_gates, uint32_t kmax, uint32_t engine, uint32_t nacc,
                                qw_dense_prog **out);
@@ -472,6 +479,11 @@ qw_status qw_dense_prog_create_block(qw_engine *e, uint32_t mode, uint32_t n,
                                      const uint32_t *qubits, uint32_t k, const double *u,
                                      uint32_t engine, uint32_t nacc, qw_dense_prog **out);
 qw_status qw_dense_prog_info(const qw_dense_prog *p, uint64_t *n_blocks, uint64_t *n_gates);
+/* The program's engine, fusion width (the largest block), accumulators and
+ * the autotuner's time estimate in ms (0 when not autotuned).  Any output
+ * pointer may be NULL. */
+qw_status qw_dense_prog_config(const qw_dense_prog *p, uint32_t *engine, uint32_t *kmax,
+                               uint32_t *nacc, double *est_ms);
 /* Applies the blocks in place to the device state (2^n float2 or double2)
  * on `stream`, asynchronously. */
 qw_status qw_dense_prog_run(qw_dense_prog *p, void *state, void *stream);

@@ -15,6 +15,9 @@ void dense_prog_run(qw_dense_prog *p, void *state, void *stream);
 qw_status dense_prog_check(qw_dense_prog *p);
 void dense_prog_destroy(qw_dense_prog *p);
 uint64_t dense_prog_blocks(const qw_dense_prog *p);
+qw_dense_prog *dense_prog_autotune(Engine *E, uint32_t mode, uint32_t n, const qw_gate *gates, uint64_t n_gates,
+                                   uint32_t kmax, uint32_t engine);
+void dense_prog_config(const qw_dense_prog *p, uint32_t *engine, uint32_t *kmax, uint32_t *nacc, double *est_ms);
 uint64_t dense_prog_gates(const qw_dense_prog *p);
 void build_plan(qw_plan *P, Engine *E, const Workload &W);
 void plan_execute(qw_plan *P, void *stream);
@@ -548,7 +551,7 @@ static void check_dense_target(uint32_t mode, uint32_t n, uint32_t engine, uint3
     if (n < DENSE_TC_MIN_QUBITS || n > QW_SV_MAX_QUBITS)
       fail(QW_ERR_UNSUPPORTED, "tensor-core dense blocks need n in [%u, %d]", DENSE_TC_MIN_QUBITS, QW_SV_MAX_QUBITS);
     if (nacc != 1 && nacc != 2 && nacc != 4) fail(QW_ERR_INVALID_ARG, "nacc must be 1, 2 or 4");
-  } else if (engine == QW_DENSE_SIMT) {
+  } else if (engine == QW_DENSE_SIMT || engine == QW_DENSE_AUTO) {
     if (n < 1 || n > QW_SV_MAX_QUBITS) fail(QW_ERR_INVALID_ARG, "n must be in [1, %d]", QW_SV_MAX_QUBITS);
   } else {
     fail(QW_ERR_INVALID_ARG, "unknown dense engine %u", engine);
@@ -586,8 +589,12 @@ qw_status qw_dense_prog_create(qw_engine *e, uint32_t mode, uint32_t n, const qw
     if (!e || !out || (n_gates && !gates)) fail(QW_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     check_dense_target(mode, n, engine, nacc);
+    if (kmax == 1 || kmax > DENSE_MAX_QUBITS) fail(QW_ERR_INVALID_ARG, "kmax must be 0 (autotune) or in [2, 5]");
     for (uint64_t i = 0; i < n_gates; i++) validate_gate(gates[i], mode, n, i);
-    *out = dense_prog_create(&e->e, mode, n, fuse_dense(gates, n_gates, kmax), n_gates, engine, nacc);
+    if (kmax == 0 || engine == QW_DENSE_AUTO)
+      *out = dense_prog_autotune(&e->e, mode, n, gates, n_gates, kmax, engine);
+    else
+      *out = dense_prog_create(&e->e, mode, n, fuse_dense(gates, n_gates, kmax), n_gates, engine, nacc);
   })
 }
 
@@ -596,6 +603,7 @@ qw_status qw_dense_prog_create_block(qw_engine *e, uint32_t mode, uint32_t n, co
   QW_GUARD({
     if (!e || !out || !qubits || !u) fail(QW_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
+    if (engine == QW_DENSE_AUTO) fail(QW_ERR_INVALID_ARG, "an explicit block takes a fixed engine");
     check_dense_target(mode, n, engine, nacc);
     if (k < 1 || k > DENSE_MAX_QUBITS || k > n) fail(QW_ERR_INVALID_ARG, "k must be in [1, min(5, n)]");
     DenseBlock b;
@@ -621,6 +629,14 @@ qw_status qw_dense_prog_info(const qw_dense_prog *p, uint64_t *n_blocks, uint64_
     if (!p) fail(QW_ERR_INVALID_ARG, "NULL program");
     if (n_blocks) *n_blocks = dense_prog_blocks(p);
     if (n_gates) *n_gates = dense_prog_gates(p);
+  })
+}
+
+qw_status qw_dense_prog_config(const qw_dense_prog *p, uint32_t *engine, uint32_t *kmax, uint32_t *nacc,
+                               double *est_ms) {
+  QW_GUARD({
+    if (!p) fail(QW_ERR_INVALID_ARG, "NULL program");
+    dense_prog_config(p, engine, kmax, nacc, est_ms);
   })
 }
 

@@ -159,7 +159,8 @@ std::vector<DenseBlock> fuse_dense(const qw_gate *gates, uint64_t n_gates, uint3
 // ---------------------------------------------------------------------------
 struct qw_dense_prog {
   qw::Engine *eng = nullptr;
-  uint32_t mode = 0, n = 0, engine = 0, nacc = 1;
+  uint32_t mode = 0, n = 0, engine = 0, nacc = 1, kmax = 0;
+  double est_ms = 0;  // the autotuner's estimate (0 when not autotuned)
   uint64_t n_gates = 0;
   std::vector<qw::DenseBlock> blocks;  // as applied (padded to 5 qubits on the tensor cores)
   void *d_ops = nullptr;               // per block: 8192 floats (tensor) or 2 * 4^k values (CUDA cores)
@@ -181,6 +182,7 @@ qw_dense_prog *dense_prog_create(Engine *E, uint32_t mode, uint32_t n, std::vect
   p->nacc = nacc;
   p->n_gates = n_gates;
   const bool fp64 = mode == QW_MODE_SV_FP64;
+  for (const DenseBlock &b : blocks) p->kmax = std::max(p->kmax, b.k);  // before widening
   std::vector<uint8_t> host;
   for (DenseBlock &b : blocks) {
     p->op_offset.push_back(host.size());
@@ -239,6 +241,132 @@ qw_status dense_prog_check(qw_dense_prog *p) {
     fail(QW_ERR_DEVICE_TIMEOUT, "a tensor-core wait of a dense block ran out; the state is undefined");
   }
   return QW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// fusion-width / engine autotuner
+// ---------------------------------------------------------------------------
+
+// Device time of one block pass (engine, k qubits, staged or direct layout)
+// on a 2^n state, measured once per engine and cached: a block of identity
+// on the k highest qubits (direct) or on qubits 0..k-1 (staged), three runs,
+// the best of the last two.
+static double block_pass_ms(Engine *E, uint32_t mode, uint32_t n, uint32_t engine, uint32_t k, bool staged) {
+  const uint64_t key = ((uint64_t)n << 16) | ((uint64_t)mode << 12) | ((uint64_t)engine << 8) | ((uint64_t)k << 1) |
+                       (staged ? 1u : 0u);
+  auto it = E->dense_ms.find(key);
+  if (it != E->dense_ms.end()) return it->second;
+  DCK(cudaSetDevice(E->device));
+  cudaStream_t s = (cudaStream_t)E->stream;
+  DenseBlock b;
+  b.k = k;
+  for (uint32_t j = 0; j < k; j++) b.q[j] = staged ? j : n - k + j;
+  const uint32_t d = 1u << k;
+  b.u.assign((size_t)d * d, 0.0);
+  for (uint32_t i = 0; i < d; i++) b.u[i * d + i] = 1.0;
+  const bool fp64 = mode == QW_MODE_SV_FP64;
+  const size_t state_bytes = ((size_t)1 << n) * (fp64 ? 16 : 8);
+  std::vector<float> ops;
+  std::vector<double> u64;
+  std::vector<float> u32;
+  if (engine == QW_DENSE_TENSOR) {
+    b = pad_block(b, n);
+    ops.resize(8192);
+    dense_tc_operands(b, ops.data());
+  } else {
+    for (const auto &z : b.u) {
+      u64.push_back(z.real());
+      u64.push_back(z.imag());
+      u32.push_back((float)z.real());
+      u32.push_back((float)z.imag());
+    }
+  }
+  void *state = nullptr, *dops = nullptr;
+  int *derr = nullptr;
+  DCK(cudaMalloc(&state, state_bytes));
+  const size_t op_bytes = engine == QW_DENSE_TENSOR ? ops.size() * 4 : (fp64 ? u64.size() * 8 : u32.size() * 4);
+  DCK(cudaMalloc(&dops, op_bytes));
+  DCK(cudaMalloc(&derr, sizeof(int)));
+  DCK(cudaMemsetAsync(state, 0, state_bytes, s));
+  DCK(cudaMemsetAsync(derr, 0, sizeof(int), s));
+  const void *src = engine == QW_DENSE_TENSOR ? (const void *)ops.data() : fp64 ? (const void *)u64.data() : (const void *)u32.data();
+  DCK(cudaMemcpyAsync(dops, src, op_bytes, cudaMemcpyHostToDevice, s));
+  cudaEvent_t e0, e1;
+  DCK(cudaEventCreate(&e0));
+  DCK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int r = 0; r < 3; r++) {
+    DCK(cudaEventRecord(e0, s));
+    if (engine == QW_DENSE_TENSOR)
+      launch_dense_tc((float2 *)state, n, b, (const float *)dops, 4, derr, E->sm_count, s);
+    else
+      launch_dense_simt(fp64, state, n, b, dops, E->sm_count, s);
+    DCK(cudaEventRecord(e1, s));
+    DCK(cudaEventSynchronize(e1));
+    float ms;
+    DCK(cudaEventElapsedTime(&ms, e0, e1));
+    if (r) best = std::min(best, ms);
+  }
+  int err = 0;
+  DCK(cudaMemcpy(&err, derr, sizeof(int), cudaMemcpyDeviceToHost));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(state);
+  cudaFree(dops);
+  cudaFree(derr);
+  if (err) fail(QW_ERR_DEVICE_TIMEOUT, "a tensor-core wait ran out while timing a dense block");
+  E->dense_ms[key] = best;
+  return best;
+}
+
+// Estimated device time of applying `blocks` with `engine`.
+static double program_ms(Engine *E, uint32_t mode, uint32_t n, uint32_t engine, const std::vector<DenseBlock> &blocks) {
+  double t = 0;
+  for (const DenseBlock &b : blocks) {
+    if (engine == QW_DENSE_TENSOR) {
+      uint32_t low = 0;  // the layout the launch will pick: staged when >= 4 of qubits 0-4 are block qubits
+      for (uint32_t j = 0; j < b.k; j++) low += b.q[j] < 5;
+      t += block_pass_ms(E, mode, n, engine, 5, low >= 4);
+    } else {
+      t += block_pass_ms(E, mode, n, engine, b.k, false);
+    }
+  }
+  return t;
+}
+
+qw_dense_prog *dense_prog_autotune(Engine *E, uint32_t mode, uint32_t n, const qw_gate *gates, uint64_t n_gates,
+                                   uint32_t kmax, uint32_t engine) {
+  const bool tc_ok = mode == QW_MODE_SV_FP32 && n >= DENSE_TC_MIN_QUBITS;
+  double best = 1e300;
+  uint32_t be = 0, bk = 0;
+  std::vector<DenseBlock> bb;
+  for (uint32_t e = QW_DENSE_TENSOR; e <= QW_DENSE_SIMT; e++) {
+    if (engine != QW_DENSE_AUTO && e != engine) continue;
+    if (e == QW_DENSE_TENSOR && !tc_ok) continue;
+    for (uint32_t k = 2; k <= DENSE_MAX_QUBITS; k++) {
+      if (kmax && k != kmax) continue;
+      std::vector<DenseBlock> blocks = fuse_dense(gates, n_gates, k);
+      const double t = program_ms(E, mode, n, e, blocks);
+      if (t < best) {
+        best = t;
+        be = e;
+        bk = k;
+        bb = std::move(blocks);
+      }
+    }
+  }
+  if (best >= 1e300) fail(QW_ERR_UNSUPPORTED, "no dense engine runs this state");
+  qw_dense_prog *p = dense_prog_create(E, mode, n, std::move(bb), n_gates, be, 4);
+  p->kmax = bk;
+  p->est_ms = best;
+  return p;
+}
+
+void dense_prog_config(const qw_dense_prog *p, uint32_t *engine, uint32_t *kmax, uint32_t *nacc, double *est_ms) {
+  if (engine) *engine = p->engine;
+  if (kmax) *kmax = p->kmax;
+  if (nacc) *nacc = p->nacc;
+  if (est_ms) *est_ms = p->est_ms;
 }
 
 uint64_t dense_prog_blocks(const qw_dense_prog *p) { return p->blocks.size(); }

@@ -147,6 +147,7 @@ struct Engine {
   uint64_t store_budget = 0, task_budget = 0;
   void *stream = nullptr;
   std::map<uint64_t, TileConfig> tiles;  // key: n << 1 | fp64
+  std::map<uint64_t, double> dense_ms;    // measured dense-block pass times (autotuner cache)
   CostModel cm;
   float *d_mlp = nullptr;  // device copy of the MLP params
   // scratch for the *_dev entry points

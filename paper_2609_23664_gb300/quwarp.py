@@ -124,12 +124,13 @@ SIGNATURES = {
     "qw_dense_prog_create": (_st, [_vp, _u32, _u32, _vp, _u64, _u32, _u32, _u32, _vp]),
     "qw_dense_prog_create_block": (_st, [_vp, _u32, _u32, _vp, _u32, _vp, _u32, _u32, _vp]),
     "qw_dense_prog_info": (_st, [_vp, _vp, _vp]),
+    "qw_dense_prog_config": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "qw_dense_prog_run": (_st, [_vp, _vp, _vp]),
     "qw_dense_prog_check": (_st, [_vp]),
     "qw_dense_prog_destroy": (None, [_vp]),
 }
 
-DENSE_TENSOR, DENSE_SIMT = 0, 1
+DENSE_TENSOR, DENSE_SIMT, DENSE_AUTO = 0, 1, 2
 
 
 def library_path() -> str:
@@ -485,6 +486,11 @@ class DenseProgram:
         nb, ng = C.c_uint64(), C.c_uint64()
         _check(lib().qw_dense_prog_info(self.h, C.byref(nb), C.byref(ng)))
         return {"blocks": nb.value, "gates": ng.value}
+
+    def config(self):
+        e, k, a, ms = C.c_uint32(), C.c_uint32(), C.c_uint32(), C.c_double()
+        _check(lib().qw_dense_prog_config(self.h, C.byref(e), C.byref(k), C.byref(a), C.byref(ms)))
+        return {"engine": e.value, "kmax": k.value, "nacc": a.value, "estimated_ms": ms.value}
 
     def run(self, state_ptr: int, stream: int = 0):
         _check(lib().qw_dense_prog_run(self.h, state_ptr, stream or None))

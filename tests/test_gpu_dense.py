@@ -150,3 +150,32 @@ def test_invalid_dense_requests_are_refused(eng):
     with pytest.raises(Q.QuwarpError) as e:
         Q.DenseProgram(eng, FP32, 14, engine_kind=T, nacc=3, block=([0, 1], u))
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("mode,n,engine", [(FP32, 14, Q.DENSE_AUTO), (FP32, 20, T), (FP64, 12, Q.DENSE_AUTO),
+                                           (FP32, 10, Q.DENSE_AUTO)])
+def test_autotuned_fusion_width_and_engine(eng, mode, n, engine):
+    # kmax = 0: the fusion width (and with DENSE_AUTO the engine) is chosen
+    # by measured block-pass times; the program still matches the oracle
+    rng = np.random.default_rng(900 + n)
+    g = random_gate_list(rng, n, 120)
+    psi = rounded(random_state(rng, n), mode)
+    prog = Q.DenseProgram(eng, mode, n, gates=g, kmax=0, engine_kind=engine)
+    cfg = prog.config()
+    assert 2 <= cfg["kmax"] <= 5 and cfg["estimated_ms"] > 0
+    if mode == FP64 or n < 12:
+        assert cfg["engine"] == S                 # the tensor cores take FP32 states of >= 12 qubits
+    if engine == T:
+        assert cfg["engine"] == T
+    got = run_prog(prog, psi, mode)
+    want = orc.sv_apply(n, psi.copy(), g)
+    tol = 1e-12 if mode == FP64 else 1e-5
+    assert np.max(np.abs(got - want)) <= tol
+    # by the same (cached) measurements, no fixed width is faster
+    if engine == Q.DENSE_AUTO:
+        for k in (2, 3, 4, 5):
+            other = Q.DenseProgram(eng, mode, n, gates=g, kmax=k, engine_kind=Q.DENSE_AUTO)
+            assert other.config()["kmax"] <= k
+            assert other.config()["estimated_ms"] >= cfg["estimated_ms"] * (1 - 1e-9)
+            other.close()
+    prog.close()
