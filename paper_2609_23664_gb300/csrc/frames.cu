@@ -100,28 +100,42 @@ __global__ void __launch_bounds__(FR_WARPS * 32) frame_kernel(FrameArgs A) {
   const bool has_task = t < A.n_tasks;
   const uint32_t ob = has_task ? A.out_base[t] : 0u;
   __syncwarp();
+  FrameLayer Ln = A.n_layers ? A.layers[0] : FrameLayer{};
   for (uint32_t l = 0; l < A.n_layers; l++) {
-    const FrameLayer L = A.layers[l];
+    const FrameLayer L = Ln;
+    if (l + 1 < A.n_layers) Ln = A.layers[l + 1];  // in flight during this layer
     const uint32_t n_gate = L.n_ops - L.n_meas;
-    for (uint32_t i = lane; i < n_gate; i += 32) {
-      const FrameOp op = A.ops[L.op_begin + i];
-      const uint32_t a = op.a, b = op.b;
-      switch (op.kind) {
-        case F_H: { const uint32_t x = X[a]; X[a] = Z[a]; Z[a] = x; break; }
-        case F_S: Z[a] ^= X[a]; break;
-        case F_CX: X[b] ^= X[a]; Z[a] ^= Z[b]; break;
-        case F_CZ: Z[a] ^= X[b]; Z[b] ^= X[a]; break;
-        case F_SWAP: {
-          const uint32_t x = X[a], z = Z[a];
-          X[a] = X[b]; Z[a] = Z[b]; X[b] = x; Z[b] = z;
-          break;
+    // the ops of a layer act on distinct qubits, so their order is free: a
+    // lane loads four ops before applying them (four loads in flight)
+    for (uint32_t i0 = lane; i0 < n_gate; i0 += 128) {
+      FrameOp ops[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const uint32_t i = i0 + 32u * k;
+        ops[k].kind = 0xFF;
+        if (i < n_gate) ops[k] = A.ops[L.op_begin + i];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const FrameOp op = ops[k];
+        const uint32_t a = op.a, b = op.b;
+        switch (op.kind) {
+          case F_H: { const uint32_t x = X[a]; X[a] = Z[a]; Z[a] = x; break; }
+          case F_S: Z[a] ^= X[a]; break;
+          case F_CX: X[b] ^= X[a]; Z[a] ^= Z[b]; break;
+          case F_CZ: Z[a] ^= X[b]; Z[b] ^= X[a]; break;
+          case F_SWAP: {
+            const uint32_t x = X[a], z = Z[a];
+            X[a] = X[b]; Z[a] = Z[b]; X[b] = x; Z[b] = z;
+            break;
+          }
+          case F_RESET: X[a] = 0u; Z[a] = 0u; break;
+          case F_EVENT:
+            X[a] ^= A.ev_x[(size_t)op.aux * A.n_words + w];
+            Z[a] ^= A.ev_z[(size_t)op.aux * A.n_words + w];
+            break;
+          default: break;
         }
-        case F_RESET: X[a] = 0u; Z[a] = 0u; break;
-        case F_EVENT:
-          X[a] ^= A.ev_x[(size_t)op.aux * A.n_words + w];
-          Z[a] ^= A.ev_z[(size_t)op.aux * A.n_words + w];
-          break;
-        default: break;
       }
     }
     __syncwarp();
