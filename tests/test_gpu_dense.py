@@ -179,3 +179,32 @@ def test_autotuned_fusion_width_and_engine(eng, mode, n, engine):
             assert other.config()["estimated_ms"] >= cfg["estimated_ms"] * (1 - 1e-9)
             other.close()
     prog.close()
+
+
+@pytest.mark.parametrize("qubits", [[5, 6, 7, 8, 9], [0, 1, 2, 3, 4], [27, 3, 14, 0, 22]])
+def test_block_at_28_qubits_sampled_groups(eng, qubits):
+    # full size (2 GiB FP32 state, 2^16 tiles): 512 sampled groups of 32
+    # amplitudes checked one by one against the oracle's operator on the
+    # group, and the norm kept
+    n = 28
+    g = torch.Generator(device="cuda").manual_seed(28)
+    st = torch.randn(1 << n, dtype=torch.complex64, device="cuda", generator=g)
+    st /= torch.linalg.vector_norm(st)
+    before = st.cpu().numpy()
+    rng = np.random.default_rng(sum(qubits))
+    u = random_unitary(rng, 32)
+    prog = Q.DenseProgram(eng, FP32, n, engine_kind=T, nacc=4, block=(qubits, u))
+    prog.run(st.data_ptr())
+    prog.check()
+    after = st.cpu().numpy()
+    assert abs(float(np.linalg.norm(after.astype(np.complex128))) - 1.0) <= 1e-5
+    other = [q for q in range(n) if q not in qubits]
+    pos = np.array([sum(((p >> j) & 1) << q for j, q in enumerate(qubits)) for p in range(32)], dtype=np.int64)
+    for gidx in rng.integers(0, 1 << (n - 5), size=512):
+        base = sum(((int(gidx) >> i) & 1) << q for i, q in enumerate(other))
+        vin = before[base + pos].astype(np.complex128)
+        want = orc.apply_matrix(5, vin, [0, 1, 2, 3, 4], u)
+        got = after[base + pos].astype(np.complex128)
+        assert np.max(np.abs(got - want)) <= 1e-5
+        assert np.linalg.norm(got - want) <= 2e-6 * np.linalg.norm(want) + 1e-12
+    prog.close()
