@@ -439,6 +439,17 @@ def run_native(a):
         line.setdefault("families", {})["dense_tc"] = dense_family(a, eng, stream, peak)
 
     line["roofline"] = roofline
+    # HBM bytes of the whole step against the measured copy bandwidth: the
+    # suffix and energy launches' DRAM bytes from the committed ncu captures
+    # (algorithmic bytes where the capture no longer matches the source),
+    # the boundary's passes algorithmic
+    b_suffix = profiled_traffic("sv_batch_kernel", wkey) or batch_alg_bytes
+    b_energy = profiled_traffic("energy_kernel", wkey) or energy_alg_bytes
+    b_prefix = float(cr.get("prefix_alg_bytes", 0.0))
+    step_bytes = b_suffix + b_energy + b_prefix
+    line["step_hbm"] = {"bytes": step_bytes, "suffix": b_suffix, "energy": b_energy, "prefix": b_prefix,
+                        "achieved_gbs": step_bytes / (ms_max * 1e-3) / 1e9,
+                        "frac_of_measured_peak": step_bytes / (ms_max * 1e-3) / 1e9 / peak}
     # every task of the default workload against the oracle's stored energies
     # (tests/golden/make_vqe24_energies.py, complex128)
     gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "vqe24_256_energies.json")

@@ -337,13 +337,14 @@ qw_status qw_cost_record_json(const qw_plan *p, char *buf, size_t cap, size_t *n
       "\"upload_ms\":%.6f,\"prefix_ms\":%.6f,\"suffix_ms\":%.6f,\"energy_ms\":%.6f,"
       "\"sampling_ms\":%.6f,\"tableau_tasks_ms\":%.6f,\"device_total_ms\":%.6f,"
       "\"kernel_launches\":%llu,\"h2d_bytes\":%llu,\"d2h_bytes\":%llu,"
-      "\"batch_alg_bytes\":%.0f,\"energy_alg_bytes\":%.0f,\"energy_l2_bytes\":%.0f,\"energy_fused\":%s,"
+      "\"batch_alg_bytes\":%.0f,\"energy_alg_bytes\":%.0f,\"energy_l2_bytes\":%.0f,\"prefix_alg_bytes\":%.0f,"
+      "\"energy_fused\":%s,"
       "\"artifacts\":%zu,\"artifact_bytes\":%llu,\"batch_ms\":[",
       p->planning_ns * 1e-6, p->est_direct_ns * 1e-6, p->est_plan_ns * 1e-6,
       p->est_plan_ns > 0 ? p->est_direct_ns / p->est_plan_ns : 1.0, p->timed, p->t_upload_ms,
       p->t_prefix_ms, p->t_suffix_ms, p->t_energy_ms, p->t_sample_ms, p->t_tab_ms, p->t_total_ms,
       (unsigned long long)p->n_launches, (unsigned long long)p->h2d_bytes,
-      (unsigned long long)p->d2h_bytes, p->batch_alg_bytes, p->energy_alg_bytes, p->energy_l2_bytes,
+      (unsigned long long)p->d2h_bytes, p->batch_alg_bytes, p->energy_alg_bytes, p->energy_l2_bytes, p->prefix_alg_bytes,
       p->energy_fused ? "true" : "false", p->mats.size(), [&] {
         unsigned long long b = 0;
         for (auto &m : p->mats) b += m.bytes;

@@ -317,6 +317,8 @@ static void prepare(qw_plan *P) {
     const MatNode &M = P->mats[m];
     if (M.mode == QW_MODE_TABLEAU) continue;
     D->mat_pass0[m] = (M.mode == QW_MODE_SV_FP64 ? b64 : b32).add(M.sv);
+    // algorithmic bytes of the boundary's passes: read and write the state once each
+    P->prefix_alg_bytes += 2.0 * (double)sv_state_bytes(M.mode == QW_MODE_SV_FP64, M.n_eff) * (double)M.sv.passes.size();
   }
   for (uint32_t t = 0; t < nt; t++) {
     const TaskPlan &tp = P->tasks[t];

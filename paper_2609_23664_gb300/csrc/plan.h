@@ -206,7 +206,7 @@ struct qw_plan {
   int timed = 0;
   std::vector<double> batch_ms;  // per wave: suffix launch(es) only
   uint64_t n_launches = 0, h2d_bytes = 0, d2h_bytes = 0;
-  double batch_alg_bytes = 0, energy_alg_bytes = 0, energy_l2_bytes = 0;
+  double batch_alg_bytes = 0, energy_alg_bytes = 0, energy_l2_bytes = 0, prefix_alg_bytes = 0;
   bool energy_fused = false;  // energy blocks ran inside the persistent suffix launch
   std::vector<std::pair<uint32_t, uint32_t>> wave_tiles;  // (tile qubits, low qubits) per wave
 };
