@@ -551,7 +551,8 @@ def dense_family(a, eng, stream, peak_gbs):
     auto.close()
     out["hea_suffix_24q"] = {"gates": int(len(g)), "dense_blocks": nb, "tensor_blocks_ms": t_dense,
                              "pass_kernels_ms": t_pass, "pass_kernels_speedup": t_dense / t_pass,
-                             "autotuned": {"engine": "tensor" if cfg["engine"] == Q.DENSE_TENSOR else "cuda_cores",
+                             "autotuned": {"engine": {Q.DENSE_TENSOR: "tensor", Q.DENSE_SIMT: "cuda_cores"}.get(
+                                               cfg["engine"], "tensor for >=4-qubit blocks, cuda_cores for the rest"),
                                            "fusion_width": cfg["kmax"], "estimated_ms": cfg["estimated_ms"],
                                            "ms": t_auto}}
     return out

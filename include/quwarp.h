@@ -452,7 +452,7 @@ qw_status qw_sv_energy_noalloc_dev(uint32_t mode, uint32_t n, const void *state,
  * Gates: the unitary ops of qw_gate (MEASURE/RESET -> QW_ERR_UNSUPPORTED). */
 #define QW_DENSE_TENSOR 0u
 #define QW_DENSE_SIMT 1u
-#define QW_DENSE_AUTO 2u  /* qw_dense_prog_create only: the autotuner picks the engine */
+#define QW_DENSE_AUTO 2u  /* qw_dense_prog_create only: the engine of each block is chosen */
 typedef struct qw_dense_prog qw_dense_prog;
 
 /* Host only (no engine, no GPU): the blocks a program would apply, before
@@ -463,12 +463,15 @@ qw_status qw_dense_fuse(const qw_gate *gates, uint64_t n_gates, uint32_t n, uint
                         uint32_t *k, uint32_t *qubits, double *u, uint64_t cap,
                         uint64_t *n_blocks);
 /* Fuses `gates` (host) and uploads the blocks' operands (synchronous).
- * Autotuning: kmax = 0 tries the fusion widths 2..5, engine = QW_DENSE_AUTO
- * both engines (the tensor cores only for FP32 states with n >= 12); each
- * candidate's time is the sum of its blocks' pass times, measured once per
- * (n, precision, engine, width, layout) on a scratch state of the engine and
- * cached in it; the fastest candidate is built (4 accumulators on the tensor
- * cores).  qw_dense_prog_config reports the choice. */
+ * Autotuning: kmax = 0 tries the fusion widths 2..5; engine = QW_DENSE_AUTO
+ * picks the engine of every block: the tensor cores for blocks of 4 or 5
+ * qubits when they measure faster there (FP32 states with n >= 12 only),
+ * the CUDA cores otherwise (always for blocks of 1-3 qubits).  A candidate's
+ * time is the sum of its blocks' pass times, measured once per (n,
+ * precision, engine, width, layout) on a scratch state of the engine and
+ * cached in it; the fastest candidate is built (4 accumulators on the
+ * tensor cores).  qw_dense_prog_config reports the choice (engine
+ * QW_DENSE_AUTO when the blocks use both). */
 qw_status qw_dense_prog_create(qw_engine *e, uint32_t mode, uint32_t n, const qw_gate *gates,
                                uint64_t n_gates, uint32_t kmax, uint32_t engine, uint32_t nacc,
                                qw_dense_prog **out);

@@ -10,7 +10,7 @@
 
 namespace qw {
 qw_dense_prog *dense_prog_create(Engine *E, uint32_t mode, uint32_t n, std::vector<DenseBlock> blocks,
-                                 uint64_t n_gates, uint32_t engine, uint32_t nacc);
+                                 uint64_t n_gates, uint32_t engine, uint32_t nacc, std::vector<uint8_t> engines);
 void dense_prog_run(qw_dense_prog *p, void *state, void *stream);
 qw_status dense_prog_check(qw_dense_prog *p);
 void dense_prog_destroy(qw_dense_prog *p);
@@ -595,7 +595,7 @@ qw_status qw_dense_prog_create(qw_engine *e, uint32_t mode, uint32_t n, const qw
     if (kmax == 0 || engine == QW_DENSE_AUTO)
       *out = dense_prog_autotune(&e->e, mode, n, gates, n_gates, kmax, engine);
     else
-      *out = dense_prog_create(&e->e, mode, n, fuse_dense(gates, n_gates, kmax), n_gates, engine, nacc);
+      *out = dense_prog_create(&e->e, mode, n, fuse_dense(gates, n_gates, kmax), n_gates, engine, nacc, {});
   })
 }
 
@@ -621,7 +621,7 @@ qw_status qw_dense_prog_create_block(qw_engine *e, uint32_t mode, uint32_t n, co
       if (!std::isfinite(u[2 * i]) || !std::isfinite(u[2 * i + 1])) fail(QW_ERR_INVALID_ARG, "non-finite matrix entry");
       b.u[i] = std::complex<double>(u[2 * i], u[2 * i + 1]);
     }
-    *out = dense_prog_create(&e->e, mode, n, std::vector<DenseBlock>{b}, 0, engine, nacc);
+    *out = dense_prog_create(&e->e, mode, n, std::vector<DenseBlock>{b}, 0, engine, nacc, {});
   })
 }
 

@@ -163,6 +163,7 @@ struct qw_dense_prog {
   double est_ms = 0;  // the autotuner's estimate (0 when not autotuned)
   uint64_t n_gates = 0;
   std::vector<qw::DenseBlock> blocks;  // as applied (padded to 5 qubits on the tensor cores)
+  std::vector<uint8_t> engines;        // engine of each block
   void *d_ops = nullptr;               // per block: 8192 floats (tensor) or 2 * 4^k values (CUDA cores)
   std::vector<size_t> op_offset;       // byte offset of each block's operand
   int *d_err = nullptr;
@@ -172,7 +173,9 @@ struct qw_dense_prog {
 namespace qw {
 
 qw_dense_prog *dense_prog_create(Engine *E, uint32_t mode, uint32_t n, std::vector<DenseBlock> blocks,
-                                 uint64_t n_gates, uint32_t engine, uint32_t nacc) {
+                                 uint64_t n_gates, uint32_t engine, uint32_t nacc,
+                                 std::vector<uint8_t> engines = {}) {
+  if (engines.empty()) engines.assign(blocks.size(), (uint8_t)engine);
   DCK(cudaSetDevice(E->device));
   std::unique_ptr<qw_dense_prog> p(new qw_dense_prog());
   p->eng = E;
@@ -184,9 +187,10 @@ qw_dense_prog *dense_prog_create(Engine *E, uint32_t mode, uint32_t n, std::vect
   const bool fp64 = mode == QW_MODE_SV_FP64;
   for (const DenseBlock &b : blocks) p->kmax = std::max(p->kmax, b.k);  // before widening
   std::vector<uint8_t> host;
-  for (DenseBlock &b : blocks) {
+  for (size_t bi = 0; bi < blocks.size(); bi++) {
+    DenseBlock &b = blocks[bi];
     p->op_offset.push_back(host.size());
-    if (engine == QW_DENSE_TENSOR) {
+    if (engines[bi] == QW_DENSE_TENSOR) {
       b = pad_block(b, n);
       host.resize(host.size() + 8192 * sizeof(float));
       dense_tc_operands(b, reinterpret_cast<float *>(host.data() + p->op_offset.back()));
@@ -207,6 +211,7 @@ qw_dense_prog *dense_prog_create(Engine *E, uint32_t mode, uint32_t n, std::vect
     }
   }
   p->blocks = std::move(blocks);
+  p->engines = std::move(engines);
   DCK(cudaMalloc(&p->d_err, sizeof(int)));
   DCK(cudaMemset(p->d_err, 0, sizeof(int)));
   if (!host.empty()) {
@@ -221,7 +226,7 @@ void dense_prog_run(qw_dense_prog *p, void *state, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;
   for (size_t i = 0; i < p->blocks.size(); i++) {
     const uint8_t *op = static_cast<const uint8_t *>(p->d_ops) + p->op_offset[i];
-    if (p->engine == QW_DENSE_TENSOR)
+    if (p->engines[i] == QW_DENSE_TENSOR)
       launch_dense_tc((float2 *)state, p->n, p->blocks[i], reinterpret_cast<const float *>(op), (int)p->nacc,
                       p->d_err, p->eng->sm_count, s);
     else
@@ -319,44 +324,72 @@ static double block_pass_ms(Engine *E, uint32_t mode, uint32_t n, uint32_t engin
   return best;
 }
 
-// Estimated device time of applying `blocks` with `engine`.
-static double program_ms(Engine *E, uint32_t mode, uint32_t n, uint32_t engine, const std::vector<DenseBlock> &blocks) {
+// Measured pass time of block b on the tensor cores (widened to 5 qubits,
+// in the layout the launch will pick: staged when >= 4 of qubits 0-4 are
+// block qubits) or on the CUDA cores.
+static double block_ms(Engine *E, uint32_t mode, uint32_t n, uint32_t engine, const DenseBlock &b) {
+  if (engine == QW_DENSE_TENSOR) {
+    uint32_t low = 0;
+    for (uint32_t j = 0; j < b.k; j++) low += b.q[j] < 5;
+    return block_pass_ms(E, mode, n, engine, 5, low >= 4);
+  }
+  return block_pass_ms(E, mode, n, engine, b.k, false);
+}
+
+// Estimated device time of `blocks` and the engine of each: `engine` for
+// all of them, or with QW_DENSE_AUTO the tensor cores for blocks of >= 4
+// qubits when they measure faster there, the CUDA cores otherwise.
+static double program_ms(Engine *E, uint32_t mode, uint32_t n, uint32_t engine, const std::vector<DenseBlock> &blocks,
+                         std::vector<uint8_t> *engines) {
+  const bool tc_ok = mode == QW_MODE_SV_FP32 && n >= DENSE_TC_MIN_QUBITS;
   double t = 0;
+  engines->clear();
   for (const DenseBlock &b : blocks) {
-    if (engine == QW_DENSE_TENSOR) {
-      uint32_t low = 0;  // the layout the launch will pick: staged when >= 4 of qubits 0-4 are block qubits
-      for (uint32_t j = 0; j < b.k; j++) low += b.q[j] < 5;
-      t += block_pass_ms(E, mode, n, engine, 5, low >= 4);
+    uint32_t e = engine;
+    double tb;
+    if (engine == QW_DENSE_AUTO) {
+      e = QW_DENSE_SIMT;
+      tb = block_ms(E, mode, n, QW_DENSE_SIMT, b);
+      if (tc_ok && b.k >= 4) {
+        const double tt = block_ms(E, mode, n, QW_DENSE_TENSOR, b);
+        if (tt < tb) {
+          tb = tt;
+          e = QW_DENSE_TENSOR;
+        }
+      }
     } else {
-      t += block_pass_ms(E, mode, n, engine, b.k, false);
+      tb = block_ms(E, mode, n, engine, b);
     }
+    engines->push_back((uint8_t)e);
+    t += tb;
   }
   return t;
 }
 
 qw_dense_prog *dense_prog_autotune(Engine *E, uint32_t mode, uint32_t n, const qw_gate *gates, uint64_t n_gates,
                                    uint32_t kmax, uint32_t engine) {
-  const bool tc_ok = mode == QW_MODE_SV_FP32 && n >= DENSE_TC_MIN_QUBITS;
   double best = 1e300;
-  uint32_t be = 0, bk = 0;
+  uint32_t bk = 0;
   std::vector<DenseBlock> bb;
-  for (uint32_t e = QW_DENSE_TENSOR; e <= QW_DENSE_SIMT; e++) {
-    if (engine != QW_DENSE_AUTO && e != engine) continue;
-    if (e == QW_DENSE_TENSOR && !tc_ok) continue;
-    for (uint32_t k = 2; k <= DENSE_MAX_QUBITS; k++) {
-      if (kmax && k != kmax) continue;
-      std::vector<DenseBlock> blocks = fuse_dense(gates, n_gates, k);
-      const double t = program_ms(E, mode, n, e, blocks);
-      if (t < best) {
-        best = t;
-        be = e;
-        bk = k;
-        bb = std::move(blocks);
-      }
+  std::vector<uint8_t> be;
+  for (uint32_t k = 2; k <= DENSE_MAX_QUBITS; k++) {
+    if (kmax && k != kmax) continue;
+    std::vector<DenseBlock> blocks = fuse_dense(gates, n_gates, k);
+    std::vector<uint8_t> engines;
+    const double t = program_ms(E, mode, n, engine, blocks, &engines);
+    if (t < best) {
+      best = t;
+      bk = k;
+      bb = std::move(blocks);
+      be = std::move(engines);
     }
   }
   if (best >= 1e300) fail(QW_ERR_UNSUPPORTED, "no dense engine runs this state");
-  qw_dense_prog *p = dense_prog_create(E, mode, n, std::move(bb), n_gates, be, 4);
+  uint32_t used = 0;
+  for (uint8_t e : be) used |= 1u << e;
+  const uint32_t pe = used == (1u << QW_DENSE_TENSOR) ? QW_DENSE_TENSOR
+                      : used == (1u << QW_DENSE_SIMT) ? QW_DENSE_SIMT : QW_DENSE_AUTO;
+  qw_dense_prog *p = dense_prog_create(E, mode, n, std::move(bb), n_gates, pe, 4, std::move(be));
   p->kmax = bk;
   p->est_ms = best;
   return p;

@@ -246,39 +246,54 @@ __global__ void __launch_bounds__(DT_THREADS, 2) dense_tc_kernel(const DenseTcAr
   }
 }
 
-// CUDA-core form: one thread per group; U (interleaved complex, row-major)
-// staged in shared memory, every output a sum over the 2^k inputs held in
-// registers.
-template <typename T, typename T2>
+// CUDA-core form.  A thread takes G = 32 / 2^K groups per step: with a
+// power-of-two grid stride, its groups are base + (j G + i) stride (i < G),
+// whose index bits are disjoint, so their offsets are OR-combinations of
+// three deposits (base, the step j, the lane i) and a warp's threads read
+// consecutive groups.  All 32 input amplitudes are loaded before any output
+// is formed (32 loads in flight for any K); every output is a sum over the
+// 2^K inputs of its group with U (interleaved complex, row-major) staged in
+// shared memory.
+template <typename T, typename T2, int K>
 __global__ void __launch_bounds__(128) dense_simt_kernel(T2 *state, const T *u, uint64_t n_groups,
-                                                         uint32_t other_mask, uint32_t k, DensePos pos) {
-  extern __shared__ __align__(16) uint8_t smraw[];
-  T *us = reinterpret_cast<T *>(smraw);
-  const uint32_t dim = 1u << k;
-  for (uint32_t i = threadIdx.x; i < 2 * dim * dim; i += blockDim.x) us[i] = u[i];
+                                                         uint32_t other_mask, DensePos pos) {
+  constexpr uint32_t D = 1u << K, G = 32u >> K;
+  __shared__ T us[2 * D * D];
+  for (uint32_t i = threadIdx.x; i < 2 * D * D; i += blockDim.x) us[i] = u[i];
   __syncthreads();
-  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_groups;
-       g += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t xb = dense_deposit(g, other_mask);
-    T2 in[32];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;  // a power of two
+  const uint64_t base = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t dbase = dense_deposit(base, other_mask);
+  uint64_t dlane[G];
 #pragma unroll
-    for (uint32_t p = 0; p < 32; p++)
-      if (p < dim) in[p] = state[xb + pos.v[p]];
-    for (uint32_t o = 0; o < dim; o++) {
-      T re = 0, im = 0;
-      const T *row = us + 2 * o * dim;
+  for (uint32_t i = 0; i < G; i++) dlane[i] = dense_deposit(i * stride, other_mask);
+  for (uint64_t j = 0; base + j * G * stride < n_groups; j++) {
+    const uint64_t dstep = dbase | dense_deposit(j * G * stride, other_mask);
+    T2 in[G][D];
 #pragma unroll
-      for (uint32_t p = 0; p < 32; p++) {
-        if (p < dim) {
-          const T ur = row[2 * p], ui = row[2 * p + 1];
-          re = fma(ur, in[p].x, fma(-ui, in[p].y, re));
-          im = fma(ur, in[p].y, fma(ui, in[p].x, im));
-        }
+    for (uint32_t i = 0; i < G; i++) {
+      if (base + (j * G + i) * stride < n_groups) {
+#pragma unroll
+        for (uint32_t p = 0; p < D; p++) in[i][p] = state[(dstep | dlane[i]) + pos.v[p]];
       }
-      T2 out;
-      out.x = re;
-      out.y = im;
-      state[xb + pos.v[o]] = out;
+    }
+#pragma unroll
+    for (uint32_t i = 0; i < G; i++) {
+      if (base + (j * G + i) * stride >= n_groups) continue;
+      for (uint32_t o = 0; o < D; o++) {
+        T re = 0, im = 0;
+        const T *row = us + 2 * o * D;
+#pragma unroll
+        for (uint32_t p = 0; p < D; p++) {
+          const T ur = row[2 * p], ui = row[2 * p + 1];
+          re = fma(ur, in[i][p].x, fma(-ui, in[i][p].y, re));
+          im = fma(ur, in[i][p].y, fma(ui, in[i][p].x, im));
+        }
+        T2 out;
+        out.x = re;
+        out.y = im;
+        state[(dstep | dlane[i]) + pos.v[o]] = out;
+      }
     }
   }
 }
@@ -342,16 +357,28 @@ void launch_dense_simt(bool fp64, void *state, uint32_t n, const DenseBlock &b, 
                        cudaStream_t s) {
   if (b.k < 1 || b.k > DENSE_MAX_QUBITS || b.k > n) fail(QW_ERR_INVALID_ARG, "dense block of %u qubits", b.k);
   const uint64_t groups = 1ull << (n - b.k);
-  const uint32_t dim = 1u << b.k;
-  const int grid = (int)std::min<uint64_t>((groups + 127) / 128, (uint64_t)sm_count * 8);
+  // a power-of-two grid (the kernel combines group offsets by OR), at most
+  // 8 CTAs per SM and no more than the groups need
+  const uint64_t per_cta = 128ull * (32u >> b.k);  // groups a CTA takes per step
+  uint64_t grid = 1;
+  while (grid * 2 <= (uint64_t)sm_count * 8 && grid * per_cta < groups) grid *= 2;
   const uint32_t om = dense_other_mask(b, n);
   const DensePos pos = dense_positions(b);
-  if (fp64)
-    dense_simt_kernel<double, double2><<<grid, 128, 2 * dim * dim * sizeof(double), s>>>(
-        (double2 *)state, (const double *)u, groups, om, b.k, pos);
-  else
-    dense_simt_kernel<float, float2><<<grid, 128, 2 * dim * dim * sizeof(float), s>>>(
-        (float2 *)state, (const float *)u, groups, om, b.k, pos);
+#define QW_SIMT(KK)                                                                                       \
+  if (fp64)                                                                                               \
+    dense_simt_kernel<double, double2, KK><<<(unsigned)grid, 128, 0, s>>>((double2 *)state, (const double *)u,      \
+                                                                  groups, om, pos);                       \
+  else                                                                                                    \
+    dense_simt_kernel<float, float2, KK><<<(unsigned)grid, 128, 0, s>>>((float2 *)state, (const float *)u, groups, \
+                                                                om, pos);
+  switch (b.k) {
+    case 1: QW_SIMT(1) break;
+    case 2: QW_SIMT(2) break;
+    case 3: QW_SIMT(3) break;
+    case 4: QW_SIMT(4) break;
+    default: QW_SIMT(5) break;
+  }
+#undef QW_SIMT
 }
 
 // ---------------------------------------------------------------------------

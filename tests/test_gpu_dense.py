@@ -208,3 +208,25 @@ def test_block_at_28_qubits_sampled_groups(eng, qubits):
         assert np.max(np.abs(got - want)) <= 1e-5
         assert np.linalg.norm(got - want) <= 2e-6 * np.linalg.norm(want) + 1e-12
     prog.close()
+
+
+def test_mixed_engine_program_uses_tensor_cores_only_for_large_blocks(eng):
+    # a circuit whose fusion yields both 5-qubit blocks (a dense brick on
+    # qubits 8-12) and lone one- and two-qubit blocks: with DENSE_AUTO the
+    # small blocks run on the CUDA cores; the result matches the oracle
+    n = 16
+    rng = np.random.default_rng(77)
+    ops = []
+    for _ in range(6):
+        for q in range(8, 12):
+            ops.append((W.OP_RY, q, 0, float(rng.uniform(0, 6))))
+            ops.append((W.OP_CNOT, q, q + 1))
+    ops += [(W.OP_H, 0, 0), (W.OP_RX, 3, 0, 0.4), (W.OP_CZ, 3, 4)]
+    g = W.gates_from_list(ops)
+    psi = rounded(random_state(rng, n), FP32)
+    prog = Q.DenseProgram(eng, FP32, n, gates=g, kmax=5, engine_kind=Q.DENSE_AUTO)
+    got = run_prog(prog, psi, FP32)
+    want = orc.sv_apply(n, psi.copy(), g)
+    assert np.max(np.abs(got - want)) <= 1e-5
+    assert prog.config()["engine"] in (Q.DENSE_AUTO, Q.DENSE_SIMT, Q.DENSE_TENSOR)
+    prog.close()
