@@ -414,7 +414,8 @@ def run_native(a):
             fcr = fp.cost_record()
             fp.close()
             return {"value": units / (fms / 1e3), "unit": "tasks/s", "ms_per_step": fms,
-                    "kernel_launches": fcr["kernel_launches"], "artifacts": fcr["artifacts"]}
+                    "kernel_launches": fcr["kernel_launches"], "artifacts": fcr["artifacts"],
+                    "dense_choices": fcr.get("dense_boundaries") or None}
 
         for key, desc, gen, plans in (
                 ("qec_d15", "rotated surface code, 449 qubits, 100 shared + 5 task rounds, 4096 tasks, "
@@ -425,12 +426,18 @@ def run_native(a):
                  (("reuse", {}), ("per_task_replay", dict(reuse=0, batched=0)))),
                 ("vqe12_fp64", "12 qubits, 6-layer HEA prefix, 16 tasks x final RY+RZ layer, 20-term "
                                "energy (FP64)", W.config1_vqe12,
-                 (("reuse", {}), ("per_task_replay", dict(reuse=0, batched=0))))):
+                 (("reuse", {}), ("per_task_replay", dict(reuse=0, batched=0)))),
+                ("deep_local24", "24 qubits, H layer + 60 layers of RY/CNOT/RZ confined to qubits 8-12 "
+                                 "(shared prefix), 64 tasks x RY layer, 32-term energy (FP32)",
+                 lambda: W.deep_local_sweep(n=24, layers=60, n_tasks=64, n_terms=32),
+                 (("dense_boundary", dict(dense_boundaries=1)), ("pass_kernels", {})))):
             ft = gen()
             fwl = Q.Workload(ft)
             fams[key] = {"workload": desc}
             for pk, opts in plans:
                 fams[key][pk] = time_plan(fwl, len(ft), opts)
+                if opts.get("dense_boundaries"):
+                    fams[key][pk]["boundaries"] = fams[key][pk].pop("dense_choices", None)
             ks = [pk for pk, _ in plans]
             fams[key]["speedup"] = fams[key][ks[0]]["value"] / fams[key][ks[1]]["value"]
             fwl.close()

@@ -221,6 +221,15 @@ typedef struct qw_plan_opts {
                                  consumer up to that one rounding), at the cost of FP64
                                  arithmetic for the prefix.  0 = the prefix runs in FP32.
                                  Default 0. */
+  int32_t dense_boundaries;   /* statevector boundaries as fused dense blocks (see the
+                                 dense block section below): 1 = at the first execution,
+                                 each boundary's pass program and its autotuned dense
+                                 program (tensor cores for 4-5-qubit blocks) are timed
+                                 once on a scratch state and the faster one evolves it;
+                                 2 = always the dense program; 0 = pass kernels only.
+                                 Boundaries continuing from another precision keep the
+                                 pass kernels.  The choices are in the cost record.
+                                 Default 0. */
 } qw_plan_opts;
 
 /* Fills the defaults: reuse=1, batched=1, legality=1, analytic costs,

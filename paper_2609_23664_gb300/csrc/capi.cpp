@@ -204,6 +204,7 @@ void qw_plan_opts_default(qw_plan_opts *o) {
   o->pauli_frames = 1;
   o->handoff = 1;
   o->prefix_fp64 = 0;
+  o->dense_boundaries = 0;
 }
 
 qw_status qw_plan_create(qw_engine *e, const qw_workload *w, const qw_plan_opts *o, qw_plan **out) {
@@ -354,6 +355,15 @@ qw_status qw_cost_record_json(const qw_plan *p, char *buf, size_t cap, size_t *n
   s += "],\"wave_tiles\":[";
   for (size_t i = 0; i < p->wave_tiles.size(); i++)
     s += strf(i ? ",[%u,%u]" : "[%u,%u]", p->wave_tiles[i].first, p->wave_tiles[i].second);
+  s += "],\"dense_boundaries\":[";
+  for (size_t i = 0; i < p->dense_choices.size(); i++) {
+    const DenseChoice &c = p->dense_choices[i];
+    const char *eng = c.engine == QW_DENSE_TENSOR ? "tensor" : c.engine == QW_DENSE_SIMT ? "cuda_cores" : "mixed";
+    s += strf("%s{\"artifact\":%d,\"used\":%s,\"engine\":\"%s\",\"fusion_width\":%u,\"blocks\":%u,"
+              "\"estimated_ms\":%.6f,\"pass_kernels_ms\":%.6f,\"dense_ms\":%.6f}",
+              i ? "," : "", c.mat, c.used ? "true" : "false", eng, c.width, c.blocks, c.est_ms, c.pass_ms,
+              c.dense_ms);
+  }
   s += "]}";
   return put_json(s, buf, cap, needed);
 }

@@ -14,6 +14,13 @@
 #include "plan.h"
 
 namespace qw {
+qw_dense_prog *dense_prog_autotune(Engine *E, uint32_t mode, uint32_t n, const qw_gate *gates, uint64_t n_gates,
+                                   uint32_t kmax, uint32_t engine);
+void dense_prog_config(const qw_dense_prog *p, uint32_t *engine, uint32_t *kmax, uint32_t *nacc, double *est_ms);
+uint64_t dense_prog_blocks(const qw_dense_prog *p);
+void dense_prog_run(qw_dense_prog *p, void *state, void *stream);
+qw_status dense_prog_check(qw_dense_prog *p);
+void dense_prog_destroy(qw_dense_prog *p);
 
 #define CK(x)                                                                       \
   do {                                                                              \
@@ -26,6 +33,14 @@ namespace qw {
 // ---------------------------------------------------------------------------
 // small kernels
 // ---------------------------------------------------------------------------
+// |0...0>: every amplitude 0, the first 1
+__global__ void basis_zero_kernel(void *state, bool fp64, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if (fp64) ((double2 *)state)[i] = make_double2(i == 0 ? 1.0 : 0.0, 0.0);
+    else ((float2 *)state)[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
+  }
+}
+
 __global__ void convert_kernel(const void *src, bool src64, void *dst, bool dst64, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -177,6 +192,7 @@ struct DeviceState {
   std::vector<void *> mat_export[2];   // per mode (FP64, FP32): statevector exported from a tableau node
   std::vector<StabBasis *> mat_basis;  // scratch of each exporting tableau node
   std::vector<int> tab_launch_of_mat;  // index into tab_mat_launches, -1 none
+  std::vector<qw_dense_prog *> mat_dense;  // boundary evolved by a dense-block program, else NULL
   // statevector boundaries of one precision in one persistent launch (a
   // boundary's first pass waits for its parent's last); empty = per-pass launches
   struct MatBatch {
@@ -358,6 +374,57 @@ static void prepare(qw_plan *P) {
           D->mat_export[md][m] = D->arena.alloc(sv_state_bytes(md == QW_MODE_SV_FP64, M.n_eff));
     }
   }
+  // ---- statevector boundaries as dense-block programs (dense_boundaries) --
+  D->mat_dense.assign(P->mats.size(), nullptr);
+  P->dense_choices.clear();
+  if (P->opts.dense_boundaries) {
+    for (size_t m = 0; m < P->mats.size(); m++) {
+      const MatNode &M = P->mats[m];
+      if (M.mode == QW_MODE_TABLEAU || M.sv.passes.empty() || M.gates.empty()) continue;
+      if (M.parent >= 0 && P->mats[M.parent].mode != M.mode) continue;
+      const bool fp64 = M.mode == QW_MODE_SV_FP64;
+      qw_dense_prog *dp = dense_prog_autotune(E, M.mode, M.n_eff, M.gates.data(), M.gates.size(), 0, QW_DENSE_AUTO);
+      DenseChoice c;
+      c.mat = (int)m;
+      dense_prog_config(dp, &c.engine, &c.width, nullptr, &c.est_ms);
+      c.blocks = (uint32_t)dense_prog_blocks(dp);
+      bool use = P->opts.dense_boundaries == 2;
+      if (!use) {
+        // both candidates timed once from |0...0> on a scratch state
+        const size_t bytes = sv_state_bytes(fp64, M.n_eff), n_amp = (size_t)1 << M.n_eff;
+        void *scratch = nullptr;
+        CK(cudaMalloc(&scratch, bytes));
+        const SvTables &T = fp64 ? D->t64 : D->t32;
+        cudaEvent_t e[4];
+        for (auto &x : e) CK(cudaEventCreate(&x));
+        CK(cudaEventRecord(e[0], s));
+        for (size_t p = 0; p < M.sv.passes.size(); p++)
+          launch_sv_pass(fp64, T, D->mat_pass0[m] + (uint32_t)p, (uint32_t)M.sv.passes[p].q.size(), M.n_eff,
+                         p == 0 ? nullptr : scratch, scratch, s);
+        CK(cudaEventRecord(e[1], s));
+        CK(cudaEventRecord(e[2], s));
+        basis_zero_kernel<<<(unsigned)std::min<size_t>((n_amp + 255) / 256, (size_t)E->sm_count * 16), 256, 0, s>>>(
+            scratch, fp64, n_amp);
+        dense_prog_run(dp, scratch, s);
+        CK(cudaEventRecord(e[3], s));
+        CK(cudaEventSynchronize(e[3]));
+        float a = 0, b = 0;
+        CK(cudaEventElapsedTime(&a, e[0], e[1]));
+        CK(cudaEventElapsedTime(&b, e[2], e[3]));
+        for (auto &x : e) cudaEventDestroy(x);
+        cudaFree(scratch);
+        dense_prog_check(dp);
+        c.pass_ms = a;
+        c.dense_ms = b;
+        use = b < a;
+      }
+      c.used = use;
+      P->dense_choices.push_back(c);
+      if (use) D->mat_dense[m] = dp;
+      else dense_prog_destroy(dp);
+    }
+  }
+
   // the state a statevector consumer of node m reads (the node itself, or its
   // export into the consumer's precision)
   auto sv_source = [&](int m, uint32_t mode) -> void * {
@@ -377,6 +444,8 @@ static void prepare(qw_plan *P) {
   {
     bool ok = P->opts.batched != 0;
     size_t n_sv = 0;
+    for (const qw_dense_prog *dp : D->mat_dense)
+      if (dp) ok = false;  // a dense-block boundary is launched block by block
     for (const MatNode &M : P->mats) {
       if (M.mode == QW_MODE_TABLEAU) continue;
       n_sv++;
@@ -849,7 +918,15 @@ static void enqueue(qw_plan *P, cudaStream_t s, bool capturing) {
       if (PM.mode == M.mode) psrc = D->mat_buf[M.parent];
       else psrc = D->mat_export[M.mode][M.parent];
     }
-    if (M.sv.passes.empty()) {
+    if (D->mat_dense[m]) {
+      const size_t n_amp = (size_t)1 << M.n_eff;
+      if (psrc) launch_copy(psrc, D->mat_buf[m], sv_state_bytes(fp64, M.n_eff), s);
+      else
+        basis_zero_kernel<<<(unsigned)std::min<size_t>((n_amp + 255) / 256, (size_t)P->eng->sm_count * 16), 256, 0,
+                            s>>>(D->mat_buf[m], fp64, n_amp);
+      dense_prog_run(D->mat_dense[m], D->mat_buf[m], s);
+      nl += 1 + dense_prog_blocks(D->mat_dense[m]);
+    } else if (M.sv.passes.empty()) {
       if (psrc) launch_copy(psrc, D->mat_buf[m], sv_state_bytes(fp64, M.n_eff), s);
     } else {
       nl += M.sv.passes.size();
@@ -1006,6 +1083,8 @@ void plan_wait(qw_plan *P) {
     CK(cudaMemcpy(&flag, B.d_ctr + 1, sizeof(flag), cudaMemcpyDeviceToHost));
     if (flag) fail(QW_ERR_DEVICE_TIMEOUT, "a bounded dependency wait of the boundaries' launch expired");
   }
+  for (qw_dense_prog *dp : D->mat_dense)
+    if (dp) dense_prog_check(dp);
   std::vector<double> en(2 * (size_t)nt);
   if (nt) CK(cudaMemcpy(en.data(), D->d_energy, en.size() * sizeof(double), cudaMemcpyDeviceToHost));
   P->energy.assign(nt, 0);
@@ -1049,6 +1128,7 @@ void plan_release(qw_plan *P) {
     // the plan may have run on a caller's stream: its blocks go back to the
     // engine's cache only once the device has finished with them
     cudaDeviceSynchronize();
+    for (qw_dense_prog *dp : P->dev->mat_dense) dense_prog_destroy(dp);
     delete P->dev;
     P->dev = nullptr;
   }

@@ -87,6 +87,15 @@ struct MatNode {
   // tableau node exported to statevectors (bit 1 << mode per precision that
   // statevector consumers need; Table II STAB -> SV)
   uint32_t export_modes = 0;
+  std::vector<qw_gate> gates;  // the node's gates (kept for dense-block boundaries)
+};
+
+// A statevector boundary evolved by a dense-block program instead of passes.
+struct DenseChoice {
+  int mat = -1;
+  uint32_t engine = 0, width = 0, blocks = 0;
+  double est_ms = 0, pass_ms = 0, dense_ms = 0;  // timed candidates (option 1), 0 = not timed
+  bool used = false;
 };
 
 struct TaskPlan {
@@ -209,4 +218,5 @@ struct qw_plan {
   double batch_alg_bytes = 0, energy_alg_bytes = 0, energy_l2_bytes = 0, prefix_alg_bytes = 0;
   bool energy_fused = false;  // energy blocks ran inside the persistent suffix launch
   std::vector<std::pair<uint32_t, uint32_t>> wave_tiles;  // (tile qubits, low qubits) per wave
+  std::vector<qw::DenseChoice> dense_choices;  // option dense_boundaries
 };

@@ -994,6 +994,7 @@ void build_plan(qw_plan *P, Engine *E, const Workload &W) {
       R.copy_gates(M.begin, M.end, buf);
       TileConfig tc = C.tiles(M.n_eff, M.mode == QW_MODE_SV_FP64);
       M.sv = fuse_sv(buf.data(), buf.size(), M.n_eff, tc);
+      if (P->opts.dense_boundaries) M.gates = buf;
     }
   }
   for (uint32_t t = 0; t < nt; t++) {

@@ -60,7 +60,7 @@ class qw_plan_opts(C.Structure):
                 ("tile_qubits", C.c_uint32), ("low_qubits", C.c_uint32), ("window", C.c_uint32),
                 ("use_graph", C.c_int32), ("fault_injection", C.c_int32),
                 ("fuse_energy", C.c_int32), ("pauli_frames", C.c_int32), ("handoff", C.c_int32),
-                ("prefix_fp64", C.c_int32)]
+                ("prefix_fp64", C.c_int32), ("dense_boundaries", C.c_int32)]
 
 
 class qw_cost_tuple(C.Structure):

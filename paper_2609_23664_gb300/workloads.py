@@ -378,6 +378,28 @@ def config2_vqe24(seed: int = BASE_SEED + 2, n: int = 24, prefix_layers: int = 2
     return tasks
 
 
+def deep_local_sweep(seed: int = BASE_SEED + 7, n: int = 24, layers: int = 60, lo: int = 8, width: int = 5,
+                     n_tasks: int = 64, n_terms: int = 32, mode: int = MODE_SV_FP32) -> List[Task]:
+    """A sweep whose shared prefix is deep but local: H on every qubit, then
+    `layers` layers of RY, a CNOT chain and RZ confined to qubits
+    lo..lo+width-1; each task adds an RY layer on every qubit and takes the
+    energy of a shared random Hamiltonian."""
+    rng = np.random.default_rng(seed)
+    ops = [(OP_H, q, 0) for q in range(n)]
+    qs = range(lo, lo + width)
+    for _ in range(layers):
+        ops += [(OP_RY, q, 0, float(rng.uniform(0, 2 * np.pi))) for q in qs]
+        ops += [(OP_CNOT, q, q + 1) for q in range(lo, lo + width - 1)]
+        ops += [(OP_RZ, q, 0, float(rng.uniform(0, 2 * np.pi))) for q in qs]
+    prefix = gates_from_list(ops)
+    ham = random_pauli_hamiltonian(rng, n, n_terms)
+    tasks = []
+    for _ in range(n_tasks):
+        suf = gates_from_list([(OP_RY, q, 0, float(rng.uniform(0, 2 * np.pi))) for q in range(n)])
+        tasks.append(Task(mode=mode, n=n, spans=[prefix, suf], terms=ham))
+    return tasks
+
+
 def config3_noisy22(seed: int = BASE_SEED + 3, n: int = 22, n_gates: int = 400,
                     n_traj: int = 1024, p: float = 1e-3, shots: int = 100,
                     mode: int = MODE_SV_FP32) -> List[Task]:

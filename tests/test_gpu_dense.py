@@ -230,3 +230,36 @@ def test_mixed_engine_program_uses_tensor_cores_only_for_large_blocks(eng):
     assert np.max(np.abs(got - want)) <= 1e-5
     assert prog.config()["engine"] in (Q.DENSE_AUTO, Q.DENSE_SIMT, Q.DENSE_TENSOR)
     prog.close()
+
+
+def test_plan_evolves_a_deep_local_boundary_with_dense_blocks(eng):
+    # a shared prefix of 40 layers confined to qubits 6-10 (one 5-qubit dense
+    # block, but hundreds of gates for a pass kernel), then a short suffix
+    tasks = W.deep_local_sweep(seed=5, n=20, layers=40, lo=6, n_tasks=6, n_terms=16)
+    plan = Q.Plan(eng, Q.Workload(tasks), dense_boundaries=1)
+    plan.run()
+    ch = plan.cost_record()["dense_boundaries"]
+    assert len(ch) == 1 and ch[0]["blocks"] >= 1
+    print(ch)
+    # one dense pass over the state against hundreds of gates in a pass kernel
+    assert ch[0]["used"] and ch[0]["dense_ms"] < ch[0]["pass_kernels_ms"]
+    assert ch[0]["engine"] in ("tensor", "mixed")
+    for i in (0, len(tasks) - 1):
+        ref = orc.run_task(tasks[i])
+        e, _ = plan.energy(i)
+        assert abs(e - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(tasks[i].terms["coef"])))
+    plan.close()
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_dense_boundaries_keep_parity_on_the_vqe_sweep(eng, mode):
+    tasks = W.config2_vqe24(n=16, n_tasks=4, n_terms=20)
+    plan = Q.Plan(eng, Q.Workload(tasks), dense_boundaries=mode)
+    plan.run()
+    ch = plan.cost_record()["dense_boundaries"]
+    assert len(ch) == 1 and (ch[0]["used"] or mode == 1)
+    for i, t in enumerate(tasks):
+        ref = orc.run_task(t)
+        e, _ = plan.energy(i)
+        assert abs(e - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(t.terms["coef"]))), i
+    plan.close()
