@@ -94,7 +94,8 @@ def eng():
 
 @pytest.mark.parametrize("seed", range(16))
 @pytest.mark.parametrize("opts", [dict(), dict(delta_frac=0.0, min_group=2), dict(batched=0),
-                                  dict(pauli_frames=0, handoff=0, prefix_fp64=1, use_graph=0)])
+                                  dict(pauli_frames=0, handoff=0, prefix_fp64=1, use_graph=0),
+                                  dict(delta_frac=0.0, dense_boundaries=2)])
 def test_random_workload_matches_oracle(eng, seed, opts):
     tasks = random_workload(1000 + seed)
     wl = Q.Workload(tasks)
