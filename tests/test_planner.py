@@ -364,3 +364,15 @@ def test_execute_without_engine_is_a_state_error():
     with pytest.raises(Q.QuwarpError) as ei:
         p.wait()
     assert ei.value.status == -6
+
+
+def test_public_header_is_plain_c():
+    # the boundary is a C ABI: the header must compile as C99 on its own
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-x", "c",
+                        os.path.join(ROOT, "include", "quwarp.h")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
