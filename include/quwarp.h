@@ -293,7 +293,7 @@ qw_status qw_fingerprint(uint32_t n_qubits, uint32_t mode, const qw_gate *gates,
 
 /* Reuse inequality, Eq. 2:
  *   (N-1) C_prefix > C_materialize + N (C_reload + C_handoff) + delta.
- * *reuse = 1 when it holds (strict), *lhs/*rhs receive both sides. */
+ * *reuse = 1 when it holds (strict), *lhs and *rhs receive both sides. */
 typedef struct qw_cost_tuple {
   double n_tasks;
   double c_prefix;
