@@ -181,12 +181,12 @@ def test_autotuned_fusion_width_and_engine(eng, mode, n, engine):
     prog.close()
 
 
-@pytest.mark.parametrize("qubits", [[5, 6, 7, 8, 9], [0, 1, 2, 3, 4], [27, 3, 14, 0, 22]])
-def test_block_at_28_qubits_sampled_groups(eng, qubits):
-    # full size (2 GiB FP32 state, 2^16 tiles): 512 sampled groups of 32
-    # amplitudes checked one by one against the oracle's operator on the
-    # group, and the norm kept
-    n = 28
+@pytest.mark.parametrize("n,qubits", [(28, [5, 6, 7, 8, 9]), (28, [0, 1, 2, 3, 4]), (28, [27, 3, 14, 0, 22]),
+                                      (30, [29, 1, 2, 3, 17])])
+def test_block_at_full_size_sampled_groups(eng, n, qubits):
+    # full size (28 qubits: 2 GiB FP32 state, 2^16 tiles; 30 qubits, the
+    # statevector cap: 8 GiB): 512 sampled groups of 32 amplitudes checked
+    # one by one against the oracle's operator on the group, and the norm kept
     g = torch.Generator(device="cuda").manual_seed(28)
     st = torch.randn(1 << n, dtype=torch.complex64, device="cuda", generator=g)
     st /= torch.linalg.vector_norm(st)
@@ -263,3 +263,15 @@ def test_dense_boundaries_keep_parity_on_the_vqe_sweep(eng, mode):
         e, _ = plan.energy(i)
         assert abs(e - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(t.terms["coef"]))), i
     plan.close()
+
+
+@pytest.mark.parametrize("engine", [T, S, Q.DENSE_AUTO])
+def test_empty_gate_list_leaves_the_state(eng, engine):
+    rng = np.random.default_rng(3)
+    psi = rounded(random_state(rng, 13), FP32)
+    prog = Q.DenseProgram(eng, FP32, 13, gates=W.gates_from_list([]), kmax=0 if engine == Q.DENSE_AUTO else 5,
+                          engine_kind=engine)
+    assert prog.info()["blocks"] == 0
+    got = run_prog(prog, psi, FP32)
+    assert np.array_equal(got, psi)
+    prog.close()
