@@ -140,16 +140,6 @@ void launch_energy(bool fp64, const EnJob *jobs, uint32_t n_jobs, uint32_t total
 // ---------------------------------------------------------------------------
 constexpr int SMP_PER_LANE = (1 << SMP_BLOCK_BITS) / 32;  // 128
 
-template <typename T>
-__device__ __forceinline__ double prob_of(const typename V2o<T>::t &v);
-template <>
-__device__ __forceinline__ double prob_of<float>(const float2 &v) {
-  return (double)fmaf(v.x, v.x, v.y * v.y);
-}
-template <>
-__device__ __forceinline__ double prob_of<double>(const double2 &v) {
-  return fma(v.x, v.x, v.y * v.y);
-}
 
 __device__ __forceinline__ uint32_t find_source(const SmpSource *srcs, uint32_t n_src, uint32_t gb) {
   uint32_t lo = 0, hi = n_src;
@@ -160,22 +150,59 @@ __device__ __forceinline__ uint32_t find_source(const SmpSource *srcs, uint32_t 
   return lo;
 }
 
+// Running sum of one lane's probabilities in index order.  FP64 states add
+// in FP64; FP32 states add their FP32 probabilities in double-float (a
+// two-sum of the high part, about 2^-44 relative, FP32 arithmetic at 64
+// times GB300's FP64 rate) and hand the sum on in FP64.  The lane sums and
+// the element scan of the shot kernel make the same additions in the same
+// order, so their partial sums agree bit for bit.
+template <typename T> struct SmpAcc;
+template <> struct SmpAcc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double p) { v += p; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+template <> struct SmpAcc<float> {
+  DFAcc a;
+  __device__ __forceinline__ void add(float p) { a.add(p); }
+  __device__ __forceinline__ double value() const { return a.value(); }
+};
+__device__ __forceinline__ float prob32(const float2 &v) { return fmaf(v.x, v.x, v.y * v.y); }
+__device__ __forceinline__ double prob32(const double2 &v) { return fma(v.x, v.x, v.y * v.y); }
+
 // lane-serial sum of the lane's 128 probabilities, lane sums chained in order
 template <typename T>
 __device__ void lane_sums(const typename V2o<T>::t *psi, uint32_t dim, uint32_t off, int ln,
                           double *lane_sum, int32_t *lane_last) {
-  double s = 0;
+  SmpAcc<T> s;
   int32_t last = -1;
   const uint32_t b0 = off + (uint32_t)ln * SMP_PER_LANE;
+  if constexpr (sizeof(T) == 4) {
+    if (b0 + SMP_PER_LANE <= dim) {  // FP32, whole segment: two amplitudes per 16-byte load
+      const float4 *q = reinterpret_cast<const float4 *>(psi + b0);
+#pragma unroll 8
+      for (int i = 0; i < SMP_PER_LANE / 2; i++) {
+        const float4 v = q[i];
+        const float p0 = fmaf(v.x, v.x, v.y * v.y), p1 = fmaf(v.z, v.z, v.w * v.w);
+        s.add(p0);
+        if (p0 > 0) last = ln * SMP_PER_LANE + 2 * i;
+        s.add(p1);
+        if (p1 > 0) last = ln * SMP_PER_LANE + 2 * i + 1;
+      }
+      *lane_sum = s.value();
+      *lane_last = last;
+      return;
+    }
+  }
   for (int i = 0; i < SMP_PER_LANE; i++) {
     const uint32_t x = b0 + i;
     if (x < dim) {
-      const double p = prob_of<T>(psi[x]);
-      s += p;
+      const auto p = prob32(psi[x]);
+      s.add(p);
       if (p > 0) last = ln * SMP_PER_LANE + i;
     }
   }
-  *lane_sum = s;
+  *lane_sum = s.value();
   *lane_last = last;
 }
 
@@ -271,16 +298,16 @@ __global__ void smp_shot_kernel(const SmpSource *__restrict__ srcs, const SmpSho
   const int L = __ffs(hit) - 1;
   if (ln == L) {
     const uint32_t b0 = (blk << SMP_BLOCK_BITS) + (uint32_t)L * SMP_PER_LANE;
-    double pre = 0;
+    SmpAcc<T> pre;
     uint64_t ans = (uint64_t)b0 + SMP_PER_LANE - 1;
     int64_t last_pos = -1;
     for (int i = 0; i < SMP_PER_LANE; i++) {
       const uint32_t x = b0 + i;
       if (x >= dim) break;
-      const double p = prob_of<T>(psi[x]);
-      pre += p;
+      const auto p = prob32(psi[x]);
+      pre.add(p);
       if (p > 0) last_pos = x;
-      if (ob + (lane_start + pre) > target) { ans = x; last_pos = -2; break; }
+      if (ob + (lane_start + pre.value()) > target) { ans = x; last_pos = -2; break; }
     }
     if (last_pos >= 0) ans = (uint64_t)last_pos;
     *Q.out = ans;
