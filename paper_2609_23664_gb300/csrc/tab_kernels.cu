@@ -33,11 +33,25 @@ struct TabSm {
   uint8_t *sign;   // rows
   uint8_t *pending;
   uint64_t *xs;    // W words (collapse scratch)
-  TabSlot *sl;     // TAB_SLOT_STAGE staged slots
+  TabSlot *sl;     // TAB_SLOT_STAGE staged slots of the current layer
+  TabSlot *sl_alt; // the other staging buffer (== sl when single-buffered)
   uint32_t *any_random;
   uint32_t W, W2;  // words per half row, per row
   uint32_t swz;    // word swizzle mask (2W - 1 when 2W is a power of two <= 16, else 0)
 };
+
+// Shared memory of a tableau of n qubits with one slot staging buffer, and
+// whether a second one fits under the size the largest tableau needs (then
+// a layer's slots are staged while the previous layer runs, saving a
+// barrier per layer).
+QW_HD inline size_t tab_smem_single(uint32_t n) {
+  const uint32_t W = (n + 63) / 64, rows = 2 * n;
+  return (size_t)rows * 2 * W * 8 + ((rows + 15) & ~15u) + ((n + 15) & ~15u) + (size_t)((W + 1) & ~1u) * 8 +
+         (size_t)TAB_SLOT_STAGE * sizeof(TabSlot) + 16;
+}
+QW_HD inline bool tab_double_buffer(uint32_t n) {
+  return tab_smem_single(n) + (size_t)TAB_SLOT_STAGE * sizeof(TabSlot) <= tab_smem_single(QW_TABLEAU_MAX_QUBITS);
+}
 
 // Word c of row r (x words 0..W-1, then z words W..2W-1).  When a row is a
 // power-of-two number of words, word c is stored at position c ^ (r mod 2W)
@@ -202,20 +216,40 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
     }
     Lafter = desc(li + 1);
   };
+  // with two staging buffers, a small layer writes the next layer's first
+  // slots into the other buffer before its closing barrier
+  TabSlot *sl_cur = S.sl, *sl_alt = S.sl_alt;
+  const bool db = sl_alt != sl_cur;
+  auto stage_next = [&](uint32_t li) {
+    if (!db || li + 1 >= P.n_layers) return false;
+    const uint32_t cn = min(TAB_SLOT_STAGE, Lnext.n_slots);
+#pragma unroll
+    for (int k = 0; k < PRE; k++) {
+      const uint32_t i = threadIdx.x + (uint32_t)k * TAB_THREADS;
+      if (i < cn) sl_alt[i] = pre[k];
+    }
+    return true;
+  };
+  bool staged = false;  // this layer's slots are already in S.sl_alt
   Lnext = desc(0);
   prefetch(0);
   for (uint32_t li = 0; li < P.n_layers; li++) {
     const TabLayer cur = Lnext;
     Lnext = Lafter;
-    {
+    if (staged) {
+      TabSlot *t = sl_cur;
+      sl_cur = sl_alt;
+      sl_alt = t;
+    } else {
       const uint32_t cn = min(TAB_SLOT_STAGE, cur.n_slots);
 #pragma unroll
       for (int k = 0; k < PRE; k++) {
         const uint32_t i = threadIdx.x + (uint32_t)k * TAB_THREADS;
-        if (i < cn) S.sl[i] = pre[k];
+        if (i < cn) sl_cur[i] = pre[k];
       }
+      __syncthreads();
     }
-    __syncthreads();
+    staged = false;
     if (cur.n_slots <= TAB_SLOT_STAGE) prefetch(li + 1);
     if (!cur.is_measure) {
       // the layer's slots are staged in shared memory (one coalesced read
@@ -223,14 +257,14 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
       for (uint32_t c0 = 0; c0 < cur.n_slots; c0 += TAB_SLOT_STAGE) {
       const uint32_t cn = min(TAB_SLOT_STAGE, cur.n_slots - c0);
       if (c0 > 0) {
-        for (uint32_t i = threadIdx.x; i < cn; i += blockDim.x) S.sl[i] = A.slots[cur.slot_begin + c0 + i];
+        for (uint32_t i = threadIdx.x; i < cn; i += blockDim.x) sl_cur[i] = A.slots[cur.slot_begin + c0 + i];
         __syncthreads();
       }
       if (S.swz) {
         // one thread per slot over all the row's words (swizzled rows keep
         // the 32 rows of a warp on different banks)
         for (uint32_t i = threadIdx.x; i < cn; i += blockDim.x) {
-          const TabSlot sl = S.sl[i];
+          const TabSlot sl = sl_cur[i];
           switch (W) {
             case 8: tab_slot<8>(S, sl); break;
             case 4: tab_slot<4>(S, sl); break;
@@ -238,6 +272,7 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
             default: tab_slot<1>(S, sl); break;
           }
         }
+        if (cur.n_slots <= TAB_SLOT_STAGE) staged = stage_next(li);
         __syncthreads();
         continue;
       }
@@ -245,7 +280,7 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
         const uint32_t si = sb + ln / lpp;
         const bool act = si < cn;
         TabSlot sl{};
-        if (act) sl = S.sl[si];
+        if (act) sl = sl_cur[si];
         int t = 0;
         if (act && sl.kind == T_PROD) {
           if (w < W) {
@@ -278,6 +313,7 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
           }
         }
       }
+      if (cur.n_slots <= TAB_SLOT_STAGE) staged = stage_next(li);
       __syncthreads();
       }
       if (cur.n_slots > TAB_SLOT_STAGE) prefetch(li + 1);
@@ -288,7 +324,7 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
       int my_pending = 0;
       if (S.swz) {  // one thread per slot (swizzled rows)
         for (uint32_t si = threadIdx.x; si < cur.n_slots; si += blockDim.x) {
-          const TabSlot sl = S.sl[si];
+          const TabSlot sl = sl_cur[si];
           const uint64_t *rr = S.R + (size_t)sl.dst * S.W2;
           const uint32_t kr = sl.dst & S.swz;
           uint64_t v = 0;
@@ -308,7 +344,7 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
           const uint32_t si = sb + ln / lpp;
           const bool act = si < cur.n_slots;
           TabSlot sl{};
-          if (act) sl = S.sl[si];
+          if (act) sl = sl_cur[si];
           uint64_t v = 0;
           if (act && w < W) v = tw(S, sl.dst, w);
           for (uint32_t o = lpp >> 1; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o, lpp);
@@ -325,12 +361,13 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
           }
         }
       }
+      staged = stage_next(li);
       // phase 2 (only when some outcome is random): one at a time, in
       // program order
       if (__syncthreads_or(my_pending)) {
         for (uint32_t si = 0; si < cur.n_slots; si++) {
           if (S.pending[si]) {
-            const TabSlot sl = S.sl[si];
+            const TabSlot sl = sl_cur[si];
             tab_collapse(A, S, sl, bits_base, out_base);
           }
         }
@@ -340,7 +377,7 @@ __device__ void tab_run_program(const TabArgs &A, TabSm &S, const TabProgram &P,
   }
 }
 
-__global__ void __launch_bounds__(TAB_THREADS) tab_kernel(TabArgs A) {
+__global__ void __launch_bounds__(TAB_THREADS, 1) tab_kernel(TabArgs A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ uint32_t s_any_random;
   if (A.run_if && *A.run_if == 0u) return;  // uniform over the grid
@@ -353,6 +390,7 @@ __global__ void __launch_bounds__(TAB_THREADS) tab_kernel(TabArgs A) {
   S.pending = S.sign + ((rows + 15) & ~15u);
   S.xs = (uint64_t *)(S.pending + ((A.n + 15) & ~15u));
   S.sl = (TabSlot *)(S.xs + ((W + 1) & ~1u));
+  S.sl_alt = tab_double_buffer(A.n) ? S.sl + TAB_SLOT_STAGE : S.sl;
   S.W = W;
   S.W2 = 2 * W;
   S.swz = (W == 1 || W == 2 || W == 4 || W == 8) ? 2 * W - 1 : 0u;
@@ -395,9 +433,7 @@ __global__ void __launch_bounds__(TAB_THREADS) tab_kernel(TabArgs A) {
 }
 
 size_t tab_smem_bytes(uint32_t n) {
-  const uint32_t W = (n + 63) / 64, rows = 2 * n;
-  return (size_t)rows * 2 * W * 8 + ((rows + 15) & ~15u) + ((n + 15) & ~15u) + (size_t)((W + 1) & ~1u) * 8 +
-         (size_t)TAB_SLOT_STAGE * sizeof(TabSlot) + 16;
+  return tab_smem_single(n) + (tab_double_buffer(n) ? (size_t)TAB_SLOT_STAGE * sizeof(TabSlot) : 0);
 }
 
 // the largest tableau (QW_TABLEAU_MAX_QUBITS) fits below the 227 KB opt-in
