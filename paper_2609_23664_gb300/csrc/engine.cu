@@ -1607,7 +1607,7 @@ qw_status sv_energy_dev(Engine *E, uint32_t mode, uint32_t n, const void *state,
   cudaStream_t s = (cudaStream_t)stream;
   const bool fp64 = mode == QW_MODE_SV_FP64;
   HamLayout H;
-  build_energy_layout(terms, n_terms, n, &H.chunk_bits, H.classes, H.terms, &H.n_blocks);
+  build_energy_layout(terms, n_terms, n, fp64 ? 16u : 8u, &H.chunk_bits, H.classes, H.terms, &H.n_blocks);
   EnClass *dc = stream_upload(H.classes, s);
   EnTerm *dt = stream_upload(H.terms, s);
   double *dout = nullptr, *dpart = nullptr;

@@ -67,8 +67,10 @@ qw_status scratch_address(int dev, NaScratch **out) {
   return QW_OK;
 }
 
-// Same term layout as the allocating entry point (classes by the flip bits
-// above the chunk, term order kept inside a class), built into fixed arrays.
+// The term layout of the allocating entry point (classes by the flip bits
+// above the chunk, term order kept inside a class) with at most 3 class
+// bits (chunks of an eighth of the state for n >= 15), built into fixed
+// arrays sized for that.
 void layout_fixed(const qw_pauli_term *terms, uint32_t n_terms, uint32_t n, NaHeader &h,
                   uint32_t *n_classes, uint32_t *n_blocks, uint32_t *chunk_bits_out) {
   uint32_t u = 0, chunk_bits = n;

@@ -941,12 +941,13 @@ void build_plan(qw_plan *P, Engine *E, const Workload &W) {
     if (T.mode == QW_MODE_TABLEAU || T.terms.empty()) continue;
     const uint32_t n_eff = std::max<uint32_t>(T.n, SV_G);
     std::string key((const char *)T.terms.data(), T.terms.size() * sizeof(qw_pauli_term));
-    key += strf("|%u", n_eff);
+    const uint32_t amp_bytes = T.mode == QW_MODE_SV_FP64 ? 16u : 8u;
+    key += strf("|%u|%u", n_eff, amp_bytes);
     auto it = ham_ids.find(key);
     if (it != ham_ids.end()) { P->tasks[t].ham = it->second; continue; }
     HamLayout H;
     H.n_eff = n_eff;
-    build_energy_layout(T.terms.data(), T.terms.size(), n_eff, &H.chunk_bits, H.classes, H.terms,
+    build_energy_layout(T.terms.data(), T.terms.size(), n_eff, amp_bytes, &H.chunk_bits, H.classes, H.terms,
                         &H.n_blocks);
     P->hams.push_back(std::move(H));
     ham_ids[key] = (int)P->hams.size() - 1;

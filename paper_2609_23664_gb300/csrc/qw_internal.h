@@ -196,8 +196,10 @@ struct SmpShot {
   uint64_t *out;
 };
 // Hamiltonian layout: classes of terms grouped by the flip-pattern bits above
-// the chunk size, so that one class touches pairs of chunks only.
-void build_energy_layout(const qw_pauli_term *terms, uint64_t n_terms, uint32_t n,
+// the chunk size, so that one class touches pairs of chunks only.  Chunks
+// hold at most EN_CHUNK_BYTES of amplitudes of amp_bytes each.
+constexpr uint64_t EN_CHUNK_BYTES = 32ull << 20;
+void build_energy_layout(const qw_pauli_term *terms, uint64_t n_terms, uint32_t n, uint32_t amp_bytes,
                          uint32_t *chunk_bits, std::vector<EnClass> &classes,
                          std::vector<EnTerm> &en_terms, uint32_t *n_blocks);
 
