@@ -94,12 +94,79 @@ struct SvTableBuilder {
           if ((v >> j) & 1u) { const uint32_t li = d.b + 6 + j; if (li < d.k) g |= 1u << hp.q[li]; }
         d.hi_tab[v] = g;
       }
+      // byte offset of the swizzled slot of a (pre-swizzle) tile index
+      const uint32_t asz = fp64 ? 16u : 8u;
+      auto slot = [&](uint32_t v) { return (fp64 ? sv_swz64(v) : sv_swz32(v)) * asz; };
+      auto phi_of = [&](const uint32_t *mcol, uint32_t mc, uint32_t l) {
+        uint32_t v = mc;
+        for (uint32_t t = 0; t < d.k; t++)
+          if ((l >> t) & 1u) v ^= mcol[t];
+        return v;
+      };
+      // every tile map must be a bijection of the k-bit tile index: the
+      // kernels address shared memory through it
+      auto check_phi = [&](const uint32_t *mcol, uint32_t mc) {
+        const uint32_t km = (1u << d.k) - 1u;
+        uint32_t basis[32] = {0};
+        bool ok = (mc & ~km) == 0;
+        for (uint32_t t = 0; t < d.k && ok; t++) {
+          uint32_t v = mcol[t];
+          if (v & ~km) { ok = false; break; }
+          for (int bit = 31; bit >= 0 && v; bit--)
+            if ((v >> bit) & 1u) {
+              if (!basis[bit]) { basis[bit] = v; break; }
+              v ^= basis[bit];
+            }
+          ok = v != 0;
+        }
+        if (!ok) fail(QW_ERR_STATE, "internal: tile map of a pass is not a bijection");
+      };
+      check_phi(hp.mcol, hp.mc);
+      for (const HostStage &hs : hp.stages) check_phi(hs.mcol, hs.mc);
+      {
+        bool ident = hp.mc == 0;
+        for (uint32_t t = 0; t < d.k; t++) ident = ident && hp.mcol[t] == (1u << t);
+        d.phi_ident = ident ? 1u : 0u;
+        const uint32_t apu_bits = fp64 ? 0u : 1u;  // amplitudes per 16-byte unit: 2^apu_bits
+        for (uint32_t v = 0; v < 64; v++) d.st_lo[v] = slot(phi_of(hp.mcol, hp.mc, v << apu_bits));
+        for (uint32_t v = 0; v < 128; v++) d.st_hi[v] = slot(phi_of(hp.mcol, 0, v << (6 + apu_bits)));
+        d.phi_pair = fp64 ? 0u : slot(hp.mcol[0]);
+      }
       for (const HostStage &hs : hp.stages) {
         SvStageDesc sd;
         memset(&sd, 0, sizeof(sd));
-        for (int j = 0; j < SV_G; j++) { sd.pos[j] = hs.pos[j]; sd.colmask[j] = hs.colmask[j]; }
-        sd.xmask = hs.xmask;
-        sd.n_ops = (uint16_t)hs.ops.size();
+        uint32_t pm = 0;
+        for (int j = 0; j < SV_G; j++) {
+          sd.roff[j] = slot(hs.mcol[hs.pos[j]]);
+          pm |= 1u << hs.pos[j];
+        }
+        sd.cst = slot(hs.mc);
+        // group bits: the first four (the lanes of a half warp) chosen so
+        // that their slots differ in the bank bits (slot bits 0-3 of 8-byte
+        // FP32 slots, 0-2 of 16-byte FP64 slots), the rest ascending
+        std::vector<uint32_t> free_pos;
+        for (uint32_t t = 0; t < d.k; t++)
+          if (!(pm & (1u << t))) free_pos.push_back(t);
+        const uint32_t bank_mask = fp64 ? 7u : 15u;
+        std::vector<uint32_t> order, basis;
+        std::vector<uint8_t> used(free_pos.size(), 0);
+        for (int pick = 0; pick < 4; pick++) {
+          int best = -1;
+          for (size_t c = 0; c < free_pos.size() && best < 0; c++) {
+            if (used[c]) continue;
+            uint32_t v = (fp64 ? sv_swz64(hs.mcol[free_pos[c]]) : sv_swz32(hs.mcol[free_pos[c]])) & bank_mask;
+            for (uint32_t bv : basis) v = std::min(v, v ^ bv);  // reduce against the echelon basis
+            if (v) { best = (int)c; basis.push_back(v); std::sort(basis.rbegin(), basis.rend()); }
+          }
+          if (best < 0) break;
+          used[best] = 1;
+          order.push_back(free_pos[best]);
+        }
+        for (size_t c = 0; c < free_pos.size(); c++)
+          if (!used[c]) order.push_back(free_pos[c]);
+        if (order.size() > (size_t)SV_MAX_GBITS) fail(QW_ERR_STATE, "internal: tile wider than the stage descriptor");
+        for (size_t t = 0; t < order.size(); t++) sd.gcol[t] = slot(hs.mcol[order[t]]);
+        sd.n_ops = (uint32_t)hs.ops.size();
         sd.op_begin = (uint32_t)(fp64 ? ops64.size() : ops32.size());
         for (const HostOp &o : hs.ops) {
           const uint32_t lo = std::min(o.a, o.b), hi = std::max(o.a, o.b);

@@ -9,7 +9,10 @@
 // Inside a pass, gates are grouped into STAGES of at most 5 tile bits; a
 // thread holds the 32 amplitudes of one stage group in registers and applies
 // the whole stage there.  Consecutive single-qubit gates on one qubit are
-// multiplied into one 2x2 matrix in double precision.
+// multiplied into one 2x2 matrix in double precision.  Permutation gates
+// (CNOT, SWAP, X) are index relabellings: the pass tracks an affine map over
+// GF(2) from logical tile index to slot, and a permutation only changes that
+// map, so CNOT chains cost no stage and no data movement.
 //
 // Tableau: a Clifford gate run becomes LAYERS of row operations on the
 // inverse tableau that touch disjoint rows, so that one layer runs fully in
@@ -78,18 +81,15 @@ static int popc32(uint32_t v) { return __builtin_popcount(v); }
 // positions; `forced` positions belong to every group.  A gate joins the
 // current group when it touches no position blocked by an earlier skipped
 // gate (it then commutes past every skipped gate) and when the positions it
-// reserves, cap_masks[i] (a superset of masks[i]), still fit.  With `perm`
-// given, a non-permutation gate is not taken after a permutation gate on one
-// of its positions, so the permutations of a group can all move to its end.
+// reserves, cap_masks[i] (a superset of masks[i]), still fit.
 static void greedy_groups(const std::vector<uint32_t> &masks, const std::vector<uint32_t> *cap_masks,
                           uint32_t n_pos, uint32_t cap, uint32_t forced,
-                          std::vector<std::vector<uint32_t>> &groups, std::vector<uint32_t> &group_masks,
-                          const std::vector<uint8_t> *perm = nullptr) {
+                          std::vector<std::vector<uint32_t>> &groups, std::vector<uint32_t> &group_masks) {
   const uint32_t full = (n_pos >= 32) ? 0xFFFFFFFFu : ((1u << n_pos) - 1);
   std::vector<uint32_t> rem(masks.size());
   for (uint32_t i = 0; i < rem.size(); i++) rem[i] = i;
   while (!rem.empty()) {
-    uint32_t Q = forced, blocked = 0, permq = 0;
+    uint32_t Q = forced, blocked = 0;
     std::vector<uint32_t> taken;
     std::vector<uint32_t> keep;
     keep.reserve(rem.size());
@@ -97,17 +97,14 @@ static void greedy_groups(const std::vector<uint32_t> &masks, const std::vector<
     for (; i < rem.size(); i++) {
       const uint32_t gi = rem[i], qs = masks[gi];
       const uint32_t cs = cap_masks ? (qs | ((*cap_masks)[gi] & ~blocked)) : qs;
-      const bool is_perm = perm && (*perm)[gi];
-      if ((qs & blocked) || (perm && !is_perm && (qs & permq))) {
+      if (qs & blocked) {
         blocked |= qs;  // must stay after an earlier skipped gate on a shared qubit
         keep.push_back(gi);
       } else if ((uint32_t)popc32(Q | cs) <= cap) {
         Q |= cs;
-        if (is_perm) permq |= qs;
         taken.push_back(gi);
       } else if ((uint32_t)popc32(Q | qs) <= cap && cs != qs && (qs & Q) == qs) {
-        if (is_perm) permq |= qs;  // fits without its reservation: positions already held
-        taken.push_back(gi);
+        taken.push_back(gi);  // fits without its reservation: positions already held
       } else {
         blocked |= qs;
         keep.push_back(gi);
@@ -116,6 +113,53 @@ static void greedy_groups(const std::vector<uint32_t> &masks, const std::vector<
     }
     for (; i < rem.size(); i++) keep.push_back(rem[i]);
     if (taken.empty()) fail(QW_ERR_INVALID_ARG, "fusion: gate does not fit a group");
+    groups.push_back(std::move(taken));
+    group_masks.push_back(Q);
+    rem.swap(keep);
+  }
+}
+
+// Stage cover of a pass's gates (positions = tile bits, at most SV_G per
+// stage).  Permutation gates hold no positions: a stage takes one unless an
+// earlier skipped gate shares a qubit with it, and it is applied after the
+// stage's other gates, so a later non-permutation gate on one of its qubits
+// waits for the next stage.  The other gates join as in greedy_groups.
+static void stage_groups(const std::vector<uint32_t> &masks, const std::vector<uint32_t> &cap_masks,
+                         const std::vector<uint8_t> &perm, std::vector<std::vector<uint32_t>> &groups,
+                         std::vector<uint32_t> &group_masks) {
+  std::vector<uint32_t> rem(masks.size());
+  for (uint32_t i = 0; i < rem.size(); i++) rem[i] = i;
+  while (!rem.empty()) {
+    uint32_t Q = 0, blocked = 0, permq = 0;
+    std::vector<uint32_t> taken, keep;
+    keep.reserve(rem.size());
+    for (const uint32_t gi : rem) {
+      const uint32_t qs = masks[gi];
+      if (perm[gi]) {
+        if (qs & blocked) {
+          blocked |= qs;
+          keep.push_back(gi);
+        } else {
+          permq |= qs;
+          taken.push_back(gi);
+        }
+        continue;
+      }
+      const uint32_t cs = qs | (cap_masks[gi] & ~blocked & ~permq);
+      if (qs & (blocked | permq)) {
+        blocked |= qs;
+        keep.push_back(gi);
+      } else if ((uint32_t)popc32(Q | cs) <= (uint32_t)SV_G) {
+        Q |= cs;
+        taken.push_back(gi);
+      } else if ((uint32_t)popc32(Q | qs) <= (uint32_t)SV_G && (qs & Q) == qs) {
+        taken.push_back(gi);
+      } else {
+        blocked |= qs;
+        keep.push_back(gi);
+      }
+    }
+    if (taken.empty()) fail(QW_ERR_INVALID_ARG, "fusion: gate does not fit a stage");
     groups.push_back(std::move(taken));
     group_masks.push_back(Q);
     rem.swap(keep);
@@ -193,9 +237,12 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
       if (Q & (1u << q)) { loc[q] = (uint32_t)hp.q.size(); hp.q.push_back(q); }
     hp.b = b;
     hp.n_gates = (uint32_t)pass_gates[p].size();
-    // stages inside the pass (positions = local tile bits).  A single-qubit
-    // gate reserves the positions of the next two-qubit gate on its qubit, so
-    // it lands in the same stage as that gate.
+    // stages inside the pass (positions = local tile bits).  Permutation
+    // gates (CNOT, SWAP, X) move no data: they update the pass's affine map
+    // from logical tile index to shared-memory slot, phi(l) = M l ^ c, at the
+    // end of the stage that takes them, so they hold no stage positions.  A
+    // single-qubit gate reserves the positions of a following two-position
+    // phase gate on its qubit, so that both land in one stage.
     const size_t np = pass_gates[p].size();
     std::vector<uint32_t> lmask(np), emask(np);
     std::vector<uint8_t> lperm(np);
@@ -210,51 +257,43 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
     for (size_t ii = np; ii-- > 0;) {
       const qw_gate &g = gates[pass_gates[p][ii]];
       const uint32_t a = loc[g.q0];
-      if (!is_two_qubit_op(g.op)) {
+      if (lperm[ii]) {
+        emask[ii] = 0;
+      } else if (!is_two_qubit_op(g.op)) {
         const int j = next_on[a];
-        emask[ii] = (j < 0) ? lmask[ii] : emask[j];
-        next_on[a] = (int)ii;
+        emask[ii] = (j < 0 || lperm[j]) ? lmask[ii] : emask[j];
       } else {
         emask[ii] = lmask[ii];
-        next_on[a] = (int)ii;
-        next_on[loc[g.q1]] = (int)ii;
       }
+      next_on[a] = (int)ii;
+      if (is_two_qubit_op(g.op)) next_on[loc[g.q1]] = (int)ii;
     }
     std::vector<std::vector<uint32_t>> st_gates;
     std::vector<uint32_t> st_masks;
-    greedy_groups(lmask, &emask, k, SV_G, 0, st_gates, st_masks, &lperm);
+    stage_groups(lmask, emask, lperm, st_gates, st_masks);
+    // phi as columns M e_t and constant c
+    uint32_t mcol[32], mc = 0;
+    for (uint32_t t = 0; t < 32; t++) mcol[t] = 1u << t;
     for (size_t s = 0; s < st_gates.size(); s++) {
       HostStage hs;
+      for (uint32_t t = 0; t < k; t++) hs.mcol[t] = mcol[t];
+      hs.mc = mc;
+      // unused register positions are taken from the top: tile bit 0 is the
+      // only one that reaches bank bit 0 of a slot, so it is kept for the
+      // lanes (group bits) where it spreads a warp's accesses over the banks
       uint32_t P = st_masks[s];
-      for (uint32_t q = 0; q < k && popc32(P) < SV_G; q++) P |= 1u << q;
+      for (uint32_t q = k; q-- > 0 && popc32(P) < SV_G;) P |= 1u << q;
       int rel[32];
       int j = 0;
       for (uint32_t q = 0; q < k; q++)
         if (P & (1u << q)) { hs.pos[j] = (uint8_t)q; rel[q] = j; j++; }
       int last1q[SV_G];
       for (int t = 0; t < SV_G; t++) last1q[t] = -1;
-      // affine index map of the stage's trailing permutations: row j of A
-      // as a mask, c = constant
-      uint8_t row[SV_G];
-      for (int t = 0; t < SV_G; t++) row[t] = (uint8_t)(1u << t);
-      uint8_t cvec = 0;
+      std::vector<uint32_t> perms;  // applied to phi after the stage's ops
       for (uint32_t gi_local : st_gates[s]) {
         const qw_gate &g = gates[pass_gates[p][gi_local]];
+        if (lperm[gi_local]) { perms.push_back(gi_local); continue; }
         const int a = rel[loc[g.q0]];
-        if (g.op == QW_OP_X) { cvec ^= (uint8_t)(1u << a); continue; }
-        if (g.op == QW_OP_CNOT) {
-          const int t = rel[loc[g.q1]];
-          row[t] ^= row[a];
-          if ((cvec >> a) & 1u) cvec ^= (uint8_t)(1u << t);
-          continue;
-        }
-        if (g.op == QW_OP_SWAP) {
-          const int t = rel[loc[g.q1]];
-          std::swap(row[a], row[t]);
-          const uint8_t ba = (cvec >> a) & 1u, bt = (cvec >> t) & 1u;
-          if (ba != bt) cvec ^= (uint8_t)((1u << a) | (1u << t));
-          continue;
-        }
         HostOp op{};
         double m[8];
         bool diag = false;
@@ -308,15 +347,19 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
         last1q[bb] = -1;
         hs.ops.push_back(op);
       }
-      for (int c = 0; c < SV_G; c++) {
-        uint8_t mk = 0;
-        for (int r = 0; r < SV_G; r++)
-          if ((row[r] >> c) & 1u) mk |= (uint8_t)(1u << r);
-        hs.colmask[c] = mk;
+      // the permutation pi of the stage's trailing gates: the amplitude of
+      // logical index pi(l) stays in the slot of l, so phi <- phi o pi^-1
+      for (uint32_t gi_local : perms) {
+        const qw_gate &g = gates[pass_gates[p][gi_local]];
+        const uint32_t a = loc[g.q0];
+        if (g.op == QW_OP_X) mc ^= mcol[a];
+        else if (g.op == QW_OP_CNOT) mcol[a] ^= mcol[loc[g.q1]];
+        else std::swap(mcol[a], mcol[loc[g.q1]]);
       }
-      hs.xmask = cvec;
-      hp.stages.push_back(std::move(hs));
+      if (!hs.ops.empty()) hp.stages.push_back(std::move(hs));
     }
+    for (uint32_t t = 0; t < k; t++) hp.mcol[t] = mcol[t];
+    hp.mc = mc;
     prog.passes.push_back(std::move(hp));
   }
   // fold the global phase into one single-qubit op (every amplitude is in

@@ -98,19 +98,25 @@ struct HostOp {
   double m[8];
   double x[4] = {0, 0, 0, 0};  // K_RP: r10, r11, pr, pi (exact factors of row 1 of m)
 };
+// A pass keeps the amplitude of logical tile index l in slot phi(l) of its
+// tile, phi(l) = M l ^ c over GF(2) (before the shared-memory swizzle):
+// permutation gates update phi instead of moving amplitudes.  phi is the
+// identity when the tile is loaded.
 struct HostStage {
-  uint8_t pos[SV_G];  // local tile bit positions (distinct)
-  // trailing CNOT/SWAP chain of the stage as a GF(2)-linear map of the
-  // stage index: column k of the map = bits j with colmask[k] bit j set
-  uint8_t colmask[SV_G];
-  uint8_t xmask = 0;  // constant part of the map (X gates)
+  uint8_t pos[SV_G] = {0, 1, 2, 3, 4};  // local tile bit positions (distinct)
+  uint32_t mcol[32];  // phi at the start of the stage: column t = M e_t
+  uint32_t mc = 0;    // and its constant c
   std::vector<HostOp> ops;
+  HostStage() { for (uint32_t t = 0; t < 32; t++) mcol[t] = 1u << t; }
 };
 struct HostPass {
   std::vector<uint32_t> q;  // local bit -> global qubit (ascending; q[i] = i for i < b)
   uint32_t b = 0;           // contiguous low qubits
   std::vector<HostStage> stages;
+  uint32_t mcol[32];        // phi after the last stage (the tile is stored through it)
+  uint32_t mc = 0;
   uint32_t n_gates = 0;     // gates of the source list absorbed by this pass
+  HostPass() { for (uint32_t t = 0; t < 32; t++) mcol[t] = 1u << t; }
 };
 struct SvProgram {
   uint32_t n = 0;  // effective qubit count (>= SV_G)
@@ -123,22 +129,38 @@ struct TileConfig {
   uint32_t b = 4;       // contiguous low qubits in every tile
 };
 
+// Shared-memory swizzle of a tile (amplitude index -> slot).  It XORs bits
+// of the index above the 16-byte unit into the unit index inside a 128-byte
+// row, so strided stage accesses spread over the banks, and it keeps every
+// 16-byte unit (two FP32 amplitudes / one FP64 amplitude) contiguous, so the
+// tile can be filled with 16-byte asynchronous copies.  It is linear over
+// GF(2): swz(a ^ b) = swz(a) ^ swz(b).
+__host__ __device__ inline uint32_t sv_swz32(uint32_t l) {
+  return l ^ ((((l >> 4) ^ (l >> 7) ^ (l >> 10) ^ (l >> 13)) & 7u) << 1);
+}
+__host__ __device__ inline uint32_t sv_swz64(uint32_t l) {
+  return l ^ (((l >> 3) ^ (l >> 6) ^ (l >> 9) ^ (l >> 12)) & 7u);
+}
+constexpr int SV_MAX_GBITS = SV_MAX_TILE_FP32 - SV_G;  // group bits of a stage
+
 // Device descriptors (plain structs, identical layout on host and device).
+// Byte offsets below are offsets into the swizzled tile.
 struct SvPassDesc {
   uint32_t k, b, n_stages, stage_begin;
-  uint32_t n_hi, pad0, pad1, pad2;
+  uint32_t n_hi, phi_ident, phi_pair, pad2;  // phi_pair: byte offset of the FP32 pair partner
   uint8_t hi_pos[32];     // global positions of the n-k non-tile bits, ascending
   uint32_t lo_tab[64];    // deposit of local bits b..b+5   (index = lh & 63)
   uint32_t hi_tab[32];    // deposit of local bits b+6..    (index = lh >> 6)
+  // store through phi (unless phi_ident): byte offset of the slot of
+  // 16-byte unit u = st_lo[u & 63] ^ st_hi[u >> 6]
+  uint32_t st_lo[64];
+  uint32_t st_hi[128];
 };
-struct SvStageDesc {
-  uint8_t pos[SV_G];
-  uint8_t colmask[SV_G];
-  uint8_t xmask;
-  uint8_t pad;
-  uint16_t n_ops;
-  uint16_t pad2;
-  uint32_t op_begin;
+struct alignas(16) SvStageDesc {
+  uint32_t roff[SV_G];           // byte offset of phi(e_pos[j]) for register bit j
+  uint32_t gcol[SV_MAX_GBITS];   // byte offsets of the group bits (zero past the tile's)
+  uint32_t cst;                  // byte offset of the constant of phi
+  uint32_t n_ops, op_begin;
 };
 template <typename T>
 struct alignas(16) SvOpDesc {

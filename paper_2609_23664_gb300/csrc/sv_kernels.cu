@@ -25,19 +25,10 @@ template <typename T> struct V2;
 template <> struct V2<float> { typedef float2 t; };
 template <> struct V2<double> { typedef double2 t; };
 
-// Shared-memory swizzle of the tile (amplitude index -> slot).  It XORs bits
-// of the index above the 16-byte unit into the unit index inside a 128-byte
-// row, so strided stage accesses spread over the banks, and it keeps every
-// 16-byte unit (two FP32 amplitudes / one FP64 amplitude) contiguous, so the
-// tile can be filled with 16-byte asynchronous copies.  It is linear over
-// GF(2): swz(a ^ b) = swz(a) ^ swz(b).
+// Shared-memory swizzle of the tile (sv_swz32 / sv_swz64).
 template <typename T> __device__ __forceinline__ uint32_t swz(uint32_t l);
-template <> __device__ __forceinline__ uint32_t swz<float>(uint32_t l) {
-  return l ^ ((((l >> 4) ^ (l >> 7) ^ (l >> 10) ^ (l >> 13)) & 7u) << 1);
-}
-template <> __device__ __forceinline__ uint32_t swz<double>(uint32_t l) {
-  return l ^ (((l >> 3) ^ (l >> 6) ^ (l >> 9) ^ (l >> 12)) & 7u);
-}
+template <> __device__ __forceinline__ uint32_t swz<float>(uint32_t l) { return sv_swz32(l); }
+template <> __device__ __forceinline__ uint32_t swz<double>(uint32_t l) { return sv_swz64(l); }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
@@ -274,54 +265,41 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
   (void)cg;
   __syncthreads();
 
+  // Stages.  The amplitude of logical tile index l sits in the slot of
+  // phi(l) (an affine map the host tracks through the pass's permutation
+  // gates), so a stage group's 32 slots are its base offset XOR combinations
+  // of the five register-bit offsets, and the stage writes its registers
+  // back to the slots it read.
   const uint32_t n_groups = 1u << (k - SV_G);
   const uint32_t n_st = pd->n_stages, st0 = pd->stage_begin;
+  const char *smc = (const char *)sm;
+  char *smw = (char *)sm;
   for (uint32_t s = 0; s < n_st; s++) {
-    const SvStageDesc st = stages[st0 + s];
-    uint32_t pos[SV_G], sp[SV_G], ss[SV_G];
-#pragma unroll
-    for (int j = 0; j < SV_G; j++) {
-      pos[j] = st.pos[j];
-      sp[j] = swz<T>(1u << pos[j]);
-    }
-    // the stage's trailing CNOT/SWAP chain maps register index i to the
-    // stage index A i: register i is stored at the offsets of A i
-#pragma unroll
-    for (int c = 0; c < SV_G; c++) {
-      const uint32_t cm = st.colmask[c];
-      ss[c] = ((cm & 1u) ? sp[0] : 0u) ^ ((cm & 2u) ? sp[1] : 0u) ^ ((cm & 4u) ? sp[2] : 0u) ^
-              ((cm & 8u) ? sp[3] : 0u) ^ ((cm & 16u) ? sp[4] : 0u);
-    }
-    uint32_t spB[SV_G], ssB[SV_G];
-#pragma unroll
-    for (int j = 0; j < SV_G; j++) {
-      spB[j] = sp[j] * (uint32_t)sizeof(C);
-      ssB[j] = ss[j] * (uint32_t)sizeof(C);
-    }
+    const uint4 *sdv = (const uint4 *)(stages + st0 + s);
+    const uint4 w0 = __ldg(sdv), w1 = __ldg(sdv + 1), w2 = __ldg(sdv + 2), w3 = __ldg(sdv + 3),
+                w4 = __ldg(sdv + 4);
+    // offsets are masked to the tile, so XOR combinations stay inside it
+    const uint32_t tm = ntile * (uint32_t)sizeof(C) - 1u;
+    const uint32_t roff[SV_G] = {w0.x & tm, w0.y & tm, w0.z & tm, w0.w & tm, w1.x & tm};
+    const uint32_t gcol[SV_MAX_GBITS] = {w1.y & tm, w1.z & tm, w1.w & tm, w2.x & tm, w2.y & tm,
+                                         w2.z & tm, w2.w & tm, w3.x & tm, w3.y & tm};
+    const uint32_t cst = w3.z & tm, nops = w3.w, op_begin = w4.x;
+    static_assert(SV_MAX_GBITS == 9 && sizeof(SvStageDesc) == 80, "stage descriptor read as five 16-byte words");
     for (uint32_t grp = threadIdx.x; grp < n_groups; grp += nt) {
-      uint32_t bse = grp;
+      uint32_t sbB = cst;
 #pragma unroll
-      for (int j = 0; j < SV_G; j++) {
-        const uint32_t p = pos[j];
-        bse = ((bse >> p) << (p + 1)) | (bse & ((1u << p) - 1u));
-      }
-      const uint32_t sb = swz<T>(bse);
-      // byte offsets into the tile: one XOR per access, the base added by
-      // the load's addressing
-      const char *smc = (const char *)sm;
-      const uint32_t sbB = sb * (uint32_t)sizeof(C);
+      for (int t = 0; t < SV_MAX_GBITS; t++) sbB ^= ((grp >> t) & 1u) ? gcol[t] : 0u;
       C a[32];
 #pragma unroll
       for (int i = 0; i < 32; i++) {
-        const uint32_t off = sbB ^ ((i & 1) ? spB[0] : 0u) ^ ((i & 2) ? spB[1] : 0u) ^
-                             ((i & 4) ? spB[2] : 0u) ^ ((i & 8) ? spB[3] : 0u) ^
-                             ((i & 16) ? spB[4] : 0u);
+        const uint32_t off = sbB ^ ((i & 1) ? roff[0] : 0u) ^ ((i & 2) ? roff[1] : 0u) ^
+                             ((i & 4) ? roff[2] : 0u) ^ ((i & 8) ? roff[3] : 0u) ^
+                             ((i & 16) ? roff[4] : 0u);
         a[i] = *(const C *)(smc + off);
       }
       {
         // the next op's parameters are loaded while the current op runs
-        const SvOpDesc<T> *op = ops + st.op_begin;
-        const uint32_t nops = st.n_ops;
+        const SvOpDesc<T> *op = ops + op_begin;
         uint32_t code = 0;
         T m[8];
         if (nops) { code = __ldg(&op->code); load_m(op, m); }
@@ -335,29 +313,45 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
           for (int t = 0; t < 8; t++) m[t] = nm[t];
         }
       }
-      // constant part of the affine map (X gates of the stage)
-      const uint32_t xm = st.xmask;
-      const uint32_t sbs = sbB ^ ((xm & 1u) ? spB[0] : 0u) ^ ((xm & 2u) ? spB[1] : 0u) ^
-                           ((xm & 4u) ? spB[2] : 0u) ^ ((xm & 8u) ? spB[3] : 0u) ^ ((xm & 16u) ? spB[4] : 0u);
-      char *smw = (char *)sm;
 #pragma unroll
       for (int i = 0; i < 32; i++) {
-        const uint32_t off = sbs ^ ((i & 1) ? ssB[0] : 0u) ^ ((i & 2) ? ssB[1] : 0u) ^
-                             ((i & 4) ? ssB[2] : 0u) ^ ((i & 8) ? ssB[3] : 0u) ^
-                             ((i & 16) ? ssB[4] : 0u);
+        const uint32_t off = sbB ^ ((i & 1) ? roff[0] : 0u) ^ ((i & 2) ? roff[1] : 0u) ^
+                             ((i & 4) ? roff[2] : 0u) ^ ((i & 8) ? roff[3] : 0u) ^
+                             ((i & 16) ? roff[4] : 0u);
         *(C *)(smw + off) = a[i];
       }
     }
     __syncthreads();
   }
 
+  if (pd->phi_ident) {
 #pragma unroll 4
-  for (uint32_t u = threadIdx.x; u < n_units; u += nt) {
-    const uint32_t l = u * APU;
-    const uint32_t lh = l >> b;
-    const uint32_t g = base | __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) |
-                       (l & lomask);
-    *(float4 *)(dst + g) = *(const float4 *)(sm + swz<T>(l));
+    for (uint32_t u = threadIdx.x; u < n_units; u += nt) {
+      const uint32_t l = u * APU;
+      const uint32_t lh = l >> b;
+      const uint32_t g = base | __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) |
+                         (l & lomask);
+      *(float4 *)(dst + g) = *(const float4 *)(sm + swz<T>(l));
+    }
+  } else {
+    // logical order to global memory, each unit's amplitudes gathered
+    // from their slots
+    const uint32_t tm = ntile * (uint32_t)sizeof(C) - 1u;
+    const uint32_t pair = pd->phi_pair & tm;
+#pragma unroll 4
+    for (uint32_t u = threadIdx.x; u < n_units; u += nt) {
+      const uint32_t l = u * APU;
+      const uint32_t lh = l >> b;
+      const uint32_t g = base | __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) |
+                         (l & lomask);
+      const uint32_t so = (__ldg(&pd->st_lo[u & 63]) ^ __ldg(&pd->st_hi[(u >> 6) & 127])) & tm;
+      if constexpr (sizeof(T) == 4) {
+        const float2 a0 = *(const float2 *)(smc + so), a1 = *(const float2 *)(smc + (so ^ pair));
+        *(float4 *)(dst + g) = make_float4(a0.x, a0.y, a1.x, a1.y);
+      } else {
+        *(double2 *)(dst + g) = *(const double2 *)(smc + so);
+      }
+    }
   }
 }
 
