@@ -131,6 +131,13 @@ struct SvTableBuilder {
         for (uint32_t v = 0; v < 64; v++) d.st_lo[v] = slot(phi_of(hp.mcol, hp.mc, v << apu_bits));
         for (uint32_t v = 0; v < 128; v++) d.st_hi[v] = slot(phi_of(hp.mcol, 0, v << (6 + apu_bits)));
         d.phi_pair = fp64 ? 0u : slot(hp.mcol[0]);
+        bool unit16 = true;  // FP64: a unit is one amplitude
+        if (!fp64) {
+          unit16 = d.phi_pair == 8u;
+          for (uint32_t v = 0; v < 64 && unit16; v++) unit16 = (d.st_lo[v] & 8u) == 0;
+          for (uint32_t v = 0; v < 128 && unit16; v++) unit16 = (d.st_hi[v] & 8u) == 0;
+        }
+        d.phi_unit16 = unit16 ? 1u : 0u;
       }
       for (const HostStage &hs : hp.stages) {
         SvStageDesc sd;

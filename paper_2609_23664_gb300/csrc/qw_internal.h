@@ -147,7 +147,9 @@ constexpr int SV_MAX_GBITS = SV_MAX_TILE_FP32 - SV_G;  // group bits of a stage
 // Byte offsets below are offsets into the swizzled tile.
 struct SvPassDesc {
   uint32_t k, b, n_stages, stage_begin;
-  uint32_t n_hi, phi_ident, phi_pair, pad2;  // phi_pair: byte offset of the FP32 pair partner
+  // phi_pair: byte offset of the FP32 pair partner; phi_unit16: every
+  // 16-byte unit's amplitudes sit in one 16-byte aligned slot pair
+  uint32_t n_hi, phi_ident, phi_pair, phi_unit16;
   uint8_t hi_pos[32];     // global positions of the n-k non-tile bits, ascending
   uint32_t lo_tab[64];    // deposit of local bits b..b+5   (index = lh & 63)
   uint32_t hi_tab[32];    // deposit of local bits b+6..    (index = lh >> 6)

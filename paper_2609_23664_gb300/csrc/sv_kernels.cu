@@ -333,6 +333,18 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
                          (l & lomask);
       *(float4 *)(dst + g) = *(const float4 *)(sm + swz<T>(l));
     }
+  } else if (pd->phi_unit16) {
+    // each unit still sits in one 16-byte slot pair, at a permuted place
+    const uint32_t tm = ntile * (uint32_t)sizeof(C) - 1u;
+#pragma unroll 4
+    for (uint32_t u = threadIdx.x; u < n_units; u += nt) {
+      const uint32_t l = u * APU;
+      const uint32_t lh = l >> b;
+      const uint32_t g = base | __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) |
+                         (l & lomask);
+      const uint32_t so = (__ldg(&pd->st_lo[u & 63]) ^ __ldg(&pd->st_hi[(u >> 6) & 127])) & tm & ~15u;
+      *(float4 *)(dst + g) = *(const float4 *)(smc + so);
+    }
   } else {
     // logical order to global memory, each unit's amplitudes gathered
     // from their slots
@@ -443,9 +455,14 @@ sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, const SvSeg *__restr
       sv_tile<T>(t.passes + job.pass, t.stages, (const SvOpDesc<T> *)t.ops, (C *)smraw, (const C *)job.src,
                  (C *)job.dst, s_unit, true);
     }
-    __threadfence();
+    // every thread's writes of the unit precede thread 0's release through
+    // the barrier (bar.sync orders them at CTA scope; the fence is
+    // cumulative), so one fence per unit suffices
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(&ctr[2 + s_job], 1u);
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&ctr[2 + s_job], 1u);
+    }
   }
 }
 
