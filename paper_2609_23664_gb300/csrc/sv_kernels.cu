@@ -225,6 +225,13 @@ __device__ __forceinline__ void apply_op(uint32_t code, const T (&m)[8], C (&a)[
   }
 }
 
+// step[t] for the bit that a Gray-code walk flips (t is a constant once
+// the walk is unrolled; the selects never index a local array)
+__device__ __forceinline__ uint32_t gray_pick(const uint32_t (&step)[6], int t) {
+  return t == 0 ? step[0] : t == 1 ? step[1] : t == 2 ? step[2] : t == 3 ? step[3] : t == 4 ? step[4]
+         : t == 5 ? step[5] : 0u;
+}
+
 // Processes one tile of one pass.  src == nullptr starts from |0...0>.
 template <typename T>
 __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__restrict__ stages,
@@ -241,21 +248,42 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
   // 16-byte units: two FP32 amplitudes or one FP64 amplitude
   constexpr uint32_t APU = (sizeof(T) == 4) ? 2u : 1u;
   const uint32_t n_units = ntile / APU;
+  // A 16-byte unit's global index (bit deposit) and slot (swizzle, tile
+  // map) are linear over GF(2) in the unit index, and a thread's units are
+  // u = tid + j nt: each thread starts from its own unit and walks j in
+  // Gray-code order, one XOR per address and unit (the table lookups stay
+  // outside the loops).
+  const uint32_t apu_bits = (APU == 2) ? 1u : 0u;
+  const uint32_t lg_nt = (uint32_t)__ffs((int)nt) - 1u;
+  const uint32_t n_iter = n_units > nt ? n_units >> lg_nt : (threadIdx.x < n_units ? 1u : 0u);
+  auto gdep = [&](uint32_t l) {
+    const uint32_t lh = l >> b;
+    return __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) | (l & lomask);
+  };
+  uint32_t gstep[6], sstep[6];
+#pragma unroll
+  for (int t = 0; t < 6; t++) {
+    const uint32_t lb = lg_nt + apu_bits + (uint32_t)t;
+    gstep[t] = lb < k ? gdep(1u << lb) : 0u;
+    sstep[t] = lb < k ? swz<T>(1u << lb) * (uint32_t)sizeof(C) : 0u;
+  }
+  const uint32_t l0 = threadIdx.x * APU;
+  const char *smc = (const char *)sm;
+  char *smw = (char *)sm;
   if (src) {
-#pragma unroll 4
-    for (uint32_t u = threadIdx.x; u < n_units; u += nt) {
-      const uint32_t l = u * APU;
-      const uint32_t lh = l >> b;
-      const uint32_t g = base | __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) |
-                         (l & lomask);
-      cp_async16(sm + swz<T>(l), src + g);
+    uint32_t g = base | gdep(l0), so = swz<T>(l0) * (uint32_t)sizeof(C);
+#pragma unroll
+    for (int j = 0; j < 64; j++) {
+      if ((uint32_t)j >= n_iter) break;
+      cp_async16(smw + so, src + g);
+      const int t = __ffs(j + 1) - 1;
+      g ^= gray_pick(gstep, t);
+      so ^= gray_pick(sstep, t);
     }
     cp_async_wait_all();
   } else {
     for (uint32_t l = threadIdx.x; l < ntile; l += nt) {
-      const uint32_t lh = l >> b;
-      const uint32_t g = base | __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) |
-                         (l & lomask);
+      const uint32_t g = base | gdep(l);
       C v;
       v.x = (g == 0) ? T(1) : T(0);
       v.y = T(0);
@@ -272,8 +300,6 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
   // back to the slots it read.
   const uint32_t n_groups = 1u << (k - SV_G);
   const uint32_t n_st = pd->n_stages, st0 = pd->stage_begin;
-  const char *smc = (const char *)sm;
-  char *smw = (char *)sm;
   for (uint32_t s = 0; s < n_st; s++) {
     const uint4 *sdv = (const uint4 *)(stages + st0 + s);
     const uint4 w0 = __ldg(sdv), w1 = __ldg(sdv + 1), w2 = __ldg(sdv + 2), w3 = __ldg(sdv + 3),
@@ -324,44 +350,54 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
     __syncthreads();
   }
 
+  const uint32_t tm = ntile * (uint32_t)sizeof(C) - 1u;
+  uint32_t g = base | gdep(l0);
   if (pd->phi_ident) {
-#pragma unroll 4
-    for (uint32_t u = threadIdx.x; u < n_units; u += nt) {
-      const uint32_t l = u * APU;
-      const uint32_t lh = l >> b;
-      const uint32_t g = base | __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) |
-                         (l & lomask);
-      *(float4 *)(dst + g) = *(const float4 *)(sm + swz<T>(l));
-    }
-  } else if (pd->phi_unit16) {
-    // each unit still sits in one 16-byte slot pair, at a permuted place
-    const uint32_t tm = ntile * (uint32_t)sizeof(C) - 1u;
-#pragma unroll 4
-    for (uint32_t u = threadIdx.x; u < n_units; u += nt) {
-      const uint32_t l = u * APU;
-      const uint32_t lh = l >> b;
-      const uint32_t g = base | __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) |
-                         (l & lomask);
-      const uint32_t so = (__ldg(&pd->st_lo[u & 63]) ^ __ldg(&pd->st_hi[(u >> 6) & 127])) & tm & ~15u;
+    uint32_t so = swz<T>(l0) * (uint32_t)sizeof(C);
+#pragma unroll
+    for (int j = 0; j < 64; j++) {
+      if ((uint32_t)j >= n_iter) break;
       *(float4 *)(dst + g) = *(const float4 *)(smc + so);
+      const int t = __ffs(j + 1) - 1;
+      g ^= gray_pick(gstep, t);
+      so ^= gray_pick(sstep, t);
     }
   } else {
-    // logical order to global memory, each unit's amplitudes gathered
-    // from their slots
-    const uint32_t tm = ntile * (uint32_t)sizeof(C) - 1u;
-    const uint32_t pair = pd->phi_pair & tm;
-#pragma unroll 4
-    for (uint32_t u = threadIdx.x; u < n_units; u += nt) {
-      const uint32_t l = u * APU;
-      const uint32_t lh = l >> b;
-      const uint32_t g = base | __ldg(&pd->lo_tab[lh & 63]) | __ldg(&pd->hi_tab[(lh >> 6) & 31]) |
-                         (l & lomask);
-      const uint32_t so = (__ldg(&pd->st_lo[u & 63]) ^ __ldg(&pd->st_hi[(u >> 6) & 127])) & tm;
-      if constexpr (sizeof(T) == 4) {
-        const float2 a0 = *(const float2 *)(smc + so), a1 = *(const float2 *)(smc + (so ^ pair));
-        *(float4 *)(dst + g) = make_float4(a0.x, a0.y, a1.x, a1.y);
-      } else {
-        *(double2 *)(dst + g) = *(const double2 *)(smc + so);
+    // slots through the final tile map: the slot of unit u is
+    // st_lo[u & 63] ^ st_hi[u >> 6] (constant folded into st_lo)
+    auto st_of = [&](uint32_t u) { return __ldg(&pd->st_lo[u & 63]) ^ __ldg(&pd->st_hi[(u >> 6) & 127]); };
+    const uint32_t c0 = __ldg(&pd->st_lo[0]);
+#pragma unroll
+    for (int t = 0; t < 6; t++) {
+      const uint32_t ub = lg_nt + (uint32_t)t;
+      sstep[t] = (ub + apu_bits < k) ? (st_of(1u << ub) ^ c0) & tm : 0u;
+    }
+    uint32_t so = st_of(threadIdx.x) & tm;
+    if (pd->phi_unit16) {
+      // each unit still sits in one 16-byte slot pair, at a permuted place
+#pragma unroll
+      for (int j = 0; j < 64; j++) {
+        if ((uint32_t)j >= n_iter) break;
+        *(float4 *)(dst + g) = *(const float4 *)(smc + (so & ~15u));
+        const int t = __ffs(j + 1) - 1;
+        g ^= gray_pick(gstep, t);
+        so ^= gray_pick(sstep, t);
+      }
+    } else {
+      // each unit's two amplitudes gathered from their slots
+      const uint32_t pair = pd->phi_pair & tm;
+#pragma unroll
+      for (int j = 0; j < 64; j++) {
+        if ((uint32_t)j >= n_iter) break;
+        if constexpr (sizeof(T) == 4) {
+          const float2 a0 = *(const float2 *)(smc + so), a1 = *(const float2 *)(smc + (so ^ pair));
+          *(float4 *)(dst + g) = make_float4(a0.x, a0.y, a1.x, a1.y);
+        } else {
+          *(double2 *)(dst + g) = *(const double2 *)(smc + so);
+        }
+        const int t = __ffs(j + 1) - 1;
+        g ^= gray_pick(gstep, t);
+        so ^= gray_pick(sstep, t);
       }
     }
   }
