@@ -173,9 +173,30 @@ struct SvTableBuilder {
           if (!used[c]) order.push_back(free_pos[c]);
         if (order.size() > (size_t)SV_MAX_GBITS) fail(QW_ERR_STATE, "internal: tile wider than the stage descriptor");
         for (size_t t = 0; t < order.size(); t++) sd.gcol[t] = slot(hs.mcol[order[t]]);
-        sd.n_ops = (uint32_t)hs.ops.size();
+        // a stage of real rotations (with or without a |1>-phase) on
+        // distinct positions runs as one straight-line sequence: the ops
+        // commute, so they are stored in position order as K_RP records
+        std::vector<HostOp> sops = hs.ops;
+        uint32_t rp_mask = 0;
+        bool rp_stage = !sops.empty();
+        for (const HostOp &o : sops) {
+          if ((o.kind != K_RP && o.kind != K_R) || (rp_mask & (1u << o.a))) { rp_stage = false; break; }
+          rp_mask |= 1u << o.a;
+        }
+        if (rp_stage) {
+          std::sort(sops.begin(), sops.end(), [](const HostOp &x, const HostOp &y) { return x.a < y.a; });
+          for (HostOp &o : sops)
+            if (o.kind == K_R) {  // {r00, 0, r01, 0, r10, 0, r11, 0} -> {r00, r01, r10, r11, 1, 0}
+              const double r[4] = {o.m[0], o.m[2], o.m[4], o.m[6]};
+              o.m[0] = r[0]; o.m[1] = r[1]; o.m[2] = r[2]; o.m[3] = r[3];
+              o.m[4] = 1.0; o.m[5] = 0.0; o.m[6] = 0.0; o.m[7] = 0.0;
+              o.kind = K_RP;
+            }
+        }
+        sd.rp_mask = rp_stage ? rp_mask : 0u;
+        sd.n_ops = (uint32_t)sops.size();
         sd.op_begin = (uint32_t)(fp64 ? ops64.size() : ops32.size());
-        for (const HostOp &o : hs.ops) {
+        for (const HostOp &o : sops) {
           const uint32_t lo = std::min(o.a, o.b), hi = std::max(o.a, o.b);
           const uint32_t code = o.kind == K_CD ? sv_op_index(o.kind, lo, hi) : sv_op_index(o.kind, o.a, 0);
           if (code >= SV_N_OP_INDEX || o.a >= SV_G || (o.kind == K_CD && (hi >= SV_G || lo == hi)))

@@ -163,6 +163,9 @@ struct alignas(16) SvStageDesc {
   uint32_t gcol[SV_MAX_GBITS];   // byte offsets of the group bits (zero past the tile's)
   uint32_t cst;                  // byte offset of the constant of phi
   uint32_t n_ops, op_begin;
+  // nonzero: the stage's ops are K_RP ops on the positions of this mask,
+  // one per position in ascending order (run without dispatch)
+  uint32_t rp_mask;
 };
 template <typename T>
 struct alignas(16) SvOpDesc {

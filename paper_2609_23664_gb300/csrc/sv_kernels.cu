@@ -196,6 +196,18 @@ __device__ __forceinline__ void load_m(const SvOpDesc<double> *op, double (&m)[8
   }
 }
 
+// K_RP at a position known once the caller's loop is unrolled
+template <typename C, typename T>
+__device__ __forceinline__ void rp_at(int P, C (&a)[32], const T (&m)[8]) {
+  switch (P) {
+    case 0: op_rp_any<C, T, 0>(a, m); break;
+    case 1: op_rp_any<C, T, 1>(a, m); break;
+    case 2: op_rp_any<C, T, 2>(a, m); break;
+    case 3: op_rp_any<C, T, 3>(a, m); break;
+    default: op_rp_any<C, T, 4>(a, m); break;
+  }
+}
+
 // dispatch on the dense op index (a jump table)
 template <typename C, typename T>
 __device__ __forceinline__ void apply_op(uint32_t code, const T (&m)[8], C (&a)[32]) {
@@ -309,7 +321,7 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
     const uint32_t roff[SV_G] = {w0.x & tm, w0.y & tm, w0.z & tm, w0.w & tm, w1.x & tm};
     const uint32_t gcol[SV_MAX_GBITS] = {w1.y & tm, w1.z & tm, w1.w & tm, w2.x & tm, w2.y & tm,
                                          w2.z & tm, w2.w & tm, w3.x & tm, w3.y & tm};
-    const uint32_t cst = w3.z & tm, nops = w3.w, op_begin = w4.x;
+    const uint32_t cst = w3.z & tm, nops = w3.w, op_begin = w4.x, rp_mask = w4.y;
     static_assert(SV_MAX_GBITS == 9 && sizeof(SvStageDesc) == 80, "stage descriptor read as five 16-byte words");
     for (uint32_t grp = threadIdx.x; grp < n_groups; grp += nt) {
       uint32_t sbB = cst;
@@ -323,7 +335,18 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
                              ((i & 16) ? roff[4] : 0u);
         a[i] = *(const C *)(smc + off);
       }
-      {
+      if (rp_mask) {
+        // rotation-and-phase ops on distinct positions, in position order
+        const SvOpDesc<T> *op = ops + op_begin;
+#pragma unroll
+        for (int P = 0; P < SV_G; P++) {
+          if (!(rp_mask & (1u << P))) continue;
+          T m[8];
+          load_m(op, m);
+          op++;
+          rp_at<C, T>(P, a, m);
+        }
+      } else {
         // the next op's parameters are loaded while the current op runs
         const SvOpDesc<T> *op = ops + op_begin;
         uint32_t code = 0;
