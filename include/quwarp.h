@@ -464,6 +464,30 @@ qw_status qw_sv_energy_noalloc_dev(uint32_t mode, uint32_t n, const void *state,
 #define QW_DENSE_AUTO 2u  /* qw_dense_prog_create only: the engine of each block is chosen */
 typedef struct qw_dense_prog qw_dense_prog;
 
+/* Host only (no engine, no GPU): the pass program that the statevector
+ * kernels would run for `gates` on n qubits (5 <= n <= QW_SV_MAX_QUBITS),
+ * with tiles of tile_qubits qubits (6..14) of which low_qubits (1 ..
+ * tile_qubits - 2) are the contiguous lowest, as a NUL-terminated JSON
+ * object written to buf (size-query idiom: *needed = bytes including the
+ * NUL; QW_ERR_BUFFER_TOO_SMALL when cap is smaller).  Layout:
+ *   {"n", "passes": [{"q": tile bit t -> qubit, "b", "map": final tile map,
+ *     "stages": [{"pos": 5 tile bits (register bit j -> tile bit pos[j]),
+ *                 "map": tile map at the stage, "ops": [{"kind", "a", "b",
+ *                 "m": 8 doubles}]}]}]}
+ * A tile map {"cols", "c"} places the amplitude of logical tile index l in
+ * slot (XOR of cols[t] over the set bits t of l) ^ c.  A stage reads its 32
+ * register amplitudes (register index i: bit j of i = logical tile bit
+ * pos[j]) through its map, applies its ops in order and writes them back
+ * to the same slots; a tile is read in logical order and written back
+ * through the pass's final map.  Op kinds act on register positions a (and
+ * b), m in the kernels' layout: "U1" 2x2 {u00,u01,u10,u11} (re, im); "D1"
+ * diag(d0, d1) in m[0..3]; "P1" diag(1, p), p in m[0..1]; "CD" multiplies
+ * the amplitudes with bits a and b set by m[0..1]; "R" real 2x2 in m[0],
+ * m[2], m[4], m[6]; "RX" [[c, -is], [-is, c]] with c, s = m[0], m[1]; "RP"
+ * the real 2x2 {m0, m1; m2, m3}, then diag(1, m4 + i m5).  For tests and
+ * inspection; the engine fuses internally. */
+qw_status qw_sv_fuse_json(const qw_gate *gates, uint64_t n_gates, uint32_t n, uint32_t tile_qubits,
+                          uint32_t low_qubits, char *buf, size_t cap, size_t *needed);
 /* Host only (no engine, no GPU): the blocks a program would apply, before
  * widening.  k[i], qubits[5 i + j] (j < k[i]), u[2048 i ..] = the 32 x 32
  * complex matrix (re, im interleaved, row-major over the 2^k x 2^k block,

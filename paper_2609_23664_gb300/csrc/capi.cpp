@@ -594,6 +594,53 @@ qw_status qw_dense_fuse(const qw_gate *gates, uint64_t n_gates, uint32_t n, uint
   })
 }
 
+// JSON of a fused statevector program (host only; see qw_sv_fuse_json)
+static std::string sv_program_json(const SvProgram &pr) {
+  static const char *kinds[16] = {"?", "U1", "D1", "?", "CD", "?", "P1", "R", "RX", "RP", "?", "?", "?", "?", "?", "?"};
+  auto map_json = [](const uint32_t *cols, uint32_t c, size_t k) {
+    std::string m = "{\"cols\":[";
+    for (size_t t = 0; t < k; t++) m += strf("%s%u", t ? "," : "", cols[t]);
+    return m + strf("],\"c\":%u}", c);
+  };
+  std::string js = strf("{\"n\":%u,\"passes\":[", pr.n);
+  for (size_t p = 0; p < pr.passes.size(); p++) {
+    const HostPass &hp = pr.passes[p];
+    js += p ? ",{\"q\":[" : "{\"q\":[";
+    for (size_t t = 0; t < hp.q.size(); t++) js += strf("%s%u", t ? "," : "", hp.q[t]);
+    js += strf("],\"b\":%u,\"map\":%s,\"stages\":[", hp.b, map_json(hp.mcol, hp.mc, hp.q.size()).c_str());
+    for (size_t s = 0; s < hp.stages.size(); s++) {
+      const HostStage &hs = hp.stages[s];
+      js += strf("%s{\"pos\":[%u,%u,%u,%u,%u],\"map\":%s,\"ops\":[", s ? "," : "", hs.pos[0], hs.pos[1],
+                 hs.pos[2], hs.pos[3], hs.pos[4], map_json(hs.mcol, hs.mc, hp.q.size()).c_str());
+      for (size_t o = 0; o < hs.ops.size(); o++) {
+        const HostOp &op = hs.ops[o];
+        js += strf("%s{\"kind\":\"%s\",\"a\":%u,\"b\":%u,\"m\":[", o ? "," : "", kinds[op.kind & 15], op.a, op.b);
+        for (int t = 0; t < 8; t++) js += strf("%s%.17g", t ? "," : "", op.m[t]);
+        js += "]}";
+      }
+      js += "]}";
+    }
+    js += "]}";
+  }
+  return js + "]}";
+}
+
+qw_status qw_sv_fuse_json(const qw_gate *gates, uint64_t n_gates, uint32_t n, uint32_t tile_qubits,
+                          uint32_t low_qubits, char *buf, size_t cap, size_t *needed) {
+  QW_GUARD({
+    if ((n_gates && !gates) || !needed) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    if (n < (uint32_t)SV_G || n > QW_SV_MAX_QUBITS) fail(QW_ERR_INVALID_ARG, "n must be in [%d, %d]", SV_G, QW_SV_MAX_QUBITS);
+    if (tile_qubits < (uint32_t)SV_G + 1 || tile_qubits > (uint32_t)SV_MAX_TILE_FP32)
+      fail(QW_ERR_INVALID_ARG, "tile_qubits must be in [%d, %d]", SV_G + 1, SV_MAX_TILE_FP32);
+    if (low_qubits < 1 || low_qubits > tile_qubits - 2) fail(QW_ERR_INVALID_ARG, "low_qubits must be in [1, tile_qubits - 2]");
+    for (uint64_t i = 0; i < n_gates; i++) validate_gate(gates[i], QW_MODE_SV_FP64, n, i);
+    TileConfig tc;
+    tc.k_max = tile_qubits;
+    tc.b = low_qubits;
+    return put_json(sv_program_json(fuse_sv(gates, n_gates, n, tc)), buf, cap, needed);
+  })
+}
+
 qw_status qw_dense_prog_create(qw_engine *e, uint32_t mode, uint32_t n, const qw_gate *gates, uint64_t n_gates,
                                uint32_t kmax, uint32_t engine, uint32_t nacc, qw_dense_prog **out) {
   QW_GUARD({

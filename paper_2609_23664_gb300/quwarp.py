@@ -121,6 +121,7 @@ SIGNATURES = {
     "qw_sv_sample_dev": (_st, [_vp, _u32, _u32, _vp, _vp, _u32, _vp, _vp]),
     "qw_sv_energy_noalloc_dev": (_st, [_u32, _u32, _vp, _vp, _u64, _vp, _vp]),
     "qw_dense_fuse": (_st, [_vp, _u64, _u32, _u32, _vp, _vp, _vp, _u64, _vp]),
+    "qw_sv_fuse_json": (_st, [_vp, _u64, _u32, _u32, _u32, _vp, _sz, _vp]),
     "qw_dense_prog_create": (_st, [_vp, _u32, _u32, _vp, _u64, _u32, _u32, _u32, _vp]),
     "qw_dense_prog_create_block": (_st, [_vp, _u32, _u32, _vp, _u32, _vp, _u32, _u32, _vp]),
     "qw_dense_prog_info": (_st, [_vp, _vp, _vp]),
@@ -438,6 +439,21 @@ def sv_energy_noalloc_dev(mode: int, n: int, state_ptr: int, terms: np.ndarray, 
     t = np.ascontiguousarray(terms, dtype=W.TERM_DTYPE)
     _check(lib().qw_sv_energy_noalloc_dev(mode, n, state_ptr, _p(t) if len(t) else None, len(t),
                                           out_ptr, stream or None))
+
+
+def sv_fuse(gates: np.ndarray, n: int, tile_qubits: int = 13, low_qubits: int = 3) -> dict:
+    """Host only: the pass program of the statevector kernels for `gates`
+    (see qw_sv_fuse_json for the layout)."""
+    g = np.ascontiguousarray(gates, dtype=W.GATE_DTYPE)
+    need = C.c_size_t()
+    st = lib().qw_sv_fuse_json(_p(g) if len(g) else None, len(g), n, tile_qubits, low_qubits, None, 0,
+                               C.byref(need))
+    if st not in (0, -7):
+        _check(st)
+    buf = C.create_string_buffer(need.value)
+    _check(lib().qw_sv_fuse_json(_p(g) if len(g) else None, len(g), n, tile_qubits, low_qubits, buf,
+                                 need.value, C.byref(need)))
+    return json.loads(buf.value.decode())
 
 
 def dense_fuse(gates: np.ndarray, n: int, kmax: int = 5):
