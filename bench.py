@@ -79,7 +79,7 @@ def workload_desc(a):
 
 
 def make_tasks(a, rank):
-    return W.config2_vqe24(seed=R.rank_seed(W.BASE_SEED + 2, rank), n=a.qubits,
+    return W.vqe24_sweep(seed=R.rank_seed(W.BASE_SEED + 2, rank), n=a.qubits,
                            prefix_layers=a.prefix_layers, n_tasks=a.tasks, n_terms=a.terms)
 
 
@@ -419,13 +419,13 @@ def run_native(a):
 
         for key, desc, gen, plans in (
                 ("qec_d15", "rotated surface code, 449 qubits, 100 shared + 5 task rounds, 4096 tasks, "
-                            "data X/Z errors p=1e-3 (stabilizer)", W.config4_qec,
+                            "data X/Z errors p=1e-3 (stabilizer)", W.qec_surface_code_tasks,
                  (("pauli_frames", dict(pauli_frames=1)), ("per_task_tableau", dict(pauli_frames=0)))),
                 ("noisy22", "22 qubits, 400-gate random circuit, 1024 Pauli-noise trajectories "
-                            "(p=1e-3), 100 shots each (FP32)", W.config3_noisy22,
+                            "(p=1e-3), 100 shots each (FP32)", W.noisy22_trajectories,
                  (("reuse", {}), ("per_task_replay", dict(reuse=0, batched=0)))),
                 ("vqe12_fp64", "12 qubits, 6-layer HEA prefix, 16 tasks x final RY+RZ layer, 20-term "
-                               "energy (FP64)", W.config1_vqe12,
+                               "energy (FP64)", W.vqe12_sweep,
                  (("reuse", {}), ("per_task_replay", dict(reuse=0, batched=0)))),
                 ("deep_local24", "24 qubits, H layer + 60 layers of RY/CNOT/RZ confined to qubits 8-12 "
                                  "(shared prefix), 64 tasks x RY layer, 32-term energy (FP32)",

@@ -635,6 +635,39 @@ static void prepare(qw_plan *P) {
   }
   size_t max_partials = 1, max_smp_blocks = 1, max_src = 1;
   const bool batched = P->opts.batched != 0;
+  // Task buffers of every group coexist for the plan's lifetime, so the
+  // groups share one task budget: each group with pooled tasks gets one
+  // buffer, then the rest of the budget goes to the groups in order of
+  // state size (smallest first) for up to one buffer per pooled task.
+  std::map<std::pair<int, uint32_t>, size_t> pool_size;
+  {
+    std::vector<std::pair<size_t, std::pair<int, uint32_t>>> order;  // (S, group)
+    std::map<std::pair<int, uint32_t>, size_t> n_pooled;
+    uint64_t committed = 0;
+    for (auto &g : groups) {
+      size_t np = 0;
+      for (uint32_t t : g.second) {
+        const TaskPlan &tp = P->tasks[t];
+        if ((!tp.sv.passes.empty() || needs_convert(tp)) && !(tp.flags & QW_TASK_KEEP_STATE)) np++;
+      }
+      const size_t S = sv_state_bytes(g.first.first != 0, g.first.second);
+      n_pooled[g.first] = np;
+      pool_size[g.first] = np ? 1 : 0;
+      if (np) {
+        committed += S;
+        order.push_back({S, g.first});
+      }
+    }
+    std::sort(order.begin(), order.end());
+    uint64_t left = E->task_budget > committed ? E->task_budget - committed : 0;
+    for (auto &o : order) {
+      if (!batched) break;
+      const size_t S = o.first;
+      const size_t extra = std::min<size_t>(n_pooled[o.second] - 1, (size_t)(left / S));
+      pool_size[o.second] += extra;
+      left -= (uint64_t)extra * S;
+    }
+  }
   for (auto &g : groups) {
     const bool fp64 = g.first.first != 0;
     const uint32_t n_eff = g.first.second;
@@ -647,13 +680,12 @@ static void prepare(qw_plan *P) {
       else { shared_src.push_back(t); D->task_state[t] = sv_source(tp.src, tp.mode); }
     }
     // KEEP_STATE tasks get dedicated buffers; the others share a pool
-    size_t per_wave = batched ? std::max<size_t>(1, E->task_budget / std::max<size_t>(S, 1)) : 1;
     std::vector<uint32_t> pooled;
     for (uint32_t t : own) {
       if (P->tasks[t].flags & QW_TASK_KEEP_STATE) D->task_state[t] = D->arena.alloc(S);
       else pooled.push_back(t);
     }
-    const size_t pool_n = std::min(per_wave, pooled.size());
+    const size_t pool_n = std::min(pool_size[g.first], pooled.size());
     std::vector<void *> pool(pool_n);
     for (auto &p : pool) p = D->arena.alloc(S);
     // waves: dedicated tasks first (one wave), then pooled chunks

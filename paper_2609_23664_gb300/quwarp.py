@@ -278,7 +278,10 @@ class Workload:
 def plan_options(**kw) -> qw_plan_opts:
     o = qw_plan_opts()
     lib().qw_plan_opts_default(C.byref(o))
+    fields = {f[0] for f in qw_plan_opts._fields_}
     for k, v in kw.items():
+        if k not in fields:
+            raise TypeError("unknown plan option %r" % k)
         setattr(o, k, v)
     return o
 

@@ -346,7 +346,7 @@ def data_errors(code: SurfaceCode, rng: np.random.Generator, p: float) -> np.nda
 
 # ---- configurations -------------------------------------------------------------
 
-def config1_vqe12(seed: int = BASE_SEED + 1, n: int = 12, layers: int = 6,
+def vqe12_sweep(seed: int = BASE_SEED + 1, n: int = 12, layers: int = 6,
                   n_tasks: int = 16, n_terms: int = 20,
                   mode: int = MODE_SV_FP64) -> List[Task]:
     """VQE sweep: shared HEA prefix of `layers` layers; each task appends one
@@ -363,7 +363,7 @@ def config1_vqe12(seed: int = BASE_SEED + 1, n: int = 12, layers: int = 6,
     return tasks
 
 
-def config2_vqe24(seed: int = BASE_SEED + 2, n: int = 24, prefix_layers: int = 20,
+def vqe24_sweep(seed: int = BASE_SEED + 2, n: int = 24, prefix_layers: int = 20,
                   n_tasks: int = 256, max_suffix_layers: int = 4,
                   n_terms: int = 200, mode: int = MODE_SV_FP32) -> List[Task]:
     """Batched VQE sweep: shared HEA prefix; each task adds L ~ U{1..4} full
@@ -400,7 +400,7 @@ def deep_local_sweep(seed: int = BASE_SEED + 7, n: int = 24, layers: int = 60, l
     return tasks
 
 
-def config3_noisy22(seed: int = BASE_SEED + 3, n: int = 22, n_gates: int = 400,
+def noisy22_trajectories(seed: int = BASE_SEED + 3, n: int = 22, n_gates: int = 400,
                     n_traj: int = 1024, p: float = 1e-3, shots: int = 100,
                     mode: int = MODE_SV_FP32) -> List[Task]:
     """Noisy multishot: one random circuit; each trajectory inserts Pauli
@@ -415,7 +415,7 @@ def config3_noisy22(seed: int = BASE_SEED + 3, n: int = 22, n_gates: int = 400,
     return tasks
 
 
-def config4_qec(seed: int = BASE_SEED + 4, d: int = 15, shared_rounds: int = 100,
+def qec_surface_code_tasks(seed: int = BASE_SEED + 4, d: int = 15, shared_rounds: int = 100,
                 task_rounds: int = 5, n_tasks: int = 4096,
                 p: float = 1e-3) -> List[Task]:
     """Stabilizer-mode QEC: `shared_rounds` noiseless syndrome rounds form the
@@ -437,7 +437,7 @@ def config4_qec(seed: int = BASE_SEED + 4, d: int = 15, shared_rounds: int = 100
     return tasks
 
 
-def config5_mixed(seed: int = BASE_SEED + 5, n_tasks: int = 2000,
+def mixed_planned(seed: int = BASE_SEED + 5, n_tasks: int = 2000,
                   shared_frac: float = 0.6, n_min: int = 16, n_max: int = 30,
                   group_min: int = 2, group_max: int = 64,
                   prefix_len=(50, 500), suffix_len=(10, 100),

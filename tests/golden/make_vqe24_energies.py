@@ -31,7 +31,7 @@ SEED = W.BASE_SEED + 2
 
 def main():
     orc.build()
-    tasks = W.config2_vqe24(seed=SEED, n=N, prefix_layers=LAYERS, n_tasks=TASKS, n_terms=TERMS)
+    tasks = W.vqe24_sweep(seed=SEED, n=N, prefix_layers=LAYERS, n_tasks=TASKS, n_terms=TERMS)
     prefix = tasks[0].spans[0]
     assert all(t.spans[0] is prefix for t in tasks)
     t0 = time.time()
@@ -46,7 +46,7 @@ def main():
     for i in (0, TASKS - 1):
         ref = orc.run_task(tasks[i])
         assert ref["energy"] == out[i]["energy"], (i, ref["energy"], out[i]["energy"])
-    doc = {"workload": "config2_vqe24(seed=BASE_SEED+2=%d, n=%d, prefix_layers=%d, n_tasks=%d, n_terms=%d)"
+    doc = {"workload": "vqe24_sweep(seed=BASE_SEED+2=%d, n=%d, prefix_layers=%d, n_tasks=%d, n_terms=%d)"
                        % (SEED, N, LAYERS, TASKS, TERMS),
            "written_by": "tests/golden/make_vqe24_energies.py (oracle only, complex128)",
            "tasks": out}

@@ -21,8 +21,8 @@ def trained():
     eng = Q.Engine(0)
     # timing corpus: the mixed family (shared prefixes and prefix-free
     # circuits) at 12..20 qubits, a training and a held-out seed
-    tr = W.config5_mixed(seed=11, n_tasks=900, n_min=12, n_max=20)
-    te = W.config5_mixed(seed=12, n_tasks=200, n_min=12, n_max=20)
+    tr = W.mixed_planned(seed=11, n_tasks=900, n_min=12, n_max=20)
+    te = W.mixed_planned(seed=12, n_tasks=200, n_min=12, n_max=20)
     f_tr, y_tr, a_tr = eng.costmodel_probe(Q.Workload(tr), 3 * len(tr))
     f_te, y_te, a_te = eng.costmodel_probe(Q.Workload(te), 3 * len(te))
     loss = eng.costmodel_train(f_tr, y_tr, epochs=60, batch=256, lr=2e-3, seed=7)
@@ -59,7 +59,7 @@ def test_parameters_roundtrip_and_forward_kernel_agree(trained):
 
 def test_planning_with_the_learned_model_stays_exact(trained):
     eng = trained[0]
-    tasks = W.config5_mixed(seed=13, n_tasks=60, n_min=12, n_max=18)
+    tasks = W.mixed_planned(seed=13, n_tasks=60, n_min=12, n_max=18)
     wl = Q.Workload(tasks)
     plan = Q.Plan(eng, wl, cost_model=Q.COST_MLP)
     ex = plan.explain()

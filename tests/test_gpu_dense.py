@@ -253,7 +253,7 @@ def test_plan_evolves_a_deep_local_boundary_with_dense_blocks(eng):
 
 @pytest.mark.parametrize("mode", [1, 2])
 def test_dense_boundaries_keep_parity_on_the_vqe_sweep(eng, mode):
-    tasks = W.config2_vqe24(n=16, n_tasks=4, n_terms=20)
+    tasks = W.vqe24_sweep(n=16, n_tasks=4, n_terms=20)
     plan = Q.Plan(eng, Q.Workload(tasks), dense_boundaries=mode)
     plan.run()
     ch = plan.cost_record()["dense_boundaries"]

@@ -150,7 +150,7 @@ def test_largest_tableau_ghz_and_noiseless_surface_code(eng):
         assert len(out) == n and np.all(out == out[0])
     # d = 17 surface code (577 qubits), noiseless: Z syndromes are 0 from the
     # first round, X syndromes repeat from the second (no detection events)
-    tasks = W.config4_qec(d=17, shared_rounds=2, task_rounds=2, n_tasks=3, p=0.0)
+    tasks = W.qec_surface_code_tasks(d=17, shared_rounds=2, task_rounds=2, n_tasks=3, p=0.0)
     p, wl = run(eng, tasks)
     code = W.rotated_surface_code(17)
     anc = sorted(code.sched.keys())
@@ -169,3 +169,32 @@ def test_l2_read_probe_exceeds_hbm_bandwidth(eng):
     l2 = eng.probe_l2()
     hbm = eng.info()["hbm_gbs"]
     assert np.isfinite(l2) and l2 > hbm, (l2, hbm)
+
+
+def test_task_budget_is_shared_by_register_sizes():
+    # prefix-free tasks of five register sizes under a 256 MB task budget:
+    # the groups' task pools share the budget (at least one buffer each),
+    # so the plan's device memory stays near 256 MB instead of the ~1 GB
+    # that one budget per group would take
+    budget = 256 << 20
+    e = Q.Engine(0, task_budget_bytes=budget)
+    rng = np.random.default_rng(77)
+    tasks = []
+    for n in (20, 21, 22, 23, 24):
+        for _ in range(8):
+            tasks.append(W.Task(mode=W.MODE_SV_FP32, n=n, spans=[W.random_circuit(rng, n, 30)],
+                                terms=W.random_pauli_hamiltonian(rng, n, 6)))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    wl = Q.Workload(tasks)
+    p = Q.Plan(e, wl, reuse=0)
+    p.run()
+    torch.cuda.synchronize()
+    used = free0 - torch.cuda.mem_get_info()[0]
+    assert used < budget + (160 << 20), used
+    for i in (0, 8):  # one task of each of the two smallest sizes
+        ref = orc.run_task(tasks[i])
+        assert abs(p.energy(i)[0] - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(tasks[i].terms["coef"])))
+    p.close()
+    wl.close()
+    e.close()

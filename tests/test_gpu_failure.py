@@ -20,7 +20,7 @@ from paper_2609_23664_gb300 import quwarp as Q  # noqa: E402
 
 def test_bounded_wait_reports_timeout_and_device_stays_usable():
     eng = Q.Engine(0)
-    tasks = W.config2_vqe24(n=16, n_tasks=6, n_terms=10)
+    tasks = W.vqe24_sweep(n=16, n_tasks=6, n_terms=10)
     bad = Q.Plan(eng, Q.Workload(tasks), fault_injection=1)
     bad.execute()
     with pytest.raises(Q.QuwarpError) as ei:
@@ -37,7 +37,7 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable():
 
 def test_destroying_the_engine_releases_its_plans():
     eng = Q.Engine(0)
-    tasks = W.config1_vqe12(n_tasks=3)
+    tasks = W.vqe12_sweep(n_tasks=3)
     plan = Q.Plan(eng, Q.Workload(tasks))
     plan.run()
     e_before, _ = plan.energy(1)

@@ -40,10 +40,10 @@ def eng():
 
 
 @pytest.mark.parametrize("prefix_fp64", [0, 1])
-def test_config2_vqe24_full_size_sampled(eng, prefix_fp64):
+def test_vqe24_full_size_sampled(eng, prefix_fp64):
     # the bench's configuration (FP32 throughout), and the same workload
     # with the shared prefix in FP64, rounded once for the FP32 suffixes
-    tasks = W.config2_vqe24()                     # 24 qubits, 256 tasks, 200 terms
+    tasks = W.vqe24_sweep()                     # 24 qubits, 256 tasks, 200 terms
     keep = 5
     tasks[keep].want_state = True
     plan = Q.Plan(eng, Q.Workload(tasks), prefix_fp64=prefix_fp64)
@@ -70,12 +70,12 @@ GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "vqe24
 
 
 @pytest.mark.parametrize("prefix_fp64", [0, 1])
-def test_config2_vqe24_every_task_against_stored_oracle(eng, prefix_fp64):
+def test_vqe24_every_task_against_stored_oracle(eng, prefix_fp64):
     # every one of the 256 tasks of the bench's workload against the oracle's
     # complex128 energies (written by tests/golden/make_vqe24_energies.py)
     doc = json.load(open(GOLD))
     ref = np.array([t["energy"] for t in doc["tasks"]])
-    tasks = W.config2_vqe24()
+    tasks = W.vqe24_sweep()
     assert [int(len(t.spans[1])) for t in tasks] == [t["suffix_gates"] for t in doc["tasks"]]
     plan = Q.Plan(eng, Q.Workload(tasks), prefix_fp64=prefix_fp64)
     plan.run()
@@ -103,8 +103,8 @@ def _oracle(tasks, i, want_state):
     return _ORACLE[key]
 
 
-def test_config3_noisy22_full_size_sampled(eng):
-    tasks = W.config3_noisy22()                   # 22 qubits, 1024 trajectories
+def test_noisy22_full_size_sampled(eng):
+    tasks = W.noisy22_trajectories()                   # 22 qubits, 1024 trajectories
     plan = Q.Plan(eng, Q.Workload(tasks))
     plan.run()
     ex = plan.explain()
@@ -125,8 +125,8 @@ def test_config3_noisy22_full_size_sampled(eng):
         assert np.all((got == ref["samples"]) | near), i
 
 
-def test_config4_qec_d15_full_size_sampled(eng):
-    tasks = W.config4_qec()                       # 449 qubits, 100 + 5 rounds, 4096 tasks
+def test_qec_d15_full_size_sampled(eng):
+    tasks = W.qec_surface_code_tasks()                       # 449 qubits, 100 + 5 rounds, 4096 tasks
     plan = Q.Plan(eng, Q.Workload(tasks))
     plan.run()
     for i in (0, 1, 4095):

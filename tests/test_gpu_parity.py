@@ -158,8 +158,8 @@ def run_plan(eng, tasks, **opts):
     return p, wl
 
 
-def test_config1_vqe12_fp64_full(eng):
-    tasks = W.config1_vqe12()
+def test_vqe12_fp64_full(eng):
+    tasks = W.vqe12_sweep()
     for t in tasks[:3]:
         t.want_state = True
     p, wl = run_plan(eng, tasks)
@@ -176,8 +176,8 @@ def test_config1_vqe12_fp64_full(eng):
 
 
 @pytest.mark.parametrize("reuse,batched,graph", [(1, 1, 1), (0, 0, 1), (0, 1, 1), (1, 0, 1), (1, 1, 0)])
-def test_config2_vqe_fp32_small(eng, reuse, batched, graph):
-    tasks = W.config2_vqe24(n=16, n_tasks=24, n_terms=40)
+def test_vqe_fp32_small(eng, reuse, batched, graph):
+    tasks = W.vqe24_sweep(n=16, n_tasks=24, n_terms=40)
     for t in tasks[:2]:
         t.want_state = True
     p, wl = run_plan(eng, tasks, reuse=reuse, batched=batched, use_graph=graph)
@@ -198,7 +198,7 @@ def test_config2_vqe_fp32_small(eng, reuse, batched, graph):
 def test_energy_fused_into_the_suffix_launch(eng, mode, n):
     # energy blocks as work items of the persistent launch: same results as
     # the separate energy launch and as the oracle
-    tasks = W.config2_vqe24(n=n, n_tasks=12, n_terms=60, mode=mode)
+    tasks = W.vqe24_sweep(n=n, n_tasks=12, n_terms=60, mode=mode)
     p, wl = run_plan(eng, tasks, fuse_energy=1, tile_qubits=13)
     assert p.cost_record()["energy_fused"] is True
     q, wl2 = run_plan(eng, tasks, tile_qubits=13)
@@ -216,8 +216,8 @@ def test_energy_fused_into_the_suffix_launch(eng, mode, n):
         assert abs(nr - nr2) <= (1e-13 if fp64 else 1e-6)
 
 
-def test_config3_noisy_small(eng):
-    tasks = W.config3_noisy22(n=14, n_gates=200, n_traj=96, p=0.01, shots=50)
+def test_noisy_small(eng):
+    tasks = W.noisy22_trajectories(n=14, n_gates=200, n_traj=96, p=0.01, shots=50)
     p, wl = run_plan(eng, tasks)
     ex = p.explain()
     assert ex["tasks_reusing"] > 0
@@ -230,8 +230,8 @@ def test_config3_noisy_small(eng):
     assert bad == 0
 
 
-def test_config4_qec_small_bit_exact(eng):
-    tasks = W.config4_qec(d=5, shared_rounds=8, task_rounds=3, n_tasks=48, p=0.02)
+def test_qec_small_bit_exact(eng):
+    tasks = W.qec_surface_code_tasks(d=5, shared_rounds=8, task_rounds=3, n_tasks=48, p=0.02)
     p, wl = run_plan(eng, tasks)
     for i, t in enumerate(tasks):
         ref = orc.tab_run(t.n, t.gates)
@@ -240,11 +240,11 @@ def test_config4_qec_small_bit_exact(eng):
 
 
 @pytest.mark.parametrize("frames,graph", [(1, 1), (0, 1), (1, 0)])
-def test_config4_qec_frames_and_tableau_agree_bit_exact(eng, frames, graph):
+def test_qec_frames_and_tableau_agree_bit_exact(eng, frames, graph):
     # Pauli frames over the shared 3-round reference vs every task on its
     # own tableau, with and without graph capture: identical syndromes,
     # equal to the oracle's
-    tasks = W.config4_qec(d=5, shared_rounds=6, task_rounds=3, n_tasks=80, p=0.02)
+    tasks = W.qec_surface_code_tasks(d=5, shared_rounds=6, task_rounds=3, n_tasks=80, p=0.02)
     p, wl = run_plan(eng, tasks, pauli_frames=frames, use_graph=graph)
     ex = p.explain()
     assert len(ex["pauli_frames"]) == frames
@@ -340,8 +340,8 @@ def test_tableau_boundary_serves_stabilizer_and_statevector_tasks(eng):
             assert abs(p.energy(i)[0] - ref["energy"]) <= 1e-12 * max(1.0, abs(ref["energy"])), i
 
 
-def test_config4_qec_replay_bit_exact(eng):
-    tasks = W.config4_qec(d=3, shared_rounds=4, task_rounds=2, n_tasks=16, p=0.05)
+def test_qec_replay_bit_exact(eng):
+    tasks = W.qec_surface_code_tasks(d=3, shared_rounds=4, task_rounds=2, n_tasks=16, p=0.05)
     p, wl = run_plan(eng, tasks, reuse=0)
     for i, t in enumerate(tasks):
         assert np.array_equal(p.syndrome(i), orc.tab_run(t.n, t.gates)), i

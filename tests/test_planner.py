@@ -146,7 +146,7 @@ def test_trie_branch_points_match_brute_force(seed):
 
 
 def test_explain_schema_and_artifact_record():
-    tasks = W.config1_vqe12(n_tasks=4)
+    tasks = W.vqe12_sweep(n_tasks=4)
     p, ex, wl = host_plan(tasks)
     assert ex["type"] == "QuWARP:ExplainTrace"
     for key in ("tasks", "decisions", "fast_path", "estimated_speedup", "planning_ns", "options"):
@@ -166,7 +166,7 @@ def test_explain_schema_and_artifact_record():
 
 
 def test_negative_control_takes_the_fast_path():
-    tasks = [t for t in W.config5_mixed(n_tasks=40, shared_frac=0.0, n_min=16, n_max=20)]
+    tasks = [t for t in W.mixed_planned(n_tasks=40, shared_frac=0.0, n_min=16, n_max=20)]
     t0 = time.perf_counter()
     p, ex, wl = host_plan(tasks)
     assert ex["fast_path"] is True
@@ -187,7 +187,7 @@ def test_threshold0_admits_what_the_guard_rejects():
 
 
 def test_early_filters():
-    tasks = W.config1_vqe12(n_tasks=2)
+    tasks = W.vqe12_sweep(n_tasks=2)
     _, ex, _ = host_plan(tasks, min_group=3)
     assert ex["decisions"][0]["decision"] == "ABSTAIN"
     assert ex["decisions"][0]["reason"] == "EARLY_FILTER_GROUP_SIZE"
@@ -230,12 +230,12 @@ def test_mixed_precision_group_refuses_minority():
 
 
 def test_reuse_off_plans_per_task_replay():
-    _, ex, _ = host_plan(W.config1_vqe12(n_tasks=4), reuse=0)
+    _, ex, _ = host_plan(W.vqe12_sweep(n_tasks=4), reuse=0)
     assert ex["artifacts"] == 0 and ex["decisions"] == []
 
 
 def test_tableau_workload_shares_the_prefix_span():
-    tasks = W.config4_qec(d=3, shared_rounds=4, task_rounds=2, n_tasks=20, p=0.05)
+    tasks = W.qec_surface_code_tasks(d=3, shared_rounds=4, task_rounds=2, n_tasks=20, p=0.05)
     _, ex, _ = host_plan(tasks)
     top = min(ex["decisions"], key=lambda d: d["branch_gate"])
     assert top["decision"] == "REUSE"
@@ -274,7 +274,7 @@ def test_noisy_trajectories_reuse_nested_boundaries():
     # multi-level reuse: trajectories share the error-free chain, then
     # sub-groups share mid-segments up to later branch points; every nested
     # boundary continues from its parent's (first_gate = parent's end)
-    tasks = W.config3_noisy22(n=10, n_gates=120, n_traj=64, p=0.02, shots=4)
+    tasks = W.noisy22_trajectories(n=10, n_gates=120, n_traj=64, p=0.02, shots=4)
     p, ex, wl = host_plan(tasks)
     arts = {d["artifact"]["id"]: d["artifact"] for d in ex["decisions"] if d["artifact"]}
     nested = [a for a in arts.values() if a["parent"] >= 0]
@@ -285,7 +285,7 @@ def test_noisy_trajectories_reuse_nested_boundaries():
 
 
 def test_full_size_qec_planning_is_fast():
-    tasks = W.config4_qec()                  # 449 qubits, 100 + 5 rounds, 4096 tasks
+    tasks = W.qec_surface_code_tasks()                  # 449 qubits, 100 + 5 rounds, 4096 tasks
     t0 = time.perf_counter()
     p, ex, wl = host_plan(tasks, pauli_frames=0)
     dt = time.perf_counter() - t0
@@ -295,7 +295,7 @@ def test_full_size_qec_planning_is_fast():
 def test_qec_tasks_become_one_pauli_frame_group():
     # the tasks differ only by data errors (Pauli gates): one boundary after
     # the shared rounds, every task a frame over the 5-round reference
-    tasks = W.config4_qec(d=5, shared_rounds=6, n_tasks=96, p=0.02)
+    tasks = W.qec_surface_code_tasks(d=5, shared_rounds=6, n_tasks=96, p=0.02)
     p, ex, wl = host_plan(tasks)
     assert ex["artifacts"] == 1 and ex["options"]["pauli_frames"] == 1
     (fr,) = ex["pauli_frames"]
@@ -322,7 +322,7 @@ def test_qec_tasks_become_one_pauli_frame_group():
 
 def test_structural_differences_prevent_frames():
     # a non-Pauli gate that differs between tasks after the boundary
-    tasks = W.config4_qec(d=3, shared_rounds=4, n_tasks=6, p=0.0)
+    tasks = W.qec_surface_code_tasks(d=3, shared_rounds=4, n_tasks=6, p=0.0)
     extra = W.gates_from_list([(W.OP_H, 0, 0)])
     tasks[3].spans = tasks[3].spans + [extra]
     p, ex, wl = host_plan(tasks)
@@ -354,7 +354,7 @@ def test_invalid_task_fields_are_rejected():
 
 
 def test_execute_without_engine_is_a_state_error():
-    p, ex, wl = host_plan(W.config1_vqe12(n_tasks=2))
+    p, ex, wl = host_plan(W.vqe12_sweep(n_tasks=2))
     with pytest.raises(Q.QuwarpError) as ei:
         p.execute()
     assert ei.value.status == -6

@@ -22,7 +22,7 @@ def _rank(rank, world, port, out):
     from paper_2609_23664_gb300 import workloads as W
     from paper_2609_23664_gb300 import quwarp as Q
     R.init(world, "gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank)
-    tasks = W.config2_vqe24(seed=R.rank_seed(W.BASE_SEED + 2, rank), n=12, prefix_layers=4, n_tasks=6,
+    tasks = W.vqe24_sweep(seed=R.rank_seed(W.BASE_SEED + 2, rank), n=12, prefix_layers=4, n_tasks=6,
                             n_terms=8)
     ex = Q.Plan(None, Q.Workload(tasks)).explain()       # host-only plan per rank
     R.barrier(world)
