@@ -470,12 +470,14 @@ typedef struct qw_dense_prog qw_dense_prog;
  * tile_qubits - 2) are the contiguous lowest, as a NUL-terminated JSON
  * object written to buf (size-query idiom: *needed = bytes including the
  * NUL; QW_ERR_BUFFER_TOO_SMALL when cap is smaller).  Layout:
- *   {"n", "passes": [{"q": tile bit t -> qubit, "b", "map": final tile map,
- *     "stages": [{"pos": 5 tile bits (register bit j -> tile bit pos[j]),
- *                 "map": tile map at the stage, "ops": [{"kind", "a", "b",
- *                 "m": 8 doubles}]}]}]}
- * A tile map {"cols", "c"} places the amplitude of logical tile index l in
- * slot (XOR of cols[t] over the set bits t of l) ^ c.  A stage reads its 32
+ *   {"n", "passes": [{"q": tile bit t -> qubit, "ctl_q": outside control
+ *     qubits, "b", "map": final tile map, "stages": [{"pos": 5 tile bits
+ *     (register bit j -> tile bit pos[j]), "map": tile map at the stage,
+ *     "ops": [{"kind", "a", "b", "m": 8 doubles}]}]}]}
+ * A tile map {"cols", "c", "ctl_w"} places the amplitude of logical tile
+ * index l in slot (XOR of cols[t] over the set bits t of l) ^ c ^ (XOR of
+ * ctl_w[i] over the outside control qubits ctl_q[i] that are 1 in the
+ * tile: CNOTs whose control is not a tile qubit).  A stage reads its 32
  * register amplitudes (register index i: bit j of i = logical tile bit
  * pos[j]) through its map, applies its ops in order and writes them back
  * to the same slots; a tile is read in logical order and written back

@@ -597,21 +597,26 @@ qw_status qw_dense_fuse(const qw_gate *gates, uint64_t n_gates, uint32_t n, uint
 // JSON of a fused statevector program (host only; see qw_sv_fuse_json)
 static std::string sv_program_json(const SvProgram &pr) {
   static const char *kinds[16] = {"?", "U1", "D1", "?", "CD", "?", "P1", "R", "RX", "RP", "?", "?", "?", "?", "?", "?"};
-  auto map_json = [](const uint32_t *cols, uint32_t c, size_t k) {
+  auto map_json = [](const uint32_t *cols, uint32_t c, size_t k, const uint32_t *ctl_w) {
     std::string m = "{\"cols\":[";
     for (size_t t = 0; t < k; t++) m += strf("%s%u", t ? "," : "", cols[t]);
-    return m + strf("],\"c\":%u}", c);
+    m += strf("],\"c\":%u,\"ctl_w\":[", c);
+    for (int t = 0; t < SV_MAX_OUT_CTL; t++) m += strf("%s%u", t ? "," : "", ctl_w[t]);
+    return m + "]}";
   };
   std::string js = strf("{\"n\":%u,\"passes\":[", pr.n);
   for (size_t p = 0; p < pr.passes.size(); p++) {
     const HostPass &hp = pr.passes[p];
     js += p ? ",{\"q\":[" : "{\"q\":[";
     for (size_t t = 0; t < hp.q.size(); t++) js += strf("%s%u", t ? "," : "", hp.q[t]);
-    js += strf("],\"b\":%u,\"map\":%s,\"stages\":[", hp.b, map_json(hp.mcol, hp.mc, hp.q.size()).c_str());
+    js += "],\"ctl_q\":[";
+    for (size_t t = 0; t < hp.ctl_q.size(); t++) js += strf("%s%u", t ? "," : "", hp.ctl_q[t]);
+    js += strf("],\"b\":%u,\"map\":%s,\"stages\":[", hp.b,
+               map_json(hp.mcol, hp.mc, hp.q.size(), hp.ctl_w).c_str());
     for (size_t s = 0; s < hp.stages.size(); s++) {
       const HostStage &hs = hp.stages[s];
       js += strf("%s{\"pos\":[%u,%u,%u,%u,%u],\"map\":%s,\"ops\":[", s ? "," : "", hs.pos[0], hs.pos[1],
-                 hs.pos[2], hs.pos[3], hs.pos[4], map_json(hs.mcol, hs.mc, hp.q.size()).c_str());
+                 hs.pos[2], hs.pos[3], hs.pos[4], map_json(hs.mcol, hs.mc, hp.q.size(), hs.ctl_w).c_str());
       for (size_t o = 0; o < hs.ops.size(); o++) {
         const HostOp &op = hs.ops[o];
         js += strf("%s{\"kind\":\"%s\",\"a\":%u,\"b\":%u,\"m\":[", o ? "," : "", kinds[op.kind & 15], op.a, op.b);

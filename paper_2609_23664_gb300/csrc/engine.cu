@@ -123,9 +123,32 @@ struct SvTableBuilder {
       };
       check_phi(hp.mcol, hp.mc);
       for (const HostStage &hs : hp.stages) check_phi(hs.mcol, hs.mc);
+      // outside control qubits -> tile-index bits; their per-tile terms
+      // must stay inside the tile like every column of the map
+      if (hp.ctl_q.size() > (size_t)SV_MAX_OUT_CTL) fail(QW_ERR_STATE, "internal: too many outside controls");
+      uint32_t ctl_tb[SV_MAX_OUT_CTL] = {0, 0, 0, 0};
+      for (size_t c = 0; c < hp.ctl_q.size(); c++) {
+        uint32_t tb = 0xFFFFFFFFu;
+        for (uint32_t i = 0; i < d.n_hi; i++)
+          if (d.hi_pos[i] == hp.ctl_q[c]) tb = i;
+        if (tb == 0xFFFFFFFFu) fail(QW_ERR_STATE, "internal: outside control %u is a tile qubit", hp.ctl_q[c]);
+        ctl_tb[c] = tb;
+      }
+      auto check_ctl = [&](const uint32_t *w) {
+        for (int c = 0; c < SV_MAX_OUT_CTL; c++)
+          if ((w[c] >> d.k) != 0 || (w[c] != 0 && (size_t)c >= hp.ctl_q.size()))
+            fail(QW_ERR_STATE, "internal: per-tile map term outside the tile");
+      };
+      check_ctl(hp.ctl_w);
+      for (const HostStage &hs : hp.stages) check_ctl(hs.ctl_w);
+      for (int c = 0; c < SV_MAX_OUT_CTL; c++) {
+        d.ctl_tb[c] = ctl_tb[c];
+        d.ctl_w[c] = slot(hp.ctl_w[c]);
+      }
       {
         bool ident = hp.mc == 0;
         for (uint32_t t = 0; t < d.k; t++) ident = ident && hp.mcol[t] == (1u << t);
+        for (int c = 0; c < SV_MAX_OUT_CTL; c++) ident = ident && hp.ctl_w[c] == 0;
         d.phi_ident = ident ? 1u : 0u;
         const uint32_t apu_bits = fp64 ? 0u : 1u;  // amplitudes per 16-byte unit: 2^apu_bits
         for (uint32_t v = 0; v < 64; v++) d.st_lo[v] = slot(phi_of(hp.mcol, hp.mc, v << apu_bits));
@@ -136,6 +159,7 @@ struct SvTableBuilder {
           unit16 = d.phi_pair == 8u;
           for (uint32_t v = 0; v < 64 && unit16; v++) unit16 = (d.st_lo[v] & 8u) == 0;
           for (uint32_t v = 0; v < 128 && unit16; v++) unit16 = (d.st_hi[v] & 8u) == 0;
+          for (int c = 0; c < SV_MAX_OUT_CTL && unit16; c++) unit16 = (d.ctl_w[c] & 8u) == 0;
         }
         d.phi_unit16 = unit16 ? 1u : 0u;
       }
@@ -148,6 +172,10 @@ struct SvTableBuilder {
           pm |= 1u << hs.pos[j];
         }
         sd.cst = slot(hs.mc);
+        for (int c = 0; c < SV_MAX_OUT_CTL; c++) {
+          sd.ctl_tb[c] = ctl_tb[c];
+          sd.ctl_w[c] = slot(hs.ctl_w[c]);
+        }
         // group bits: the first four (the lanes of a half warp) chosen so
         // that their slots differ in the bank bits (slot bits 0-3 of 8-byte
         // FP32 slots, 0-2 of 16-byte FP64 slots), the rest ascending

@@ -119,6 +119,53 @@ static void greedy_groups(const std::vector<uint32_t> &masks, const std::vector<
   }
 }
 
+// Pass cover of the gates (tile qubits, at most k; `forced` in every pass),
+// as greedy_groups, and one more rule: a CNOT whose control is not in the
+// tile yet may join with its control left outside (the control's bit is
+// then fixed within each tile).  Such a control stays out of the pass: a
+// later gate that acts on it, other than as the control of such a CNOT,
+// waits for a later pass.  pass_out[i] = the outside controls of pass i.
+static void pass_groups(const qw_gate *gates, const std::vector<uint32_t> &masks, uint32_t n_pos, uint32_t k,
+                        uint32_t forced, std::vector<std::vector<uint32_t>> &groups,
+                        std::vector<uint32_t> &group_masks, std::vector<uint32_t> &pass_out) {
+  const uint32_t full = (n_pos >= 32) ? 0xFFFFFFFFu : ((1u << n_pos) - 1);
+  std::vector<uint32_t> rem(masks.size());
+  for (uint32_t i = 0; i < rem.size(); i++) rem[i] = i;
+  while (!rem.empty()) {
+    uint32_t Q = forced, blocked = 0, out = 0;
+    std::vector<uint32_t> taken, keep;
+    keep.reserve(rem.size());
+    size_t i = 0;
+    for (; i < rem.size(); i++) {
+      const uint32_t gi = rem[i], qs = masks[gi];
+      const qw_gate &g = gates[gi];
+      if (qs & blocked) {
+        blocked |= qs;
+        keep.push_back(gi);
+      } else if (!(qs & out) && (uint32_t)popc32(Q | qs) <= k) {
+        Q |= qs;
+        taken.push_back(gi);
+      } else if (g.op == QW_OP_CNOT && !(Q & (1u << g.q0)) && !(out & (1u << g.q1)) &&
+                 (uint32_t)popc32(Q | (1u << g.q1)) <= k &&
+                 ((out & (1u << g.q0)) || popc32(out) < SV_MAX_OUT_CTL)) {
+        Q |= 1u << g.q1;
+        out |= 1u << g.q0;
+        taken.push_back(gi);
+      } else {
+        blocked |= qs;
+        keep.push_back(gi);
+      }
+      if (blocked == full) { i++; break; }
+    }
+    for (; i < rem.size(); i++) keep.push_back(rem[i]);
+    if (taken.empty()) fail(QW_ERR_INVALID_ARG, "fusion: gate does not fit a pass");
+    groups.push_back(std::move(taken));
+    group_masks.push_back(Q);
+    pass_out.push_back(out);
+    rem.swap(keep);
+  }
+}
+
 // Stage cover of a pass's gates (positions = tile bits, at most SV_G per
 // stage).  Permutation gates hold no positions: a stage takes one unless an
 // earlier skipped gate shares a qubit with it, and it is applied after the
@@ -216,25 +263,32 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
   for (uint64_t i = 0; i < n_gates; i++) masks[i] = gate_mask(gates[i]);
 
   std::vector<std::vector<uint32_t>> pass_gates;
-  std::vector<uint32_t> pass_masks;
+  std::vector<uint32_t> pass_masks, pass_out;
   if (single) {
     std::vector<uint32_t> all(n_gates);
     for (uint64_t i = 0; i < n_gates; i++) all[i] = (uint32_t)i;
     pass_gates.push_back(all);
     pass_masks.push_back((n_eff >= 32) ? 0xFFFFFFFFu : ((1u << n_eff) - 1));
+    pass_out.push_back(0);
   } else {
-    greedy_groups(masks, nullptr, n_eff, k, forced, pass_gates, pass_masks);
+    pass_groups(gates, masks, n_eff, k, forced, pass_gates, pass_masks, pass_out);
   }
 
   cd gphase(1.0, 0.0);  // global phase pulled out of diagonal gates
   for (size_t p = 0; p < pass_gates.size(); p++) {
     HostPass hp;
     uint32_t Q = pass_masks[p];
-    // pad Q up to k with the lowest unused qubits
-    for (uint32_t q = 0; q < n_eff && (uint32_t)popc32(Q) < k; q++) Q |= 1u << q;
+    const uint32_t out = pass_out[p];
+    // pad Q up to k with the lowest unused qubits (outside controls stay out)
+    for (uint32_t q = 0; q < n_eff && (uint32_t)popc32(Q) < k; q++)
+      if (!(out & (1u << q))) Q |= 1u << q;
     uint32_t loc[32];
     for (uint32_t q = 0; q < n_eff; q++)
       if (Q & (1u << q)) { loc[q] = (uint32_t)hp.q.size(); hp.q.push_back(q); }
+    int ctl_slot[32];
+    for (uint32_t q = 0; q < 32; q++) ctl_slot[q] = -1;
+    for (uint32_t q = 0; q < n_eff; q++)
+      if (out & (1u << q)) { ctl_slot[q] = (int)hp.ctl_q.size(); hp.ctl_q.push_back(q); }
     hp.b = b;
     hp.n_gates = (uint32_t)pass_gates[p].size();
     // stages inside the pass (positions = local tile bits).  Permutation
@@ -246,9 +300,10 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
     const size_t np = pass_gates[p].size();
     std::vector<uint32_t> lmask(np), emask(np);
     std::vector<uint8_t> lperm(np);
+    auto outside_ctl = [&](const qw_gate &g) { return g.op == QW_OP_CNOT && (out & (1u << g.q0)); };
     for (size_t i = 0; i < np; i++) {
       const qw_gate &g = gates[pass_gates[p][i]];
-      uint32_t m = 1u << loc[g.q0];
+      uint32_t m = outside_ctl(g) ? 0u : 1u << loc[g.q0];
       if (is_two_qubit_op(g.op)) m |= 1u << loc[g.q1];
       lmask[i] = m;
       lperm[i] = (g.op == QW_OP_CNOT || g.op == QW_OP_SWAP || g.op == QW_OP_X) ? 1 : 0;
@@ -256,6 +311,11 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
     std::vector<int> next_on(32, -1);
     for (size_t ii = np; ii-- > 0;) {
       const qw_gate &g = gates[pass_gates[p][ii]];
+      if (outside_ctl(g)) {
+        emask[ii] = 0;
+        next_on[loc[g.q1]] = (int)ii;
+        continue;
+      }
       const uint32_t a = loc[g.q0];
       if (lperm[ii]) {
         emask[ii] = 0;
@@ -272,12 +332,13 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
     std::vector<uint32_t> st_masks;
     stage_groups(lmask, emask, lperm, st_gates, st_masks);
     // phi as columns M e_t and constant c
-    uint32_t mcol[32], mc = 0;
+    uint32_t mcol[32], mc = 0, ctl_w[SV_MAX_OUT_CTL] = {0, 0, 0, 0};
     for (uint32_t t = 0; t < 32; t++) mcol[t] = 1u << t;
     for (size_t s = 0; s < st_gates.size(); s++) {
       HostStage hs;
       for (uint32_t t = 0; t < k; t++) hs.mcol[t] = mcol[t];
       hs.mc = mc;
+      for (int c = 0; c < SV_MAX_OUT_CTL; c++) hs.ctl_w[c] = ctl_w[c];
       // unused register positions are taken from the top: tile bit 0 is the
       // only one that reaches bank bit 0 of a slot, so it is kept for the
       // lanes (group bits) where it spreads a warp's accesses over the banks
@@ -351,6 +412,10 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
       // logical index pi(l) stays in the slot of l, so phi <- phi o pi^-1
       for (uint32_t gi_local : perms) {
         const qw_gate &g = gates[pass_gates[p][gi_local]];
+        if (outside_ctl(g)) {  // X on the target in tiles whose control bit is set
+          ctl_w[ctl_slot[g.q0]] ^= mcol[loc[g.q1]];
+          continue;
+        }
         const uint32_t a = loc[g.q0];
         if (g.op == QW_OP_X) mc ^= mcol[a];
         else if (g.op == QW_OP_CNOT) mcol[a] ^= mcol[loc[g.q1]];
@@ -360,6 +425,7 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
     }
     for (uint32_t t = 0; t < k; t++) hp.mcol[t] = mcol[t];
     hp.mc = mc;
+    for (int c = 0; c < SV_MAX_OUT_CTL; c++) hp.ctl_w[c] = ctl_w[c];
     prog.passes.push_back(std::move(hp));
   }
   // fold the global phase into one single-qubit op (every amplitude is in

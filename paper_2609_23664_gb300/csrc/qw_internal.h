@@ -102,10 +102,15 @@ struct HostOp {
 // tile, phi(l) = M l ^ c over GF(2) (before the shared-memory swizzle):
 // permutation gates update phi instead of moving amplitudes.  phi is the
 // identity when the tile is loaded.
+// A CNOT whose control qubit lies outside the tile is an X on its target
+// in the tiles whose control bit is set: it adds a per-tile term to c, the
+// XOR of ctl_w[i] over the outside control qubits ctl_q[i] set in the tile.
+constexpr int SV_MAX_OUT_CTL = 4;  // outside control qubits per pass
 struct HostStage {
   uint8_t pos[SV_G] = {0, 1, 2, 3, 4};  // local tile bit positions (distinct)
   uint32_t mcol[32];  // phi at the start of the stage: column t = M e_t
   uint32_t mc = 0;    // and its constant c
+  uint32_t ctl_w[SV_MAX_OUT_CTL] = {0, 0, 0, 0};  // per-tile terms of c (pass's ctl_q)
   std::vector<HostOp> ops;
   HostStage() { for (uint32_t t = 0; t < 32; t++) mcol[t] = 1u << t; }
 };
@@ -115,6 +120,8 @@ struct HostPass {
   std::vector<HostStage> stages;
   uint32_t mcol[32];        // phi after the last stage (the tile is stored through it)
   uint32_t mc = 0;
+  uint32_t ctl_w[SV_MAX_OUT_CTL] = {0, 0, 0, 0};
+  std::vector<uint32_t> ctl_q;  // outside control qubits (global), at most SV_MAX_OUT_CTL
   uint32_t n_gates = 0;     // gates of the source list absorbed by this pass
   HostPass() { for (uint32_t t = 0; t < 32; t++) mcol[t] = 1u << t; }
 };
@@ -157,6 +164,9 @@ struct SvPassDesc {
   // 16-byte unit u = st_lo[u & 63] ^ st_hi[u >> 6]
   uint32_t st_lo[64];
   uint32_t st_hi[128];
+  // per-tile terms of the final map's constant: XOR ctl_w[i] when bit
+  // ctl_tb[i] of the tile index is set (ctl_w[i] = 0: unused)
+  uint32_t ctl_tb[SV_MAX_OUT_CTL], ctl_w[SV_MAX_OUT_CTL];
 };
 struct alignas(16) SvStageDesc {
   uint32_t roff[SV_G];           // byte offset of phi(e_pos[j]) for register bit j
@@ -166,7 +176,11 @@ struct alignas(16) SvStageDesc {
   // nonzero: the stage's ops are K_RP ops on the positions of this mask,
   // one per position in ascending order (run without dispatch)
   uint32_t rp_mask;
+  uint32_t pad[2];
+  // per-tile terms of cst: XOR ctl_w[i] when bit ctl_tb[i] of the tile index is set
+  uint32_t ctl_tb[SV_MAX_OUT_CTL], ctl_w[SV_MAX_OUT_CTL];
 };
+static_assert(sizeof(SvStageDesc) == 112, "stage descriptor read as seven 16-byte words");
 template <typename T>
 struct alignas(16) SvOpDesc {
   T m[8];         // read as 16-byte vectors

@@ -315,14 +315,18 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
   for (uint32_t s = 0; s < n_st; s++) {
     const uint4 *sdv = (const uint4 *)(stages + st0 + s);
     const uint4 w0 = __ldg(sdv), w1 = __ldg(sdv + 1), w2 = __ldg(sdv + 2), w3 = __ldg(sdv + 3),
-                w4 = __ldg(sdv + 4);
+                w4 = __ldg(sdv + 4), w5 = __ldg(sdv + 5), w6 = __ldg(sdv + 6);
     // offsets are masked to the tile, so XOR combinations stay inside it
     const uint32_t tm = ntile * (uint32_t)sizeof(C) - 1u;
     const uint32_t roff[SV_G] = {w0.x & tm, w0.y & tm, w0.z & tm, w0.w & tm, w1.x & tm};
     const uint32_t gcol[SV_MAX_GBITS] = {w1.y & tm, w1.z & tm, w1.w & tm, w2.x & tm, w2.y & tm,
                                          w2.z & tm, w2.w & tm, w3.x & tm, w3.y & tm};
-    const uint32_t cst = w3.z & tm, nops = w3.w, op_begin = w4.x, rp_mask = w4.y;
-    static_assert(SV_MAX_GBITS == 9 && sizeof(SvStageDesc) == 80, "stage descriptor read as five 16-byte words");
+    // the map's constant, with the per-tile terms of outside-control CNOTs
+    const uint32_t cst = (w3.z ^ (((tile >> w5.x) & 1u) ? w6.x : 0u) ^ (((tile >> w5.y) & 1u) ? w6.y : 0u) ^
+                          (((tile >> w5.z) & 1u) ? w6.z : 0u) ^ (((tile >> w5.w) & 1u) ? w6.w : 0u)) & tm;
+    const uint32_t nops = w3.w, op_begin = w4.x, rp_mask = w4.y;
+    static_assert(SV_MAX_GBITS == 9 && SV_MAX_OUT_CTL == 4 && sizeof(SvStageDesc) == 112,
+                  "stage descriptor read as seven 16-byte words");
     for (uint32_t grp = threadIdx.x; grp < n_groups; grp += nt) {
       uint32_t sbB = cst;
 #pragma unroll
@@ -395,7 +399,11 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
       const uint32_t ub = lg_nt + (uint32_t)t;
       sstep[t] = (ub + apu_bits < k) ? (st_of(1u << ub) ^ c0) & tm : 0u;
     }
-    uint32_t so = st_of(threadIdx.x) & tm;
+    uint32_t so = st_of(threadIdx.x);
+#pragma unroll
+    for (int c = 0; c < SV_MAX_OUT_CTL; c++)
+      so ^= ((tile >> pd->ctl_tb[c]) & 1u) ? pd->ctl_w[c] : 0u;
+    so &= tm;
     if (pd->phi_unit16) {
       // each unit still sits in one 16-byte slot pair, at a permuted place
 #pragma unroll

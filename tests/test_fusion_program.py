@@ -41,6 +41,14 @@ def tile_map(m, k):
     return phi
 
 
+def tile_terms(m, ctl_q, tile_base):
+    """per tile: XOR of ctl_w[i] over the outside control qubits set in the tile"""
+    out = np.zeros(len(tile_base), dtype=np.int64)
+    for i, q in enumerate(ctl_q):
+        out ^= np.where((tile_base >> q) & 1, m["ctl_w"][i], 0)
+    return out
+
+
 def apply_op(op, A):
     m = op["m"]
     a, b = op["a"], op["b"]
@@ -89,27 +97,31 @@ def replay(prog, n):
             tg |= ((ts >> t) & 1) << v
         G = tg[:, None] | lg[None, :]
         slots = psi[G].copy()  # identity map when the tile is loaded
+        rows = np.arange(len(tg))[:, None, None]
         for S in P["stages"]:
             phi = tile_map(S["map"], k)
             pos = S["pos"]
             smask = sum(1 << p for p in pos)
             base = ls[(ls & smask) == 0]
             reg = np.array([sum(((i >> j) & 1) << pos[j] for j in range(5)) for i in range(32)])
-            idx = phi[base[:, None] | reg[None, :]]
-            A = slots[:, idx]
+            idx = phi[base[:, None] | reg[None, :]][None, :, :] ^ tile_terms(S["map"], P["ctl_q"], tg)[:, None, None]
+            A = slots[rows, idx]
             for op in S["ops"]:
                 apply_op(op, A)
-            slots[:, idx] = A
-        psi[G] = slots[:, tile_map(P["map"], k)]
+            slots[rows, idx] = A
+        fin = tile_map(P["map"], k)[None, :] ^ tile_terms(P["map"], P["ctl_q"], tg)[:, None]
+        psi[G] = slots[np.arange(len(tg))[:, None], fin]
     return psi
 
 
 def assert_bijective_maps(prog):
     for P in prog["passes"]:
         k = len(P["q"])
+        assert not set(P["ctl_q"]) & set(P["q"])
         for m in [P["map"]] + [S["map"] for S in P["stages"]]:
             phi = tile_map(m, k)
             assert np.array_equal(np.sort(phi), np.arange(1 << k))
+            assert all(w >> k == 0 for w in m["ctl_w"])
 
 
 @pytest.mark.parametrize("n,tile,low", [(5, 6, 2), (7, 6, 1), (8, 7, 2), (10, 7, 3), (10, 9, 4), (11, 13, 3)])
@@ -145,6 +157,29 @@ def test_permutation_only_program_has_no_stages():
     prog = Q.sv_fuse(g, n, 7, 2)
     assert all(len(P["stages"]) == 0 for P in prog["passes"])
     assert np.max(np.abs(replay(prog, n) - orc.sv_run(n, g))) <= 1e-12
+
+
+@pytest.mark.parametrize("layers", [1, 2, 3])
+def test_chains_across_tiles_replay_to_the_oracle_state(layers):
+    """18 qubits in tiles of 9 (3 contiguous): the CNOT chain crosses tile
+    boundaries, so passes take CNOTs whose control lies outside the tile"""
+    rng = np.random.default_rng(950 + layers)
+    n = 18
+    g = W.hea_circuit(rng, n, layers)
+    prog = Q.sv_fuse(g, n, 9, 3)
+    assert any(P["ctl_q"] for P in prog["passes"])
+    assert_bijective_maps(prog)
+    assert np.max(np.abs(replay(prog, n) - orc.sv_run(n, g))) <= 1e-12
+
+
+def test_hea_passes_with_outside_controls():
+    """24 qubits, tiles of 13 (3 contiguous): CNOTs whose control lies outside
+    the tile join the pass, so hardware-efficient layers take 3, 4, 4 and 6
+    passes for 1-4 layers (4, 5, 7, 8 when every CNOT needs both qubits in
+    the tile)"""
+    rng = np.random.default_rng(12)
+    got = [len(Q.sv_fuse(W.hea_circuit(rng, 24, L), 24, 13, 3)["passes"]) for L in (1, 2, 3, 4)]
+    assert got == [3, 4, 4, 6], got
 
 
 def test_cnot_chains_hold_no_stage_positions():
