@@ -77,52 +77,12 @@ static uint32_t gate_mask(const qw_gate &g) {
 
 static int popc32(uint32_t v) { return __builtin_popcount(v); }
 
-// Greedy cover of the gates (in order) by groups of at most `cap`
-// positions; `forced` positions belong to every group.  A gate joins the
-// current group when it touches no position blocked by an earlier skipped
-// gate (it then commutes past every skipped gate) and when the positions it
-// reserves, cap_masks[i] (a superset of masks[i]), still fit.
-static void greedy_groups(const std::vector<uint32_t> &masks, const std::vector<uint32_t> *cap_masks,
-                          uint32_t n_pos, uint32_t cap, uint32_t forced,
-                          std::vector<std::vector<uint32_t>> &groups, std::vector<uint32_t> &group_masks) {
-  const uint32_t full = (n_pos >= 32) ? 0xFFFFFFFFu : ((1u << n_pos) - 1);
-  std::vector<uint32_t> rem(masks.size());
-  for (uint32_t i = 0; i < rem.size(); i++) rem[i] = i;
-  while (!rem.empty()) {
-    uint32_t Q = forced, blocked = 0;
-    std::vector<uint32_t> taken;
-    std::vector<uint32_t> keep;
-    keep.reserve(rem.size());
-    size_t i = 0;
-    for (; i < rem.size(); i++) {
-      const uint32_t gi = rem[i], qs = masks[gi];
-      const uint32_t cs = cap_masks ? (qs | ((*cap_masks)[gi] & ~blocked)) : qs;
-      if (qs & blocked) {
-        blocked |= qs;  // must stay after an earlier skipped gate on a shared qubit
-        keep.push_back(gi);
-      } else if ((uint32_t)popc32(Q | cs) <= cap) {
-        Q |= cs;
-        taken.push_back(gi);
-      } else if ((uint32_t)popc32(Q | qs) <= cap && cs != qs && (qs & Q) == qs) {
-        taken.push_back(gi);  // fits without its reservation: positions already held
-      } else {
-        blocked |= qs;
-        keep.push_back(gi);
-      }
-      if (blocked == full) { i++; break; }
-    }
-    for (; i < rem.size(); i++) keep.push_back(rem[i]);
-    if (taken.empty()) fail(QW_ERR_INVALID_ARG, "fusion: gate does not fit a group");
-    groups.push_back(std::move(taken));
-    group_masks.push_back(Q);
-    rem.swap(keep);
-  }
-}
-
-// Pass cover of the gates (tile qubits, at most k; `forced` in every pass),
-// as greedy_groups, and one more rule: a CNOT whose control is not in the
-// tile yet may join with its control left outside (the control's bit is
-// then fixed within each tile).  Such a control stays out of the pass: a
+// Greedy pass cover of the gates, in order (tile qubits, at most k;
+// `forced` in every pass).  A gate joins the current pass when it touches no
+// qubit blocked by an earlier skipped gate (it then commutes past every
+// skipped gate) and its qubits still fit.  A CNOT whose control is not in
+// the tile yet may also join with its control left outside (the control's
+// bit is then fixed within each tile).  Such a control stays out of the pass: a
 // later gate that acts on it, other than as the control of such a CNOT,
 // waits for a later pass.  pass_out[i] = the outside controls of pass i.
 static void pass_groups(const qw_gate *gates, const std::vector<uint32_t> &masks, uint32_t n_pos, uint32_t k,
@@ -170,7 +130,9 @@ static void pass_groups(const qw_gate *gates, const std::vector<uint32_t> &masks
 // stage).  Permutation gates hold no positions: a stage takes one unless an
 // earlier skipped gate shares a qubit with it, and it is applied after the
 // stage's other gates, so a later non-permutation gate on one of its qubits
-// waits for the next stage.  The other gates join as in greedy_groups.
+// waits for the next stage.  Another gate joins when no earlier skipped
+// gate or taken permutation shares a position with it and the positions it
+// reserves (cap_masks[i], a superset of masks[i]) still fit.
 static void stage_groups(const std::vector<uint32_t> &masks, const std::vector<uint32_t> &cap_masks,
                          const std::vector<uint8_t> &perm, std::vector<std::vector<uint32_t>> &groups,
                          std::vector<uint32_t> &group_masks) {
