@@ -230,12 +230,29 @@ typedef struct qw_plan_opts {
                                  Boundaries continuing from another precision keep the
                                  pass kernels.  The choices are in the cost record.
                                  Default 0. */
+  int32_t fp32_arith;         /* gate arithmetic of FP32 statevector tasks (storage stays
+                                 FP32 either way):
+                                 QW_FP32_COMPENSATED (default): every amplitude is held
+                                 as an unevaluated sum of two FP32 numbers while gates
+                                 run (error-free products and sums on the FP32 units,
+                                 gate constants to 2^-48), so a state is rounded only
+                                 when it is stored: the passes of a boundary keep their
+                                 FP32 remainder in a second array and round once, into
+                                 the boundary; a task's suffix passes round at each
+                                 stage of a pass; per-task launches (batched = 0) keep
+                                 the remainder like a boundary.
+                                 QW_FP32_PLAIN: FP32 arithmetic (faster; its rounding
+                                 through long circuits moves energies by about 1e-6 of
+                                 their size at 24 qubits). */
 } qw_plan_opts;
+
+#define QW_FP32_COMPENSATED 0
+#define QW_FP32_PLAIN 1
 
 /* Fills the defaults: reuse=1, batched=1, legality=1, analytic costs,
  * delta_frac=0.10, min_group=2, min_prefix_gates=1, min_prefix_cost_ns=0,
  * autotuned tiles, use_graph=1, fault_injection=0, fuse_energy=0, pauli_frames=1,
- * handoff=1, prefix_fp64=0. */
+ * handoff=1, prefix_fp64=0, dense_boundaries=0, fp32_arith=QW_FP32_COMPENSATED. */
 void qw_plan_opts_default(qw_plan_opts *o);
 
 typedef struct qw_plan qw_plan;
@@ -409,26 +426,31 @@ qw_status qw_sv_sample_dev(qw_engine *e, uint32_t mode, uint32_t n, const void *
 
 /* ---- energy without device allocation --------------------------------------
  * The paper has no counterpart of this entry point; it exists for callers of
- * this library that cannot allocate device memory: code issuing work while a
- * CUDA graph is captured in global mode (cudaMalloc/cudaFree are not allowed
- * there), programs whose device memory is owned by another allocator, and
- * latency-bound loops that cannot pay the device synchronization of
- * cudaFree.  It computes what qw_sv_energy_dev computes, with the same
- * kernels, but needs no engine and allocates nothing: the term layout, the
- * job record and the per-block partial sums live in one fixed device array
- * of the library (about 1.2 MB, held by every GPU that loads the library
- * until the process exits).
+ * this library that cannot allocate device memory: programs whose device
+ * memory is owned by another allocator (a framework's caching allocator that
+ * has reserved the pool), and latency-bound loops with a fixed memory
+ * footprint that cannot pay the device synchronization of cudaFree.  It
+ * computes what qw_sv_energy_dev computes, with the same kernels, but needs
+ * no engine and allocates nothing: the term layout, the job record and the
+ * per-block partial sums live in one fixed device array of the library
+ * (about 1.2 MB, held by every GPU that loads the library until the process
+ * exits).  Its term classes are fixed (chunks of an eighth of the state from
+ * 15 qubits on), so its sums run in another order than qw_sv_energy_dev's.
  *   state : device, 2^n amplitudes (double2 for QW_MODE_SV_FP64, float2 for
  *           QW_MODE_SV_FP32), n in [5, QW_NOALLOC_MAX_QUBITS].
  *   terms : host, n_terms <= QW_NOALLOC_MAX_TERMS; masks within n bits.
  *   out   : device, 2 doubles {energy, <psi|psi>}, written asynchronously on
  *           `stream` (a cudaStream_t; NULL = legacy default stream).
- * Larger n or n_terms return QW_ERR_BUDGET.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress), which loads the
- * module; make that first call before any stream capture.  Every call uses
- * the same array: calls whose work overlaps on the GPU (different streams,
- * or host threads without ordering) race and corrupt each other's results;
- * serialize them on one stream.  The array keeps the last call's contents. */
+ * n < 5, NULL pointers and masks outside the register return
+ * QW_ERR_INVALID_ARG; n > QW_NOALLOC_MAX_QUBITS or more terms than
+ * QW_NOALLOC_MAX_TERMS return QW_ERR_BUDGET.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress), which loads
+ * the module; make that first call before any stream capture.  Every call
+ * uses the same array: calls whose work overlaps on the GPU (different
+ * streams, or host threads without ordering) race and corrupt each other's
+ * results; serialize them on one stream.  The array keeps the last call's
+ * contents; every partial sum is rewritten before it is read, so nothing
+ * needs clearing between calls. */
 #define QW_NOALLOC_MAX_QUBITS 26
 #define QW_NOALLOC_MAX_TERMS 1024
 qw_status qw_sv_energy_noalloc_dev(uint32_t mode, uint32_t n, const void *state,

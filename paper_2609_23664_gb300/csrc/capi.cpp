@@ -205,6 +205,7 @@ void qw_plan_opts_default(qw_plan_opts *o) {
   o->handoff = 1;
   o->prefix_fp64 = 0;
   o->dense_boundaries = 0;
+  o->fp32_arith = QW_FP32_COMPENSATED;
 }
 
 qw_status qw_plan_create(qw_engine *e, const qw_workload *w, const qw_plan_opts *o, qw_plan **out) {
@@ -339,14 +340,15 @@ qw_status qw_cost_record_json(const qw_plan *p, char *buf, size_t cap, size_t *n
       "\"sampling_ms\":%.6f,\"tableau_tasks_ms\":%.6f,\"device_total_ms\":%.6f,"
       "\"kernel_launches\":%llu,\"h2d_bytes\":%llu,\"d2h_bytes\":%llu,"
       "\"batch_alg_bytes\":%.0f,\"energy_alg_bytes\":%.0f,\"energy_l2_bytes\":%.0f,\"prefix_alg_bytes\":%.0f,"
-      "\"energy_fused\":%s,"
+      "\"energy_fused\":%s,\"fp32_arith\":\"%s\","
       "\"artifacts\":%zu,\"artifact_bytes\":%llu,\"batch_ms\":[",
       p->planning_ns * 1e-6, p->est_direct_ns * 1e-6, p->est_plan_ns * 1e-6,
       p->est_plan_ns > 0 ? p->est_direct_ns / p->est_plan_ns : 1.0, p->timed, p->t_upload_ms,
       p->t_prefix_ms, p->t_suffix_ms, p->t_energy_ms, p->t_sample_ms, p->t_tab_ms, p->t_total_ms,
       (unsigned long long)p->n_launches, (unsigned long long)p->h2d_bytes,
       (unsigned long long)p->d2h_bytes, p->batch_alg_bytes, p->energy_alg_bytes, p->energy_l2_bytes, p->prefix_alg_bytes,
-      p->energy_fused ? "true" : "false", p->mats.size(), [&] {
+      p->energy_fused ? "true" : "false", p->opts.fp32_arith == QW_FP32_PLAIN ? "plain" : "compensated",
+      p->mats.size(), [&] {
         unsigned long long b = 0;
         for (auto &m : p->mats) b += m.bytes;
         return b;
@@ -360,9 +362,9 @@ qw_status qw_cost_record_json(const qw_plan *p, char *buf, size_t cap, size_t *n
     const DenseChoice &c = p->dense_choices[i];
     const char *eng = c.engine == QW_DENSE_TENSOR ? "tensor" : c.engine == QW_DENSE_SIMT ? "cuda_cores" : "mixed";
     s += strf("%s{\"artifact\":%d,\"used\":%s,\"engine\":\"%s\",\"fusion_width\":%u,\"blocks\":%u,"
-              "\"estimated_ms\":%.6f,\"pass_kernels_ms\":%.6f,\"dense_ms\":%.6f}",
+              "\"estimated_ms\":%.6f,\"pass_kernels_ms\":%.6f,\"dense_ms\":%.6f,\"over_accuracy_budget\":%s}",
               i ? "," : "", c.mat, c.used ? "true" : "false", eng, c.width, c.blocks, c.est_ms, c.pass_ms,
-              c.dense_ms);
+              c.dense_ms, c.over_budget ? "true" : "false");
   }
   s += "]}";
   return put_json(s, buf, cap, needed);
@@ -495,11 +497,12 @@ qw_status qw_costmodel_features(const qw_engine *e, const qw_workload *w, uint64
     const TaskData &t = w->w.tasks[task];
     if (gate_begin > gate_end || gate_end > t.n_gates) fail(QW_ERR_INVALID_ARG, "bad gate range");
     TileConfig tc;
-    tc.k_max = (t.mode == QW_MODE_SV_FP64) ? SV_MAX_TILE_FP64 : SV_MAX_TILE_FP32;
+    // tiles of the default arithmetic (compensated FP32)
+    tc.k_max = (t.mode == QW_MODE_SV_FP64) ? SV_MAX_TILE_FP64 : SV_MAX_TILE_FP32_COMP;
     tc.b = 4;
     if (e) {
-      auto it = e->e.tiles.find(((uint64_t)std::min<uint32_t>(std::max<uint32_t>(t.n, SV_G), 26) << 1) |
-                                (t.mode == QW_MODE_SV_FP64 ? 1 : 0));
+      auto it = e->e.tiles.find(Engine::tile_key(std::max<uint32_t>(t.n, SV_G), t.mode == QW_MODE_SV_FP64,
+                                                 SV_AR_COMP));
       if (it != e->e.tiles.end()) tc = it->second;
     }
     features_for(t, gate_begin, gate_end, n_sharing, tc, 0.0, out);

@@ -62,6 +62,7 @@ struct SvTableBuilder {
   std::vector<SvPassDesc> passes;
   std::vector<SvStageDesc> stages;
   std::vector<SvOpDesc<float>> ops32;
+  std::vector<float> ops32lo;  // m[t] - (float)m[t] per FP32 op (compensated passes)
   std::vector<SvOpDesc<double>> ops64;
   bool fp64;
   explicit SvTableBuilder(bool f) : fp64(f) {}
@@ -237,7 +238,10 @@ struct SvTableBuilder {
           } else {
             SvOpDesc<float> od{};
             od.code = code;
-            for (int t = 0; t < 8; t++) od.m[t] = (float)o.m[t];
+            for (int t = 0; t < 8; t++) {
+              od.m[t] = (float)o.m[t];
+              ops32lo.push_back((float)(o.m[t] - (double)od.m[t]));
+            }
             ops32.push_back(od);
           }
         }
@@ -281,6 +285,8 @@ struct DevArena {
 
 struct Wave {
   bool fp64 = false;
+  bool per_pass = false;                  // one launch per pass (else one persistent launch)
+  int ar = SV_AR_PLAIN;                   // arithmetic of the wave's FP32 passes
   uint32_t k_max = 13;
   int grid = 0;
   std::vector<uint32_t> tasks;            // tasks run in this wave (own buffers)
@@ -310,6 +316,12 @@ struct DeviceState {
   DevArena arena;
   cudaStream_t stream = nullptr;
   SvTables t32{}, t64{};
+  // FP32 arithmetic: of the boundaries' passes and per-task launches
+  // (ar_chain: SV_AR_REM, or SV_AR_PLAIN) and of the persistent suffix
+  // launches (ar_batch: SV_AR_COMP or SV_AR_PLAIN); `rem` is the remainder
+  // array those chains share (they run one after another on the stream)
+  int ar_chain = SV_AR_PLAIN, ar_batch = SV_AR_PLAIN;
+  void *rem = nullptr;
   std::vector<uint32_t> mat_pass0, task_pass0;
   std::vector<void *> mat_buf;
   std::vector<void *> mat_export[2];   // per mode (FP64, FP32): statevector exported from a tableau node
@@ -370,6 +382,24 @@ struct DeviceState {
 };
 
 static size_t sv_state_bytes(bool fp64, uint32_t n_eff) { return (size_t)(fp64 ? 16 : 8) << n_eff; }
+
+// HBM bytes of a chain of `passes` passes over a state of S bytes: the state
+// is read and written once per pass; with a remainder array (SV_AR_REM)
+// every pass but the first also reads it and every pass but the last writes it
+static double chain_bytes(double S, size_t passes, int ar) {
+  const double p = (double)passes;
+  return 2.0 * S * p + ((ar == SV_AR_REM && passes > 1) ? 2.0 * S * (p - 1.0) : 0.0);
+}
+// remainder arrays of pass p of a chain of n passes (SV_AR_REM)
+static const void *chain_src_lo(const DeviceState *D, int ar, size_t p) {
+  return (ar == SV_AR_REM && p > 0) ? D->rem : nullptr;
+}
+static void *chain_dst_lo(const DeviceState *D, int ar, size_t p, size_t n) {
+  return (ar == SV_AR_REM && p + 1 < n) ? D->rem : nullptr;
+}
+int plan_ar_batch(const qw_plan *P) {
+  return P->opts.fp32_arith == QW_FP32_PLAIN ? SV_AR_PLAIN : SV_AR_COMP;
+}
 
 // Segment size of a persistent work list: the largest power of two (at most
 // 64) that no job's unit count falls below, so that few items are empty.
@@ -452,12 +482,19 @@ static void prepare(qw_plan *P) {
   SvTableBuilder b32(false), b64(true);
   D->mat_pass0.assign(P->mats.size(), 0);
   D->task_pass0.assign(nt, 0);
+  D->ar_batch = plan_ar_batch(P);
+  D->ar_chain = D->ar_batch == SV_AR_COMP ? SV_AR_REM : SV_AR_PLAIN;
+  size_t rem_bytes = 0;  // largest FP32 chain that keeps a remainder
   for (size_t m = 0; m < P->mats.size(); m++) {
     const MatNode &M = P->mats[m];
     if (M.mode == QW_MODE_TABLEAU) continue;
     D->mat_pass0[m] = (M.mode == QW_MODE_SV_FP64 ? b64 : b32).add(M.sv);
-    // algorithmic bytes of the boundary's passes: read and write the state once each
-    P->prefix_alg_bytes += 2.0 * (double)sv_state_bytes(M.mode == QW_MODE_SV_FP64, M.n_eff) * (double)M.sv.passes.size();
+    const bool f64 = M.mode == QW_MODE_SV_FP64;
+    const int ar = f64 ? SV_AR_PLAIN : D->ar_chain;
+    const size_t S = sv_state_bytes(f64, M.n_eff);
+    // algorithmic bytes of the boundary's passes (state, and the remainder between passes)
+    P->prefix_alg_bytes += chain_bytes((double)S, M.sv.passes.size(), ar);
+    if (ar == SV_AR_REM && M.sv.passes.size() > 1) rem_bytes = std::max(rem_bytes, S);
   }
   for (uint32_t t = 0; t < nt; t++) {
     const TaskPlan &tp = P->tasks[t];
@@ -467,6 +504,7 @@ static void prepare(qw_plan *P) {
   D->t32.passes = D->arena.upload(b32.passes, s);
   D->t32.stages = D->arena.upload(b32.stages, s);
   D->t32.ops = D->arena.upload(b32.ops32, s);
+  D->t32.ops_lo = D->arena.upload(b32.ops32lo, s);
   D->t64.passes = D->arena.upload(b64.passes, s);
   D->t64.stages = D->arena.upload(b64.stages, s);
   D->t64.ops = D->arena.upload(b64.ops64, s);
@@ -511,19 +549,24 @@ static void prepare(qw_plan *P) {
       c.mat = (int)m;
       dense_prog_config(dp, &c.engine, &c.width, nullptr, &c.est_ms);
       c.blocks = (uint32_t)dense_prog_blocks(dp);
-      bool use = P->opts.dense_boundaries == 2;
-      if (!use) {
+      c.over_budget = !fp64 && D->ar_chain == SV_AR_REM && c.blocks > DENSE_COMP_MAX_BLOCKS;
+      bool use = P->opts.dense_boundaries == 2 && !c.over_budget;
+      if (!use && !c.over_budget) {
         // both candidates timed once from |0...0> on a scratch state
         const size_t bytes = sv_state_bytes(fp64, M.n_eff), n_amp = (size_t)1 << M.n_eff;
-        void *scratch = nullptr;
+        void *scratch = nullptr, *scratch_lo = nullptr;
+        const int ar = fp64 ? SV_AR_PLAIN : D->ar_chain;
         CK(cudaMalloc(&scratch, bytes));
+        if (ar == SV_AR_REM) CK(cudaMalloc(&scratch_lo, bytes));
         const SvTables &T = fp64 ? D->t64 : D->t32;
         cudaEvent_t e[4];
         for (auto &x : e) CK(cudaEventCreate(&x));
         CK(cudaEventRecord(e[0], s));
-        for (size_t p = 0; p < M.sv.passes.size(); p++)
+        const size_t np = M.sv.passes.size();
+        for (size_t p = 0; p < np; p++)
           launch_sv_pass(fp64, T, D->mat_pass0[m] + (uint32_t)p, (uint32_t)M.sv.passes[p].q.size(), M.n_eff,
-                         p == 0 ? nullptr : scratch, scratch, s);
+                         p == 0 ? nullptr : scratch, scratch, s, ar, (ar == SV_AR_REM && p > 0) ? scratch_lo : nullptr,
+                         (ar == SV_AR_REM && p + 1 < np) ? scratch_lo : nullptr);
         CK(cudaEventRecord(e[1], s));
         CK(cudaEventRecord(e[2], s));
         basis_zero_kernel<<<(unsigned)std::min<size_t>((n_amp + 255) / 256, (size_t)E->sm_count * 16), 256, 0, s>>>(
@@ -536,6 +579,7 @@ static void prepare(qw_plan *P) {
         CK(cudaEventElapsedTime(&b, e[2], e[3]));
         for (auto &x : e) cudaEventDestroy(x);
         cudaFree(scratch);
+        if (scratch_lo) cudaFree(scratch_lo);
         dense_prog_check(dp);
         c.pass_ms = a;
         c.dense_ms = b;
@@ -574,6 +618,9 @@ static void prepare(qw_plan *P) {
       n_sv++;
       if (M.sv.passes.empty()) ok = false;
       if (M.parent >= 0 && P->mats[M.parent].mode != M.mode) ok = false;
+      // compensated FP32 boundaries keep their remainder between passes,
+      // which the persistent launch does not carry: pass by pass
+      if (M.mode == QW_MODE_SV_FP32 && D->ar_chain == SV_AR_REM) ok = false;
     }
     // a single boundary is a chain of dependent passes: separate launches
     // serve it as well, without CTAs waiting on the previous pass
@@ -663,6 +710,13 @@ static void prepare(qw_plan *P) {
   }
   size_t max_partials = 1, max_smp_blocks = 1, max_src = 1;
   const bool batched = P->opts.batched != 0;
+  // compensated FP32 tasks with long programs leave the persistent launch
+  // (which rounds at every stage) for a chain of launches of their own that
+  // keeps the remainder, one task after another
+  auto long_chain = [&](const TaskPlan &tp) {
+    return batched && D->ar_batch == SV_AR_COMP && tp.mode == QW_MODE_SV_FP32 &&
+           tp.sv.passes.size() > (size_t)SV_COMP_MAX_BATCH_PASSES;
+  };
   // Task buffers of every group coexist for the plan's lifetime, so the
   // groups share one task budget: each group with pooled tasks gets one
   // buffer, then the rest of the budget goes to the groups in order of
@@ -674,10 +728,15 @@ static void prepare(qw_plan *P) {
     uint64_t committed = 0;
     for (auto &g : groups) {
       size_t np = 0;
+      bool any_long = false;
       for (uint32_t t : g.second) {
         const TaskPlan &tp = P->tasks[t];
-        if ((!tp.sv.passes.empty() || needs_convert(tp)) && !(tp.flags & QW_TASK_KEEP_STATE)) np++;
+        if ((!tp.sv.passes.empty() || needs_convert(tp)) && !(tp.flags & QW_TASK_KEEP_STATE)) {
+          if (long_chain(tp)) any_long = true;
+          else np++;
+        }
       }
+      if (any_long && np == 0) np = 1;
       const size_t S = sv_state_bytes(g.first.first != 0, g.first.second);
       n_pooled[g.first] = np;
       pool_size[g.first] = np ? 1 : 0;
@@ -713,26 +772,38 @@ static void prepare(qw_plan *P) {
       if (P->tasks[t].flags & QW_TASK_KEEP_STATE) D->task_state[t] = D->arena.alloc(S);
       else pooled.push_back(t);
     }
-    const size_t pool_n = std::min(pool_size[g.first], pooled.size());
+    // waves: dedicated tasks first (one wave), then pooled chunks; long
+    // compensated chains one task per wave, launched pass by pass
+    std::vector<uint32_t> dedicated, ded_short, pool_short, longs;
+    for (uint32_t t : own) if (P->tasks[t].flags & QW_TASK_KEEP_STATE) dedicated.push_back(t);
+    for (uint32_t t : dedicated) (long_chain(P->tasks[t]) ? longs : ded_short).push_back(t);
+    bool pooled_long = false;
+    for (uint32_t t : pooled) {
+      if (long_chain(P->tasks[t])) { longs.push_back(t); pooled_long = true; }
+      else pool_short.push_back(t);
+    }
+    const size_t pool_n =
+        std::min(pool_size[g.first], std::max(pool_short.size(), (size_t)(pooled_long ? 1 : 0)));
     std::vector<void *> pool(pool_n);
     for (auto &p : pool) p = D->arena.alloc(S);
-    // waves: dedicated tasks first (one wave), then pooled chunks
-    std::vector<std::vector<uint32_t>> wave_tasks;
-    std::vector<uint32_t> dedicated;
-    for (uint32_t t : own) if (P->tasks[t].flags & QW_TASK_KEEP_STATE) dedicated.push_back(t);
+    std::vector<std::pair<std::vector<uint32_t>, bool>> wave_tasks;  // (tasks, per-pass launches)
     if (batched) {
-      if (!dedicated.empty()) wave_tasks.push_back(dedicated);
-      for (size_t i = 0; i < pooled.size(); i += pool_n)
-        wave_tasks.push_back(std::vector<uint32_t>(pooled.begin() + i,
-                                                   pooled.begin() + std::min(pooled.size(), i + pool_n)));
+      if (!ded_short.empty()) wave_tasks.push_back({ded_short, false});
+      for (size_t i = 0; i < pool_short.size(); i += pool_n)
+        wave_tasks.push_back({std::vector<uint32_t>(pool_short.begin() + i,
+                                                    pool_short.begin() + std::min(pool_short.size(), i + pool_n)),
+                              false});
+      for (uint32_t t : longs) wave_tasks.push_back({{t}, true});
     } else {
-      for (uint32_t t : own) wave_tasks.push_back({t});
+      for (uint32_t t : own) wave_tasks.push_back({{t}, true});
     }
-    if (wave_tasks.empty()) wave_tasks.push_back({});
+    if (wave_tasks.empty()) wave_tasks.push_back({{}, !batched});
     for (size_t w = 0; w < wave_tasks.size(); w++) {
       Wave W;
       W.fp64 = fp64;
-      W.tasks = wave_tasks[w];
+      W.per_pass = wave_tasks[w].second;
+      W.ar = fp64 ? SV_AR_PLAIN : (W.per_pass ? D->ar_chain : D->ar_batch);
+      W.tasks = wave_tasks[w].first;
       uint32_t kmax = 5;
       for (size_t i = 0; i < W.tasks.size(); i++) {
         const uint32_t t = W.tasks[i];
@@ -833,7 +904,12 @@ static void prepare(qw_plan *P) {
       max_src = std::max<size_t>(max_src, W.src.size());
       // algorithmic bytes: every pass reads and writes its state once; the
       // energy of a task reads every amplitude once per term class
-      for (const SvJob &j : W.jobs) P->batch_alg_bytes += 2.0 * (double)S;
+      if (W.ar == SV_AR_REM) {  // one task, its passes in order
+        P->batch_alg_bytes += chain_bytes((double)S, W.jobs.size(), W.ar);
+        if (W.jobs.size() > 1) rem_bytes = std::max(rem_bytes, S);
+      } else {
+        for (const SvJob &j : W.jobs) { (void)j; P->batch_alg_bytes += 2.0 * (double)S; }
+      }
       for (size_t e = 0; e < W.en.size(); e++) {
         const EnJob &j = W.en[e];
         const double Sj = (double)sv_state_bytes(fp64, j.n);
@@ -848,8 +924,9 @@ static void prepare(qw_plan *P) {
       // persistent work list: pass jobs, then (fused) the energy jobs,
       // released in the order their states finish
       std::vector<SvJob> up = W.jobs;
-      W.grid = batched ? sv_batch_grid(fp64, W.k_max, E->sm_count) : 0;
-      W.fused_energy = batched && P->opts.fuse_energy && !W.en.empty() && sv_threads_for_k(W.k_max) == 128;
+      W.grid = !W.per_pass ? sv_batch_grid(fp64, W.k_max, E->sm_count, W.ar) : 0;
+      W.fused_energy =
+          !W.per_pass && P->opts.fuse_energy && !W.en.empty() && sv_threads_for_k(W.k_max, W.ar) == 128;
       if (W.fused_energy) {
         std::vector<SvJob> ej;
         for (size_t e = 0; e < W.en.size(); e++) {
@@ -866,7 +943,7 @@ static void prepare(qw_plan *P) {
         std::stable_sort(ej.begin(), ej.end(), [](const SvJob &a, const SvJob &b) { return a.dep < b.dep; });
         up.insert(up.end(), ej.begin(), ej.end());
       }
-      if (batched) {
+      if (!W.per_pass) {
         W.seg_bits = segment_bits(up);
         build_segments(up, W.jobs.size(), W.seg_bits, 2ull * (uint64_t)W.grid, W.segs);
         if (((uint64_t)W.segs.size() << W.seg_bits) > 0xFFFFFFF0ull)
@@ -877,7 +954,7 @@ static void prepare(qw_plan *P) {
       // With fault injection (tests only) the first job waits on an extra
       // job that has no segment, so no CTA ever takes it: its counter never
       // reaches the one unit it needs and the bounded wait runs out.
-      if (P->opts.fault_injection && batched && !up.empty()) {
+      if (P->opts.fault_injection && !W.per_pass && !up.empty()) {
         SvJob ph{};
         ph.n_tiles = 1;
         ph.dep = -1;
@@ -896,6 +973,7 @@ static void prepare(qw_plan *P) {
     }
   }
   D->d_partials = (double *)D->arena.alloc(sizeof(double) * 2 * max_partials);
+  if (rem_bytes) D->rem = D->arena.alloc(rem_bytes);
   D->d_bsum = (double *)D->arena.alloc(sizeof(double) * max_smp_blocks);
   D->d_blast = (int32_t *)D->arena.alloc(sizeof(int32_t) * max_smp_blocks);
   D->d_boff = (double *)D->arena.alloc(sizeof(double) * (max_smp_blocks + max_src));
@@ -1084,10 +1162,15 @@ static void enqueue(qw_plan *P, cudaStream_t s, bool capturing) {
     } else if (M.sv.passes.empty()) {
       if (psrc) launch_copy(psrc, D->mat_buf[m], sv_state_bytes(fp64, M.n_eff), s);
     } else {
-      nl += M.sv.passes.size();
-      for (size_t p = 0; p < M.sv.passes.size(); p++) {
+      // compensated FP32: the remainder stays in D->rem between the passes
+      // and the last pass rounds the state once, into the boundary
+      const int ar = fp64 ? SV_AR_PLAIN : D->ar_chain;
+      const size_t np = M.sv.passes.size();
+      nl += np;
+      for (size_t p = 0; p < np; p++) {
         launch_sv_pass(fp64, T, D->mat_pass0[m] + (uint32_t)p, (uint32_t)M.sv.passes[p].q.size(), M.n_eff,
-                       p == 0 ? psrc : D->mat_buf[m], D->mat_buf[m], s);
+                       p == 0 ? psrc : D->mat_buf[m], D->mat_buf[m], s, ar, chain_src_lo(D, ar, p),
+                       chain_dst_lo(D, ar, p, np));
       }
     }
     // the boundary rounded once into the other precision its consumers use
@@ -1132,19 +1215,22 @@ static void enqueue(qw_plan *P, cudaStream_t s, bool capturing) {
       convert_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
           c.second.first, P->mats[tp.src].mode == QW_MODE_SV_FP64, c.second.second, W.fp64, n);
     }
-    if (P->opts.batched) {
+    if (!W.per_pass) {
       if (W.total_items) {
         CK(cudaMemsetAsync(W.d_ctr, 0, W.ctr_words * sizeof(unsigned int), s));
         EnTables et{W.d_en, D->d_classes, D->d_terms, D->d_partials};
         launch_sv_batch(W.fp64, T, W.d_jobs, W.d_segs, W.seg_bits, W.total_items, W.k_max, W.d_ctr, et,
-                        W.grid, s);
+                        W.grid, s, W.ar);
         nl += 1;
       }
     } else {
+      // one task per wave, its passes in order (SV_AR_REM: one rounding, at the end)
       nl += W.jobs.size();
-      for (const SvJob &j : W.jobs) {
+      for (size_t i = 0; i < W.jobs.size(); i++) {
+        const SvJob &j = W.jobs[i];
         const uint32_t k = j.n - (uint32_t)std::log2((double)j.n_tiles);
-        launch_sv_pass(W.fp64, T, j.pass, k, j.n, j.src, j.dst, s);
+        launch_sv_pass(W.fp64, T, j.pass, k, j.n, j.src, j.dst, s, W.ar, chain_src_lo(D, W.ar, i),
+                       chain_dst_lo(D, W.ar, i, W.jobs.size()));
       }
     }
     CK(rec(D->wave_ev[4 * wi + 1]));
@@ -1228,7 +1314,7 @@ void plan_wait(qw_plan *P) {
   const uint32_t nt = (uint32_t)P->tasks.size();
   // device error flags of the persistent launches
   for (auto &W : D->waves) {
-    if (!W.total_items || !P->opts.batched) continue;
+    if (!W.total_items || W.per_pass) continue;
     unsigned int flag = 0;
     CK(cudaMemcpy(&flag, W.d_ctr + 1, sizeof(flag), cudaMemcpyDeviceToHost));
     if (flag) fail(QW_ERR_DEVICE_TIMEOUT, "a bounded dependency wait of the persistent batch expired");
@@ -1460,13 +1546,14 @@ void *Engine::ensure_scratch(size_t bytes) {
 // Autotuner: times one synthetic hardware-efficient layer stack under each
 // candidate (tile qubits, contiguous low qubits) and keeps the fastest per
 // (qubit count, precision).
-TileConfig Engine::tile_config(uint32_t n_eff, bool fp64) {
+TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar) {
   const uint32_t key_n = std::min<uint32_t>(n_eff, 26);
-  const uint64_t key = ((uint64_t)key_n << 1) | (fp64 ? 1 : 0);
+  if (fp64 || ar == SV_AR_REM) ar = SV_AR_PLAIN;
+  const uint64_t key = tile_key(n_eff, fp64, ar);
   auto it = tiles.find(key);
   if (it != tiles.end()) return it->second;
   TileConfig best;
-  best.k_max = fp64 ? SV_MAX_TILE_FP64 : SV_MAX_TILE_FP32;
+  best.k_max = fp64 ? SV_MAX_TILE_FP64 : (ar == SV_AR_PLAIN ? SV_MAX_TILE_FP32 : SV_MAX_TILE_FP32_COMP);
   best.b = 4;
   if (key_n <= best.k_max) { tiles[key] = best; return best; }
   CK(cudaSetDevice(device));
@@ -1492,25 +1579,27 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64) {
   cudaEventCreate(&e1);
   const uint32_t ks32[3] = {12, 13, 14}, ks64[3] = {11, 12, 13}, bs[3] = {3, 4, 5};
   float best_ms = 1e30f;
+  const uint32_t best_cap = best.k_max;
   for (int ki = 0; ki < 3; ki++) {
     for (int bi = 0; bi < 3; bi++) {
       TileConfig tc;
       tc.k_max = fp64 ? ks64[ki] : ks32[ki];
       tc.b = bs[bi];
-      if (tc.b + 2 > tc.k_max) continue;
+      if (tc.b + 2 > tc.k_max || tc.k_max > best_cap) continue;
       SvProgram pr = fuse_sv(g.data(), g.size(), key_n, tc);
       SvTableBuilder tb(fp64);
       tb.add(pr);
       SvTables T;
-      DevArena ar;
-      T.passes = ar.upload(tb.passes, s);
-      T.stages = ar.upload(tb.stages, s);
-      T.ops = fp64 ? (const void *)ar.upload(tb.ops64, s) : (const void *)ar.upload(tb.ops32, s);
+      DevArena dar;
+      T.passes = dar.upload(tb.passes, s);
+      T.stages = dar.upload(tb.stages, s);
+      T.ops = fp64 ? (const void *)dar.upload(tb.ops64, s) : (const void *)dar.upload(tb.ops32, s);
+      T.ops_lo = fp64 ? nullptr : dar.upload(tb.ops32lo, s);
       float tot = 0;
       for (int r = 0; r < 3; r++) {
         cudaEventRecord(e0, s);
         for (size_t p = 0; p < pr.passes.size(); p++)
-          launch_sv_pass(fp64, T, (uint32_t)p, (uint32_t)pr.passes[p].q.size(), key_n, buf, buf, s);
+          launch_sv_pass(fp64, T, (uint32_t)p, (uint32_t)pr.passes[p].q.size(), key_n, buf, buf, s, ar);
         cudaEventRecord(e1, s);
         CK(cudaEventSynchronize(e1));
         float ms;
@@ -1518,7 +1607,7 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64) {
         if (r) tot += ms;
       }
       CK(cudaStreamSynchronize(s));
-      ar.release();
+      dar.release();
       if (tot < best_ms) { best_ms = tot; best = tc; }
     }
   }
@@ -1662,7 +1751,10 @@ void costmodel_probe(Engine *E, const Workload &W, float *feat, float *tgt, floa
     if (T.mode == QW_MODE_TABLEAU || T.n_gates == 0) continue;
     const bool fp64 = T.mode == QW_MODE_SV_FP64;
     const uint32_t n_eff = std::max<uint32_t>(T.n, SV_G);
-    TileConfig tc = E->tile_config(n_eff, fp64);
+    // timings of the default FP32 arithmetic (compensated, as the
+    // persistent suffix launch runs it)
+    const int par = fp64 ? SV_AR_PLAIN : SV_AR_COMP;
+    TileConfig tc = E->tile_config(n_eff, fp64, par);
     const size_t S = sv_state_bytes(fp64, n_eff);
     void *st = E->ensure_scratch(S);
     CK(cudaMemsetAsync(st, 0, S, s));
@@ -1680,11 +1772,12 @@ void costmodel_probe(Engine *E, const Workload &W, float *feat, float *tgt, floa
       Tt.passes = ar.upload(tb.passes, s);
       Tt.stages = ar.upload(tb.stages, s);
       Tt.ops = fp64 ? (const void *)ar.upload(tb.ops64, s) : (const void *)ar.upload(tb.ops32, s);
+      Tt.ops_lo = fp64 ? nullptr : ar.upload(tb.ops32lo, s);
       float best = 1e30f;
       for (int r = 0; r < 3; r++) {
         cudaEventRecord(e0, s);
         for (size_t p = 0; p < pr.passes.size(); p++)
-          launch_sv_pass(fp64, Tt, (uint32_t)p, (uint32_t)pr.passes[p].q.size(), n_eff, st, st, s);
+          launch_sv_pass(fp64, Tt, (uint32_t)p, (uint32_t)pr.passes[p].q.size(), n_eff, st, st, s, par);
         cudaEventRecord(e1, s);
         CK(cudaEventSynchronize(e1));
         float ms;
@@ -1727,7 +1820,10 @@ qw_status sv_apply_dev(Engine *E, uint32_t mode, uint32_t n, void *state, const 
   CK(cudaSetDevice(E->device));
   cudaStream_t s = (cudaStream_t)stream;
   const bool fp64 = mode == QW_MODE_SV_FP64;
-  TileConfig tc = E->tile_config(n, fp64);
+  // FP32: compensated arithmetic with the remainder kept between passes, so
+  // the state is rounded once, by the last pass
+  const int ar = fp64 ? SV_AR_PLAIN : SV_AR_REM;
+  TileConfig tc = E->tile_config(n, fp64, SV_AR_COMP);
   SvProgram pr = fuse_sv(gates, n_gates, n, tc);
   if (pr.passes.empty()) {
     if (!init) return QW_OK;
@@ -1743,16 +1839,24 @@ qw_status sv_apply_dev(Engine *E, uint32_t mode, uint32_t n, void *state, const 
   SvPassDesc *dp = stream_upload(tb.passes, s);
   SvStageDesc *ds = stream_upload(tb.stages, s);
   void *dop = fp64 ? (void *)stream_upload(tb.ops64, s) : (void *)stream_upload(tb.ops32, s);
+  float *dlo = fp64 ? nullptr : stream_upload(tb.ops32lo, s);
+  const size_t np = pr.passes.size();
+  void *rem = nullptr;
+  if (ar == SV_AR_REM && np > 1) CK(cudaMallocAsync(&rem, sv_state_bytes(false, n), s));
   T.passes = dp;
   T.stages = ds;
   T.ops = dop;
-  for (size_t p = 0; p < pr.passes.size(); p++)
+  T.ops_lo = dlo;
+  for (size_t p = 0; p < np; p++)
     launch_sv_pass(fp64, T, (uint32_t)p, (uint32_t)pr.passes[p].q.size(), n,
-                   (p == 0 && init) ? nullptr : state, state, s);
+                   (p == 0 && init) ? nullptr : state, state, s, ar, p > 0 ? rem : nullptr,
+                   p + 1 < np ? rem : nullptr);
   CK(cudaGetLastError());
   CK(cudaFreeAsync(dp, s));
   CK(cudaFreeAsync(ds, s));
   CK(cudaFreeAsync(dop, s));
+  if (dlo) CK(cudaFreeAsync(dlo, s));
+  if (rem) CK(cudaFreeAsync(rem, s));
   return QW_OK;
 }
 

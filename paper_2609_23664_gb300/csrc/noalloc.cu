@@ -1,15 +1,15 @@
 // Pauli-sum energy of a caller-owned device state without any device
 // allocation: qw_sv_energy_noalloc_dev.
 //
-// Some callers cannot allocate device memory: code that issues work while a
-// CUDA graph is being captured in global mode (cudaMalloc / cudaFree are not
-// permitted there), programs whose device memory is fully owned by another
-// allocator (for example a framework's caching allocator that reserved the
-// pool), and latency-bound loops that cannot accept the implicit device
-// synchronization of cudaFree.  They pass the state and an output buffer;
-// everything else the energy kernels need (term layout, job record, per-block
-// partial sums) lives in one file-scope device array of fixed size, which
-// every GPU that loads this library holds until the process exits.
+// Some callers cannot allocate device memory: programs whose device memory
+// is fully owned by another allocator (for example a framework's caching
+// allocator that has reserved the whole pool, where a cudaMalloc beside it
+// fails or fragments it), and latency-bound loops with a fixed memory
+// footprint that cannot accept the implicit device synchronization of
+// cudaFree.  They pass the state and an output buffer; everything else the
+// energy kernels need (term layout, job record, per-block partial sums)
+// lives in one file-scope device array of fixed size, which every GPU that
+// loads this library holds until the process exits.
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -67,10 +67,14 @@ qw_status scratch_address(int dev, NaScratch **out) {
   return QW_OK;
 }
 
-// The term layout of the allocating entry point (classes by the flip bits
-// above the chunk, term order kept inside a class) with at most 3 class
-// bits (chunks of an eighth of the state for n >= 15), built into fixed
-// arrays sized for that.
+// Term layout for the fixed arrays: classes by the flip bits above the
+// chunk, term order kept inside a class, as in the allocating entry point,
+// but always with 3 class bits once n >= 15 (chunks of an eighth of the
+// state), so that every layout fits NA_MAX_CLASSES and NA_MAX_BLOCKS.  The
+// allocating entry point sizes chunks to at most EN_CHUNK_BYTES instead
+// (one class for FP32 states up to 22 qubits, chunks of 64 MB at 26): the
+// two compute the same terms with the same kernel, adding them in a
+// different order and at a different speed.
 void layout_fixed(const qw_pauli_term *terms, uint32_t n_terms, uint32_t n, NaHeader &h,
                   uint32_t *n_classes, uint32_t *n_blocks, uint32_t *chunk_bits_out) {
   uint32_t u = 0, chunk_bits = n;
@@ -115,8 +119,7 @@ void layout_fixed(const qw_pauli_term *terms, uint32_t n_terms, uint32_t n, NaHe
 }
 
 // Copies the host-built layout, passed by value as the kernel's parameter
-// (no host memory is read by the device, so the launch is capturable), into
-// the scratch array.
+// (the device reads no host memory), into the scratch array.
 __global__ void na_setup_kernel(const NaHeader h, NaHeader *dst, uint32_t words) {
   const uint32_t *src = (const uint32_t *)&h;
   uint32_t *d = (uint32_t *)dst;
@@ -141,9 +144,13 @@ extern "C" qw_status qw_sv_energy_noalloc_dev(uint32_t mode, uint32_t n, const v
     set_last_error("NULL argument");
     return QW_ERR_INVALID_ARG;
   }
-  if (n < SV_G || n > QW_NOALLOC_MAX_QUBITS) {
-    set_last_error("n must be in [5, " + std::to_string(QW_NOALLOC_MAX_QUBITS) +
-                   "] for the non-allocating energy");
+  if (n < SV_G) {
+    set_last_error("n must be at least 5 (states are padded to 5 qubits)");
+    return QW_ERR_INVALID_ARG;
+  }
+  if (n > QW_NOALLOC_MAX_QUBITS) {
+    set_last_error("n must be at most " + std::to_string(QW_NOALLOC_MAX_QUBITS) +
+                   " for the non-allocating energy's scratch array");
     return QW_ERR_BUDGET;
   }
   if (n_terms > QW_NOALLOC_MAX_TERMS) {

@@ -96,7 +96,15 @@ struct DenseChoice {
   uint32_t engine = 0, width = 0, blocks = 0;
   double est_ms = 0, pass_ms = 0, dense_ms = 0;  // timed candidates (option 1), 0 = not timed
   bool used = false;
+  bool over_budget = false;  // compensated FP32: more blocks than the accuracy budget allows
 };
+// Compensated FP32 boundaries take the tensor-core dense form only up to
+// this many blocks: each 3xTF32 block perturbs the state by about 1e-7 of
+// its norm (FP32 accumulation inside the tensor core), which moves a
+// Pauli-sum energy by about 1.4e-7 of its typical size; four such blocks
+// (2.8e-7, adding in quadrature) leave room within the 1e-6 energy target,
+// where the compensated passes keep a whole prefix near 1e-7
+constexpr uint32_t DENSE_COMP_MAX_BLOCKS = 4;
 
 struct TaskPlan {
   uint32_t mode = 0, n = 0, n_eff = 0, flags = 0, shots = 0;
@@ -139,6 +147,8 @@ struct DeviceState;  // engine.cu
 std::string json_escape(const std::string &s);
 std::string hex32(const uint8_t h[32]);
 void sha256(const void *data, size_t len, uint8_t out[32]);
+// FP32 arithmetic of a plan's persistent suffix launches (SV_AR_COMP or SV_AR_PLAIN)
+int plan_ar_batch(const qw_plan *P);
 void fingerprint(uint32_t n, uint32_t mode, const TaskData &t, uint64_t b, uint64_t e, uint8_t out[32]);
 bool legality(const qw_artifact_desc &a, uint32_t target_backend, const uint8_t *expected,
               qw_refusal *out);
@@ -155,7 +165,7 @@ struct Engine {
   double launch_ns = 4000;
   uint64_t store_budget = 0, task_budget = 0;
   void *stream = nullptr;
-  std::map<uint64_t, TileConfig> tiles;  // key: n << 1 | fp64
+  std::map<uint64_t, TileConfig> tiles;  // key: n << 3 | arithmetic << 1 | fp64
   std::map<uint64_t, double> dense_ms;    // measured dense-block pass times (autotuner cache)
   CostModel cm;
   float *d_mlp = nullptr;  // device copy of the MLP params
@@ -171,7 +181,12 @@ struct Engine {
   void dev_free(void *p, size_t bytes);
   void trim_cache();
   std::set<qw_plan *> plans;  // live plans (released when the engine is destroyed)
-  TileConfig tile_config(uint32_t n_eff, bool fp64);
+  // autotuned tile shape for FP32 arithmetic `ar` (SV_AR_PLAIN or SV_AR_COMP)
+  TileConfig tile_config(uint32_t n_eff, bool fp64, int ar);
+  static uint64_t tile_key(uint32_t n_eff, bool fp64, int ar) {
+    if (fp64 || ar == SV_AR_REM) ar = SV_AR_PLAIN;
+    return ((uint64_t)std::min<uint32_t>(n_eff, 26) << 3) | ((uint64_t)ar << 1) | (fp64 ? 1 : 0);
+  }
   double predict_log2ns(const float *feat, uint32_t rows, float *out);
   void *ensure_scratch(size_t bytes);
 };

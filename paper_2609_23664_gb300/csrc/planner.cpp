@@ -429,8 +429,11 @@ struct PlanCtx {
     TileConfig tc;
     tc.k_max = fp64 ? 12 : 13;
     tc.b = 4;
-    if (E) tc = E->tile_config(n_eff, fp64);
-    if (P->opts.tile_qubits) tc.k_max = std::min<uint32_t>(P->opts.tile_qubits, fp64 ? SV_MAX_TILE_FP64 : SV_MAX_TILE_FP32);
+    if (E) tc = E->tile_config(n_eff, fp64, fp64 ? SV_AR_PLAIN : plan_ar_batch(P));
+    const uint32_t kcap = fp64 ? SV_MAX_TILE_FP64
+                               : (plan_ar_batch(P) == SV_AR_PLAIN ? SV_MAX_TILE_FP32 : SV_MAX_TILE_FP32_COMP);
+    if (P->opts.tile_qubits) tc.k_max = std::min<uint32_t>(P->opts.tile_qubits, kcap);
+    tc.k_max = std::min<uint32_t>(tc.k_max, kcap);
     if (P->opts.low_qubits) tc.b = P->opts.low_qubits;
     if (tc.k_max < SV_G + 2) tc.k_max = SV_G + 2;
     if (tc.b + 2 > tc.k_max) tc.b = tc.k_max - 2;

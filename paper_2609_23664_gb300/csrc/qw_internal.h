@@ -92,6 +92,13 @@ __host__ __device__ constexpr uint32_t sv_op_index(uint32_t kind, uint32_t a, ui
 }
 constexpr int SV_MAX_TILE_FP32 = 14;
 constexpr int SV_MAX_TILE_FP64 = 13;
+// compensated FP32 passes keep a remainder plane beside the tile (16 bytes
+// of shared memory per amplitude), so their tiles stop at 2^13
+constexpr int SV_MAX_TILE_FP32_COMP = 13;
+// a compensated FP32 task whose program has more passes than this runs as
+// its own chain of launches that keeps the remainder (persistent launches
+// round at every stage, which suits short suffixes only)
+constexpr uint32_t SV_COMP_MAX_BATCH_PASSES = 8;
 
 struct HostOp {
   uint8_t kind, a, b;
@@ -284,8 +291,16 @@ TabHostProgram compile_tab(const qw_gate *gates, uint64_t n_gates, uint32_t n);
 struct SvTables {
   const SvPassDesc *passes;
   const SvStageDesc *stages;
-  const void *ops;  // SvOpDesc<T>*
+  const void *ops;       // SvOpDesc<T>*
+  const float *ops_lo;   // FP32: m[t] - (float)m[t] of every op, 8 floats per op (compensated passes)
 };
+// Arithmetic of FP32 statevector passes.  PLAIN: FP32 registers.  COMP:
+// double-float registers (every op exact to about 2^-48), the amplitude
+// rounded to FP32 when its stage writes it back.  REM: double-float
+// through the whole pass (a remainder plane beside the shared-memory tile)
+// and between passes (remainder arrays beside the state), so a chain of
+// passes rounds once, when it writes a state without its remainder.
+enum SvArith : int { SV_AR_PLAIN = 0, SV_AR_COMP = 1, SV_AR_REM = 2 };
 // A job of the persistent launch: one pass over one state (n_tiles tiles),
 // or the energy blocks of one state (kind SVJ_ENERGY, n_tiles blocks).
 enum SvJobKind : uint32_t { SVJ_PASS = 0, SVJ_ENERGY = 1 };
@@ -315,18 +330,21 @@ struct EnTables {
 // kernel attributes (dynamic shared memory limits); the first failure is returned
 cudaError_t sv_init_attrs();
 cudaError_t tab_init_attrs();
-int sv_threads_for_k(uint32_t k);
-size_t sv_smem_bytes(bool fp64, uint32_t k);
-// one pass over one state (grid = tiles)
+int sv_threads_for_k(uint32_t k, int ar = SV_AR_PLAIN);
+size_t sv_smem_bytes(bool fp64, uint32_t k, int ar = SV_AR_PLAIN);
+// one pass over one state (grid = tiles); ar applies to FP32 states; the
+// remainder arrays (float2 per amplitude, NULL allowed) to SV_AR_REM only
 void launch_sv_pass(bool fp64, const SvTables &t, uint32_t pass_idx, uint32_t k, uint32_t n,
-                    const void *src, void *dst, void *stream);
+                    const void *src, void *dst, void *stream, int ar = SV_AR_PLAIN,
+                    const void *src_lo = nullptr, void *dst_lo = nullptr);
 // persistent batch over jobs; counters: [0] = next item, [1] = error flag,
 // [2..] = per-job completed units (all zeroed by the caller beforehand).
-// Energy jobs need 128-thread CTAs (sv_threads_for_k(k_max) == 128).
+// Energy jobs need 128-thread CTAs (sv_threads_for_k(k_max) == 128).  ar:
+// SV_AR_PLAIN or SV_AR_COMP (FP32 states; SV_AR_REM is taken as PLAIN).
 void launch_sv_batch(bool fp64, const SvTables &t, const SvJob *jobs, const SvSeg *segs, uint32_t seg_bits,
                      uint32_t total_items, uint32_t k_max, unsigned int *counters, const EnTables &en,
-                     int grid, void *stream);
-int sv_batch_grid(bool fp64, uint32_t k, int sm_count);
+                     int grid, void *stream, int ar = SV_AR_PLAIN);
+int sv_batch_grid(bool fp64, uint32_t k, int sm_count, int ar = SV_AR_PLAIN);
 void launch_copy(const void *src, void *dst, size_t bytes, void *stream);
 
 // energy: per-block partials (2 doubles per block), then one reduction

@@ -18,6 +18,7 @@
 
 #include "energy_block.cuh"
 #include "qw_internal.h"
+#include "sv_df.cuh"
 
 namespace qw {
 
@@ -244,13 +245,73 @@ __device__ __forceinline__ uint32_t gray_pick(const uint32_t (&step)[6], int t) 
          : t == 5 ? step[5] : 0u;
 }
 
+// One stage group in compensated FP32: the 32 amplitudes at byte offsets
+// sbB ^ (XOR combinations of roff) are read with a zero remainder
+// (SV_AR_COMP) or with their remainder from the plane at lo_off
+// (SV_AR_REM), the stage's ops run in double-float, and the renormalized
+// pair is written back (SV_AR_COMP keeps only the rounded value).
+template <int AR>
+__device__ __forceinline__ void sv_stage_df(char *smw, uint32_t lo_off, uint32_t sbB, const uint32_t (&roff)[SV_G],
+                                            const SvOpDesc<float> *__restrict__ ops,
+                                            const float *__restrict__ ops_lo, uint32_t op_begin, uint32_t nops,
+                                            uint32_t rp_mask) {
+  float2 h[32], l[32];
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    const uint32_t off = sbB ^ ((i & 1) ? roff[0] : 0u) ^ ((i & 2) ? roff[1] : 0u) ^ ((i & 4) ? roff[2] : 0u) ^
+                         ((i & 8) ? roff[3] : 0u) ^ ((i & 16) ? roff[4] : 0u);
+    h[i] = *(const float2 *)(smw + off);
+    if constexpr (AR == SV_AR_REM) l[i] = *(const float2 *)(smw + lo_off + off);
+    else l[i] = make_float2(0.f, 0.f);
+  }
+  auto load_ml = [&](uint32_t o, float (&m)[8], float (&ml)[8]) {
+    load_m(ops + o, m);
+    const float4 u = __ldg((const float4 *)(ops_lo + 8 * (size_t)o));
+    const float4 v = __ldg((const float4 *)(ops_lo + 8 * (size_t)o + 4));
+    ml[0] = u.x; ml[1] = u.y; ml[2] = u.z; ml[3] = u.w;
+    ml[4] = v.x; ml[5] = v.y; ml[6] = v.z; ml[7] = v.w;
+  };
+  if (rp_mask) {
+    uint32_t o = op_begin;
+#pragma unroll
+    for (int P = 0; P < SV_G; P++) {
+      if (!(rp_mask & (1u << P))) continue;
+      float m[8], ml[8];
+      load_ml(o, m, ml);
+      o++;
+      df_rp_at(P, h, l, m, ml);
+    }
+  } else {
+    for (uint32_t o = 0; o < nops; o++) {
+      float m[8], ml[8];
+      load_ml(op_begin + o, m, ml);
+      df_apply_op(__ldg(&ops[op_begin + o].code), m, ml, h, l);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    df_renorm(h[i], l[i]);
+    const uint32_t off = sbB ^ ((i & 1) ? roff[0] : 0u) ^ ((i & 2) ? roff[1] : 0u) ^ ((i & 4) ? roff[2] : 0u) ^
+                         ((i & 8) ? roff[3] : 0u) ^ ((i & 16) ? roff[4] : 0u);
+    *(float2 *)(smw + off) = h[i];
+    if constexpr (AR == SV_AR_REM) *(float2 *)(smw + lo_off + off) = l[i];
+  }
+}
+
 // Processes one tile of one pass.  src == nullptr starts from |0...0>.
-template <typename T>
+// AR selects the arithmetic of FP32 passes: SV_AR_PLAIN, SV_AR_COMP
+// (double-float registers, rounded to FP32 when a stage writes its
+// amplitudes back) or SV_AR_REM (double-float kept through the whole pass
+// in a second shared-memory plane, and between passes in the remainder
+// arrays src_lo / dst_lo, either of which may be NULL: zero remainder on
+// load, none stored).  FP64 passes are plain.
+template <typename T, int AR>
 __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__restrict__ stages,
-                        const SvOpDesc<T> *__restrict__ ops, typename V2<T>::t *sm,
-                        const typename V2<T>::t *src, typename V2<T>::t *dst, uint32_t tile,
-                        bool cg) {
+                        const SvOpDesc<T> *__restrict__ ops, const float *__restrict__ ops_lo,
+                        typename V2<T>::t *sm, const typename V2<T>::t *src, typename V2<T>::t *dst,
+                        const float2 *src_lo, float2 *dst_lo, uint32_t tile) {
   typedef typename V2<T>::t C;
+  static_assert(AR == SV_AR_PLAIN || sizeof(T) == 4, "compensated arithmetic is for FP32 states");
   const uint32_t k = pd->k, b = pd->b, n_hi = pd->n_hi;
   uint32_t base = 0;
   for (uint32_t i = 0; i < n_hi; i++) base |= ((tile >> i) & 1u) << pd->hi_pos[i];
@@ -282,12 +343,18 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
   const uint32_t l0 = threadIdx.x * APU;
   const char *smc = (const char *)sm;
   char *smw = (char *)sm;
+  // SV_AR_REM: the remainder plane follows the tile, same slot layout
+  const uint32_t lo_off = ntile * (uint32_t)sizeof(C);
   if (src) {
     uint32_t g = base | gdep(l0), so = swz<T>(l0) * (uint32_t)sizeof(C);
 #pragma unroll
     for (int j = 0; j < 64; j++) {
       if ((uint32_t)j >= n_iter) break;
       cp_async16(smw + so, src + g);
+      if constexpr (AR == SV_AR_REM) {
+        if (src_lo) cp_async16(smw + lo_off + so, src_lo + g);
+        else *(float4 *)(smw + lo_off + so) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
       const int t = __ffs(j + 1) - 1;
       g ^= gray_pick(gstep, t);
       so ^= gray_pick(sstep, t);
@@ -300,9 +367,9 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
       v.x = (g == 0) ? T(1) : T(0);
       v.y = T(0);
       sm[swz<T>(l)] = v;
+      if constexpr (AR == SV_AR_REM) *(float2 *)(smw + lo_off + swz<T>(l) * (uint32_t)sizeof(C)) = make_float2(0.f, 0.f);
     }
   }
-  (void)cg;
   __syncthreads();
 
   // Stages.  The amplitude of logical tile index l sits in the slot of
@@ -331,6 +398,10 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
       uint32_t sbB = cst;
 #pragma unroll
       for (int t = 0; t < SV_MAX_GBITS; t++) sbB ^= ((grp >> t) & 1u) ? gcol[t] : 0u;
+      if constexpr (AR != SV_AR_PLAIN) {
+        sv_stage_df<AR>(smw, lo_off, sbB, roff, ops, ops_lo, op_begin, nops, rp_mask);
+        continue;
+      }
       C a[32];
 #pragma unroll
       for (int i = 0; i < 32; i++) {
@@ -385,6 +456,9 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
     for (int j = 0; j < 64; j++) {
       if ((uint32_t)j >= n_iter) break;
       *(float4 *)(dst + g) = *(const float4 *)(smc + so);
+      if constexpr (AR == SV_AR_REM) {
+        if (dst_lo) *(float4 *)(dst_lo + g) = *(const float4 *)(smc + lo_off + so);
+      }
       const int t = __ffs(j + 1) - 1;
       g ^= gray_pick(gstep, t);
       so ^= gray_pick(sstep, t);
@@ -410,6 +484,9 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
       for (int j = 0; j < 64; j++) {
         if ((uint32_t)j >= n_iter) break;
         *(float4 *)(dst + g) = *(const float4 *)(smc + (so & ~15u));
+        if constexpr (AR == SV_AR_REM) {
+          if (dst_lo) *(float4 *)(dst_lo + g) = *(const float4 *)(smc + lo_off + (so & ~15u));
+        }
         const int t = __ffs(j + 1) - 1;
         g ^= gray_pick(gstep, t);
         so ^= gray_pick(sstep, t);
@@ -423,6 +500,12 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
         if constexpr (sizeof(T) == 4) {
           const float2 a0 = *(const float2 *)(smc + so), a1 = *(const float2 *)(smc + (so ^ pair));
           *(float4 *)(dst + g) = make_float4(a0.x, a0.y, a1.x, a1.y);
+          if constexpr (AR == SV_AR_REM) {
+            if (dst_lo) {
+              const float2 r0 = *(const float2 *)(smc + lo_off + so), r1 = *(const float2 *)(smc + lo_off + (so ^ pair));
+              *(float4 *)(dst_lo + g) = make_float4(r0.x, r0.y, r1.x, r1.y);
+            }
+          }
         } else {
           *(double2 *)(dst + g) = *(const double2 *)(smc + so);
         }
@@ -434,13 +517,16 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 3 : 1))
-sv_pass_kernel(SvTables t, uint32_t pass, const typename V2<T>::t *src, typename V2<T>::t *dst) {
+// NT threads at most (the launch uses sv_threads_for_k), MINB CTAs per SM
+// for the register budget.
+template <typename T, int AR, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+sv_pass_kernel(SvTables t, uint32_t pass, const typename V2<T>::t *src, typename V2<T>::t *dst,
+               const float2 *src_lo, float2 *dst_lo) {
   extern __shared__ __align__(16) unsigned char smraw[];
   typedef typename V2<T>::t C;
-  sv_tile<T>(t.passes + pass, t.stages, (const SvOpDesc<T> *)t.ops, (C *)smraw, src, dst,
-             blockIdx.x, false);
+  sv_tile<T, AR>(t.passes + pass, t.stages, (const SvOpDesc<T> *)t.ops, t.ops_lo, (C *)smraw, src, dst, src_lo,
+                 dst_lo, blockIdx.x);
 }
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const unsigned int *p) {
@@ -465,8 +551,10 @@ constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per dependency wait
 // drains.
 // MINB: CTAs per SM the registers are budgeted for.  Tiles of 2^13 FP32
 // amplitudes (64 KB) fit three CTAs per SM; smaller tiles fit four, which
-// the 128-register build (MINB 4) can use.
-template <typename T, int MINB>
+// the 128-register build (MINB 4) can use.  Compensated passes (AR =
+// SV_AR_COMP) hold two FP32 complex values per amplitude in registers and
+// are budgeted for two CTAs.
+template <typename T, int MINB, int AR>
 __global__ void __launch_bounds__(128, MINB)
 sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, const SvSeg *__restrict__ segs,
                 uint32_t seg_bits, uint32_t total, unsigned int *ctr, EnTables en) {
@@ -519,8 +607,8 @@ sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, const SvSeg *__restr
       energy_block<T, 128, false>(J, s_unit, en.classes, en.terms,
                                   en.partials + 2 * (size_t)(J.block_begin + s_unit));
     } else {
-      sv_tile<T>(t.passes + job.pass, t.stages, (const SvOpDesc<T> *)t.ops, (C *)smraw, (const C *)job.src,
-                 (C *)job.dst, s_unit, true);
+      sv_tile<T, AR>(t.passes + job.pass, t.stages, (const SvOpDesc<T> *)t.ops, t.ops_lo, (C *)smraw,
+                     (const C *)job.src, (C *)job.dst, nullptr, nullptr, s_unit);
     }
     // every thread's writes of the unit precede thread 0's release through
     // the barrier (bar.sync orders them at CTA scope; the fence is
@@ -535,20 +623,30 @@ sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, const SvSeg *__restr
 
 // ---- host launchers -----------------------------------------------------------
 // 128 threads: every thread owns at least two stage groups of a 2^13 tile,
-// and three CTAs fit on an SM (registers and shared memory).
-int sv_threads_for_k(uint32_t k) {
-  const uint32_t g = 1u << (k - SV_G - 1);
-  return (int)(g < 32 ? 32 : (g > 128 ? 128 : g));
+// and three CTAs fit on an SM (registers and shared memory).  Passes with a
+// remainder plane (twice the shared memory, one CTA per SM) give every
+// stage group of the tile its own thread, up to 256.
+int sv_threads_for_k(uint32_t k, int ar) {
+  const uint32_t g = (ar == SV_AR_REM) ? 1u << (k - SV_G) : 1u << (k - SV_G - 1);
+  const uint32_t cap = (ar == SV_AR_REM) ? 256u : 128u;
+  return (int)(g < 32 ? 32 : (g > cap ? cap : g));
 }
-size_t sv_smem_bytes(bool fp64, uint32_t k) { return (size_t)(fp64 ? 16 : 8) << k; }
+size_t sv_smem_bytes(bool fp64, uint32_t k, int ar) {
+  return (size_t)(fp64 ? 16 : 8) << k << (ar == SV_AR_REM ? 1 : 0);
+}
 
 // Kernel attributes are set once, before any stream capture (a capture
 // fails on attribute changes).
 cudaError_t sv_init_attrs() {
   const int bytes = 200 * 1024;
-  const void *k[5] = {(const void *)sv_pass_kernel<float>, (const void *)sv_pass_kernel<double>,
-                      (const void *)sv_batch_kernel<float, 3>, (const void *)sv_batch_kernel<float, 4>,
-                      (const void *)sv_batch_kernel<double, 1>};
+  const void *k[] = {(const void *)sv_pass_kernel<float, SV_AR_PLAIN, 128, 3>,
+                     (const void *)sv_pass_kernel<float, SV_AR_COMP, 128, 2>,
+                     (const void *)sv_pass_kernel<float, SV_AR_REM, 256, 1>,
+                     (const void *)sv_pass_kernel<double, SV_AR_PLAIN, 128, 1>,
+                     (const void *)sv_batch_kernel<float, 3, SV_AR_PLAIN>,
+                     (const void *)sv_batch_kernel<float, 4, SV_AR_PLAIN>,
+                     (const void *)sv_batch_kernel<float, 2, SV_AR_COMP>,
+                     (const void *)sv_batch_kernel<double, 1, SV_AR_PLAIN>};
   for (const void *f : k) {
     const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
@@ -556,31 +654,43 @@ cudaError_t sv_init_attrs() {
   return cudaSuccess;
 }
 
-void launch_sv_pass(bool fp64, const SvTables &t, uint32_t pass_idx, uint32_t k, uint32_t n,
-                    const void *src, void *dst, void *stream) {
+void launch_sv_pass(bool fp64, const SvTables &t, uint32_t pass_idx, uint32_t k, uint32_t n, const void *src,
+                    void *dst, void *stream, int ar, const void *src_lo, void *dst_lo) {
   const uint32_t tiles = 1u << (n - k);
-  const int threads = sv_threads_for_k(k);
-  const size_t smem = sv_smem_bytes(fp64, k);
+  if (fp64) ar = SV_AR_PLAIN;
+  const int threads = sv_threads_for_k(k, ar);
+  const size_t smem = sv_smem_bytes(fp64, k, ar);
   cudaStream_t s = (cudaStream_t)stream;
+  const float2 *sl = (const float2 *)src_lo;
+  float2 *dl = (float2 *)dst_lo;
   if (fp64) {
-    sv_pass_kernel<double><<<tiles, threads, smem, s>>>(t, pass_idx, (const double2 *)src,
-                                                        (double2 *)dst);
+    sv_pass_kernel<double, SV_AR_PLAIN, 128, 1><<<tiles, threads, smem, s>>>(t, pass_idx, (const double2 *)src,
+                                                                              (double2 *)dst, nullptr, nullptr);
+  } else if (ar == SV_AR_REM) {
+    sv_pass_kernel<float, SV_AR_REM, 256, 1><<<tiles, threads, smem, s>>>(t, pass_idx, (const float2 *)src,
+                                                                           (float2 *)dst, sl, dl);
+  } else if (ar == SV_AR_COMP) {
+    sv_pass_kernel<float, SV_AR_COMP, 128, 2><<<tiles, threads, smem, s>>>(t, pass_idx, (const float2 *)src,
+                                                                            (float2 *)dst, nullptr, nullptr);
   } else {
-    sv_pass_kernel<float><<<tiles, threads, smem, s>>>(t, pass_idx, (const float2 *)src,
-                                                       (float2 *)dst);
+    sv_pass_kernel<float, SV_AR_PLAIN, 128, 3><<<tiles, threads, smem, s>>>(t, pass_idx, (const float2 *)src,
+                                                                             (float2 *)dst, nullptr, nullptr);
   }
 }
 
-int sv_batch_grid(bool fp64, uint32_t k, int sm_count) {
-  const int threads = sv_threads_for_k(k);
-  const size_t smem = sv_smem_bytes(fp64, k);
+int sv_batch_grid(bool fp64, uint32_t k, int sm_count, int ar) {
+  if (fp64 || ar == SV_AR_REM) ar = SV_AR_PLAIN;
+  const int threads = sv_threads_for_k(k, ar);
+  const size_t smem = sv_smem_bytes(fp64, k, ar);
   int per_sm = 0;
   if (fp64) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<double, 1>, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<double, 1, SV_AR_PLAIN>, threads, smem);
+  } else if (ar == SV_AR_COMP) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float, 2, SV_AR_COMP>, threads, smem);
   } else if (k <= 12) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float, 4>, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float, 4, SV_AR_PLAIN>, threads, smem);
   } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float, 3>, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float, 3, SV_AR_PLAIN>, threads, smem);
   }
   if (per_sm < 1) per_sm = 1;
   return per_sm * sm_count;
@@ -588,16 +698,23 @@ int sv_batch_grid(bool fp64, uint32_t k, int sm_count) {
 
 void launch_sv_batch(bool fp64, const SvTables &t, const SvJob *jobs, const SvSeg *segs, uint32_t seg_bits,
                      uint32_t total_items, uint32_t k_max, unsigned int *counters, const EnTables &en,
-                     int grid, void *stream) {
-  const int threads = sv_threads_for_k(k_max);
-  const size_t smem = sv_smem_bytes(fp64, k_max);
+                     int grid, void *stream, int ar) {
+  if (fp64 || ar == SV_AR_REM) ar = SV_AR_PLAIN;
+  const int threads = sv_threads_for_k(k_max, ar);
+  const size_t smem = sv_smem_bytes(fp64, k_max, ar);
   cudaStream_t s = (cudaStream_t)stream;
   if (fp64)
-    sv_batch_kernel<double, 1><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items, counters, en);
+    sv_batch_kernel<double, 1, SV_AR_PLAIN><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items,
+                                                                        counters, en);
+  else if (ar == SV_AR_COMP)
+    sv_batch_kernel<float, 2, SV_AR_COMP><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items,
+                                                                      counters, en);
   else if (k_max <= 12)
-    sv_batch_kernel<float, 4><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items, counters, en);
+    sv_batch_kernel<float, 4, SV_AR_PLAIN><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items,
+                                                                       counters, en);
   else
-    sv_batch_kernel<float, 3><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items, counters, en);
+    sv_batch_kernel<float, 3, SV_AR_PLAIN><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items,
+                                                                       counters, en);
 }
 
 }  // namespace qw

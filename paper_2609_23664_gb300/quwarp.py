@@ -26,6 +26,7 @@ QW_OK = 0
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "BUDGET", -4: "CUDA", -5: "DEVICE_TIMEOUT",
           -6: "STATE", -7: "BUFFER_TOO_SMALL", -8: "NOT_FOUND", -9: "UNSUPPORTED"}
 COST_ANALYTIC, COST_MLP = 0, 1
+FP32_COMPENSATED, FP32_PLAIN = 0, 1
 TASK_KEEP_STATE = 1
 MLP_IN, MLP_HID = 12, 64
 MLP_PARAMS = MLP_IN * MLP_HID + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID + 1
@@ -60,7 +61,8 @@ class qw_plan_opts(C.Structure):
                 ("tile_qubits", C.c_uint32), ("low_qubits", C.c_uint32), ("window", C.c_uint32),
                 ("use_graph", C.c_int32), ("fault_injection", C.c_int32),
                 ("fuse_energy", C.c_int32), ("pauli_frames", C.c_int32), ("handoff", C.c_int32),
-                ("prefix_fp64", C.c_int32), ("dense_boundaries", C.c_int32)]
+                ("prefix_fp64", C.c_int32), ("dense_boundaries", C.c_int32),
+                ("fp32_arith", C.c_int32)]
 
 
 class qw_cost_tuple(C.Structure):

@@ -4,6 +4,7 @@ on held-out engine timings, and that plans built with it stay exact."""
 import numpy as np
 import pytest
 
+from energy_tol import FP32_ENERGY_TOL, energy_error
 from oracle import oracle as orc
 from paper_2609_23664_gb300 import workloads as W
 
@@ -69,4 +70,4 @@ def test_planning_with_the_learned_model_stays_exact(trained):
     for i in range(0, len(tasks), 7):
         ref = orc.run_task(tasks[i])
         e, _ = plan.energy(i)
-        assert abs(e - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(tasks[i].terms["coef"])))
+        assert energy_error(e, ref["energy"], tasks[i].terms, tasks[i].n) <= FP32_ENERGY_TOL, i

@@ -5,6 +5,7 @@ unitaries on arbitrary qubits, 1 to 5 qubits), fused gate lists, and the
 import numpy as np
 import pytest
 
+from energy_tol import FP32_ENERGY_TOL, energy_error
 from oracle import oracle as orc
 from paper_2609_23664_gb300 import workloads as W
 
@@ -244,24 +245,31 @@ def test_plan_evolves_a_deep_local_boundary_with_dense_blocks(eng):
     # one dense pass over the state against hundreds of gates in a pass kernel
     assert ch[0]["used"] and ch[0]["dense_ms"] < ch[0]["pass_kernels_ms"]
     assert ch[0]["engine"] in ("tensor", "mixed")
-    for i in (0, len(tasks) - 1):
+    for i in range(len(tasks)):
         ref = orc.run_task(tasks[i])
         e, _ = plan.energy(i)
-        assert abs(e - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(tasks[i].terms["coef"])))
+        err = energy_error(e, ref["energy"], tasks[i].terms, tasks[i].n)
+        print("dense boundary (%d blocks) task %d energy error %.2e" % (ch[0]["blocks"], i, err))
+        assert err <= FP32_ENERGY_TOL, i
     plan.close()
 
 
 @pytest.mark.parametrize("mode", [1, 2])
 def test_dense_boundaries_keep_parity_on_the_vqe_sweep(eng, mode):
+    # a 20-layer prefix is ~100 dense blocks: beyond the accuracy budget of
+    # compensated FP32 (each 3xTF32 block perturbs the state at FP32 level),
+    # so the boundary keeps the compensated pass kernels, even when forced
     tasks = W.vqe24_sweep(n=16, n_tasks=4, n_terms=20)
     plan = Q.Plan(eng, Q.Workload(tasks), dense_boundaries=mode)
     plan.run()
     ch = plan.cost_record()["dense_boundaries"]
-    assert len(ch) == 1 and (ch[0]["used"] or mode == 1)
+    assert len(ch) == 1 and ch[0]["over_accuracy_budget"] and not ch[0]["used"]
     for i, t in enumerate(tasks):
         ref = orc.run_task(t)
         e, _ = plan.energy(i)
-        assert abs(e - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(t.terms["coef"]))), i
+        err = energy_error(e, ref["energy"], t.terms, t.n)
+        print("dense_boundaries %d task %d energy error %.2e" % (mode, i, err))
+        assert err <= FP32_ENERGY_TOL, (i, err)
     plan.close()
 
 

@@ -5,6 +5,7 @@ engines checked against closed forms."""
 import numpy as np
 import pytest
 
+from energy_tol import FP32_ENERGY_TOL, energy_error
 from oracle import oracle as orc
 from paper_2609_23664_gb300 import workloads as W
 
@@ -88,7 +89,7 @@ def test_identical_tasks_read_the_boundary(eng):
     assert ex["artifacts"] == 1 and ex["tasks_reusing"] == 5
     ref = orc.run_task(tasks[0])
     for i in range(5):
-        assert abs(p.energy(i)[0] - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(terms["coef"])))
+        assert energy_error(p.energy(i)[0], ref["energy"], terms, 14) <= FP32_ENERGY_TOL
 
 
 def test_ragged_mixed_workload(eng):
@@ -118,9 +119,10 @@ def test_ragged_mixed_workload(eng):
             assert np.array_equal(p.syndrome(i), orc.tab_run(t.n, t.gates)), i
         else:
             ref = orc.run_task(t)
-            assert abs(p.energy(i)[0] - ref["energy"]) <= (
-                tol(t.mode, ref["energy"]) if t.mode == W.MODE_SV_FP64
-                else 2e-5 * float(np.sum(np.abs(t.terms["coef"])))), i
+            if t.mode == W.MODE_SV_FP64:
+                assert abs(p.energy(i)[0] - ref["energy"]) <= tol(t.mode, ref["energy"]), i
+            else:
+                assert energy_error(p.energy(i)[0], ref["energy"], t.terms, t.n) <= FP32_ENERGY_TOL, i
 
 
 def test_largest_statevector_ghz_closed_form(eng):
@@ -194,7 +196,7 @@ def test_task_budget_is_shared_by_register_sizes():
     assert used < budget + (160 << 20), used
     for i in (0, 8):  # one task of each of the two smallest sizes
         ref = orc.run_task(tasks[i])
-        assert abs(p.energy(i)[0] - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(tasks[i].terms["coef"])))
+        assert energy_error(p.energy(i)[0], ref["energy"], tasks[i].terms, tasks[i].n) <= FP32_ENERGY_TOL
     p.close()
     wl.close()
     e.close()

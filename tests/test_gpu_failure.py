@@ -6,6 +6,7 @@ usable for the next plan."""
 import numpy as np
 import pytest
 
+from energy_tol import FP32_ENERGY_TOL, energy_error
 from oracle import oracle as orc
 from paper_2609_23664_gb300 import workloads as W
 
@@ -31,7 +32,7 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable():
     good.run()
     ref = orc.run_task(tasks[0])
     e, _ = good.energy(0)
-    assert abs(e - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(tasks[0].terms["coef"])))
+    assert energy_error(e, ref["energy"], tasks[0].terms, tasks[0].n) <= FP32_ENERGY_TOL
     eng.close()
 
 

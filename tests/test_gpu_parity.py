@@ -2,18 +2,18 @@
 same seeded inputs.
 
 Tolerances (stated by the target): FP64 statevector max-abs amplitude error
-<= 1e-12; FP32 statevector max-abs amplitude error <= 1e-5; tableau outcomes
-bit-exact.  Energies of FP32 states are compared against the oracle's energy
-of the same (FP32-rounded) input state within a bound derived from FP32
-products with compensated accumulation; against the exact FP64 evolution the
-per-task relative error is reported.  Sampling: a shot may differ from the
-oracle only where its uniform lies within 1e-5 of the CDF value at the
-oracle's outcome boundary."""
+<= 1e-12; FP32 statevector max-abs amplitude error <= 1e-5 and energy error
+<= 1e-6 relative to max(|E_ref|, E_typ) (energy_tol.py); tableau outcomes
+bit-exact.  The energy kernel alone is checked on FP32-representable states
+against the oracle's energy of the same state, within 4e-7 of the same
+scale.  Sampling: a shot may differ from the oracle only where its uniform
+lies within 1e-5 of the CDF value at the oracle's outcome boundary."""
 import math
 
 import numpy as np
 import pytest
 
+from energy_tol import FP32_ENERGY_TOL, energy_error, energy_ok
 from oracle import mlp_oracle as MO
 from oracle import oracle as orc
 from paper_2609_23664_gb300 import workloads as W
@@ -91,21 +91,24 @@ def test_sv_apply_every_gate_every_position(eng, mode):
                 assert np.max(np.abs(got - ref)) <= TOL_AMP[mode], (op, a, b)
 
 
-def energy_bound(terms, psi):
-    # |error| of FP32 products summed with compensation: a few ulps of the
-    # sum of absolute contributions
-    return 5e-7 * float(np.sum(np.abs(terms["coef"]))) * float(np.vdot(psi, psi).real) + 1e-12
+# The energy kernel's own error on an FP32 state: FP32 products and +-1
+# butterflies, accumulated in double-float then FP64.  Emulating its
+# operation order on random 14-qubit states gives errors of 7e-8 rms, 2e-7
+# max, relative to max(|E|, E_typ); 4e-7 leaves room while still seeing an
+# error of 1e-6.
+KERNEL_ENERGY_TOL = 4e-7
 
 
-@pytest.mark.parametrize("mode,n", [(W.MODE_SV_FP64, 6), (W.MODE_SV_FP64, 12), (W.MODE_SV_FP32, 10),
-                                    (W.MODE_SV_FP32, 15), (W.MODE_SV_FP32, 18)])
-def test_energy_dev(eng, mode, n):
+@pytest.mark.parametrize("mode,n,k", [(W.MODE_SV_FP64, 6, 60), (W.MODE_SV_FP64, 12, 60), (W.MODE_SV_FP32, 10, 60),
+                                      (W.MODE_SV_FP32, 15, 60), (W.MODE_SV_FP32, 18, 60),
+                                      (W.MODE_SV_FP32, 24, 200)])
+def test_energy_dev(eng, mode, n, k):
     rng = np.random.default_rng(200 + n)
     psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
     psi *= 1.3 / np.linalg.norm(psi)
     if mode == W.MODE_SV_FP32:
         psi = psi.astype(np.complex64).astype(np.complex128)
-    terms = W.random_pauli_hamiltonian(rng, n, 60)
+    terms = W.random_pauli_hamiltonian(rng, n, k)
     terms[0]["xmask"] = 0  # include diagonal and identity-like terms
     terms[1]["xmask"] = 0
     terms[1]["zmask"] = 0
@@ -113,8 +116,12 @@ def test_energy_dev(eng, mode, n):
     e, nr = Q.sv_energy_dev(eng, mode, n, st.data_ptr(), terms)
     e_ref, n_ref, _ = orc.energy(n, psi, terms)
     assert abs(nr - n_ref) <= (1e-13 if mode == W.MODE_SV_FP64 else 1e-6) * n_ref
-    tol = 1e-12 * max(1.0, abs(e_ref)) if mode == W.MODE_SV_FP64 else energy_bound(terms, psi)
-    assert abs(e - e_ref) <= tol, (e, e_ref, tol)
+    if mode == W.MODE_SV_FP64:
+        assert abs(e - e_ref) <= 1e-12 * max(1.0, abs(e_ref)), (e, e_ref)
+    else:
+        err = energy_error(e, e_ref, terms, n)
+        print("n %d: energy kernel error %.2e of max(|E|, E_typ)" % (n, err))
+        assert err <= KERNEL_ENERGY_TOL, (e, e_ref, err)
 
 
 def sample_agrees(got, ref, psi, u):
@@ -186,8 +193,8 @@ def test_vqe_fp32_small(eng, reuse, batched, graph):
     for i, t in enumerate(tasks):
         ref = orc.run_task(t, want_state=i < 2)
         e, nr = p.energy(i)
-        rel = abs(e - ref["energy"]) / max(abs(ref["energy"]), 1e-30)
-        assert abs(e - ref["energy"]) <= 2e-5 * float(np.sum(np.abs(t.terms["coef"]))), (i, rel)
+        err = energy_error(e, ref["energy"], t.terms, t.n)
+        assert err <= FP32_ENERGY_TOL, (i, err)
         assert abs(nr - 1.0) < 1e-5
         if i < 2:
             got = p.state(i, t.n, False).astype(np.complex128)
@@ -209,8 +216,7 @@ def test_energy_fused_into_the_suffix_launch(eng, mode, n):
         e, nr = p.energy(i)
         e2, nr2 = q.energy(i)
         c1 = float(np.sum(np.abs(t.terms["coef"])))
-        tol = 1e-12 * max(1.0, abs(ref["energy"])) if fp64 else 2e-5 * c1
-        assert abs(e - ref["energy"]) <= tol, (i, e, ref["energy"])
+        assert energy_ok(e, ref["energy"], t.terms, t.n, fp64), (i, e, ref["energy"])
         # the two launches differ only in the order of the block sums
         assert abs(e - e2) <= (1e-13 if fp64 else 1e-6) * c1, (i, e, e2)
         assert abs(nr - nr2) <= (1e-13 if fp64 else 1e-6)
@@ -301,8 +307,7 @@ def test_tableau_handoff_to_statevector(eng, mode, n):
     for i, t in enumerate(tasks):
         ref = orc.run_task(t, want_state=i < 2)
         e, nr = p.energy(i)
-        c1 = float(np.sum(np.abs(t.terms["coef"])))
-        assert abs(e - ref["energy"]) <= (1e-12 * max(1.0, abs(ref["energy"])) if fp64 else 2e-5 * c1), i
+        assert energy_ok(e, ref["energy"], t.terms, t.n, fp64), i
         assert abs(nr - 1.0) < (1e-12 if fp64 else 1e-5)
         if i < 2:
             got = p.state(i, n, fp64).astype(np.complex128)

@@ -6,6 +6,7 @@ plan options.  Every task is compared with the oracle."""
 import numpy as np
 import pytest
 
+from energy_tol import FP32_ENERGY_TOL, energy_error
 from oracle import oracle as orc
 from paper_2609_23664_gb300 import workloads as W
 
@@ -73,7 +74,7 @@ def check(p, tasks):
         if t.mode == W.MODE_SV_FP64:
             assert abs(e - ref["energy"]) <= 1e-11 * max(1.0, float(np.sum(np.abs(t.terms["coef"])))), i
         else:
-            assert abs(e - ref["energy"]) <= 2e-5 * max(1.0, float(np.sum(np.abs(t.terms["coef"])))), i
+            assert energy_error(e, ref["energy"], t.terms, t.n) <= FP32_ENERGY_TOL, i
         if t.shots:
             got = p.samples(i)
             pr = np.abs(ref["state"]) ** 2

@@ -46,16 +46,22 @@ CASES = [(W.MODE_SV_FP32, 7, 1), (W.MODE_SV_FP32, 8, 2), (W.MODE_SV_FP32, 9, 3),
          (W.MODE_SV_FP64, 7, 2), (W.MODE_SV_FP64, 10, 3), (W.MODE_SV_FP64, 12, 4), (W.MODE_SV_FP64, 13, 3)]
 
 
+@pytest.mark.parametrize("arith", [Q.FP32_COMPENSATED, Q.FP32_PLAIN])
 @pytest.mark.parametrize("mode,tile,low", CASES)
-def test_forced_tile_shapes_match_the_oracle(eng, mode, tile, low):
+def test_forced_tile_shapes_match_the_oracle(eng, mode, tile, low, arith):
+    if mode == W.MODE_SV_FP64 and arith == Q.FP32_PLAIN:
+        pytest.skip("FP64 passes have one arithmetic")
     n = 16
     rng = np.random.default_rng(4000 + 37 * tile + 5 * low + mode)
     pre = rand_gates(rng, n, 120)
     hea = W.hea_circuit(rng, n, 2)
     tasks = [W.Task(mode=mode, n=n, spans=[pre, hea, rand_gates(rng, n, 40)], want_state=True)
              for _ in range(3)]
-    p = Q.Plan(eng, Q.Workload(tasks), tile_qubits=tile, low_qubits=low)
+    p = Q.Plan(eng, Q.Workload(tasks), tile_qubits=tile, low_qubits=low, fp32_arith=arith)
     p.run()
+    # compensated FP32 tiles stop at 13 qubits (their remainder plane)
+    cap = 13 if (mode == W.MODE_SV_FP64 or arith == Q.FP32_COMPENSATED) else 14
+    assert all(k == min(tile, cap) for k, _ in p.cost_record()["wave_tiles"])
     for i, t in enumerate(tasks):
         got = p.state(i, n, mode == W.MODE_SV_FP64).astype(np.complex128)
         ref = orc.sv_run(n, t.gates)
