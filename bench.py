@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--no-replay", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-tasks", type=int, default=1)
+    ap.add_argument("--cpu-families", type=int, default=1,
+                    help="1: also time the oracle on every workload family (all cores and one core)")
     ap.add_argument("--qec-steps", type=int, default=3,
                     help="also time the QEC, noisy and small-VQE families (steps each); 0 = skip")
     ap.add_argument("--fuse-energy", type=int, default=0,
@@ -150,6 +152,19 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def fp32_peak_tflops(sm_count: int):
+    """FP32 peak from unit counts and the maximum SM clock: 128 FP32 lanes
+    per SM, an FMA counted as two operations."""
+    mhz, src = 2070.0, "maximum SM clock 2070 MHz (nominal)"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+        src = "maximum SM clock %.0f MHz (MEASURED_PEAKS.json)" % mhz
+    except Exception:
+        pass
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12, "%d SMs x 128 FP32 lanes x 2 (FMA) x %s" % (sm_count, src)
+
+
 def profiled_traffic(kernel: str, workload_key: str, field: str = "dram"):
     """DRAM bytes per launch from the committed ncu summary, if its source
     hash matches the kernel source compiled now (else None)."""
@@ -198,6 +213,99 @@ def oracle_tasks_per_s(a, n_tasks: int):
     energies = [orc.run_task(t)["energy"] for t in tasks]
     dt = time.perf_counter() - t0
     return n_tasks / dt, dt, orc.num_threads(), energies
+
+
+_ORACLE_TIMER = r"""
+import json, os, sys, time
+sys.path.insert(0, %r)
+from oracle import oracle as orc
+from paper_2609_23664_gb300 import workloads as W
+orc.build()
+fam, count, gate_frac, term_frac = %r, %d, %r, %r
+if fam == "vqe12_fp64":
+    tasks = W.vqe12_sweep()
+elif fam == "vqe24_fp32":
+    tasks = W.vqe24_sweep()
+elif fam == "noisy22":
+    tasks = W.noisy22_trajectories()
+elif fam == "qec_d15":
+    tasks = W.qec_surface_code_tasks()
+else:
+    tasks = [t for t in W.mixed_planned() if t.n <= 20]
+tasks = tasks[:count]
+t0 = time.perf_counter()
+tg = te = 0.0
+for t in tasks:
+    if t.mode == 2:
+        orc.tab_run(t.n, t.gates)
+    elif gate_frac is None:
+        orc.run_task(t)
+    else:
+        g = t.gates
+        a = time.perf_counter()
+        psi = orc.sv_run(t.n, g[:max(1, int(len(g) * gate_frac))])
+        b = time.perf_counter()
+        orc.energy(t.n, psi, t.terms[:max(1, int(len(t.terms) * term_frac))])
+        tg += b - a
+        te += time.perf_counter() - b
+print(json.dumps({"s": time.perf_counter() - t0, "threads": orc.num_threads(), "tasks": len(tasks),
+                  "gates_s": tg, "energy_s": te}))
+"""
+
+
+def oracle_time(family, count, threads=None, gate_frac=None, term_frac=None):
+    """Seconds the oracle takes for the first `count` tasks of a workload
+    family, in a fresh process (OMP_NUM_THREADS = threads when given);
+    with gate_frac / term_frac only that fraction of each task's gates and
+    Hamiltonian terms runs (for an extrapolated single-core figure)."""
+    env = dict(os.environ)
+    if threads:
+        env["OMP_NUM_THREADS"] = str(threads)
+    code = _ORACLE_TIMER % (ROOT, family, count, gate_frac, term_frac)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return None
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baselines(n_vqe24):
+    """The oracle (per-task rerun from |0...0>, complex128 / unpacked
+    tableau) on bounded samples of every workload family, on all host
+    cores and on one core."""
+    out = {}
+    specs = [
+        ("vqe12_fp64", 16, 16, "all 16 tasks (config 1, in full)", None),
+        ("vqe24_fp32", 256, 2, "2 of 256 tasks (config 2)", (0.125, 0.1)),
+        ("noisy22", 1024, 4, "4 of 1024 trajectories at 22 qubits (config 3)", None),
+        ("qec_d15", 4096, 8, "8 of 4096 tasks from |0...0>, 105 rounds each (config 4)", None),
+        ("mixed_n_le_20", 2000, 8, "the first 8 tasks with n <= 20 of the 2000-task mixed workload (config 5)",
+         None),
+    ]
+    for fam, total, count, sample, partial in specs:
+        allc = oracle_time(fam, count)
+        if not allc:
+            continue
+        ent = {"unit": "tasks/s", "kind": "oracle", "sample": sample, "tasks_in_workload": total,
+               "value": allc["tasks"] / allc["s"], "cores": allc["threads"], "seconds": allc["s"]}
+        if fam == "qec_d15":
+            # the tableau oracle's loops are sequential: one core either way
+            ent["cores"] = 1
+            ent["single_core_value"] = ent["value"]
+        elif partial:
+            one = oracle_time(fam, 1, threads=1, gate_frac=partial[0], term_frac=partial[1])
+            if one:
+                # gate passes and energy terms scale linearly with their count
+                est = one["gates_s"] / partial[0] + one["energy_s"] / partial[1]
+                ent["single_core_value"] = 1.0 / est
+                ent["single_core_note"] = ("extrapolated from %.1f%% of one task's gates and %.0f%% of its "
+                                           "terms on one core" % (100 * partial[0], 100 * partial[1]))
+        else:
+            one = oracle_time(fam, max(1, count // 4), threads=1)
+            if one:
+                ent["single_core_value"] = one["tasks"] / one["s"]
+        ent["extrapolated_workload_s"] = total / ent["value"]
+        out[fam] = ent
+    return out
 
 
 def run_reference(a):
@@ -258,10 +366,15 @@ def run_native(a):
     sptr = stream.cuda_stream
 
     wl = Q.Workload(tasks)
-    t0 = time.perf_counter()
-    plan = Q.Plan(eng, wl, **plan_opts(a))
-    planning_ms = (time.perf_counter() - t0) * 1e3
+    plan = Q.Plan(eng, wl, **plan_opts(a))   # the first plan also autotunes the tiles
     ex = plan.explain()
+    # planning time (host): median of three plans of the same workload
+    pts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        Q.Plan(eng, wl, **plan_opts(a)).close()
+        pts.append((time.perf_counter() - t0) * 1e3)
+    planning_ms = statistics.median(pts)
     for _ in range(max(1, a.warmup)):
         plan.execute(sptr)
         plan.wait()
@@ -273,16 +386,20 @@ def run_native(a):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     recs = []
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
     ev0.record(stream)
-    for _ in range(a.steps):
+    evs[0].record(stream)
+    for k in range(a.steps):
         plan.execute(sptr)
         plan.wait()
+        evs[k + 1].record(stream)
         recs.append(plan.cost_record())
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1) / a.steps
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(a.steps)]
     ms_max = max_over_ranks(ms, world)
     value = R.whole_job_rate(n_tasks, world, ms_max)
     cr = recs[-1]
@@ -298,34 +415,52 @@ def run_native(a):
     S = 8 << a.qubits
     batch_alg_bytes = float(cr.get("batch_alg_bytes", 0.0))
     energy_alg_bytes = float(cr.get("energy_alg_bytes", 0.0))
+    batch_flops = float(cr.get("batch_alg_flops", 0.0))
     wkey = "vqe%d_%dtasks" % (a.qubits, a.tasks)
-    if cr.get("energy_fused"):
-        # energy blocks run inside the persistent suffix launch: one kernel
-        # moves the pass bytes and the energy bytes
-        kern, dur, alg = "sv_batch_kernel", suffix_ms, batch_alg_bytes + energy_alg_bytes
-    elif energy_ms >= suffix_ms:
-        kern, dur, alg = "energy_kernel", energy_ms, energy_alg_bytes
-    else:
-        kern, dur, alg = "sv_batch_kernel", suffix_ms, batch_alg_bytes
-    achieved = alg / (dur * 1e-3) / 1e9
+    comp = cr.get("fp32_arith") == "compensated"
     l2_bytes = float(cr.get("energy_l2_bytes", 0.0))
-    l2_gbs = l2_bytes / (energy_ms * 1e-3) / 1e9 if energy_ms > 0 else None
     l2_peak = eng.probe_l2()
-    roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_src,
-                "traffic": profiled_traffic(kern, wkey),
-                "algorithmic_bytes_per_launch": alg, "launch_ms": dur,
-                "algorithmic_bytes": {"sv_batch_kernel": batch_alg_bytes, "energy_kernel": energy_alg_bytes},
-                # the energy kernel's partner reads are served by L2: its
-                # L2->SM bytes and rate against the L2 read bandwidth the
-                # engine measures for the same access pattern
-                "energy_l2": {"bytes": l2_bytes, "achieved_gbs": l2_gbs,
-                              "peak_gbs": l2_peak, "peak_source": "measured (qw_engine_probe_l2: hashed "
-                                                                  "64 KB blocks of an L2-resident buffer)",
-                              "frac": (l2_gbs / l2_peak) if (l2_gbs and l2_peak) else None,
-                              "ncu_lts_throughput_pct": profiled_traffic("energy_kernel", wkey, "lts_pct")},
-                "other_kernels_ms": {"sv_batch_kernel": suffix_ms, "energy": energy_ms,
-                                     "prefix_passes": prefix_ms}}
+    fp32_peak, fp32_src = fp32_peak_tflops(int(info["sm_count"]))
+
+    def hbm(alg, dur):
+        g = alg / (dur * 1e-3) / 1e9
+        return {"achieved": g, "peak": peak, "unit": "GB/s", "frac": g / peak, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": alg}
+
+    # the persistent suffix launch: compensated FP32 passes are bound by
+    # FP32 arithmetic (double-float: ~16 packed operations per two-term
+    # output), plain ones by latency against HBM
+    t_sv = batch_flops / (suffix_ms * 1e-3) / 1e12 if suffix_ms > 0 else 0.0
+    sv = {"kernel": "sv_batch_kernel", "launch_ms": suffix_ms, "fp32_arith": cr.get("fp32_arith"),
+          "hbm": hbm(batch_alg_bytes, suffix_ms),
+          "alu": {"achieved": t_sv, "peak": fp32_peak, "unit": "TFLOP/s", "frac": t_sv / fp32_peak,
+                  "peak_source": fp32_src, "algorithmic_flops_per_launch": batch_flops},
+          "traffic": profiled_traffic("sv_batch_kernel", wkey),
+          "traffic_source": "ncu dram__bytes of the committed capture (profiles/), scaled to the launch; "
+                            "null when the kernel source changed since"}
+    # the energy launch: every term's partner amplitudes come from L2
+    l2_gbs = l2_bytes / (energy_ms * 1e-3) / 1e9 if energy_ms > 0 else None
+    en = {"kernel": "energy_kernel", "launch_ms": energy_ms, "hbm": hbm(energy_alg_bytes, energy_ms),
+          "l2": {"achieved": l2_gbs, "peak": l2_peak, "unit": "GB/s",
+                 "frac": (l2_gbs / l2_peak) if (l2_gbs and l2_peak) else None,
+                 "peak_source": "measured in this run (qw_engine_probe_l2: hashed 64 KB blocks of an "
+                                "L2-resident buffer, the kernel's access pattern)",
+                 "algorithmic_bytes_per_launch": l2_bytes,
+                 "ncu_lts_throughput_pct": profiled_traffic("energy_kernel", wkey, "lts_pct")},
+          "traffic": profiled_traffic("energy_kernel", wkey),
+          "traffic_source": "ncu dram__bytes of the committed capture (profiles/), scaled to the launch; "
+                            "null when the kernel source changed since"}
+    if suffix_ms >= energy_ms:
+        b = "alu" if comp else "hbm"
+        sel = sv["alu"] if comp else sv["hbm"]
+        roofline = {"bound": b, "kernel": "sv_batch_kernel", "launch_ms": suffix_ms, "traffic": sv["traffic"]}
+    else:
+        b, sel = "l2", en["l2"]
+        roofline = {"bound": "l2", "kernel": "energy_kernel", "launch_ms": energy_ms, "traffic": en["traffic"]}
+    roofline.update({k: sel[k] for k in ("achieved", "peak", "unit", "frac", "peak_source")})
+    roofline["kernels"] = {"sv_batch_kernel": sv, "energy_kernel": en,
+                           "prefix_passes": {"ms": prefix_ms, "algorithmic_bytes": float(cr.get("prefix_alg_bytes", 0.0)),
+                                             "algorithmic_flops": float(cr.get("prefix_alg_flops", 0.0))}}
 
     line = {"metric": METRIC, "value": value, "unit": "tasks/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True,
@@ -336,7 +471,13 @@ def run_native(a):
                            n_tasks * S / 2 ** 30, info["l2_bytes"] / 1e6),
                        "parallelism": "replicas (one independent workload per GPU)"},
             "gpu_launches": launches * a.steps,
-            "planning_ms": planning_ms, "artifacts": ex["artifacts"],
+            "median_ms_per_step": statistics.median(step_ms),
+            "planning_ms": planning_ms,
+            # planning included: the workload planned once per execution
+            "planning_inclusive": {"value": world * n_tasks / ((ms_max + planning_ms) / 1e3), "unit": "tasks/s",
+                                   "ms_per_step": ms_max + planning_ms},
+            "fp32_arith": cr.get("fp32_arith"),
+            "artifacts": ex["artifacts"],
             "tiles": cr.get("wave_tiles"),
             "estimated_speedup": ex["estimated_speedup"],
             "engine_hbm_gbs": info["hbm_gbs"]}
@@ -472,6 +613,9 @@ def run_native(a):
                                     "median_rel_energy_error": float(np.median(rel)),
                                     "tasks_rel_above_1e-6": int(np.sum(rel > 1e-6)),
                                     "e_typ": e_typ, "max_error_over_max_absE_etyp": float(normed.max()),
+                                    "median_error_over_max_absE_etyp": float(np.median(normed)),
+                                    "tasks_above_tolerance": int(np.sum(normed > 1e-6)),
+                                    "tolerance": "1e-6 of max(|E_ref|, E_typ), E_typ = ||c||_2 2^(-n/2)",
                                     "reference": "oracle energies, complex128, tests/golden/vqe24_256_energies.json"}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         from oracle import oracle as orc
@@ -486,6 +630,9 @@ def run_native(a):
                                           "(%d gates each incl. shared prefix) + %d-term energy; "
                                           "%.1f s" % (a.cpu_sample_tasks, a.tasks,
                                                       tasks[0].n_gates, a.terms, dt)}
+        # the oracle on every workload family, all cores and one core
+        if a.cpu_families:
+            line["cpu_baselines"] = cpu_baselines(a.tasks)
     if rank == 0:
         print(json.dumps(line), flush=True)
     R.finish(world)

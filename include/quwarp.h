@@ -291,6 +291,20 @@ qw_status qw_get_syndrome(const qw_plan *p, uint64_t task, uint8_t *bits, size_t
  * 2^n complex numbers as interleaved (re, im) doubles (FP64 mode) or floats
  * (FP32 mode); `bytes` must equal that size. */
 qw_status qw_get_state(const qw_plan *p, uint64_t task, void *host_dst, size_t bytes);
+/* Final state of a tableau task submitted with QW_TASK_KEEP_STATE, as the
+ * stabilizer generators of the state (the STAB artifacts of Table II are
+ * stabilizer tableaus; Sec. IV-B): generator i (i < n) is
+ *   S_i = (-1)^sign[i] i^{popc(x_i & z_i)} X^{x_i} Z^{z_i},
+ * x and z row-major, n bytes per generator (one byte per qubit, 0/1), the
+ * image of Z_i under the task's circuit (measurements and resets included).
+ * They generate the task's stabilizer group; its canonical form (reduced
+ * row echelon over (x | z) with signs) equals the oracle's for the same
+ * circuit.  x, z: host, n_qubits * n_qubits bytes; sign: host, n_qubits
+ * bytes.  QW_ERR_NOT_FOUND without QW_TASK_KEEP_STATE (such a task never
+ * runs as a Pauli frame), QW_ERR_INVALID_ARG for a statevector task or a
+ * wrong n_qubits, QW_ERR_STATE before qw_execute. */
+qw_status qw_get_stabilizers(const qw_plan *p, uint64_t task, uint8_t *x, uint8_t *z, uint8_t *sign,
+                             size_t n_qubits);
 
 /* EXPLAIN trace (Sec. III-A; Sec. IV-B refusal record) and realized-cost
  * record (Sec. V-E metrics) as JSON.  Size-query idiom: with cap too small

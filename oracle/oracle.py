@@ -58,6 +58,8 @@ def lib():
             L.orc_sv_sample.restype = i
             L.orc_tab_run.argtypes = [i, c_p, sz, c_p, sz, ctypes.POINTER(sz), c_p, c_p, c_p]
             L.orc_tab_run.restype = i
+            L.orc_tab_run_from.argtypes = [i, c_p, c_p, c_p, c_p, sz, c_p, sz, ctypes.POINTER(sz), c_p, c_p, c_p]
+            L.orc_tab_run_from.restype = i
             L.orc_num_threads.restype = i
             _lib = L
     return _lib
@@ -163,6 +165,28 @@ def tab_run(n: int, gates: np.ndarray, want_tableau: bool = False):
     else:
         rc = lib().orc_tab_run(n, _ptr(g), len(g), _ptr(out), len(out), ctypes.byref(n_out),
                                None, None, None)
+    if rc != 0:
+        raise ValueError("oracle tableau run failed (rc=%d)" % rc)
+    outs = out[:n_out.value].copy()
+    return (outs, (x, z, r)) if want_tableau else outs
+
+
+def tab_run_from(n: int, tableau, gates: np.ndarray, want_tableau: bool = False):
+    """tab_run continued from a tableau (x, z, r) that tab_run exported."""
+    x0, z0, r0 = (np.ascontiguousarray(a, dtype=np.uint8) for a in tableau)
+    g = np.ascontiguousarray(gates)
+    n_meas = int(np.count_nonzero(g["op"] == 30))
+    out = np.zeros(max(n_meas, 1), dtype=np.uint8)
+    n_out = ctypes.c_size_t()
+    if want_tableau:
+        x = np.zeros((2 * n, n), dtype=np.uint8)
+        z = np.zeros((2 * n, n), dtype=np.uint8)
+        r = np.zeros(2 * n, dtype=np.uint8)
+        ptrs = (_ptr(x), _ptr(z), _ptr(r))
+    else:
+        ptrs = (None, None, None)
+    rc = lib().orc_tab_run_from(n, _ptr(x0), _ptr(z0), _ptr(r0), _ptr(g), len(g), _ptr(out), len(out),
+                                ctypes.byref(n_out), *ptrs)
     if rc != 0:
         raise ValueError("oracle tableau run failed (rc=%d)" % rc)
     outs = out[:n_out.value].copy()

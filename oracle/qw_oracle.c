@@ -336,6 +336,53 @@ static int tab_measure(tab *t, int a, int rand_bit) {
   return t->r[s];
 }
 
+/* Applies gates[0..n_gates) to the tableau t; outcomes as in orc_tab_run. */
+static int tab_apply(tab *t, const orc_gate *gates, size_t n_gates, uint8_t *outcomes, size_t cap_out,
+                     size_t *n_out) {
+  const int n = t->n;
+  size_t k_out = 0;
+  int rc = 0;
+  for (size_t k = 0; k < n_gates && rc == 0; k++) {
+    const orc_gate *g = &gates[k];
+    int a = (int)g->q0, b = (int)g->q1;
+    if (a < 0 || a >= n) { rc = -1; break; }
+    int two = (g->op == O_CNOT || g->op == O_CZ || g->op == O_SWAP);
+    if (two && (b < 0 || b >= n || a == b)) { rc = -1; break; }
+    switch (g->op) {
+      case O_H: tab_h(t, a); break;
+      case O_S: tab_s(t, a); break;
+      case O_SDG: tab_s(t, a); tab_s(t, a); tab_s(t, a); break;
+      case O_X: tab_pauli(t, a, 1, 0); break;
+      case O_Y: tab_pauli(t, a, 1, 1); break;
+      case O_Z: tab_pauli(t, a, 0, 1); break;
+      case O_CNOT: tab_cnot(t, a, b); break;
+      case O_CZ: tab_h(t, b); tab_cnot(t, a, b); tab_h(t, b); break;
+      case O_SWAP: tab_cnot(t, a, b); tab_cnot(t, b, a); tab_cnot(t, a, b); break;
+      case O_MEASURE: {
+        int o = tab_measure(t, a, (int)g->theta);
+        if (k_out >= cap_out) { rc = -3; break; }
+        outcomes[k_out++] = (uint8_t)o;
+        break;
+      }
+      case O_RESET: {
+        int o = tab_measure(t, a, (int)g->theta);
+        if (o) tab_pauli(t, a, 1, 0);
+        break;
+      }
+      default: rc = -1;
+    }
+  }
+  *n_out = k_out;
+  return rc;
+}
+
+static void tab_export(const tab *t, uint8_t *x_out, uint8_t *z_out, uint8_t *r_out) {
+  const size_t n = (size_t)t->n;
+  memcpy(x_out, t->x, 2 * n * n);
+  memcpy(z_out, t->z, 2 * n * n);
+  memcpy(r_out, t->r, 2 * n);
+}
+
 /*
  * Runs a tableau circuit from |0...0>.  Writes the outcome of every MEASURE
  * (in order) to `outcomes` (capacity cap_out); *n_out = number of MEASURE ops.
@@ -348,44 +395,31 @@ int orc_tab_run(int n, const orc_gate *gates, size_t n_gates, uint8_t *outcomes,
                 uint8_t *r_out) {
   tab t;
   if (tab_init(&t, n)) { tab_free(&t); return -2; }
-  size_t k_out = 0;
-  int rc = 0;
-  for (size_t k = 0; k < n_gates && rc == 0; k++) {
-    const orc_gate *g = &gates[k];
-    int a = (int)g->q0, b = (int)g->q1;
-    if (a < 0 || a >= n) { rc = -1; break; }
-    int two = (g->op == O_CNOT || g->op == O_CZ || g->op == O_SWAP);
-    if (two && (b < 0 || b >= n || a == b)) { rc = -1; break; }
-    switch (g->op) {
-      case O_H: tab_h(&t, a); break;
-      case O_S: tab_s(&t, a); break;
-      case O_SDG: tab_s(&t, a); tab_s(&t, a); tab_s(&t, a); break;
-      case O_X: tab_pauli(&t, a, 1, 0); break;
-      case O_Y: tab_pauli(&t, a, 1, 1); break;
-      case O_Z: tab_pauli(&t, a, 0, 1); break;
-      case O_CNOT: tab_cnot(&t, a, b); break;
-      case O_CZ: tab_h(&t, b); tab_cnot(&t, a, b); tab_h(&t, b); break;
-      case O_SWAP: tab_cnot(&t, a, b); tab_cnot(&t, b, a); tab_cnot(&t, a, b); break;
-      case O_MEASURE: {
-        int o = tab_measure(&t, a, (int)g->theta);
-        if (k_out >= cap_out) { rc = -3; break; }
-        outcomes[k_out++] = (uint8_t)o;
-        break;
-      }
-      case O_RESET: {
-        int o = tab_measure(&t, a, (int)g->theta);
-        if (o) tab_pauli(&t, a, 1, 0);
-        break;
-      }
-      default: rc = -1;
-    }
-  }
-  *n_out = k_out;
-  if (rc == 0 && x_out) {
-    memcpy(x_out, t.x, (size_t)2 * n * n);
-    memcpy(z_out, t.z, (size_t)2 * n * n);
-    memcpy(r_out, t.r, (size_t)2 * n);
-  }
+  int rc = tab_apply(&t, gates, n_gates, outcomes, cap_out, n_out);
+  if (rc == 0 && x_out) tab_export(&t, x_out, z_out, r_out);
+  tab_free(&t);
+  return rc;
+}
+
+/*
+ * The same algorithm continued from a given tableau: x_in/z_in/r_in are 2n
+ * rows in the layout orc_tab_run exports (the rows of an earlier run), the
+ * circuit is applied to them as orc_tab_run applies it to |0...0>.  The
+ * algorithm is deterministic, so orc_tab_run(prefix || suffix) equals
+ * orc_tab_run_from(rows after prefix, suffix) bit for bit (the outcomes of
+ * the suffix and the final rows); test code uses it to check many tasks
+ * that share one long prefix.
+ */
+int orc_tab_run_from(int n, const uint8_t *x_in, const uint8_t *z_in, const uint8_t *r_in,
+                     const orc_gate *gates, size_t n_gates, uint8_t *outcomes, size_t cap_out,
+                     size_t *n_out, uint8_t *x_out, uint8_t *z_out, uint8_t *r_out) {
+  tab t;
+  if (tab_init(&t, n)) { tab_free(&t); return -2; }
+  memcpy(t.x, x_in, 2 * (size_t)n * n);
+  memcpy(t.z, z_in, 2 * (size_t)n * n);
+  memcpy(t.r, r_in, 2 * (size_t)n);
+  int rc = tab_apply(&t, gates, n_gates, outcomes, cap_out, n_out);
+  if (rc == 0 && x_out) tab_export(&t, x_out, z_out, r_out);
   tab_free(&t);
   return rc;
 }

@@ -24,6 +24,7 @@ void plan_execute(qw_plan *P, void *stream);
 void plan_wait(qw_plan *P);
 void plan_release(qw_plan *P);
 void *plan_state_ptr(const qw_plan *P, uint64_t t);
+bool plan_tableau_keep(const qw_plan *P, uint64_t t, const uint64_t **rows, const uint8_t **sign);
 void engine_init(Engine *E, const qw_engine_opts *o);
 void engine_release(Engine *E);
 double engine_probe_l2(Engine *E);
@@ -314,6 +315,31 @@ qw_status qw_get_state(const qw_plan *p, uint64_t task, void *host_dst, size_t b
   })
 }
 
+qw_status qw_get_stabilizers(const qw_plan *p, uint64_t task, uint8_t *x, uint8_t *z, uint8_t *sign,
+                             size_t n_qubits) {
+  QW_GUARD({
+    const TaskPlan &tp = task_of(p, task);
+    if (tp.mode != QW_MODE_TABLEAU) fail(QW_ERR_INVALID_ARG, "task %llu is not a tableau task", (unsigned long long)task);
+    if (!(tp.flags & QW_TASK_KEEP_STATE))
+      fail(QW_ERR_NOT_FOUND, "task %llu was not submitted with QW_TASK_KEEP_STATE", (unsigned long long)task);
+    if (n_qubits != tp.n) fail(QW_ERR_INVALID_ARG, "task %llu has %u qubits", (unsigned long long)task, tp.n);
+    if (!x || !z || !sign) fail(QW_ERR_INVALID_ARG, "NULL output");
+    const uint64_t *rows = nullptr;
+    const uint8_t *sg = nullptr;
+    if (!p->eng || !p->executed || !plan_tableau_keep(p, task, &rows, &sg))
+      fail(QW_ERR_STATE, "the plan has not been executed, or its device memory was released");
+    const uint32_t n = tp.n;
+    const uint32_t W = (n + 63) / 64;
+    std::vector<uint64_t> hr((size_t)2 * n * 2 * W);
+    std::vector<uint8_t> hs(2 * (size_t)n);
+    cudaSetDevice(p->eng->device);
+    if (cudaMemcpy(hr.data(), rows, hr.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(hs.data(), sg, hs.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+      fail(QW_ERR_CUDA, "tableau copy failed");
+    stabilizers_from_inverse(n, hr.data(), hs.data(), x, z, sign);
+  })
+}
+
 static qw_status put_json(const std::string &s, char *buf, size_t cap, size_t *needed) {
   if (needed) *needed = s.size() + 1;
   if (!buf || cap < s.size() + 1) {
@@ -340,6 +366,7 @@ qw_status qw_cost_record_json(const qw_plan *p, char *buf, size_t cap, size_t *n
       "\"sampling_ms\":%.6f,\"tableau_tasks_ms\":%.6f,\"device_total_ms\":%.6f,"
       "\"kernel_launches\":%llu,\"h2d_bytes\":%llu,\"d2h_bytes\":%llu,"
       "\"batch_alg_bytes\":%.0f,\"energy_alg_bytes\":%.0f,\"energy_l2_bytes\":%.0f,\"prefix_alg_bytes\":%.0f,"
+      "\"batch_alg_flops\":%.0f,\"prefix_alg_flops\":%.0f,"
       "\"energy_fused\":%s,\"fp32_arith\":\"%s\","
       "\"artifacts\":%zu,\"artifact_bytes\":%llu,\"batch_ms\":[",
       p->planning_ns * 1e-6, p->est_direct_ns * 1e-6, p->est_plan_ns * 1e-6,
@@ -347,6 +374,7 @@ qw_status qw_cost_record_json(const qw_plan *p, char *buf, size_t cap, size_t *n
       p->t_prefix_ms, p->t_suffix_ms, p->t_energy_ms, p->t_sample_ms, p->t_tab_ms, p->t_total_ms,
       (unsigned long long)p->n_launches, (unsigned long long)p->h2d_bytes,
       (unsigned long long)p->d2h_bytes, p->batch_alg_bytes, p->energy_alg_bytes, p->energy_l2_bytes, p->prefix_alg_bytes,
+      p->batch_alg_flops, p->prefix_alg_flops,
       p->energy_fused ? "true" : "false", p->opts.fp32_arith == QW_FP32_PLAIN ? "plain" : "compensated",
       p->mats.size(), [&] {
         unsigned long long b = 0;

@@ -168,7 +168,7 @@ struct SvTableBuilder {
         SvStageDesc sd;
         memset(&sd, 0, sizeof(sd));
         uint32_t pm = 0;
-        for (int j = 0; j < SV_G; j++) {
+        for (uint32_t j = 0; j < pr.g; j++) {
           sd.roff[j] = slot(hs.mcol[hs.pos[j]]);
           pm |= 1u << hs.pos[j];
         }
@@ -228,7 +228,7 @@ struct SvTableBuilder {
         for (const HostOp &o : sops) {
           const uint32_t lo = std::min(o.a, o.b), hi = std::max(o.a, o.b);
           const uint32_t code = o.kind == K_CD ? sv_op_index(o.kind, lo, hi) : sv_op_index(o.kind, o.a, 0);
-          if (code >= SV_N_OP_INDEX || o.a >= SV_G || (o.kind == K_CD && (hi >= SV_G || lo == hi)))
+          if (code >= SV_N_OP_INDEX || o.a >= pr.g || (o.kind == K_CD && (hi >= pr.g || lo == hi)))
             fail(QW_ERR_STATE, "internal: op outside the stage dispatch table");
           if (fp64) {
             SvOpDesc<double> od{};
@@ -363,6 +363,9 @@ struct DeviceState {
     int frame;  // >= 0: preceded by the reference run and the frame launch of this frame group
   };
   std::vector<TabLaunch> tab_mat_launches, tab_task_launches;
+  // final inverse tableau of each tableau task submitted with
+  // QW_TASK_KEEP_STATE: 2n rows of 2W words, then 2n sign bytes elsewhere
+  std::vector<std::pair<const uint64_t *, const uint8_t *>> tab_keep;
   struct FrameLaunch {
     TabArgs ref;  // the reference suffix on the tableau (one CTA), outcomes and random flag
     FrameArgs fa;
@@ -397,6 +400,37 @@ static const void *chain_src_lo(const DeviceState *D, int ar, size_t p) {
 static void *chain_dst_lo(const DeviceState *D, int ar, size_t p, size_t n) {
   return (ar == SV_AR_REM && p + 1 < n) ? D->rem : nullptr;
 }
+// Algorithmic floating-point operations of one pass over 2^n amplitudes
+// (an FMA counts two, an add or a multiply one), from its stages' register
+// ops under the arithmetic `ar`, per group of A = 2^g amplitudes:
+//   plain: a real rotation output costs 6 (packed multiply + FMA on both
+//   components), a complex product 6, a general 2x2 output 14;
+//   compensated: every two-term output (df_lin2: 2 multiplies, 6 FMAs and
+//   8 adds per component) costs 44, a general 2x2 output two of them plus a
+//   double-float add (104), and every stage renormalizes each amplitude (6).
+static double pass_flops(const HostPass &hp, uint32_t n, uint32_t g, int ar) {
+  const bool comp = ar != SV_AR_PLAIN;
+  const double groups = std::ldexp(1.0, (int)n - (int)g), A = std::ldexp(1.0, (int)g);
+  const double lin = comp ? 44.0 : 6.0, cm = comp ? 44.0 : 6.0, u1 = comp ? 104.0 : 14.0;
+  double f = 0;
+  for (const HostStage &st : hp.stages) {
+    double fg = comp ? A * 6.0 : 0.0;
+    for (const HostOp &o : st.ops) {
+      switch (o.kind) {
+        case K_R: case K_RX: fg += A * lin; break;
+        case K_RP: fg += A * lin + A / 2 * cm; break;
+        case K_U1: fg += A * u1; break;
+        case K_D1: fg += A * cm; break;
+        case K_P1: fg += A / 2 * cm; break;
+        case K_CD: fg += (comp && o.m[0] == -1.0 && o.m[1] == 0.0) ? 0.0 : A / 4 * cm; break;
+        default: break;
+      }
+    }
+    f += fg * groups;
+  }
+  return f;
+}
+
 int plan_ar_batch(const qw_plan *P) {
   return P->opts.fp32_arith == QW_FP32_PLAIN ? SV_AR_PLAIN : SV_AR_COMP;
 }
@@ -494,6 +528,7 @@ static void prepare(qw_plan *P) {
     const size_t S = sv_state_bytes(f64, M.n_eff);
     // algorithmic bytes of the boundary's passes (state, and the remainder between passes)
     P->prefix_alg_bytes += chain_bytes((double)S, M.sv.passes.size(), ar);
+    for (const HostPass &hp : M.sv.passes) P->prefix_alg_flops += pass_flops(hp, M.n_eff, M.sv.g, ar);
     if (ar == SV_AR_REM && M.sv.passes.size() > 1) rem_bytes = std::max(rem_bytes, S);
   }
   for (uint32_t t = 0; t < nt; t++) {
@@ -839,6 +874,7 @@ static void prepare(qw_plan *P) {
             j.dst = D->task_state[t];
             j.pass = D->task_pass0[t] + (uint32_t)p;
             j.n_tiles = 1u << (tp.n_eff - (uint32_t)tp.sv.passes[p].q.size());
+            P->batch_alg_flops += pass_flops(tp.sv.passes[p], tp.n_eff, tp.sv.g, W.ar);
             j.dep = last[i];
             j.kind = SVJ_PASS;
             j.n = tp.n_eff;
@@ -1047,6 +1083,7 @@ static void prepare(qw_plan *P) {
     std::map<std::pair<int, uint32_t>, std::vector<uint32_t>> by_src;
     for (uint32_t t = 0; t < nt; t++)
       if (P->tasks[t].mode == QW_MODE_TABLEAU) by_src[{P->tasks[t].src, P->tasks[t].n}].push_back(t);
+    D->tab_keep.assign(nt, {nullptr, nullptr});
     for (auto &g : by_src) {
       std::vector<TabTaskDesc> descs;
       std::vector<TabSegment> segs;
@@ -1063,9 +1100,23 @@ static void prepare(qw_plan *P) {
         d.n_segs = (uint32_t)segs.size() - d.seg_begin;
         descs.push_back(d);
       }
+      // tasks that keep their final tableau: the whole launch writes its
+      // tableaus back (rows of every task, then the signs of every task)
+      bool keep = false;
+      for (uint32_t t : g.second) keep = keep || (P->tasks[t].flags & QW_TASK_KEEP_STATE);
+      void *keep_buf = nullptr;
+      const uint32_t kn = g.first.second, kW = (kn + 63) / 64;
+      const size_t kwords = (size_t)2 * kn * 2 * kW, nk = g.second.size();
+      if (keep) keep_buf = D->arena.alloc(nk * (kwords * 8 + 2 * kn));
       add_launch(D->tab_task_launches, g.first.second,
-                 g.first.first >= 0 ? D->mat_buf[g.first.first] : nullptr, nullptr, descs, segs,
+                 g.first.first >= 0 ? D->mat_buf[g.first.first] : nullptr, keep_buf, descs, segs,
                  D->d_outs);
+      if (keep) {
+        uint8_t *signs = (uint8_t *)((uint64_t *)keep_buf + nk * kwords);
+        D->tab_task_launches.back().a.out_sign = signs;
+        for (size_t k = 0; k < nk; k++)
+          D->tab_keep[g.second[k]] = {(const uint64_t *)keep_buf + k * kwords, signs + k * 2 * kn};
+      }
       const int fg = P->task_frame_group[g.second[0]];
       if (fg >= 0) {
         // Pauli frames: the reference suffix once on the tableau, then the
@@ -1379,6 +1430,13 @@ void *plan_state_ptr(const qw_plan *P, uint64_t t) {
   return P->dev ? P->dev->task_state[t] : nullptr;
 }
 
+bool plan_tableau_keep(const qw_plan *P, uint64_t t, const uint64_t **rows, const uint8_t **sign) {
+  if (!P->dev || t >= P->dev->tab_keep.size() || !P->dev->tab_keep[t].first) return false;
+  *rows = P->dev->tab_keep[t].first;
+  *sign = P->dev->tab_keep[t].second;
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // engine
 // ---------------------------------------------------------------------------
@@ -1555,7 +1613,7 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar) {
   TileConfig best;
   best.k_max = fp64 ? SV_MAX_TILE_FP64 : (ar == SV_AR_PLAIN ? SV_MAX_TILE_FP32 : SV_MAX_TILE_FP32_COMP);
   best.b = 4;
-  if (key_n <= best.k_max) { tiles[key] = best; return best; }
+  best.g = (ar == SV_AR_PLAIN) ? SV_G : SV_G_COMP;
   CK(cudaSetDevice(device));
   cudaStream_t s = (cudaStream_t)stream;
   std::mt19937_64 rng(12345);
@@ -1580,11 +1638,20 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar) {
   const uint32_t ks32[3] = {12, 13, 14}, ks64[3] = {11, 12, 13}, bs[3] = {3, 4, 5};
   float best_ms = 1e30f;
   const uint32_t best_cap = best.k_max;
+  // a register that fits one tile is timed with that single shape (its
+  // per-pass time calibrates the analytic cost model)
+  const bool one_tile = key_n <= best.k_max;
   for (int ki = 0; ki < 3; ki++) {
     for (int bi = 0; bi < 3; bi++) {
       TileConfig tc;
       tc.k_max = fp64 ? ks64[ki] : ks32[ki];
       tc.b = bs[bi];
+      tc.g = best.g;
+      if (one_tile) {
+        if (ki || bi) continue;
+        tc.k_max = best.k_max;
+        tc.b = best.b;
+      }
       if (tc.b + 2 > tc.k_max || tc.k_max > best_cap) continue;
       SvProgram pr = fuse_sv(g.data(), g.size(), key_n, tc);
       SvTableBuilder tb(fp64);
@@ -1608,7 +1675,11 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar) {
       }
       CK(cudaStreamSynchronize(s));
       dar.release();
-      if (tot < best_ms) { best_ms = tot; best = tc; }
+      if (tot < best_ms) {
+        best_ms = tot;
+        best = tc;
+        best.pass_ns = (double)tot * 1e6 / 2.0 / std::max<double>(1.0, (double)pr.passes.size());
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -1788,7 +1859,9 @@ void costmodel_probe(Engine *E, const Workload &W, float *feat, float *tgt, floa
       features_for(T, sg.first, sg.second, 1, tc, 0.0, feat + rows * QW_MLP_IN);
       tgt[rows] = (float)std::log2(std::max(1.0, (double)best * 1e6));
       if (analytic) {
-        const double ns = (double)pr.passes.size() * (2.0 * (double)S / E->hbm_gbs + E->launch_ns);
+        // the planner's analytic cost: passes x measured time per pass
+        const double per = tc.pass_ns > 0 ? tc.pass_ns : 2.0 * (double)S / E->hbm_gbs + E->launch_ns;
+        const double ns = (double)pr.passes.size() * per;
         analytic[rows] = (float)std::log2(std::max(1.0, ns));
       }
       rows++;

@@ -126,7 +126,7 @@ static void pass_groups(const qw_gate *gates, const std::vector<uint32_t> &masks
   }
 }
 
-// Stage cover of a pass's gates (positions = tile bits, at most SV_G per
+// Stage cover of a pass's gates (positions = tile bits, at most g per
 // stage).  Permutation gates hold no positions: a stage takes one unless an
 // earlier skipped gate shares a qubit with it, and it is applied after the
 // stage's other gates, so a later non-permutation gate on one of its qubits
@@ -134,7 +134,7 @@ static void pass_groups(const qw_gate *gates, const std::vector<uint32_t> &masks
 // gate or taken permutation shares a position with it and the positions it
 // reserves (cap_masks[i], a superset of masks[i]) still fit.
 static void stage_groups(const std::vector<uint32_t> &masks, const std::vector<uint32_t> &cap_masks,
-                         const std::vector<uint8_t> &perm, std::vector<std::vector<uint32_t>> &groups,
+                         const std::vector<uint8_t> &perm, uint32_t g, std::vector<std::vector<uint32_t>> &groups,
                          std::vector<uint32_t> &group_masks) {
   std::vector<uint32_t> rem(masks.size());
   for (uint32_t i = 0; i < rem.size(); i++) rem[i] = i;
@@ -158,10 +158,10 @@ static void stage_groups(const std::vector<uint32_t> &masks, const std::vector<u
       if (qs & (blocked | permq)) {
         blocked |= qs;
         keep.push_back(gi);
-      } else if ((uint32_t)popc32(Q | cs) <= (uint32_t)SV_G) {
+      } else if ((uint32_t)popc32(Q | cs) <= g) {
         Q |= cs;
         taken.push_back(gi);
-      } else if ((uint32_t)popc32(Q | qs) <= (uint32_t)SV_G && (qs & Q) == qs) {
+      } else if ((uint32_t)popc32(Q | qs) <= g && (qs & Q) == qs) {
         taken.push_back(gi);
       } else {
         blocked |= qs;
@@ -215,6 +215,9 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
   SvProgram prog;
   prog.n = n_eff;
   prog.n_gates = n_gates;
+  const uint32_t G = tc.g;
+  prog.g = G;
+  if (G != (uint32_t)SV_G && G != (uint32_t)SV_G_COMP) fail(QW_ERR_STATE, "internal: stage width %u", G);
   if (n_gates == 0) return prog;
   const uint32_t k = std::min(tc.k_max, n_eff);
   const bool single = (n_eff <= tc.k_max);
@@ -292,7 +295,7 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
     }
     std::vector<std::vector<uint32_t>> st_gates;
     std::vector<uint32_t> st_masks;
-    stage_groups(lmask, emask, lperm, st_gates, st_masks);
+    stage_groups(lmask, emask, lperm, G, st_gates, st_masks);
     // phi as columns M e_t and constant c
     uint32_t mcol[32], mc = 0, ctl_w[SV_MAX_OUT_CTL] = {0, 0, 0, 0};
     for (uint32_t t = 0; t < 32; t++) mcol[t] = 1u << t;
@@ -305,7 +308,7 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
       // only one that reaches bank bit 0 of a slot, so it is kept for the
       // lanes (group bits) where it spreads a warp's accesses over the banks
       uint32_t P = st_masks[s];
-      for (uint32_t q = k; q-- > 0 && popc32(P) < SV_G;) P |= 1u << q;
+      for (uint32_t q = k; q-- > 0 && popc32(P) < G;) P |= 1u << q;
       int rel[32];
       int j = 0;
       for (uint32_t q = 0; q < k; q++)
@@ -513,6 +516,70 @@ TabHostProgram compile_tab(const qw_gate *gates, uint64_t n_gates, uint32_t n) {
     }
   }
   return P;
+}
+
+}  // namespace qw
+
+namespace qw {
+
+// ---------------------------------------------------------------------------
+// forward stabilizers of a kept inverse tableau (host)
+// ---------------------------------------------------------------------------
+// The tableau kernels keep T(P) = C^-1 P C: row j < n is T(X_j), row n + j
+// is T(Z_j), each as W x-words then W z-words, and sign byte r (bit 0) of
+// the row (-1)^r i^{popc(x & z)} X^x Z^z.  The state C|0...0> has the
+// stabilizer generators S_i = C Z_i C^-1.  For the symplectic map T the
+// inverse is Omega M^T Omega, so S_i has X-bit j = x-bit i of T(Z_j) and
+// Z-bit j = x-bit i of T(X_j); its sign follows from T(S_i) = Z_i, with
+// T(i^{u.v} X^u Z^v) = i^{u.v} prod_{j in u} T(X_j) prod_{j in v} T(Z_j)
+// and Paulis kept as i^e X^x Z^z:
+//   (e1, x1, z1)(e2, x2, z2) = (e1 + e2 + 2 popc(z1 & x2), x1 ^ x2, z1 ^ z2).
+void stabilizers_from_inverse(uint32_t n, const uint64_t *rows, const uint8_t *sign, uint8_t *x, uint8_t *z,
+                              uint8_t *s) {
+  const uint32_t W = (n + 63) / 64;
+  auto xw = [&](uint32_t r, uint32_t w) { return rows[(size_t)r * 2 * W + w]; };
+  auto zw = [&](uint32_t r, uint32_t w) { return rows[(size_t)r * 2 * W + W + w]; };
+  auto xbit = [&](uint32_t r, uint32_t i) { return (uint32_t)((xw(r, i >> 6) >> (i & 63)) & 1ull); };
+  std::vector<uint64_t> ax(W), az(W);
+  for (uint32_t i = 0; i < n; i++) {
+    uint32_t e = 0;
+    std::fill(ax.begin(), ax.end(), 0ull);
+    std::fill(az.begin(), az.end(), 0ull);
+    uint32_t uv = 0;
+    for (uint32_t j = 0; j < n; j++) {
+      const uint32_t u = xbit(n + j, i), v = xbit(j, i);
+      x[(size_t)i * n + j] = (uint8_t)u;
+      z[(size_t)i * n + j] = (uint8_t)v;
+      uv += u & v;
+    }
+    e = uv & 3u;
+    // acc = i^{u.v} * prod_{j in u} T(X_j) * prod_{j in v} T(Z_j)
+    auto mul_row = [&](uint32_t r) {
+      uint32_t c = 0, own = 0;
+      for (uint32_t w = 0; w < W; w++) {
+        c += (uint32_t)__builtin_popcountll(az[w] & xw(r, w));
+        own += (uint32_t)__builtin_popcountll(xw(r, w) & zw(r, w));
+      }
+      const uint32_t er = (2u * (sign[r] & 1u) + own) & 3u;
+      e = (e + er + 2u * c) & 3u;
+      for (uint32_t w = 0; w < W; w++) {
+        ax[w] ^= xw(r, w);
+        az[w] ^= zw(r, w);
+      }
+    };
+    for (uint32_t j = 0; j < n; j++)
+      if (x[(size_t)i * n + j]) mul_row(j);
+    for (uint32_t j = 0; j < n; j++)
+      if (z[(size_t)i * n + j]) mul_row(n + j);
+    // acc must be i^e Z_i with e in {0, 2}
+    bool ok = (e & 1u) == 0;
+    for (uint32_t w = 0; w < W && ok; w++) {
+      const uint64_t zi = ((i >> 6) == w) ? (1ull << (i & 63)) : 0ull;
+      ok = ax[w] == 0ull && az[w] == zi;
+    }
+    if (!ok) fail(QW_ERR_STATE, "the kept tableau is not a valid stabilizer tableau");
+    s[i] = (uint8_t)(e == 2 ? 1 : 0);  // S_i = i^{-e} i^{u.v} X^u Z^v
+  }
 }
 
 }  // namespace qw

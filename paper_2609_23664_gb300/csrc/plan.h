@@ -231,6 +231,7 @@ struct qw_plan {
   std::vector<double> batch_ms;  // per wave: suffix launch(es) only
   uint64_t n_launches = 0, h2d_bytes = 0, d2h_bytes = 0;
   double batch_alg_bytes = 0, energy_alg_bytes = 0, energy_l2_bytes = 0, prefix_alg_bytes = 0;
+  double batch_alg_flops = 0, prefix_alg_flops = 0;  // gate arithmetic of the suffix passes / boundaries
   bool energy_fused = false;  // energy blocks ran inside the persistent suffix launch
   std::vector<std::pair<uint32_t, uint32_t>> wave_tiles;  // (tile qubits, low qubits) per wave
   std::vector<qw::DenseChoice> dense_choices;  // option dense_boundaries

@@ -429,6 +429,7 @@ struct PlanCtx {
     TileConfig tc;
     tc.k_max = fp64 ? 12 : 13;
     tc.b = 4;
+    tc.g = (fp64 || plan_ar_batch(P) == SV_AR_PLAIN) ? SV_G : SV_G_COMP;
     if (E) tc = E->tile_config(n_eff, fp64, fp64 ? SV_AR_PLAIN : plan_ar_batch(P));
     const uint32_t kcap = fp64 ? SV_MAX_TILE_FP64
                                : (plan_ar_batch(P) == SV_AR_PLAIN ? SV_MAX_TILE_FP32 : SV_MAX_TILE_FP32_COMP);
@@ -465,7 +466,9 @@ struct PlanCtx {
   }
 
   // analytic cost of executing gates [b, e) of task t (Sec. VI-D gate-count
-  // proxy calibrated by passes x bytes / measured bandwidth)
+  // proxy): estimated passes x the time of one pass, measured by the
+  // engine for this register size, precision and arithmetic when it tuned
+  // the tile shape (else bytes / measured bandwidth + a launch)
   double seg_cost(const TaskData &t, uint32_t mode, uint64_t b, uint64_t e) {
     if (e <= b) return 0.0;
     const double S = state_bytes(mode, t.n);
@@ -473,7 +476,7 @@ struct PlanCtx {
     const uint32_t n_eff = std::max<uint32_t>(t.n, SV_G);
     TileConfig tc = tiles(n_eff, mode == QW_MODE_SV_FP64);
     const double p = estimate_passes(e - b, n_eff, tc, gates_per_pass(mode, t.n, t));
-    return p * (2.0 * S / bw_gbs + launch_ns);
+    return p * (tc.pass_ns > 0 ? tc.pass_ns : 2.0 * S / bw_gbs + launch_ns);
   }
 
   bool cost_mlp(const TaskData &t, uint64_t b, uint64_t e, uint32_t sharing, double *ns) {
@@ -801,6 +804,10 @@ static void build_frame_groups(qw_plan *P, const Workload &W) {
   for (auto &c : cand) {
     const std::vector<uint32_t> &tasks = c.second;
     if (tasks.size() < 2) continue;
+    // a task that keeps its final tableau runs on its own tableau
+    bool keep = false;
+    for (uint32_t t : tasks) keep = keep || (P->tasks[t].flags & QW_TASK_KEEP_STATE);
+    if (keep) continue;
     FrameGroup G;
     G.src = c.first.first;
     G.n = c.first.second;
@@ -1112,7 +1119,17 @@ void build_plan(qw_plan *P, Engine *E, const Workload &W) {
           s += strf("%s\"%s\"", first_e ? "" : ",", backend_name(backend_of_mode(md)));
           first_e = false;
         }
-      s += "]},";
+      // a consumer of another precision or representation reads the
+      // artifact rounded once into its own precision (FP64 -> FP32, or the
+      // tableau's amplitudes +-i^e 2^(-k/2) written in FP32 / FP64)
+      s += "],\"consumer_exactness\":{";
+      first_e = true;
+      for (uint32_t md = 0; md < 2; md++)
+        if ((M.export_modes >> md) & 1u) {
+          s += strf("%s\"%s\":\"EXACT_UP_TO_ONE_ROUNDING\"", first_e ? "" : ",", backend_name(backend_of_mode(md)));
+          first_e = false;
+        }
+      s += "}},";
     } else {
       s += "\"artifact\":null,";
     }

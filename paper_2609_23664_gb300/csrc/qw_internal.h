@@ -75,6 +75,9 @@ enum SvKind : uint8_t {
   K_RP = 9,    // diag(1, p) after a real 2x2 on a: m = {r00, r01, r10, r11, pr, pi}
 };
 constexpr int SV_G = 5;            // positions per stage (32 register amplitudes)
+// Compensated FP32 passes hold two FP32 complex values per amplitude in
+// registers, so their stages take four positions (16 amplitudes)
+constexpr int SV_G_COMP = 4;
 
 // Dense index of an op for the kernels' jump table: each one-position kind
 // takes SV_G consecutive slots (its stage position), the controlled phase
@@ -134,6 +137,7 @@ struct HostPass {
 };
 struct SvProgram {
   uint32_t n = 0;  // effective qubit count (>= SV_G)
+  uint32_t g = SV_G;  // positions per stage (SV_G, or SV_G_COMP for compensated FP32)
   std::vector<HostPass> passes;
   uint64_t n_gates = 0;
 };
@@ -141,6 +145,10 @@ struct SvProgram {
 struct TileConfig {
   uint32_t k_max = 13;  // tile qubits
   uint32_t b = 4;       // contiguous low qubits in every tile
+  uint32_t g = SV_G;    // positions per stage
+  // measured time of one pass of the autotuning circuit with this tile
+  // shape and arithmetic (ns, launch included); 0 = not measured
+  double pass_ns = 0;
 };
 
 // Shared-memory swizzle of a tile (amplitude index -> slot).  It XORs bits
@@ -284,6 +292,11 @@ struct TabHostProgram {
 };
 // compiles a Clifford gate run (n qubits) into layers of independent row ops
 TabHostProgram compile_tab(const qw_gate *gates, uint64_t n_gates, uint32_t n);
+// forward stabilizer generators S_i = C Z_i C^-1 of a kept inverse tableau
+// (2n rows of 2W words, 2n sign bytes): x, z n*n bytes (row i = S_i), s n
+// bytes, S_i = (-1)^s i^{popc(x & z)} X^x Z^z
+void stabilizers_from_inverse(uint32_t n, const uint64_t *rows, const uint8_t *sign, uint8_t *x, uint8_t *z,
+                              uint8_t *s);
 
 // ---------------------------------------------------------------------------
 // kernel launchers (defined in the .cu files)
@@ -301,6 +314,8 @@ struct SvTables {
 // and between passes (remainder arrays beside the state), so a chain of
 // passes rounds once, when it writes a state without its remainder.
 enum SvArith : int { SV_AR_PLAIN = 0, SV_AR_COMP = 1, SV_AR_REM = 2 };
+// stage positions of a pass kernel with arithmetic `ar`
+QW_HD constexpr int sv_stage_width(int ar) { return ar == SV_AR_PLAIN ? SV_G : SV_G_COMP; }
 // A job of the persistent launch: one pass over one state (n_tiles tiles),
 // or the energy blocks of one state (kind SVJ_ENERGY, n_tiles blocks).
 enum SvJobKind : uint32_t { SVJ_PASS = 0, SVJ_ENERGY = 1 };

@@ -74,18 +74,18 @@ __device__ __forceinline__ void df_renorm(float2 &h, float2 &l) {
   h = s;
 }
 
-// ---- register operations on the 32 amplitudes of a stage group ------------
+// ---- register operations on the N = 2^G amplitudes of a stage group ------
 // m / ml: the op's parameters (see SvKind) and their FP32 remainders.
 
 // real 2x2 {r00, r01; r10, r11} on position P, then (when phase) diag(1, p)
 // with p = (m[4], m[5]): K_RP layout {r00, r01, r10, r11, pr, pi}
-template <int P>
-__device__ __forceinline__ void dfop_rp(float2 (&h)[32], float2 (&l)[32], const float (&m)[8], const float (&ml)[8],
+template <int P, int N>
+__device__ __forceinline__ void dfop_rp(float2 (&h)[N], float2 (&l)[N], const float (&m)[8], const float (&ml)[8],
                                         bool phase) {
   const float2 r00 = f2s(m[0]), r01 = f2s(m[1]), r10 = f2s(m[2]), r11 = f2s(m[3]);
   const float2 e00 = f2s(ml[0]), e01 = f2s(ml[1]), e10 = f2s(ml[2]), e11 = f2s(ml[3]);
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
+  for (int i = 0; i < N; i++) {
     if (i & (1 << P)) continue;
     const int j = i | (1 << P);
     const float2 xh = h[i], xl = l[i], yh = h[j], yl = l[j];
@@ -95,12 +95,12 @@ __device__ __forceinline__ void dfop_rp(float2 (&h)[32], float2 (&l)[32], const 
   }
 }
 // K_R layout {r00, 0, r01, 0, r10, 0, r11, 0}
-template <int P>
-__device__ __forceinline__ void dfop_r(float2 (&h)[32], float2 (&l)[32], const float (&m)[8], const float (&ml)[8]) {
+template <int P, int N>
+__device__ __forceinline__ void dfop_r(float2 (&h)[N], float2 (&l)[N], const float (&m)[8], const float (&ml)[8]) {
   const float2 r00 = f2s(m[0]), r01 = f2s(m[2]), r10 = f2s(m[4]), r11 = f2s(m[6]);
   const float2 e00 = f2s(ml[0]), e01 = f2s(ml[2]), e10 = f2s(ml[4]), e11 = f2s(ml[6]);
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
+  for (int i = 0; i < N; i++) {
     if (i & (1 << P)) continue;
     const int j = i | (1 << P);
     const float2 xh = h[i], xl = l[i], yh = h[j], yl = l[j];
@@ -109,10 +109,10 @@ __device__ __forceinline__ void dfop_r(float2 (&h)[32], float2 (&l)[32], const f
   }
 }
 // general 2x2 {u00, u01; u10, u11}, complex entries (re, im) in m[0..7]
-template <int P>
-__device__ __forceinline__ void dfop_u1(float2 (&h)[32], float2 (&l)[32], const float (&m)[8], const float (&ml)[8]) {
+template <int P, int N>
+__device__ __forceinline__ void dfop_u1(float2 (&h)[N], float2 (&l)[N], const float (&m)[8], const float (&ml)[8]) {
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
+  for (int i = 0; i < N; i++) {
     if (i & (1 << P)) continue;
     const int j = i | (1 << P);
     const float2 xh = h[i], xl = l[i], yh = h[j], yl = l[j];
@@ -131,27 +131,27 @@ __device__ __forceinline__ void dfop_u1(float2 (&h)[32], float2 (&l)[32], const 
   }
 }
 // diag(d0, d1): m = {d0r, d0i, d1r, d1i}
-template <int P>
-__device__ __forceinline__ void dfop_d1(float2 (&h)[32], float2 (&l)[32], const float (&m)[8], const float (&ml)[8]) {
+template <int P, int N>
+__device__ __forceinline__ void dfop_d1(float2 (&h)[N], float2 (&l)[N], const float (&m)[8], const float (&ml)[8]) {
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
+  for (int i = 0; i < N; i++) {
     const int o = (i & (1 << P)) ? 2 : 0;
     df_cmul(m[o], ml[o], m[o + 1], ml[o + 1], h[i], l[i]);
   }
 }
 // diag(1, p): m = {pr, pi}
-template <int P>
-__device__ __forceinline__ void dfop_p1(float2 (&h)[32], float2 (&l)[32], const float (&m)[8], const float (&ml)[8]) {
+template <int P, int N>
+__device__ __forceinline__ void dfop_p1(float2 (&h)[N], float2 (&l)[N], const float (&m)[8], const float (&ml)[8]) {
 #pragma unroll
-  for (int i = 0; i < 32; i++)
+  for (int i = 0; i < N; i++)
     if (i & (1 << P)) df_cmul(m[0], ml[0], m[1], ml[1], h[i], l[i]);
 }
 // amplitudes with bits A and B set times p = {pr, pi}; p = -1 (CZ) negates
-template <int A, int B>
-__device__ __forceinline__ void dfop_cd(float2 (&h)[32], float2 (&l)[32], const float (&m)[8], const float (&ml)[8]) {
+template <int A, int B, int N>
+__device__ __forceinline__ void dfop_cd(float2 (&h)[N], float2 (&l)[N], const float (&m)[8], const float (&ml)[8]) {
   const bool neg = m[0] == -1.f && m[1] == 0.f && ml[0] == 0.f && ml[1] == 0.f;
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
+  for (int i = 0; i < N; i++) {
     if (!(i & (1 << A)) || !(i & (1 << B))) continue;
     if (neg) {
       h[i] = f2neg(h[i]);
@@ -164,12 +164,12 @@ __device__ __forceinline__ void dfop_cd(float2 (&h)[32], float2 (&l)[32], const 
 // [[c, -is], [-is, c]]: m = {c, s}
 //   x' = c x - i s y = c (xr, xi) + (s, -s) (yi, yr)
 //   y' = c y - i s x = c (yr, yi) + (s, -s) (xi, xr)
-template <int P>
-__device__ __forceinline__ void dfop_rx(float2 (&h)[32], float2 (&l)[32], const float (&m)[8], const float (&ml)[8]) {
+template <int P, int N>
+__device__ __forceinline__ void dfop_rx(float2 (&h)[N], float2 (&l)[N], const float (&m)[8], const float (&ml)[8]) {
   const float2 c = f2s(m[0]), cl = f2s(ml[0]);
   const float2 s = make_float2(m[1], -m[1]), sl = make_float2(ml[1], -ml[1]);
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
+  for (int i = 0; i < N; i++) {
     if (i & (1 << P)) continue;
     const int j = i | (1 << P);
     const float2 xh = h[i], xl = l[i], yh = h[j], yl = l[j];
@@ -178,29 +178,26 @@ __device__ __forceinline__ void dfop_rx(float2 (&h)[32], float2 (&l)[32], const 
   }
 }
 
-// dispatch on the dense op index (the same table as the plain kernels)
-__device__ __forceinline__ void df_apply_op(uint32_t code, const float (&m)[8], const float (&ml)[8], float2 (&h)[32],
-                                            float2 (&l)[32]) {
+// dispatch on the dense op index (the same table as the plain kernels);
+// positions beyond the group (1 << P >= N) never occur in its programs
+template <int N>
+__device__ __forceinline__ void df_apply_op(uint32_t code, const float (&m)[8], const float (&ml)[8], float2 (&h)[N],
+                                            float2 (&l)[N]) {
   switch (code) {
-#define U1(P) case sv_op_index(K_U1, P, 0): dfop_u1<P>(h, l, m, ml); break;
-#define D1(P) case sv_op_index(K_D1, P, 0): dfop_d1<P>(h, l, m, ml); break;
-#define P1(P) case sv_op_index(K_P1, P, 0): dfop_p1<P>(h, l, m, ml); break;
-#define RR(P) case sv_op_index(K_R, P, 0): dfop_r<P>(h, l, m, ml); break;
-#define RX(P) case sv_op_index(K_RX, P, 0): dfop_rx<P>(h, l, m, ml); break;
-#define RP(P) case sv_op_index(K_RP, P, 0): dfop_rp<P>(h, l, m, ml, true); break;
-    U1(0) U1(1) U1(2) U1(3) U1(4)
-    D1(0) D1(1) D1(2) D1(3) D1(4)
-    P1(0) P1(1) P1(2) P1(3) P1(4)
-    RR(0) RR(1) RR(2) RR(3) RR(4)
-    RX(0) RX(1) RX(2) RX(3) RX(4)
+#define QW_ONE(K, P, F) \
+  case sv_op_index(K, P, 0): if constexpr ((1 << P) < N) F<P, N>(h, l, m, ml); break;
+#define QW_ALL(K, F) QW_ONE(K, 0, F) QW_ONE(K, 1, F) QW_ONE(K, 2, F) QW_ONE(K, 3, F) QW_ONE(K, 4, F)
+    QW_ALL(K_U1, dfop_u1)
+    QW_ALL(K_D1, dfop_d1)
+    QW_ALL(K_P1, dfop_p1)
+    QW_ALL(K_R, dfop_r)
+    QW_ALL(K_RX, dfop_rx)
+#undef QW_ALL
+#undef QW_ONE
+#define RP(P) case sv_op_index(K_RP, P, 0): if constexpr ((1 << P) < N) dfop_rp<P, N>(h, l, m, ml, true); break;
     RP(0) RP(1) RP(2) RP(3) RP(4)
-#undef U1
-#undef D1
-#undef P1
-#undef RR
-#undef RX
 #undef RP
-#define CD(x, y) case sv_op_index(K_CD, x, y): dfop_cd<x, y>(h, l, m, ml); break;
+#define CD(x, y) case sv_op_index(K_CD, x, y): if constexpr ((1 << y) < N) dfop_cd<x, y, N>(h, l, m, ml); break;
     CD(0, 1) CD(0, 2) CD(0, 3) CD(0, 4) CD(1, 2) CD(1, 3) CD(1, 4) CD(2, 3) CD(2, 4) CD(3, 4)
 #undef CD
     default: break;
@@ -209,15 +206,16 @@ __device__ __forceinline__ void df_apply_op(uint32_t code, const float (&m)[8], 
 
 // K_RP at a position known once the caller's loop is unrolled; a rotation
 // without phase (p = 1 exactly) skips the complex product
-__device__ __forceinline__ void df_rp_at(int P, float2 (&h)[32], float2 (&l)[32], const float (&m)[8],
+template <int N>
+__device__ __forceinline__ void df_rp_at(int P, float2 (&h)[N], float2 (&l)[N], const float (&m)[8],
                                          const float (&ml)[8]) {
   const bool phase = !(m[4] == 1.f && m[5] == 0.f && ml[4] == 0.f && ml[5] == 0.f);
   switch (P) {
-    case 0: dfop_rp<0>(h, l, m, ml, phase); break;
-    case 1: dfop_rp<1>(h, l, m, ml, phase); break;
-    case 2: dfop_rp<2>(h, l, m, ml, phase); break;
-    case 3: dfop_rp<3>(h, l, m, ml, phase); break;
-    default: dfop_rp<4>(h, l, m, ml, phase); break;
+    case 0: dfop_rp<0, N>(h, l, m, ml, phase); break;
+    case 1: dfop_rp<1, N>(h, l, m, ml, phase); break;
+    case 2: dfop_rp<2, N>(h, l, m, ml, phase); break;
+    case 3: dfop_rp<3, N>(h, l, m, ml, phase); break;
+    default: if constexpr (N > 16) dfop_rp<4, N>(h, l, m, ml, phase); break;
   }
 }
 

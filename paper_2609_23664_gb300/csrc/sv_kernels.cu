@@ -245,21 +245,22 @@ __device__ __forceinline__ uint32_t gray_pick(const uint32_t (&step)[6], int t) 
          : t == 5 ? step[5] : 0u;
 }
 
-// One stage group in compensated FP32: the 32 amplitudes at byte offsets
-// sbB ^ (XOR combinations of roff) are read with a zero remainder
+// One stage group in compensated FP32: the N = 2^G amplitudes at byte
+// offsets sbB ^ (XOR combinations of roff) are read with a zero remainder
 // (SV_AR_COMP) or with their remainder from the plane at lo_off
 // (SV_AR_REM), the stage's ops run in double-float, and the renormalized
 // pair is written back (SV_AR_COMP keeps only the rounded value).
-template <int AR>
+template <int AR, int G>
 __device__ __forceinline__ void sv_stage_df(char *smw, uint32_t lo_off, uint32_t sbB, const uint32_t (&roff)[SV_G],
                                             const SvOpDesc<float> *__restrict__ ops,
                                             const float *__restrict__ ops_lo, uint32_t op_begin, uint32_t nops,
                                             uint32_t rp_mask) {
-  float2 h[32], l[32];
+  constexpr int N = 1 << G;
+  float2 h[N], l[N];
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
+  for (int i = 0; i < N; i++) {
     const uint32_t off = sbB ^ ((i & 1) ? roff[0] : 0u) ^ ((i & 2) ? roff[1] : 0u) ^ ((i & 4) ? roff[2] : 0u) ^
-                         ((i & 8) ? roff[3] : 0u) ^ ((i & 16) ? roff[4] : 0u);
+                         ((i & 8) ? roff[3] : 0u) ^ ((G > 4 && (i & 16)) ? roff[4] : 0u);
     h[i] = *(const float2 *)(smw + off);
     if constexpr (AR == SV_AR_REM) l[i] = *(const float2 *)(smw + lo_off + off);
     else l[i] = make_float2(0.f, 0.f);
@@ -274,25 +275,25 @@ __device__ __forceinline__ void sv_stage_df(char *smw, uint32_t lo_off, uint32_t
   if (rp_mask) {
     uint32_t o = op_begin;
 #pragma unroll
-    for (int P = 0; P < SV_G; P++) {
+    for (int P = 0; P < G; P++) {
       if (!(rp_mask & (1u << P))) continue;
       float m[8], ml[8];
       load_ml(o, m, ml);
       o++;
-      df_rp_at(P, h, l, m, ml);
+      df_rp_at<N>(P, h, l, m, ml);
     }
   } else {
     for (uint32_t o = 0; o < nops; o++) {
       float m[8], ml[8];
       load_ml(op_begin + o, m, ml);
-      df_apply_op(__ldg(&ops[op_begin + o].code), m, ml, h, l);
+      df_apply_op<N>(__ldg(&ops[op_begin + o].code), m, ml, h, l);
     }
   }
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
+  for (int i = 0; i < N; i++) {
     df_renorm(h[i], l[i]);
     const uint32_t off = sbB ^ ((i & 1) ? roff[0] : 0u) ^ ((i & 2) ? roff[1] : 0u) ^ ((i & 4) ? roff[2] : 0u) ^
-                         ((i & 8) ? roff[3] : 0u) ^ ((i & 16) ? roff[4] : 0u);
+                         ((i & 8) ? roff[3] : 0u) ^ ((G > 4 && (i & 16)) ? roff[4] : 0u);
     *(float2 *)(smw + off) = h[i];
     if constexpr (AR == SV_AR_REM) *(float2 *)(smw + lo_off + off) = l[i];
   }
@@ -305,13 +306,14 @@ __device__ __forceinline__ void sv_stage_df(char *smw, uint32_t lo_off, uint32_t
 // in a second shared-memory plane, and between passes in the remainder
 // arrays src_lo / dst_lo, either of which may be NULL: zero remainder on
 // load, none stored).  FP64 passes are plain.
-template <typename T, int AR>
+template <typename T, int AR, int G>
 __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__restrict__ stages,
                         const SvOpDesc<T> *__restrict__ ops, const float *__restrict__ ops_lo,
                         typename V2<T>::t *sm, const typename V2<T>::t *src, typename V2<T>::t *dst,
                         const float2 *src_lo, float2 *dst_lo, uint32_t tile) {
   typedef typename V2<T>::t C;
   static_assert(AR == SV_AR_PLAIN || sizeof(T) == 4, "compensated arithmetic is for FP32 states");
+  static_assert((AR == SV_AR_PLAIN) == (G == SV_G), "plain passes run stages of SV_G positions");
   const uint32_t k = pd->k, b = pd->b, n_hi = pd->n_hi;
   uint32_t base = 0;
   for (uint32_t i = 0; i < n_hi; i++) base |= ((tile >> i) & 1u) << pd->hi_pos[i];
@@ -377,7 +379,7 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
   // gates), so a stage group's 32 slots are its base offset XOR combinations
   // of the five register-bit offsets, and the stage writes its registers
   // back to the slots it read.
-  const uint32_t n_groups = 1u << (k - SV_G);
+  const uint32_t n_groups = 1u << (k - G);
   const uint32_t n_st = pd->n_stages, st0 = pd->stage_begin;
   for (uint32_t s = 0; s < n_st; s++) {
     const uint4 *sdv = (const uint4 *)(stages + st0 + s);
@@ -399,9 +401,8 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
 #pragma unroll
       for (int t = 0; t < SV_MAX_GBITS; t++) sbB ^= ((grp >> t) & 1u) ? gcol[t] : 0u;
       if constexpr (AR != SV_AR_PLAIN) {
-        sv_stage_df<AR>(smw, lo_off, sbB, roff, ops, ops_lo, op_begin, nops, rp_mask);
-        continue;
-      }
+        sv_stage_df<AR, G>(smw, lo_off, sbB, roff, ops, ops_lo, op_begin, nops, rp_mask);
+      } else {
       C a[32];
 #pragma unroll
       for (int i = 0; i < 32; i++) {
@@ -443,6 +444,7 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
                              ((i & 4) ? roff[2] : 0u) ^ ((i & 8) ? roff[3] : 0u) ^
                              ((i & 16) ? roff[4] : 0u);
         *(C *)(smw + off) = a[i];
+      }
       }
     }
     __syncthreads();
@@ -525,8 +527,8 @@ sv_pass_kernel(SvTables t, uint32_t pass, const typename V2<T>::t *src, typename
                const float2 *src_lo, float2 *dst_lo) {
   extern __shared__ __align__(16) unsigned char smraw[];
   typedef typename V2<T>::t C;
-  sv_tile<T, AR>(t.passes + pass, t.stages, (const SvOpDesc<T> *)t.ops, t.ops_lo, (C *)smraw, src, dst, src_lo,
-                 dst_lo, blockIdx.x);
+  sv_tile<T, AR, sv_stage_width(AR)>(t.passes + pass, t.stages, (const SvOpDesc<T> *)t.ops, t.ops_lo, (C *)smraw,
+                                     src, dst, src_lo, dst_lo, blockIdx.x);
 }
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const unsigned int *p) {
@@ -552,8 +554,8 @@ constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per dependency wait
 // MINB: CTAs per SM the registers are budgeted for.  Tiles of 2^13 FP32
 // amplitudes (64 KB) fit three CTAs per SM; smaller tiles fit four, which
 // the 128-register build (MINB 4) can use.  Compensated passes (AR =
-// SV_AR_COMP) hold two FP32 complex values per amplitude in registers and
-// are budgeted for two CTAs.
+// SV_AR_COMP) hold two FP32 complex values per amplitude in registers, 16
+// amplitudes per stage group, and are budgeted for three CTAs.
 template <typename T, int MINB, int AR>
 __global__ void __launch_bounds__(128, MINB)
 sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, const SvSeg *__restrict__ segs,
@@ -607,8 +609,8 @@ sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, const SvSeg *__restr
       energy_block<T, 128, false>(J, s_unit, en.classes, en.terms,
                                   en.partials + 2 * (size_t)(J.block_begin + s_unit));
     } else {
-      sv_tile<T, AR>(t.passes + job.pass, t.stages, (const SvOpDesc<T> *)t.ops, t.ops_lo, (C *)smraw,
-                     (const C *)job.src, (C *)job.dst, nullptr, nullptr, s_unit);
+      sv_tile<T, AR, sv_stage_width(AR)>(t.passes + job.pass, t.stages, (const SvOpDesc<T> *)t.ops, t.ops_lo,
+                                         (C *)smraw, (const C *)job.src, (C *)job.dst, nullptr, nullptr, s_unit);
     }
     // every thread's writes of the unit precede thread 0's release through
     // the barrier (bar.sync orders them at CTA scope; the fence is
@@ -625,9 +627,11 @@ sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, const SvSeg *__restr
 // 128 threads: every thread owns at least two stage groups of a 2^13 tile,
 // and three CTAs fit on an SM (registers and shared memory).  Passes with a
 // remainder plane (twice the shared memory, one CTA per SM) give every
-// stage group of the tile its own thread, up to 256.
+// stage group of the tile its own thread, up to 256.  Compensated passes
+// run stages of four positions (16 amplitudes per group).
 int sv_threads_for_k(uint32_t k, int ar) {
-  const uint32_t g = (ar == SV_AR_REM) ? 1u << (k - SV_G) : 1u << (k - SV_G - 1);
+  const uint32_t G = (uint32_t)sv_stage_width(ar);
+  const uint32_t g = (ar == SV_AR_REM) ? 1u << (k - G) : 1u << (k - G - 1);
   const uint32_t cap = (ar == SV_AR_REM) ? 256u : 128u;
   return (int)(g < 32 ? 32 : (g > cap ? cap : g));
 }
@@ -640,12 +644,12 @@ size_t sv_smem_bytes(bool fp64, uint32_t k, int ar) {
 cudaError_t sv_init_attrs() {
   const int bytes = 200 * 1024;
   const void *k[] = {(const void *)sv_pass_kernel<float, SV_AR_PLAIN, 128, 3>,
-                     (const void *)sv_pass_kernel<float, SV_AR_COMP, 128, 2>,
+                     (const void *)sv_pass_kernel<float, SV_AR_COMP, 128, 3>,
                      (const void *)sv_pass_kernel<float, SV_AR_REM, 256, 1>,
                      (const void *)sv_pass_kernel<double, SV_AR_PLAIN, 128, 1>,
                      (const void *)sv_batch_kernel<float, 3, SV_AR_PLAIN>,
                      (const void *)sv_batch_kernel<float, 4, SV_AR_PLAIN>,
-                     (const void *)sv_batch_kernel<float, 2, SV_AR_COMP>,
+                     (const void *)sv_batch_kernel<float, 3, SV_AR_COMP>,
                      (const void *)sv_batch_kernel<double, 1, SV_AR_PLAIN>};
   for (const void *f : k) {
     const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -670,7 +674,7 @@ void launch_sv_pass(bool fp64, const SvTables &t, uint32_t pass_idx, uint32_t k,
     sv_pass_kernel<float, SV_AR_REM, 256, 1><<<tiles, threads, smem, s>>>(t, pass_idx, (const float2 *)src,
                                                                            (float2 *)dst, sl, dl);
   } else if (ar == SV_AR_COMP) {
-    sv_pass_kernel<float, SV_AR_COMP, 128, 2><<<tiles, threads, smem, s>>>(t, pass_idx, (const float2 *)src,
+    sv_pass_kernel<float, SV_AR_COMP, 128, 3><<<tiles, threads, smem, s>>>(t, pass_idx, (const float2 *)src,
                                                                             (float2 *)dst, nullptr, nullptr);
   } else {
     sv_pass_kernel<float, SV_AR_PLAIN, 128, 3><<<tiles, threads, smem, s>>>(t, pass_idx, (const float2 *)src,
@@ -686,7 +690,7 @@ int sv_batch_grid(bool fp64, uint32_t k, int sm_count, int ar) {
   if (fp64) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<double, 1, SV_AR_PLAIN>, threads, smem);
   } else if (ar == SV_AR_COMP) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float, 2, SV_AR_COMP>, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float, 3, SV_AR_COMP>, threads, smem);
   } else if (k <= 12) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float, 4, SV_AR_PLAIN>, threads, smem);
   } else {
@@ -707,7 +711,7 @@ void launch_sv_batch(bool fp64, const SvTables &t, const SvJob *jobs, const SvSe
     sv_batch_kernel<double, 1, SV_AR_PLAIN><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items,
                                                                         counters, en);
   else if (ar == SV_AR_COMP)
-    sv_batch_kernel<float, 2, SV_AR_COMP><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items,
+    sv_batch_kernel<float, 3, SV_AR_COMP><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items,
                                                                       counters, en);
   else if (k_max <= 12)
     sv_batch_kernel<float, 4, SV_AR_PLAIN><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items,

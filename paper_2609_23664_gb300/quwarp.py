@@ -103,6 +103,7 @@ SIGNATURES = {
     "qw_get_samples": (_st, [_vp, _u64, _vp, _sz, _vp]),
     "qw_get_syndrome": (_st, [_vp, _u64, _vp, _sz, _vp]),
     "qw_get_state": (_st, [_vp, _u64, _vp, _sz]),
+    "qw_get_stabilizers": (_st, [_vp, _u64, _vp, _vp, _vp, _sz]),
     "qw_explain_json": (_st, [_vp, _vp, _sz, _vp]),
     "qw_cost_record_json": (_st, [_vp, _vp, _sz, _vp]),
     "qw_sha256": (_st, [_vp, _sz, _vp]),
@@ -334,6 +335,15 @@ class Plan:
         out = np.zeros(1 << n, dtype=np.complex128 if fp64 else np.complex64)
         _check(lib().qw_get_state(self.h, t, _p(out), out.nbytes))
         return out
+
+    def stabilizers(self, t: int, n: int):
+        """(x, z, sign) of a tableau task kept with want_state: generator i
+        is (-1)^sign[i] i^{x.z} X^x[i] Z^z[i] (see qw_get_stabilizers)."""
+        x = np.zeros((n, n), dtype=np.uint8)
+        z = np.zeros((n, n), dtype=np.uint8)
+        sg = np.zeros(n, dtype=np.uint8)
+        _check(lib().qw_get_stabilizers(self.h, t, _p(x), _p(z), _p(sg), n))
+        return x, z, sg
 
     def _json(self, fn) -> dict:
         need = C.c_size_t()

@@ -400,6 +400,32 @@ def deep_local_sweep(seed: int = BASE_SEED + 7, n: int = 24, layers: int = 60, l
     return tasks
 
 
+def dense_prefix_groups(seed: int = BASE_SEED + 8, n: int = 20, groups: int = 6, group_size: int = 4,
+                        prefix_gates: int = 400, prefix_qubits: int = 12, suffix_layers: int = 6,
+                        n_terms: int = 16, mode: int = MODE_SV_FP32) -> List[Task]:
+    """Groups of tasks whose shared prefix is many gates on few qubits and
+    whose suffixes are a few sparse layers over every qubit: each group
+    shares a random circuit of `prefix_gates` gates on qubits
+    0..prefix_qubits-1 (gate set of random_circuit), and every task adds
+    `suffix_layers` layers of RY on every qubit (angles U[0, 2pi)) each
+    followed by a CNOT chain; one random Hamiltonian per group.  Counted in
+    passes over the state the prefix is the cheap part (its gates fit one
+    tile); counted in arithmetic it is the expensive one."""
+    rng = np.random.default_rng(seed)
+    tasks = []
+    for _ in range(groups):
+        pre = random_circuit(rng, prefix_qubits, prefix_gates)
+        ham = random_pauli_hamiltonian(rng, n, n_terms)
+        for _ in range(group_size):
+            g = []
+            for _ in range(suffix_layers):
+                g += [(OP_RY, q, 0, float(rng.uniform(0, 2 * np.pi))) for q in range(n)]
+                g += [(OP_CNOT, q, q + 1, 0.0) for q in range(n - 1)]
+            suf = gates_from_list(g)
+            tasks.append(Task(mode=mode, n=n, spans=[pre, suf], terms=ham))
+    return tasks
+
+
 def noisy22_trajectories(seed: int = BASE_SEED + 3, n: int = 22, n_gates: int = 400,
                     n_traj: int = 1024, p: float = 1e-3, shots: int = 100,
                     mode: int = MODE_SV_FP32) -> List[Task]:

@@ -39,6 +39,10 @@ def test_vqe24_full_size_sampled(eng, prefix_fp64):
     plan.run()
     ex = plan.explain()
     assert ex["artifacts"] == 1 and ex["tasks_reusing"] == 256
+    # an FP64 boundary serves the FP32 tasks rounded once (legality reading:
+    # exact up to that one rounding), and EXPLAIN says so
+    art = ex["decisions"][0]["artifact"]
+    assert art["consumer_exactness"] == ({"GPU_SV_FP32": "EXACT_UP_TO_ONE_ROUNDING"} if prefix_fp64 else {})
     for i in (0, keep, 255):
         ref = _oracle(tasks, i, i == keep)
         e, nr = plan.energy(i)
@@ -129,17 +133,28 @@ def _oracle(tasks, i, want_state):
     return _ORACLE[key]
 
 
-def test_noisy22_full_size_sampled(eng):
+def _first_error(t, base_len):
+    # gate index of the trajectory's first inserted error (base_len if none)
+    return len(t.spans[0]) if len(t.spans) > 1 else base_len
+
+
+def test_noisy22_full_size_32_trajectories(eng):
+    # the full 1024-trajectory workload on the GPU; 32 trajectories against
+    # the oracle: 8 error-free ones (the shared CDF of the error-free chain)
+    # and the 12 earliest and 12 latest first-error forks
     tasks = W.noisy22_trajectories()                   # 22 qubits, 1024 trajectories
     plan = Q.Plan(eng, Q.Workload(tasks))
     plan.run()
     ex = plan.explain()
     assert ex["tasks_reusing"] > 900
-    # earliest / latest error trajectories and error-free ones
     n_gates = np.array([t.n_gates for t in tasks])
     free = np.nonzero(n_gates == 400)[0]
     noisy = np.nonzero(n_gates > 400)[0]
-    sample = [int(free[0]), int(free[-1]), int(noisy[0]), int(noisy[-1])]
+    order = sorted(noisy, key=lambda i: _first_error(tasks[i], 400))
+    rng = np.random.default_rng(20260923)
+    sample = sorted(set([int(i) for i in rng.choice(free, 8, replace=False)] + [int(i) for i in order[:12]] +
+                        [int(i) for i in order[-12:]]))
+    assert len(sample) == 32
     for i in sample:
         ref = orc.run_task(tasks[i], want_state=True)
         got = plan.samples(i)
@@ -148,15 +163,48 @@ def test_noisy22_full_size_sampled(eng):
         r = ref["samples"].astype(np.int64)
         near = (np.abs(F[np.minimum(r, len(F) - 1)] - tasks[i].uniforms) < 1e-5) | \
                (np.abs(F[np.maximum(r - 1, 0)] - tasks[i].uniforms) < 1e-5)
+        print("trajectory %d (first error at gate %d): %d of %d shots equal, %d within 1e-5 of a CDF boundary"
+              % (i, _first_error(tasks[i], 400), int(np.sum(got == ref["samples"])), len(got),
+                 int(np.sum((got != ref["samples"]) & near))))
         assert np.all((got == ref["samples"]) | near), i
 
 
-def test_qec_d15_full_size_sampled(eng):
-    tasks = W.qec_surface_code_tasks()                       # 449 qubits, 100 + 5 rounds, 4096 tasks
-    plan = Q.Plan(eng, Q.Workload(tasks))
+_QEC = {}
+
+
+def _qec_reference():
+    # The oracle's syndromes of all 4096 tasks.  The 100 shared rounds are
+    # run once and every task's five rounds continue from the exported rows
+    # (orc.tab_run_from; the tableau algorithm is deterministic, so this is
+    # bit for bit the run from |0...0>, which tasks 0, 1 and 4095 also get).
+    if not _QEC:
+        from concurrent.futures import ThreadPoolExecutor
+        tasks = W.qec_surface_code_tasks()             # 449 qubits, 100 + 5 rounds, 4096 tasks
+        n = tasks[0].n
+        pre_out, rows = orc.tab_run(n, tasks[0].spans[0], want_tableau=True)
+
+        def ref(i):
+            t = tasks[i]
+            assert t.spans[0] is tasks[0].spans[0]
+            return np.concatenate([pre_out, orc.tab_run_from(n, rows, W.concat(*t.spans[1:]))])
+
+        with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:  # ctypes calls release the GIL
+            refs = list(ex.map(ref, range(len(tasks))))
+        for i in (0, 1, 4095):
+            assert np.array_equal(refs[i], orc.tab_run(n, tasks[i].gates)), i
+        _QEC["tasks"], _QEC["refs"] = tasks, refs
+    return _QEC["tasks"], _QEC["refs"]
+
+
+@pytest.mark.parametrize("frames", [1, 0])
+def test_qec_d15_every_task_bit_exact(eng, frames):
+    # Pauli frames over the shared rounds (the bench's plan) and every task
+    # on its own tableau: all 4096 syndromes equal the oracle's
+    tasks, refs = _qec_reference()
+    plan = Q.Plan(eng, Q.Workload(tasks), pauli_frames=frames)
     plan.run()
-    for i in (0, 1, 4095):
-        ref = orc.tab_run(tasks[i].n, tasks[i].gates)
-        got = plan.syndrome(i)
-        assert len(got) == 105 * 224
-        assert np.array_equal(got, ref), i
+    assert len(plan.explain()["pauli_frames"]) == frames
+    bad = [i for i in range(len(tasks)) if not np.array_equal(plan.syndrome(i), refs[i])]
+    print("frames %d: %d of %d tasks differ" % (frames, len(bad), len(tasks)))
+    assert not bad, bad[:10]
+    plan.close()

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as orc
+from stab_canonical import canonical
 from paper_2609_23664_gb300 import workloads as W
 
 CLIFF_1Q = [W.OP_H, W.OP_S, W.OP_SDG, W.OP_X, W.OP_Y, W.OP_Z]
@@ -130,3 +131,58 @@ def test_surface_code_d15_size():
     assert code.n == 449 and len(code.x_anc) == 112 and len(code.z_anc) == 112
     cnots = sum(1 for a in code.sched for q in code.sched[a] if q is not None)
     assert cnots == 840
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_continuing_from_exported_rows_equals_the_run_from_zero(seed):
+    # the tableau algorithm is deterministic: running a prefix, exporting its
+    # rows and continuing with the suffix gives the outcomes and the final
+    # rows of the whole circuit run from |0...0>, random-outcome
+    # measurements and resets included
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(3, 9))
+    ops = [W.OP_H, W.OP_S, W.OP_SDG, W.OP_X, W.OP_Y, W.OP_Z, W.OP_CNOT, W.OP_CZ, W.OP_SWAP,
+           W.OP_MEASURE, W.OP_RESET]
+    g = []
+    for _ in range(120):
+        op = ops[int(rng.integers(0, len(ops)))]
+        a, b = (int(v) for v in rng.choice(n, 2, replace=False))
+        g.append((op, a, b, float(rng.integers(0, 2))))
+    gates = W.gates_from_list(g)
+    cut = int(rng.integers(1, len(gates)))
+    pre, suf = gates[:cut], gates[cut:]
+    whole, t_whole = orc.tab_run(n, gates, want_tableau=True)
+    out_pre, t_pre = orc.tab_run(n, pre, want_tableau=True)
+    out_suf, t_suf = orc.tab_run_from(n, t_pre, suf, want_tableau=True)
+    assert np.array_equal(whole, np.concatenate([out_pre, out_suf]))
+    for a, b in zip(t_whole, t_suf):
+        assert np.array_equal(a, b)
+
+
+def test_continuing_a_surface_code_task_from_its_shared_rounds():
+    tasks = W.qec_surface_code_tasks(d=5, shared_rounds=6, task_rounds=3, n_tasks=4, p=0.05)
+    pre_out, rows = orc.tab_run(tasks[0].n, tasks[0].spans[0], want_tableau=True)
+    for t in tasks:
+        assert t.spans[0] is tasks[0].spans[0]
+        suf = W.concat(*t.spans[1:])
+        got = np.concatenate([pre_out, orc.tab_run_from(t.n, rows, suf)])
+        assert np.array_equal(got, orc.tab_run(t.n, t.gates))
+
+
+def test_canonical_form_is_a_group_invariant():
+    # the same group from two different generating sets: the oracle's
+    # stabilizers, and the same rows each multiplied by the next one
+    rng = np.random.default_rng(3)
+    t = W.Task(mode=W.MODE_TABLEAU, n=9, spans=[rand_clifford(rng, 9, 200, p_meas=0.08, p_reset=0.04)])
+    _, (x, z, r) = orc.tab_run(t.n, t.gates, want_tableau=True)
+    n = t.n
+    x, z, r = x[n:].astype(np.uint8), z[n:].astype(np.uint8), r[n:].astype(np.uint8)
+    e = (2 * r.astype(np.int64) + np.sum(x.astype(np.int64) & z, axis=1)) % 4
+    x2, z2, e2 = x.copy(), z.copy(), e.copy()
+    for i in range(n - 1):
+        e2[i] = (e[i] + e[i + 1] + 2 * int(np.sum(z[i].astype(np.int64) & x[i + 1]))) % 4
+        x2[i] ^= x[i + 1]
+        z2[i] ^= z[i + 1]
+    r2 = ((e2 - np.sum(x2.astype(np.int64) & z2, axis=1)) % 4 // 2).astype(np.uint8)
+    for a, b in zip(canonical(x, z, r), canonical(x2, z2, r2)):
+        assert np.array_equal(a, b)
