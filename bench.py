@@ -171,7 +171,7 @@ def profiled_traffic(kernel: str, workload_key: str, field: str = "dram"):
     import hashlib
     src = os.path.join(ROOT, "paper_2609_23664_gb300", "csrc")
     h = hashlib.sha256()
-    for fn in ("sv_kernels.cu", "obs_kernels.cu", "energy_block.cuh", "qw_internal.h"):
+    for fn in ("sv_kernels.cu", "sv_df.cuh", "obs_kernels.cu", "energy_block.cuh", "qw_internal.h"):
         with open(os.path.join(src, fn), "rb") as f:
             h.update(f.read())
     digest = h.hexdigest()[:16]
@@ -278,7 +278,7 @@ def cpu_baselines(n_vqe24):
         ("vqe24_fp32", 256, 2, "2 of 256 tasks (config 2)", (0.125, 0.1)),
         ("noisy22", 1024, 4, "4 of 1024 trajectories at 22 qubits (config 3)", None),
         ("qec_d15", 4096, 8, "8 of 4096 tasks from |0...0>, 105 rounds each (config 4)", None),
-        ("mixed_n_le_20", 2000, 8, "the first 8 tasks with n <= 20 of the 2000-task mixed workload (config 5)",
+        ("mixed_n_le_20", 2000, 40, "the first 40 tasks with n <= 20 of the 2000-task mixed workload (config 5)",
          None),
     ]
     for fam, total, count, sample, partial in specs:

@@ -400,29 +400,26 @@ def deep_local_sweep(seed: int = BASE_SEED + 7, n: int = 24, layers: int = 60, l
     return tasks
 
 
-def dense_prefix_groups(seed: int = BASE_SEED + 8, n: int = 20, groups: int = 6, group_size: int = 4,
-                        prefix_gates: int = 400, prefix_qubits: int = 12, suffix_layers: int = 6,
-                        n_terms: int = 16, mode: int = MODE_SV_FP32) -> List[Task]:
-    """Groups of tasks whose shared prefix is many gates on few qubits and
-    whose suffixes are a few sparse layers over every qubit: each group
-    shares a random circuit of `prefix_gates` gates on qubits
-    0..prefix_qubits-1 (gate set of random_circuit), and every task adds
-    `suffix_layers` layers of RY on every qubit (angles U[0, 2pi)) each
-    followed by a CNOT chain; one random Hamiltonian per group.  Counted in
-    passes over the state the prefix is the cheap part (its gates fit one
-    tile); counted in arithmetic it is the expensive one."""
+def costly_prefix_groups(seed: int = BASE_SEED + 8, n: int = 20, groups: int = 8, group_size: int = 4,
+                         prefix_gates: int = 240, suffix_gates: int = 8000, suffix_qubits: int = 12,
+                         n_terms: int = 16, mode: int = MODE_SV_FP32) -> List[Task]:
+    """Groups of tasks whose gates differ in cost: each group shares a
+    prefix of `prefix_gates` rotations (RX, RY or RZ, uniform, angles
+    U[0, 2pi)) on uniform qubits, and every task adds a network of
+    `suffix_gates` CNOTs on uniform pairs of qubits 0..suffix_qubits-1; one
+    random Hamiltonian per group.  A rotation is arithmetic on every
+    amplitude, a CNOT only relabels amplitudes, so the prefix is the costly
+    part although it has far fewer gates."""
     rng = np.random.default_rng(seed)
     tasks = []
     for _ in range(groups):
-        pre = random_circuit(rng, prefix_qubits, prefix_gates)
+        pre = gates_from_list([(int(rng.choice([OP_RX, OP_RY, OP_RZ])), int(rng.integers(0, n)), 0,
+                                float(rng.uniform(0, 2 * np.pi))) for _ in range(prefix_gates)])
         ham = random_pauli_hamiltonian(rng, n, n_terms)
         for _ in range(group_size):
-            g = []
-            for _ in range(suffix_layers):
-                g += [(OP_RY, q, 0, float(rng.uniform(0, 2 * np.pi))) for q in range(n)]
-                g += [(OP_CNOT, q, q + 1, 0.0) for q in range(n - 1)]
-            suf = gates_from_list(g)
-            tasks.append(Task(mode=mode, n=n, spans=[pre, suf], terms=ham))
+            g = [(OP_CNOT, int(a), int(b), 0.0)
+                 for a, b in (rng.choice(suffix_qubits, 2, replace=False) for _ in range(suffix_gates))]
+            tasks.append(Task(mode=mode, n=n, spans=[pre, gates_from_list(g)], terms=ham))
     return tasks
 
 
