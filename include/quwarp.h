@@ -232,7 +232,12 @@ typedef struct qw_plan_opts {
                                  Default 0. */
   int32_t fp32_arith;         /* gate arithmetic of FP32 statevector tasks (storage stays
                                  FP32 either way):
-                                 QW_FP32_COMPENSATED (default): every amplitude is held
+                                 QW_FP32_AUTO (default): compensated when some FP32
+                                 task of the workload has Pauli terms (its energy is
+                                 held to 1e-6 relative), plain otherwise (states and
+                                 samples need 1e-5 max-abs amplitude error, which plain
+                                 FP32 meets).
+                                 QW_FP32_COMPENSATED: every amplitude is held
                                  as an unevaluated sum of two FP32 numbers while gates
                                  run (error-free products and sums on the FP32 units,
                                  gate constants to 2^-48), so a state is rounded only
@@ -246,13 +251,14 @@ typedef struct qw_plan_opts {
                                  their size at 24 qubits). */
 } qw_plan_opts;
 
-#define QW_FP32_COMPENSATED 0
+#define QW_FP32_AUTO 0
 #define QW_FP32_PLAIN 1
+#define QW_FP32_COMPENSATED 2
 
 /* Fills the defaults: reuse=1, batched=1, legality=1, analytic costs,
  * delta_frac=0.10, min_group=2, min_prefix_gates=1, min_prefix_cost_ns=0,
  * autotuned tiles, use_graph=1, fault_injection=0, fuse_energy=0, pauli_frames=1,
- * handoff=1, prefix_fp64=0, dense_boundaries=0, fp32_arith=QW_FP32_COMPENSATED. */
+ * handoff=1, prefix_fp64=0, dense_boundaries=0, fp32_arith=QW_FP32_AUTO. */
 void qw_plan_opts_default(qw_plan_opts *o);
 
 typedef struct qw_plan qw_plan;

@@ -206,7 +206,7 @@ void qw_plan_opts_default(qw_plan_opts *o) {
   o->handoff = 1;
   o->prefix_fp64 = 0;
   o->dense_boundaries = 0;
-  o->fp32_arith = QW_FP32_COMPENSATED;
+  o->fp32_arith = QW_FP32_AUTO;
 }
 
 qw_status qw_plan_create(qw_engine *e, const qw_workload *w, const qw_plan_opts *o, qw_plan **out) {
@@ -375,7 +375,7 @@ qw_status qw_cost_record_json(const qw_plan *p, char *buf, size_t cap, size_t *n
       (unsigned long long)p->n_launches, (unsigned long long)p->h2d_bytes,
       (unsigned long long)p->d2h_bytes, p->batch_alg_bytes, p->energy_alg_bytes, p->energy_l2_bytes, p->prefix_alg_bytes,
       p->batch_alg_flops, p->prefix_alg_flops,
-      p->energy_fused ? "true" : "false", p->opts.fp32_arith == QW_FP32_PLAIN ? "plain" : "compensated",
+      p->energy_fused ? "true" : "false", p->fp32_compensated ? "compensated" : "plain",
       p->mats.size(), [&] {
         unsigned long long b = 0;
         for (auto &m : p->mats) b += m.bytes;

@@ -431,9 +431,7 @@ static double pass_flops(const HostPass &hp, uint32_t n, uint32_t g, int ar) {
   return f;
 }
 
-int plan_ar_batch(const qw_plan *P) {
-  return P->opts.fp32_arith == QW_FP32_PLAIN ? SV_AR_PLAIN : SV_AR_COMP;
-}
+int plan_ar_batch(const qw_plan *P) { return P->fp32_compensated ? SV_AR_COMP : SV_AR_PLAIN; }
 
 // Segment size of a persistent work list: the largest power of two (at most
 // 64) that no job's unit count falls below, so that few items are empty.

@@ -200,6 +200,7 @@ struct qw_engine {
 struct qw_plan {
   qw::Engine *eng = nullptr;
   qw_plan_opts opts;
+  bool fp32_compensated = true;  // FP32 gate arithmetic of this plan (from opts.fp32_arith and the workload)
   std::vector<qw::TaskPlan> tasks;
   std::vector<qw::MatNode> mats;
   std::vector<qw::Decision> decisions;

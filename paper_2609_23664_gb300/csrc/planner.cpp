@@ -876,6 +876,13 @@ static void build_frame_groups(qw_plan *P, const Workload &W) {
 
 void build_plan(qw_plan *P, Engine *E, const Workload &W) {
   const auto t0 = std::chrono::steady_clock::now();
+  // FP32 arithmetic: QW_FP32_AUTO compensates when some FP32 task asks for
+  // a Pauli-sum energy (the 1e-6 relative energy target); samples and
+  // states alone need the 1e-5 amplitude bound, which plain FP32 meets
+  P->fp32_compensated = P->opts.fp32_arith == QW_FP32_COMPENSATED;
+  if (P->opts.fp32_arith == QW_FP32_AUTO)
+    for (const TaskData &T : W.tasks)
+      if (T.mode == QW_MODE_SV_FP32 && !T.terms.empty()) P->fp32_compensated = true;
   PlanCtx C(P, E, W);
   C.bw_gbs = E ? E->hbm_gbs : 6000.0;
   C.launch_ns = E ? E->launch_ns : 4000.0;

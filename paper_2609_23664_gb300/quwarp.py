@@ -26,7 +26,7 @@ QW_OK = 0
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "BUDGET", -4: "CUDA", -5: "DEVICE_TIMEOUT",
           -6: "STATE", -7: "BUFFER_TOO_SMALL", -8: "NOT_FOUND", -9: "UNSUPPORTED"}
 COST_ANALYTIC, COST_MLP = 0, 1
-FP32_COMPENSATED, FP32_PLAIN = 0, 1
+FP32_AUTO, FP32_PLAIN, FP32_COMPENSATED = 0, 1, 2
 TASK_KEEP_STATE = 1
 MLP_IN, MLP_HID = 12, 64
 MLP_PARAMS = MLP_IN * MLP_HID + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID + 1
