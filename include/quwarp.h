@@ -160,6 +160,22 @@ qw_status qw_engine_info(const qw_engine *e, double *hbm_gbs, int32_t *sm_count,
  * evaluation), so this, not the HBM bandwidth, bounds it.  Synchronous;
  * allocates and frees its buffer. */
 qw_status qw_engine_probe_l2(qw_engine *e, double *l2_read_gbs);
+/* Tile-shape tuning (the autotuner of the statevector passes: tile qubits,
+ * contiguous low qubits, stage width, and the measured time of one pass that
+ * calibrates the analytic cost of Eq. 2), kept per (qubit count, precision,
+ * FP32 arithmetic, gate mix) and measured on first use.  The gate mix is
+ * "layered" (at most 35 % two-qubit gates, hardware-efficient layers) or
+ * "entangling" (more), each tuned on a circuit of its kind.  _json writes
+ * the engine's tuning as JSON (size-query idiom, as qw_explain_json), with
+ * the GPU model it was measured on and the number of shapes this engine
+ * timed itself; _load adds the entries of such a record to an engine on the
+ * same GPU model, so a later process plans without timing them again.
+ * QW_ERR_INVALID_ARG for another model, a record of another kind, a
+ * malformed entry or a shape the pass kernels cannot run; a refused record
+ * adds nothing (all entries or none).  Not thread-safe against planning on
+ * the same engine. */
+qw_status qw_engine_tuning_json(const qw_engine *e, char *buf, size_t cap, size_t *needed);
+qw_status qw_engine_tuning_load(qw_engine *e, const char *json);
 
 /* Message of the last error on the calling thread ("" if none).  Valid until
  * the next qw_* call on this thread. */

@@ -110,6 +110,78 @@ qw_status qw_engine_info(const qw_engine *e, double *hbm_gbs, int32_t *sm_count,
   })
 }
 
+static qw_status put_json(const std::string &s, char *buf, size_t cap, size_t *needed);
+
+// the GPU model a tuning belongs to (tile shapes are measured on it)
+static std::string device_tag(int dev) {
+  cudaDeviceProp pr;
+  if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return "unknown";
+  std::string nm = strf("%s sm_%d%d %d SMs", pr.name, pr.major, pr.minor, pr.multiProcessorCount);
+  for (char &c : nm)
+    if (c == '"' || c == '\\') c = ' ';
+  return nm;
+}
+
+qw_status qw_engine_tuning_json(const qw_engine *e, char *buf, size_t cap, size_t *needed) {
+  if (!e) { set_last_error("engine is NULL"); return QW_ERR_INVALID_ARG; }
+  set_last_error("");
+  std::string s = strf("{\"type\":\"QuWARP:Tuning\",\"device\":\"%s\",\"tuning_runs\":%llu,\"tiles\":[",
+                       device_tag(e->e.device).c_str(), (unsigned long long)e->e.tuning_runs);
+  bool first = true;
+  for (const auto &kv : e->e.tiles) {
+    const uint64_t k = kv.first;
+    const TileConfig &t = kv.second;
+    s += strf("%s{\"n\":%llu,\"mix\":%llu,\"arith\":%llu,\"fp64\":%llu,\"k\":%u,\"b\":%u,\"g\":%u,"
+              "\"pass_ns\":%.17g}",
+              first ? "" : ",", (unsigned long long)(k >> 4), (unsigned long long)((k >> 3) & 1u),
+              (unsigned long long)((k >> 1) & 3u), (unsigned long long)(k & 1u), t.k_max, t.b, t.g, t.pass_ns);
+    first = false;
+  }
+  s += "]}";
+  return put_json(s, buf, cap, needed);
+}
+
+static void load_tuning(qw_engine *e, const char *json) {
+  const std::string s(json);
+  const std::string dev = "\"device\":\"" + device_tag(e->e.device) + "\"";
+  if (s.find("\"type\":\"QuWARP:Tuning\"") == std::string::npos)
+    fail(QW_ERR_INVALID_ARG, "not a tuning record of this library");
+  if (s.find(dev) == std::string::npos)
+    fail(QW_ERR_INVALID_ARG, "the tuning was measured on another GPU model");
+  std::map<uint64_t, TileConfig> got;
+  size_t pos = s.find("\"tiles\":[");
+  while (pos != std::string::npos && (pos = s.find("{\"n\":", pos)) != std::string::npos) {
+    unsigned long long n = 0, mix = 0, ar = 0, f64 = 0;
+    unsigned k = 0, b = 0, g = 0;
+    double pns = 0;
+    if (sscanf(s.c_str() + pos,
+               "{\"n\":%llu,\"mix\":%llu,\"arith\":%llu,\"fp64\":%llu,\"k\":%u,\"b\":%u,\"g\":%u,"
+               "\"pass_ns\":%lf}",
+               &n, &mix, &ar, &f64, &k, &b, &g, &pns) != 8)
+      fail(QW_ERR_INVALID_ARG, "malformed tile entry at offset %zu", pos);
+    const uint32_t kcap = f64 ? SV_MAX_TILE_FP64 : (ar == SV_AR_PLAIN ? SV_MAX_TILE_FP32 : SV_MAX_TILE_FP32_COMP);
+    const uint32_t gw = (!f64 && ar != SV_AR_PLAIN) ? SV_G_COMP : SV_G;
+    if (n < 1 || n > QW_SV_MAX_QUBITS || mix > 1 || ar > SV_AR_COMP || f64 > 1 || k < SV_G + 1 || k > kcap ||
+        b + 2 > k || g != gw || !(pns >= 0))
+      fail(QW_ERR_INVALID_ARG, "tile entry out of range at offset %zu", pos);
+    TileConfig t;
+    t.k_max = k;
+    t.b = b;
+    t.g = g;
+    t.pass_ns = pns;
+    got[Engine::tile_key((uint32_t)n, f64 != 0, (int)ar, (uint32_t)mix)] = t;
+    pos++;
+  }
+  for (auto &kv : got) e->e.tiles[kv.first] = kv.second;
+}
+
+qw_status qw_engine_tuning_load(qw_engine *e, const char *json) {
+  QW_GUARD({
+    if (!e || !json) fail(QW_ERR_INVALID_ARG, "NULL argument");
+    load_tuning(e, json);
+  })
+}
+
 qw_status qw_workload_create(qw_workload **out) {
   QW_GUARD({
     if (!out) fail(QW_ERR_INVALID_ARG, "out is NULL");
@@ -529,8 +601,10 @@ qw_status qw_costmodel_features(const qw_engine *e, const qw_workload *w, uint64
     tc.k_max = (t.mode == QW_MODE_SV_FP64) ? SV_MAX_TILE_FP64 : SV_MAX_TILE_FP32_COMP;
     tc.b = 4;
     if (e) {
+      uint64_t n2 = 0;
+      for (uint64_t i = 0; i < t.n_gates; i++) n2 += is_two_qubit_op(t.gate(i)->op) ? 1 : 0;
       auto it = e->e.tiles.find(Engine::tile_key(std::max<uint32_t>(t.n, SV_G), t.mode == QW_MODE_SV_FP64,
-                                                 SV_AR_COMP));
+                                                 SV_AR_COMP, gate_mix(n2, t.n_gates)));
       if (it != e->e.tiles.end()) tc = it->second;
     }
     features_for(t, gate_begin, gate_end, n_sharing, tc, 0.0, out);

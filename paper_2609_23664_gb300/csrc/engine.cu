@@ -1602,10 +1602,11 @@ void *Engine::ensure_scratch(size_t bytes) {
 // Autotuner: times one synthetic hardware-efficient layer stack under each
 // candidate (tile qubits, contiguous low qubits) and keeps the fastest per
 // (qubit count, precision).
-TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar) {
+TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar, uint32_t mix) {
   const uint32_t key_n = std::min<uint32_t>(n_eff, 26);
   if (fp64 || ar == SV_AR_REM) ar = SV_AR_PLAIN;
-  const uint64_t key = tile_key(n_eff, fp64, ar);
+  mix &= 1u;
+  const uint64_t key = tile_key(n_eff, fp64, ar, mix);
   auto it = tiles.find(key);
   if (it != tiles.end()) return it->second;
   TileConfig best;
@@ -1616,15 +1617,23 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar) {
   cudaStream_t s = (cudaStream_t)stream;
   std::mt19937_64 rng(12345);
   std::uniform_real_distribution<double> U(0, 6.283185307179586);
+  // the tuning circuit of the gate mix: layered (hardware-efficient layers:
+  // rotations on every qubit, a CNOT chain) or entangling (random circuit,
+  // half of its gates CNOT / CZ on random pairs)
   std::vector<qw_gate> g;
-  for (int l = 0; l < 3; l++) {
-    for (uint32_t q = 0; q < key_n; q++) g.push_back({QW_OP_RY, q, 0, 0, U(rng)});
-    for (uint32_t q = 0; q < key_n; q++) g.push_back({QW_OP_RZ, q, 0, 0, U(rng)});
-    for (uint32_t q = 0; q + 1 < key_n; q++) g.push_back({QW_OP_CNOT, q, q + 1, 0, 0.0});
-  }
-  for (int i = 0; i < 40 * (int)key_n; i++) {
-    const uint32_t a = (uint32_t)(rng() % key_n), b = (uint32_t)((a + 1 + rng() % (key_n - 1)) % key_n);
-    g.push_back({i % 3 == 0 ? (uint32_t)QW_OP_CZ : (uint32_t)QW_OP_RX, a, i % 3 == 0 ? b : 0, 0, U(rng)});
+  if (mix == 0) {
+    for (int l = 0; l < 4; l++) {
+      for (uint32_t q = 0; q < key_n; q++) g.push_back({QW_OP_RY, q, 0, 0, U(rng)});
+      for (uint32_t q = 0; q < key_n; q++) g.push_back({QW_OP_RZ, q, 0, 0, U(rng)});
+      for (uint32_t q = 0; q + 1 < key_n; q++) g.push_back({QW_OP_CNOT, q, q + 1, 0, 0.0});
+    }
+  } else {
+    for (int i = 0; i < 40 * (int)key_n; i++) {
+      const uint32_t a = (uint32_t)(rng() % key_n), b = (uint32_t)((a + 1 + rng() % (key_n - 1)) % key_n);
+      const uint32_t r = (uint32_t)(rng() % 4);
+      const uint32_t op = r == 0 ? QW_OP_CZ : r == 1 ? QW_OP_CNOT : r == 2 ? QW_OP_RX : QW_OP_RZ;
+      g.push_back({op, a, r < 2 ? b : 0, 0, U(rng)});
+    }
   }
   const size_t S = sv_state_bytes(fp64, key_n);
   void *buf = nullptr;
@@ -1685,6 +1694,7 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar) {
   cudaFree(buf);
   CK(cudaGetLastError());
   tiles[key] = best;
+  tuning_runs++;
   return best;
 }
 
@@ -1823,7 +1833,9 @@ void costmodel_probe(Engine *E, const Workload &W, float *feat, float *tgt, floa
     // timings of the default FP32 arithmetic (compensated, as the
     // persistent suffix launch runs it)
     const int par = fp64 ? SV_AR_PLAIN : SV_AR_COMP;
-    TileConfig tc = E->tile_config(n_eff, fp64, par);
+    uint64_t n2 = 0;
+    for (uint64_t i = 0; i < T.n_gates; i++) n2 += is_two_qubit_op(T.gate(i)->op) ? 1 : 0;
+    TileConfig tc = E->tile_config(n_eff, fp64, par, gate_mix(n2, T.n_gates));
     const size_t S = sv_state_bytes(fp64, n_eff);
     void *st = E->ensure_scratch(S);
     CK(cudaMemsetAsync(st, 0, S, s));
@@ -1894,7 +1906,9 @@ qw_status sv_apply_dev(Engine *E, uint32_t mode, uint32_t n, void *state, const 
   // FP32: compensated arithmetic with the remainder kept between passes, so
   // the state is rounded once, by the last pass
   const int ar = fp64 ? SV_AR_PLAIN : SV_AR_REM;
-  TileConfig tc = E->tile_config(n, fp64, SV_AR_COMP);
+  uint64_t n2 = 0;
+  for (uint64_t i = 0; i < n_gates; i++) n2 += is_two_qubit_op(gates[i].op) ? 1 : 0;
+  TileConfig tc = E->tile_config(n, fp64, SV_AR_COMP, gate_mix(n2, n_gates));
   SvProgram pr = fuse_sv(gates, n_gates, n, tc);
   if (pr.passes.empty()) {
     if (!init) return QW_OK;

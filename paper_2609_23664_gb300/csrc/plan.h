@@ -149,6 +149,13 @@ std::string hex32(const uint8_t h[32]);
 void sha256(const void *data, size_t len, uint8_t out[32]);
 // FP32 arithmetic of a plan's persistent suffix launches (SV_AR_COMP or SV_AR_PLAIN)
 int plan_ar_batch(const qw_plan *P);
+// Gate-mix class of a gate list for the tile autotuner: 0 = layered (at
+// most 35 % two-qubit gates, e.g. hardware-efficient layers), 1 = entangling
+// (more, e.g. random circuits)
+constexpr double GATE_MIX_TWO_QUBIT_SHARE = 0.35;
+inline uint32_t gate_mix(uint64_t n_two, uint64_t n_all) {
+  return (n_all && (double)n_two > GATE_MIX_TWO_QUBIT_SHARE * (double)n_all) ? 1u : 0u;
+}
 void fingerprint(uint32_t n, uint32_t mode, const TaskData &t, uint64_t b, uint64_t e, uint8_t out[32]);
 bool legality(const qw_artifact_desc &a, uint32_t target_backend, const uint8_t *expected,
               qw_refusal *out);
@@ -165,7 +172,8 @@ struct Engine {
   double launch_ns = 4000;
   uint64_t store_budget = 0, task_budget = 0;
   void *stream = nullptr;
-  std::map<uint64_t, TileConfig> tiles;  // key: n << 3 | arithmetic << 1 | fp64
+  std::map<uint64_t, TileConfig> tiles;  // key: tile_key(n, fp64, arithmetic, gate mix)
+  uint64_t tuning_runs = 0;               // tile shapes timed by this engine (not loaded)
   std::map<uint64_t, double> dense_ms;    // measured dense-block pass times (autotuner cache)
   CostModel cm;
   float *d_mlp = nullptr;  // device copy of the MLP params
@@ -182,10 +190,12 @@ struct Engine {
   void trim_cache();
   std::set<qw_plan *> plans;  // live plans (released when the engine is destroyed)
   // autotuned tile shape for FP32 arithmetic `ar` (SV_AR_PLAIN or SV_AR_COMP)
-  TileConfig tile_config(uint32_t n_eff, bool fp64, int ar);
-  static uint64_t tile_key(uint32_t n_eff, bool fp64, int ar) {
+  // and gate mix `mix` (gate_mix of the gates it will run)
+  TileConfig tile_config(uint32_t n_eff, bool fp64, int ar, uint32_t mix);
+  static uint64_t tile_key(uint32_t n_eff, bool fp64, int ar, uint32_t mix) {
     if (fp64 || ar == SV_AR_REM) ar = SV_AR_PLAIN;
-    return ((uint64_t)std::min<uint32_t>(n_eff, 26) << 3) | ((uint64_t)ar << 1) | (fp64 ? 1 : 0);
+    return ((uint64_t)std::min<uint32_t>(n_eff, 26) << 4) | ((uint64_t)(mix & 1u) << 3) | ((uint64_t)ar << 1) |
+           (fp64 ? 1 : 0);
   }
   double predict_log2ns(const float *feat, uint32_t rows, float *out);
   void *ensure_scratch(size_t bytes);

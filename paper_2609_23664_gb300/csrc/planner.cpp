@@ -425,12 +425,30 @@ struct PlanCtx {
     return (uint64_t)handoff_run[t];
   }
 
+  // gate mix of the workload's statevector tasks of one size and precision
+  std::map<uint64_t, uint32_t> mix_of;
+  uint32_t mix(uint32_t n_eff, bool fp64) {
+    const uint64_t key = ((uint64_t)n_eff << 1) | (fp64 ? 1 : 0);
+    auto it = mix_of.find(key);
+    if (it != mix_of.end()) return it->second;
+    uint64_t n2 = 0, all = 0;
+    for (const TaskData &T : W.tasks) {
+      if (T.mode == QW_MODE_TABLEAU || std::max<uint32_t>(T.n, SV_G) != n_eff ||
+          (T.mode == QW_MODE_SV_FP64) != fp64)
+        continue;
+      for (const Span &sp : T.spans)
+        for (uint64_t i = 0; i < sp.n; i++) n2 += is_two_qubit_op(sp.g[i].op) ? 1 : 0;
+      all += T.n_gates;
+    }
+    return mix_of[key] = gate_mix(n2, all);
+  }
+
   TileConfig tiles(uint32_t n_eff, bool fp64) {
     TileConfig tc;
     tc.k_max = fp64 ? 12 : 13;
     tc.b = 4;
     tc.g = (fp64 || plan_ar_batch(P) == SV_AR_PLAIN) ? SV_G : SV_G_COMP;
-    if (E) tc = E->tile_config(n_eff, fp64, fp64 ? SV_AR_PLAIN : plan_ar_batch(P));
+    if (E) tc = E->tile_config(n_eff, fp64, fp64 ? SV_AR_PLAIN : plan_ar_batch(P), mix(n_eff, fp64));
     const uint32_t kcap = fp64 ? SV_MAX_TILE_FP64
                                : (plan_ar_batch(P) == SV_AR_PLAIN ? SV_MAX_TILE_FP32 : SV_MAX_TILE_FP32_COMP);
     if (P->opts.tile_qubits) tc.k_max = std::min<uint32_t>(P->opts.tile_qubits, kcap);

@@ -90,6 +90,8 @@ SIGNATURES = {
     "qw_engine_destroy": (None, [_vp]),
     "qw_engine_info": (_st, [_vp, _vp, _vp, _vp]),
     "qw_engine_probe_l2": (_st, [_vp, _vp]),
+    "qw_engine_tuning_json": (_st, [_vp, _vp, _sz, _vp]),
+    "qw_engine_tuning_load": (_st, [_vp, C.c_char_p]),
     "qw_last_error": (C.c_char_p, []),
     "qw_workload_create": (_st, [_vp]),
     "qw_workload_add_task": (_st, [_vp, _vp, _vp]),
@@ -186,6 +188,18 @@ class Engine:
         v = C.c_double()
         _check(lib().qw_engine_probe_l2(self.h, C.byref(v)))
         return v.value
+
+    def tuning(self) -> dict:
+        """The engine's tile-shape tuning (see qw_engine_tuning_json)."""
+        need = C.c_size_t()
+        lib().qw_engine_tuning_json(self.h, None, 0, C.byref(need))
+        buf = C.create_string_buffer(need.value)
+        _check(lib().qw_engine_tuning_json(self.h, buf, need.value, C.byref(need)))
+        return json.loads(buf.value.decode())
+
+    def load_tuning(self, record: dict):
+        """Adds a tuning record written on the same GPU model."""
+        _check(lib().qw_engine_tuning_load(self.h, json.dumps(record, separators=(",", ":")).encode()))
 
     def close(self):
         if getattr(self, "h", None):
