@@ -1617,23 +1617,30 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar, uint32_t mix) 
   cudaStream_t s = (cudaStream_t)stream;
   std::mt19937_64 rng(12345);
   std::uniform_real_distribution<double> U(0, 6.283185307179586);
-  // the tuning circuit of the gate mix: layered (hardware-efficient layers:
-  // rotations on every qubit, a CNOT chain) or entangling (random circuit,
-  // half of its gates CNOT / CZ on random pairs)
-  std::vector<qw_gate> g;
+  // the tuning circuits of the gate mix: layered (hardware-efficient layers,
+  // rotations on every qubit and a CNOT chain, 1 to 4 layers as in a sweep's
+  // suffixes; their times are summed) or entangling (a random circuit, half
+  // of its gates CNOT / CZ on random pairs)
+  std::vector<std::vector<qw_gate>> circuits;
   if (mix == 0) {
-    for (int l = 0; l < 4; l++) {
-      for (uint32_t q = 0; q < key_n; q++) g.push_back({QW_OP_RY, q, 0, 0, U(rng)});
-      for (uint32_t q = 0; q < key_n; q++) g.push_back({QW_OP_RZ, q, 0, 0, U(rng)});
-      for (uint32_t q = 0; q + 1 < key_n; q++) g.push_back({QW_OP_CNOT, q, q + 1, 0, 0.0});
+    for (int layers = 1; layers <= 4; layers++) {
+      std::vector<qw_gate> g;
+      for (int l = 0; l < layers; l++) {
+        for (uint32_t q = 0; q < key_n; q++) g.push_back({QW_OP_RY, q, 0, 0, U(rng)});
+        for (uint32_t q = 0; q < key_n; q++) g.push_back({QW_OP_RZ, q, 0, 0, U(rng)});
+        for (uint32_t q = 0; q + 1 < key_n; q++) g.push_back({QW_OP_CNOT, q, q + 1, 0, 0.0});
+      }
+      circuits.push_back(std::move(g));
     }
   } else {
+    std::vector<qw_gate> g;
     for (int i = 0; i < 40 * (int)key_n; i++) {
       const uint32_t a = (uint32_t)(rng() % key_n), b = (uint32_t)((a + 1 + rng() % (key_n - 1)) % key_n);
       const uint32_t r = (uint32_t)(rng() % 4);
       const uint32_t op = r == 0 ? QW_OP_CZ : r == 1 ? QW_OP_CNOT : r == 2 ? QW_OP_RX : QW_OP_RZ;
       g.push_back({op, a, r < 2 ? b : 0, 0, U(rng)});
     }
+    circuits.push_back(std::move(g));
   }
   const size_t S = sv_state_bytes(fp64, key_n);
   void *buf = nullptr;
@@ -1660,32 +1667,63 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar, uint32_t mix) 
         tc.b = best.b;
       }
       if (tc.b + 2 > tc.k_max || tc.k_max > best_cap) continue;
-      SvProgram pr = fuse_sv(g.data(), g.size(), key_n, tc);
-      SvTableBuilder tb(fp64);
-      tb.add(pr);
-      SvTables T;
-      DevArena dar;
-      T.passes = dar.upload(tb.passes, s);
-      T.stages = dar.upload(tb.stages, s);
-      T.ops = fp64 ? (const void *)dar.upload(tb.ops64, s) : (const void *)dar.upload(tb.ops32, s);
-      T.ops_lo = fp64 ? nullptr : dar.upload(tb.ops32lo, s);
       float tot = 0;
-      for (int r = 0; r < 3; r++) {
-        cudaEventRecord(e0, s);
-        for (size_t p = 0; p < pr.passes.size(); p++)
-          launch_sv_pass(fp64, T, (uint32_t)p, (uint32_t)pr.passes[p].q.size(), key_n, buf, buf, s, ar);
-        cudaEventRecord(e1, s);
-        CK(cudaEventSynchronize(e1));
-        float ms;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (r) tot += ms;
+      size_t n_passes = 0;
+      for (const auto &g : circuits) {
+        SvProgram pr = fuse_sv(g.data(), g.size(), key_n, tc);
+        SvTableBuilder tb(fp64);
+        tb.add(pr);
+        SvTables T;
+        DevArena dar;
+        T.passes = dar.upload(tb.passes, s);
+        T.stages = dar.upload(tb.stages, s);
+        T.ops = fp64 ? (const void *)dar.upload(tb.ops64, s) : (const void *)dar.upload(tb.ops32, s);
+        T.ops_lo = fp64 ? nullptr : dar.upload(tb.ops32lo, s);
+        // timed in the persistent batch kernel that runs the suffixes: the
+        // passes as one state's chain of jobs, each waiting for the last
+        std::vector<SvJob> jobs;
+        uint32_t kmax = 5;
+        for (size_t p = 0; p < pr.passes.size(); p++) {
+          SvJob j{};
+          const uint32_t kp = (uint32_t)pr.passes[p].q.size();
+          j.src = buf;
+          j.dst = buf;
+          j.pass = (uint32_t)p;
+          j.n_tiles = 1u << (key_n - kp);
+          j.dep = p ? (int32_t)p - 1 : -1;
+          j.kind = SVJ_PASS;
+          j.n = key_n;
+          jobs.push_back(j);
+          kmax = std::max(kmax, kp);
+        }
+        const int grid = sv_batch_grid(fp64, kmax, sm_count, ar);
+        const uint32_t seg_bits = segment_bits(jobs);
+        std::vector<SvSeg> segs;
+        build_segments(jobs, jobs.size(), seg_bits, 2ull * (uint64_t)grid, segs);
+        const uint32_t total = (uint32_t)(segs.size() << seg_bits);
+        const SvJob *dj = dar.upload(jobs, s);
+        const SvSeg *dsg = dar.upload(segs, s);
+        const size_t ctr_bytes = (2 + jobs.size()) * sizeof(unsigned int);
+        unsigned int *ctr = (unsigned int *)dar.alloc(ctr_bytes);
+        const EnTables no_energy{};
+        for (int r = 0; r < 3; r++) {  // one warm-up, two timed
+          CK(cudaMemsetAsync(ctr, 0, ctr_bytes, s));
+          cudaEventRecord(e0, s);
+          launch_sv_batch(fp64, T, dj, dsg, seg_bits, total, kmax, ctr, no_energy, grid, s, ar);
+          cudaEventRecord(e1, s);
+          CK(cudaEventSynchronize(e1));
+          float ms;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (r) tot += ms;
+        }
+        CK(cudaStreamSynchronize(s));
+        dar.release();
+        n_passes += pr.passes.size();
       }
-      CK(cudaStreamSynchronize(s));
-      dar.release();
       if (tot < best_ms) {
         best_ms = tot;
         best = tc;
-        best.pass_ns = (double)tot * 1e6 / 2.0 / std::max<double>(1.0, (double)pr.passes.size());
+        best.pass_ns = (double)tot * 1e6 / 2.0 / std::max<double>(1.0, (double)n_passes);
       }
     }
   }

@@ -43,7 +43,7 @@ def entangling_tasks():
 def run(eng, tasks):
     p = Q.Plan(eng, Q.Workload(tasks))
     p.run()
-    tiles = p.cost()["wave_tiles"]
+    tiles = p.cost_record()["wave_tiles"]
     e = [p.energy(i) for i in range(len(tasks))]
     p.close()
     return tiles, e
