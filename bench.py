@@ -72,6 +72,8 @@ def parse_args():
                     help="run only the dense-block family (one JSON line)")
     ap.add_argument("--window", type=int, default=0,
                     help="tasks advanced together in the persistent launch (0: all of a wave)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -387,6 +389,8 @@ def run_native(a):
     ev1 = torch.cuda.Event(enable_timing=True)
     recs = []
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    if a.profile_range:
+        torch.cuda.profiler.start()
     ev0.record(stream)
     evs[0].record(stream)
     for k in range(a.steps):
@@ -396,6 +400,8 @@ def run_native(a):
         recs.append(plan.cost_record())
     ev1.record(stream)
     torch.cuda.synchronize()
+    if a.profile_range:
+        torch.cuda.profiler.stop()
     barrier(world)
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1) / a.steps

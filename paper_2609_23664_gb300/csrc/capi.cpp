@@ -159,8 +159,8 @@ static void load_tuning(qw_engine *e, const char *json) {
                "\"pass_ns\":%lf}",
                &n, &mix, &ar, &f64, &k, &b, &g, &pns) != 8)
       fail(QW_ERR_INVALID_ARG, "malformed tile entry at offset %zu", pos);
-    const uint32_t kcap = f64 ? SV_MAX_TILE_FP64 : (ar == SV_AR_PLAIN ? SV_MAX_TILE_FP32 : SV_MAX_TILE_FP32_COMP);
-    const uint32_t gw = (!f64 && ar != SV_AR_PLAIN) ? SV_G_COMP : SV_G;
+    const uint32_t kcap = sv_max_tile((int)ar, f64 != 0);
+    const uint32_t gw = sv_stage_width((int)ar, f64 != 0);
     if (n < 1 || n > QW_SV_MAX_QUBITS || mix > 1 || ar > SV_AR_COMP || f64 > 1 || k < SV_G + 1 || k > kcap ||
         b + 2 > k || g != gw || !(pns >= 0))
       fail(QW_ERR_INVALID_ARG, "tile entry out of range at offset %zu", pos);

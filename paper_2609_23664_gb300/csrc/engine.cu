@@ -960,7 +960,7 @@ static void prepare(qw_plan *P) {
       std::vector<SvJob> up = W.jobs;
       W.grid = !W.per_pass ? sv_batch_grid(fp64, W.k_max, E->sm_count, W.ar) : 0;
       W.fused_energy =
-          !W.per_pass && P->opts.fuse_energy && !W.en.empty() && sv_threads_for_k(W.k_max, W.ar) == 128;
+          !W.per_pass && P->opts.fuse_energy && !W.en.empty() && sv_threads_for_k(W.k_max, W.ar, fp64) == 128;
       if (W.fused_energy) {
         std::vector<SvJob> ej;
         for (size_t e = 0; e < W.en.size(); e++) {
@@ -1610,9 +1610,9 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar, uint32_t mix) 
   auto it = tiles.find(key);
   if (it != tiles.end()) return it->second;
   TileConfig best;
-  best.k_max = fp64 ? SV_MAX_TILE_FP64 : (ar == SV_AR_PLAIN ? SV_MAX_TILE_FP32 : SV_MAX_TILE_FP32_COMP);
+  best.k_max = sv_max_tile(ar, fp64);
   best.b = 4;
-  best.g = (ar == SV_AR_PLAIN) ? SV_G : SV_G_COMP;
+  best.g = sv_stage_width(ar, fp64);
   CK(cudaSetDevice(device));
   cudaStream_t s = (cudaStream_t)stream;
   std::mt19937_64 rng(12345);
@@ -1642,10 +1642,13 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar, uint32_t mix) 
     }
     circuits.push_back(std::move(g));
   }
+  // independent states advanced together, as a wave's tasks are (so that
+  // the tail of each pass overlaps the other states' work): up to 8, within 1 GB
   const size_t S = sv_state_bytes(fp64, key_n);
+  const uint32_t chains = (uint32_t)std::max<size_t>(1, std::min<size_t>(8, ((size_t)1 << 30) / S));
   void *buf = nullptr;
-  CK(cudaMalloc(&buf, S));
-  CK(cudaMemsetAsync(buf, 0, S, s));
+  CK(cudaMalloc(&buf, S * chains));
+  CK(cudaMemsetAsync(buf, 0, S * chains, s));
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1679,21 +1682,24 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar, uint32_t mix) 
         T.stages = dar.upload(tb.stages, s);
         T.ops = fp64 ? (const void *)dar.upload(tb.ops64, s) : (const void *)dar.upload(tb.ops32, s);
         T.ops_lo = fp64 ? nullptr : dar.upload(tb.ops32lo, s);
-        // timed in the persistent batch kernel that runs the suffixes: the
-        // passes as one state's chain of jobs, each waiting for the last
+        // timed in the persistent batch kernel that runs the suffixes: each
+        // state's passes a chain of jobs (each waiting for the last), the
+        // chains interleaved pass by pass
         std::vector<SvJob> jobs;
         uint32_t kmax = 5;
         for (size_t p = 0; p < pr.passes.size(); p++) {
-          SvJob j{};
           const uint32_t kp = (uint32_t)pr.passes[p].q.size();
-          j.src = buf;
-          j.dst = buf;
-          j.pass = (uint32_t)p;
-          j.n_tiles = 1u << (key_n - kp);
-          j.dep = p ? (int32_t)p - 1 : -1;
-          j.kind = SVJ_PASS;
-          j.n = key_n;
-          jobs.push_back(j);
+          for (uint32_t c = 0; c < chains; c++) {
+            SvJob j{};
+            j.src = (char *)buf + (size_t)c * S;
+            j.dst = (char *)buf + (size_t)c * S;
+            j.pass = (uint32_t)p;
+            j.n_tiles = 1u << (key_n - kp);
+            j.dep = p ? (int32_t)jobs.size() - (int32_t)chains : -1;
+            j.kind = SVJ_PASS;
+            j.n = key_n;
+            jobs.push_back(j);
+          }
           kmax = std::max(kmax, kp);
         }
         const int grid = sv_batch_grid(fp64, kmax, sm_count, ar);
@@ -1718,7 +1724,7 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar, uint32_t mix) 
         }
         CK(cudaStreamSynchronize(s));
         dar.release();
-        n_passes += pr.passes.size();
+        n_passes += pr.passes.size() * chains;
       }
       if (tot < best_ms) {
         best_ms = tot;

@@ -447,10 +447,10 @@ struct PlanCtx {
     TileConfig tc;
     tc.k_max = fp64 ? 12 : 13;
     tc.b = 4;
-    tc.g = (fp64 || plan_ar_batch(P) == SV_AR_PLAIN) ? SV_G : SV_G_COMP;
-    if (E) tc = E->tile_config(n_eff, fp64, fp64 ? SV_AR_PLAIN : plan_ar_batch(P), mix(n_eff, fp64));
-    const uint32_t kcap = fp64 ? SV_MAX_TILE_FP64
-                               : (plan_ar_batch(P) == SV_AR_PLAIN ? SV_MAX_TILE_FP32 : SV_MAX_TILE_FP32_COMP);
+    const int ar = fp64 ? SV_AR_PLAIN : plan_ar_batch(P);
+    tc.g = sv_stage_width(ar, fp64);
+    if (E) tc = E->tile_config(n_eff, fp64, ar, mix(n_eff, fp64));
+    const uint32_t kcap = sv_max_tile(ar, fp64);
     if (P->opts.tile_qubits) tc.k_max = std::min<uint32_t>(P->opts.tile_qubits, kcap);
     tc.k_max = std::min<uint32_t>(tc.k_max, kcap);
     if (P->opts.low_qubits) tc.b = P->opts.low_qubits;

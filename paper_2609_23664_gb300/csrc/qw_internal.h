@@ -78,6 +78,11 @@ constexpr int SV_G = 5;            // positions per stage (32 register amplitude
 // Compensated FP32 passes hold two FP32 complex values per amplitude in
 // registers, so their stages take four positions (16 amplitudes)
 constexpr int SV_G_COMP = 4;
+// Plain FP32 passes take five positions, as FP64 ones (measured on GB300:
+// four positions in 256-thread CTAs, 24 warps per SM at 80 registers, ran
+// the 24-qubit plain suffix in 138 ms against 115 ms, the extra stage
+// passes through shared memory costing more than the occupancy gained)
+constexpr int SV_G_PLAIN32 = 5;
 
 // Dense index of an op for the kernels' jump table: each one-position kind
 // takes SV_G consecutive slots (its stage position), the controlled phase
@@ -314,8 +319,14 @@ struct SvTables {
 // and between passes (remainder arrays beside the state), so a chain of
 // passes rounds once, when it writes a state without its remainder.
 enum SvArith : int { SV_AR_PLAIN = 0, SV_AR_COMP = 1, SV_AR_REM = 2 };
-// stage positions of a pass kernel with arithmetic `ar`
-QW_HD constexpr int sv_stage_width(int ar) { return ar == SV_AR_PLAIN ? SV_G : SV_G_COMP; }
+// stage positions of a pass kernel with arithmetic `ar` (FP64 passes are plain)
+QW_HD constexpr int sv_stage_width(int ar, bool fp64 = false) {
+  return fp64 ? SV_G : (ar == SV_AR_PLAIN ? SV_G_PLAIN32 : SV_G_COMP);
+}
+// largest tile of those passes (a stage's group bits are at most SV_MAX_GBITS)
+QW_HD constexpr int sv_max_tile(int ar, bool fp64) {
+  return fp64 ? SV_MAX_TILE_FP64 : (sv_stage_width(ar, fp64) == 4 ? SV_MAX_TILE_FP32_COMP : SV_MAX_TILE_FP32);
+}
 // A job of the persistent launch: one pass over one state (n_tiles tiles),
 // or the energy blocks of one state (kind SVJ_ENERGY, n_tiles blocks).
 enum SvJobKind : uint32_t { SVJ_PASS = 0, SVJ_ENERGY = 1 };
@@ -345,7 +356,7 @@ struct EnTables {
 // kernel attributes (dynamic shared memory limits); the first failure is returned
 cudaError_t sv_init_attrs();
 cudaError_t tab_init_attrs();
-int sv_threads_for_k(uint32_t k, int ar = SV_AR_PLAIN);
+int sv_threads_for_k(uint32_t k, int ar = SV_AR_PLAIN, bool fp64 = false);
 size_t sv_smem_bytes(bool fp64, uint32_t k, int ar = SV_AR_PLAIN);
 // one pass over one state (grid = tiles); ar applies to FP32 states; the
 // remainder arrays (float2 per amplitude, NULL allowed) to SV_AR_REM only

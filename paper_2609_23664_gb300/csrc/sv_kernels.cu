@@ -37,11 +37,11 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// ---- register operations on the 32 amplitudes of a stage group -------------
-template <typename C, typename T, int P>
-__device__ __forceinline__ void op_u1(C (&a)[32], const T (&m)[8]) {
+// ---- register operations on the N = 2^G amplitudes of a stage group -------
+template <typename C, typename T, int P, int N>
+__device__ __forceinline__ void op_u1(C (&a)[N], const T (&m)[8]) {
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
+  for (int i = 0; i < N; i++) {
     if (i & (1 << P)) continue;
     const int j = i | (1 << P);
     const C x = a[i], y = a[j];
@@ -51,10 +51,10 @@ __device__ __forceinline__ void op_u1(C (&a)[32], const T (&m)[8]) {
     a[j].y = m[4] * x.y + m[5] * x.x + m[6] * y.y + m[7] * y.x;
   }
 }
-template <typename C, typename T, int P>
-__device__ __forceinline__ void op_d1(C (&a)[32], const T (&m)[8]) {
+template <typename C, typename T, int P, int N>
+__device__ __forceinline__ void op_d1(C (&a)[N], const T (&m)[8]) {
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
+  for (int i = 0; i < N; i++) {
     const T dr = (i & (1 << P)) ? m[2] : m[0];
     const T di = (i & (1 << P)) ? m[3] : m[1];
     const C x = a[i];
@@ -62,10 +62,10 @@ __device__ __forceinline__ void op_d1(C (&a)[32], const T (&m)[8]) {
     a[i].y = dr * x.y + di * x.x;
   }
 }
-template <typename C, typename T, int A, int B>
-__device__ __forceinline__ void op_cd(C (&a)[32], const T (&m)[8]) {
+template <typename C, typename T, int A, int B, int N>
+__device__ __forceinline__ void op_cd(C (&a)[N], const T (&m)[8]) {
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
+  for (int i = 0; i < N; i++) {
     if (!(i & (1 << A)) || !(i & (1 << B))) continue;
     const C x = a[i];
     a[i].x = m[0] * x.x - m[1] * x.y;
@@ -73,105 +73,81 @@ __device__ __forceinline__ void op_cd(C (&a)[32], const T (&m)[8]) {
   }
 }
 // diag(1, p): only the amplitudes with bit P set change
-template <typename C, typename T, int P>
-__device__ __forceinline__ void op_p1(C (&a)[32], const T (&m)[8]) {
+template <typename C, typename T, int P, int N>
+__device__ __forceinline__ void op_p1(C (&a)[N], const T (&m)[8]) {
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
+  for (int i = 0; i < N; i++) {
     if (!(i & (1 << P))) continue;
     const C x = a[i];
     a[i].x = m[0] * x.x - m[1] * x.y;
     a[i].y = m[0] * x.y + m[1] * x.x;
   }
 }
-// real 2x2 matrix {m0, m2; m4, m6}
-template <typename C, typename T, int P>
-__device__ __forceinline__ void op_r(C (&a)[32], const T (&m)[8]) {
+// real 2x2 matrix {m0, m2; m4, m6}; FP32: both components of an amplitude
+// in one packed op
+template <typename C, typename T, int P, int N>
+__device__ __forceinline__ void op_r(C (&a)[N], const T (&m)[8]) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 m0 = make_float2(m[0], m[0]), m2 = make_float2(m[2], m[2]);
+    const float2 m4 = make_float2(m[4], m[4]), m6 = make_float2(m[6], m[6]);
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
-    if (i & (1 << P)) continue;
-    const int j = i | (1 << P);
-    const C x = a[i], y = a[j];
-    a[i].x = m[0] * x.x + m[2] * y.x;
-    a[i].y = m[0] * x.y + m[2] * y.y;
-    a[j].x = m[4] * x.x + m[6] * y.x;
-    a[j].y = m[4] * x.y + m[6] * y.y;
+    for (int i = 0; i < N; i++) {
+      if (i & (1 << P)) continue;
+      const int j = i | (1 << P);
+      const float2 x = a[i], y = a[j];
+      a[i] = __ffma2_rn(m2, y, __fmul2_rn(m0, x));
+      a[j] = __ffma2_rn(m6, y, __fmul2_rn(m4, x));
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      if (i & (1 << P)) continue;
+      const int j = i | (1 << P);
+      const C x = a[i], y = a[j];
+      a[i].x = m[0] * x.x + m[2] * y.x;
+      a[i].y = m[0] * x.y + m[2] * y.y;
+      a[j].x = m[4] * x.x + m[6] * y.x;
+      a[j].y = m[4] * x.y + m[6] * y.y;
+    }
   }
 }
-// FP32 real matrix: both components of an amplitude in one packed op
-template <int P>
-__device__ __forceinline__ void op_r_f2(float2 (&a)[32], const float (&m)[8]) {
-  const float2 m0 = make_float2(m[0], m[0]), m2 = make_float2(m[2], m[2]);
-  const float2 m4 = make_float2(m[4], m[4]), m6 = make_float2(m[6], m[6]);
-#pragma unroll
-  for (int i = 0; i < 32; i++) {
-    if (i & (1 << P)) continue;
-    const int j = i | (1 << P);
-    const float2 x = a[i], y = a[j];
-    a[i] = __ffma2_rn(m2, y, __fmul2_rn(m0, x));
-    a[j] = __ffma2_rn(m6, y, __fmul2_rn(m4, x));
-  }
-}
-template <typename C, typename T, int P>
-__device__ __forceinline__ void op_r_any(C (&a)[32], const T (&m)[8]) { op_r<C, T, P>(a, m); }
-template <>
-__device__ __forceinline__ void op_r_any<float2, float, 0>(float2 (&a)[32], const float (&m)[8]) { op_r_f2<0>(a, m); }
-template <>
-__device__ __forceinline__ void op_r_any<float2, float, 1>(float2 (&a)[32], const float (&m)[8]) { op_r_f2<1>(a, m); }
-template <>
-__device__ __forceinline__ void op_r_any<float2, float, 2>(float2 (&a)[32], const float (&m)[8]) { op_r_f2<2>(a, m); }
-template <>
-__device__ __forceinline__ void op_r_any<float2, float, 3>(float2 (&a)[32], const float (&m)[8]) { op_r_f2<3>(a, m); }
-template <>
-__device__ __forceinline__ void op_r_any<float2, float, 4>(float2 (&a)[32], const float (&m)[8]) { op_r_f2<4>(a, m); }
 
 // diag(1, p) after the real 2x2 {r00, r01; r10, r11}: m = {r00, r01, r10, r11, pr, pi}
-template <typename C, typename T, int P>
-__device__ __forceinline__ void op_rp(C (&a)[32], const T (&m)[8]) {
+template <typename C, typename T, int P, int N>
+__device__ __forceinline__ void op_rp(C (&a)[N], const T (&m)[8]) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 m0 = make_float2(m[0], m[0]), m1 = make_float2(m[1], m[1]);
+    const float2 m2 = make_float2(m[2], m[2]), m3 = make_float2(m[3], m[3]);
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
-    if (i & (1 << P)) continue;
-    const int j = i | (1 << P);
-    const C x = a[i], y = a[j];
-    a[i].x = m[0] * x.x + m[1] * y.x;
-    a[i].y = m[0] * x.y + m[1] * y.y;
-    const T tx = m[2] * x.x + m[3] * y.x, ty = m[2] * x.y + m[3] * y.y;
-    a[j].x = m[4] * tx - m[5] * ty;
-    a[j].y = m[4] * ty + m[5] * tx;
+    for (int i = 0; i < N; i++) {
+      if (i & (1 << P)) continue;
+      const int j = i | (1 << P);
+      const float2 x = a[i], y = a[j];
+      a[i] = __ffma2_rn(m1, y, __fmul2_rn(m0, x));
+      const float2 t = __ffma2_rn(m3, y, __fmul2_rn(m2, x));
+      a[j].x = m[4] * t.x - m[5] * t.y;
+      a[j].y = m[4] * t.y + m[5] * t.x;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      if (i & (1 << P)) continue;
+      const int j = i | (1 << P);
+      const C x = a[i], y = a[j];
+      a[i].x = m[0] * x.x + m[1] * y.x;
+      a[i].y = m[0] * x.y + m[1] * y.y;
+      const T tx = m[2] * x.x + m[3] * y.x, ty = m[2] * x.y + m[3] * y.y;
+      a[j].x = m[4] * tx - m[5] * ty;
+      a[j].y = m[4] * ty + m[5] * tx;
+    }
   }
 }
-template <int P>
-__device__ __forceinline__ void op_rp_f2(float2 (&a)[32], const float (&m)[8]) {
-  const float2 m0 = make_float2(m[0], m[0]), m1 = make_float2(m[1], m[1]);
-  const float2 m2 = make_float2(m[2], m[2]), m3 = make_float2(m[3], m[3]);
-#pragma unroll
-  for (int i = 0; i < 32; i++) {
-    if (i & (1 << P)) continue;
-    const int j = i | (1 << P);
-    const float2 x = a[i], y = a[j];
-    a[i] = __ffma2_rn(m1, y, __fmul2_rn(m0, x));
-    const float2 t = __ffma2_rn(m3, y, __fmul2_rn(m2, x));
-    a[j].x = m[4] * t.x - m[5] * t.y;
-    a[j].y = m[4] * t.y + m[5] * t.x;
-  }
-}
-template <typename C, typename T, int P>
-__device__ __forceinline__ void op_rp_any(C (&a)[32], const T (&m)[8]) { op_rp<C, T, P>(a, m); }
-template <>
-__device__ __forceinline__ void op_rp_any<float2, float, 0>(float2 (&a)[32], const float (&m)[8]) { op_rp_f2<0>(a, m); }
-template <>
-__device__ __forceinline__ void op_rp_any<float2, float, 1>(float2 (&a)[32], const float (&m)[8]) { op_rp_f2<1>(a, m); }
-template <>
-__device__ __forceinline__ void op_rp_any<float2, float, 2>(float2 (&a)[32], const float (&m)[8]) { op_rp_f2<2>(a, m); }
-template <>
-__device__ __forceinline__ void op_rp_any<float2, float, 3>(float2 (&a)[32], const float (&m)[8]) { op_rp_f2<3>(a, m); }
-template <>
-__device__ __forceinline__ void op_rp_any<float2, float, 4>(float2 (&a)[32], const float (&m)[8]) { op_rp_f2<4>(a, m); }
 
 // [[c, -is], [-is, c]] with c = m0, s = m1
-template <typename C, typename T, int P>
-__device__ __forceinline__ void op_rx(C (&a)[32], const T (&m)[8]) {
+template <typename C, typename T, int P, int N>
+__device__ __forceinline__ void op_rx(C (&a)[N], const T (&m)[8]) {
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
+  for (int i = 0; i < N; i++) {
     if (i & (1 << P)) continue;
     const int j = i | (1 << P);
     const C x = a[i], y = a[j];
@@ -198,42 +174,37 @@ __device__ __forceinline__ void load_m(const SvOpDesc<double> *op, double (&m)[8
 }
 
 // K_RP at a position known once the caller's loop is unrolled
-template <typename C, typename T>
-__device__ __forceinline__ void rp_at(int P, C (&a)[32], const T (&m)[8]) {
+template <typename C, typename T, int N>
+__device__ __forceinline__ void rp_at(int P, C (&a)[N], const T (&m)[8]) {
   switch (P) {
-    case 0: op_rp_any<C, T, 0>(a, m); break;
-    case 1: op_rp_any<C, T, 1>(a, m); break;
-    case 2: op_rp_any<C, T, 2>(a, m); break;
-    case 3: op_rp_any<C, T, 3>(a, m); break;
-    default: op_rp_any<C, T, 4>(a, m); break;
+    case 0: op_rp<C, T, 0, N>(a, m); break;
+    case 1: op_rp<C, T, 1, N>(a, m); break;
+    case 2: op_rp<C, T, 2, N>(a, m); break;
+    case 3: op_rp<C, T, 3, N>(a, m); break;
+    default: if constexpr (N > 16) op_rp<C, T, 4, N>(a, m); break;
   }
 }
 
-// dispatch on the dense op index (a jump table)
-template <typename C, typename T>
-__device__ __forceinline__ void apply_op(uint32_t code, const T (&m)[8], C (&a)[32]) {
+// dispatch on the dense op index (a jump table); positions beyond the
+// stage's 2^G amplitudes never occur
+template <typename C, typename T, int N>
+__device__ __forceinline__ void apply_op(uint32_t code, const T (&m)[8], C (&a)[N]) {
   switch (code) {
-#define U1(P) case sv_op_index(K_U1, P, 0): op_u1<C, T, P>(a, m); break;
-#define D1(P) case sv_op_index(K_D1, P, 0): op_d1<C, T, P>(a, m); break;
-#define P1(P) case sv_op_index(K_P1, P, 0): op_p1<C, T, P>(a, m); break;
-#define RR(P) case sv_op_index(K_R, P, 0): op_r_any<C, T, P>(a, m); break;
-#define RX(P) case sv_op_index(K_RX, P, 0): op_rx<C, T, P>(a, m); break;
-    U1(0) U1(1) U1(2) U1(3) U1(4)
-    D1(0) D1(1) D1(2) D1(3) D1(4)
-    P1(0) P1(1) P1(2) P1(3) P1(4)
-    RR(0) RR(1) RR(2) RR(3) RR(4)
-    RX(0) RX(1) RX(2) RX(3) RX(4)
-#undef U1
-#undef D1
-#undef P1
-#undef RR
-#undef RX
-#define CD(x, y) case sv_op_index(K_CD, x, y): op_cd<C, T, x, y>(a, m); break;
+#define QW_ONE(K, P, F) \
+  case sv_op_index(K, P, 0): if constexpr ((1 << P) < N) F<C, T, P, N>(a, m); break;
+#define QW_ALL(K, F) QW_ONE(K, 0, F) QW_ONE(K, 1, F) QW_ONE(K, 2, F) QW_ONE(K, 3, F) QW_ONE(K, 4, F)
+    QW_ALL(K_U1, op_u1)
+    QW_ALL(K_D1, op_d1)
+    QW_ALL(K_P1, op_p1)
+    QW_ALL(K_R, op_r)
+    QW_ALL(K_RX, op_rx)
+    QW_ALL(K_RP, op_rp)
+#undef QW_ALL
+#undef QW_ONE
+#define CD(x, y) \
+  case sv_op_index(K_CD, x, y): if constexpr ((1 << y) < N) op_cd<C, T, x, y, N>(a, m); break;
     CD(0, 1) CD(0, 2) CD(0, 3) CD(0, 4) CD(1, 2) CD(1, 3) CD(1, 4) CD(2, 3) CD(2, 4) CD(3, 4)
 #undef CD
-#define RP(P) case sv_op_index(K_RP, P, 0): op_rp_any<C, T, P>(a, m); break;
-    RP(0) RP(1) RP(2) RP(3) RP(4)
-#undef RP
     default: break;
   }
 }
@@ -313,7 +284,7 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
                         const float2 *src_lo, float2 *dst_lo, uint32_t tile) {
   typedef typename V2<T>::t C;
   static_assert(AR == SV_AR_PLAIN || sizeof(T) == 4, "compensated arithmetic is for FP32 states");
-  static_assert((AR == SV_AR_PLAIN) == (G == SV_G), "plain passes run stages of SV_G positions");
+  static_assert(AR == SV_AR_PLAIN ? (G == SV_G || G == SV_G_PLAIN32) : G == SV_G_COMP, "stage width");
   const uint32_t k = pd->k, b = pd->b, n_hi = pd->n_hi;
   uint32_t base = 0;
   for (uint32_t i = 0; i < n_hi; i++) base |= ((tile >> i) & 1u) << pd->hi_pos[i];
@@ -403,24 +374,25 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
       if constexpr (AR != SV_AR_PLAIN) {
         sv_stage_df<AR, G>(smw, lo_off, sbB, roff, ops, ops_lo, op_begin, nops, rp_mask);
       } else {
-      C a[32];
+      constexpr int N = 1 << G;
+      C a[N];
 #pragma unroll
-      for (int i = 0; i < 32; i++) {
+      for (int i = 0; i < N; i++) {
         const uint32_t off = sbB ^ ((i & 1) ? roff[0] : 0u) ^ ((i & 2) ? roff[1] : 0u) ^
                              ((i & 4) ? roff[2] : 0u) ^ ((i & 8) ? roff[3] : 0u) ^
-                             ((i & 16) ? roff[4] : 0u);
+                             ((G > 4 && (i & 16)) ? roff[4] : 0u);
         a[i] = *(const C *)(smc + off);
       }
       if (rp_mask) {
         // rotation-and-phase ops on distinct positions, in position order
         const SvOpDesc<T> *op = ops + op_begin;
 #pragma unroll
-        for (int P = 0; P < SV_G; P++) {
+        for (int P = 0; P < G; P++) {
           if (!(rp_mask & (1u << P))) continue;
           T m[8];
           load_m(op, m);
           op++;
-          rp_at<C, T>(P, a, m);
+          rp_at<C, T, N>(P, a, m);
         }
       } else {
         // the next op's parameters are loaded while the current op runs
@@ -432,17 +404,17 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
           uint32_t ncode = 0;
           T nm[8];
           if (o + 1 < nops) { ncode = __ldg(&op[o + 1].code); load_m(op + o + 1, nm); }
-          apply_op<C, T>(code, m, a);
+          apply_op<C, T, N>(code, m, a);
           code = ncode;
 #pragma unroll
           for (int t = 0; t < 8; t++) m[t] = nm[t];
         }
       }
 #pragma unroll
-      for (int i = 0; i < 32; i++) {
+      for (int i = 0; i < N; i++) {
         const uint32_t off = sbB ^ ((i & 1) ? roff[0] : 0u) ^ ((i & 2) ? roff[1] : 0u) ^
                              ((i & 4) ? roff[2] : 0u) ^ ((i & 8) ? roff[3] : 0u) ^
-                             ((i & 16) ? roff[4] : 0u);
+                             ((G > 4 && (i & 16)) ? roff[4] : 0u);
         *(C *)(smw + off) = a[i];
       }
       }
@@ -527,8 +499,8 @@ sv_pass_kernel(SvTables t, uint32_t pass, const typename V2<T>::t *src, typename
                const float2 *src_lo, float2 *dst_lo) {
   extern __shared__ __align__(16) unsigned char smraw[];
   typedef typename V2<T>::t C;
-  sv_tile<T, AR, sv_stage_width(AR)>(t.passes + pass, t.stages, (const SvOpDesc<T> *)t.ops, t.ops_lo, (C *)smraw,
-                                     src, dst, src_lo, dst_lo, blockIdx.x);
+  sv_tile<T, AR, sv_stage_width(AR, sizeof(T) == 8)>(t.passes + pass, t.stages, (const SvOpDesc<T> *)t.ops, t.ops_lo,
+                                                     (C *)smraw, src, dst, src_lo, dst_lo, blockIdx.x);
 }
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const unsigned int *p) {
@@ -556,8 +528,8 @@ constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per dependency wait
 // the 128-register build (MINB 4) can use.  Compensated passes (AR =
 // SV_AR_COMP) hold two FP32 complex values per amplitude in registers, 16
 // amplitudes per stage group, and are budgeted for three CTAs.
-template <typename T, int MINB, int AR>
-__global__ void __launch_bounds__(128, MINB)
+template <typename T, int MINB, int AR, int NT>
+__global__ void __launch_bounds__(NT, MINB)
 sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, const SvSeg *__restrict__ segs,
                 uint32_t seg_bits, uint32_t total, unsigned int *ctr, EnTables en) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -605,12 +577,15 @@ sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, const SvSeg *__restr
     }
     const SvJob job = jobs[s_job];
     if (job.kind == SVJ_ENERGY) {
-      const EnJob J = en.jobs[job.pass];
-      energy_block<T, 128, false>(J, s_unit, en.classes, en.terms,
-                                  en.partials + 2 * (size_t)(J.block_begin + s_unit));
+      if constexpr (NT == 128) {  // energy work items run in 128-thread CTAs only
+        const EnJob J = en.jobs[job.pass];
+        energy_block<T, 128, false>(J, s_unit, en.classes, en.terms,
+                                    en.partials + 2 * (size_t)(J.block_begin + s_unit));
+      }
     } else {
-      sv_tile<T, AR, sv_stage_width(AR)>(t.passes + job.pass, t.stages, (const SvOpDesc<T> *)t.ops, t.ops_lo,
-                                         (C *)smraw, (const C *)job.src, (C *)job.dst, nullptr, nullptr, s_unit);
+      sv_tile<T, AR, sv_stage_width(AR, sizeof(T) == 8)>(t.passes + job.pass, t.stages, (const SvOpDesc<T> *)t.ops,
+                                                         t.ops_lo, (C *)smraw, (const C *)job.src, (C *)job.dst,
+                                                         nullptr, nullptr, s_unit);
     }
     // every thread's writes of the unit precede thread 0's release through
     // the barrier (bar.sync orders them at CTA scope; the fence is
@@ -624,33 +599,50 @@ sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, const SvSeg *__restr
 }
 
 // ---- host launchers -----------------------------------------------------------
-// 128 threads: every thread owns at least two stage groups of a 2^13 tile,
-// and three CTAs fit on an SM (registers and shared memory).  Passes with a
-// remainder plane (twice the shared memory, one CTA per SM) give every
-// stage group of the tile its own thread, up to 256.  Compensated passes
-// run stages of four positions (16 amplitudes per group).
-int sv_threads_for_k(uint32_t k, int ar) {
-  const uint32_t G = (uint32_t)sv_stage_width(ar);
+// Compensated passes (two FP32 values per amplitude) run stages of four
+// positions, 16 amplitudes per group; plain passes stages of SV_G_PLAIN32
+// (FP32) or five (FP64) positions.  Threads: every thread owns at least two
+// stage groups of a 2^13 tile (128 threads; 256 for plain FP32 passes with
+// four-position stages, whose register budget fits three such CTAs per
+// SM); passes with a remainder plane (twice the shared memory, one CTA per
+// SM) give every stage group its own thread, up to 256.
+constexpr int SV_NT_PLAIN32 = (SV_G_PLAIN32 == 4) ? 256 : 128;
+int sv_threads_for_k(uint32_t k, int ar, bool fp64) {
+  const uint32_t G = (uint32_t)sv_stage_width(ar, fp64);
   const uint32_t g = (ar == SV_AR_REM) ? 1u << (k - G) : 1u << (k - G - 1);
-  const uint32_t cap = (ar == SV_AR_REM) ? 256u : 128u;
+  const uint32_t cap = (ar == SV_AR_REM) ? 256u : (!fp64 && ar == SV_AR_PLAIN) ? (uint32_t)SV_NT_PLAIN32 : 128u;
   return (int)(g < 32 ? 32 : (g > cap ? cap : g));
 }
 size_t sv_smem_bytes(bool fp64, uint32_t k, int ar) {
   return (size_t)(fp64 ? 16 : 8) << k << (ar == SV_AR_REM ? 1 : 0);
 }
 
+// the plain FP32 batch kernel for tiles of k qubits: with 32-amplitude
+// stages a 128-register build (four CTAs per SM) serves tiles of at most 12
+// qubits; 16-amplitude stages use one build
+typedef void (*SvBatchKernel)(SvTables, const SvJob *, const SvSeg *, uint32_t, uint32_t, unsigned int *, EnTables);
+static SvBatchKernel plain32_batch(uint32_t k) {
+  if constexpr (SV_G_PLAIN32 == 4) {
+    (void)k;
+    return sv_batch_kernel<float, 3, SV_AR_PLAIN, SV_NT_PLAIN32>;
+  } else {
+    return k > 12 ? sv_batch_kernel<float, 3, SV_AR_PLAIN, SV_NT_PLAIN32>
+                  : sv_batch_kernel<float, 4, SV_AR_PLAIN, SV_NT_PLAIN32>;
+  }
+}
+
 // Kernel attributes are set once, before any stream capture (a capture
 // fails on attribute changes).
 cudaError_t sv_init_attrs() {
   const int bytes = 200 * 1024;
-  const void *k[] = {(const void *)sv_pass_kernel<float, SV_AR_PLAIN, 128, 3>,
+  const void *k[] = {(const void *)sv_pass_kernel<float, SV_AR_PLAIN, SV_NT_PLAIN32, 3>,
                      (const void *)sv_pass_kernel<float, SV_AR_COMP, 128, 3>,
                      (const void *)sv_pass_kernel<float, SV_AR_REM, 256, 1>,
                      (const void *)sv_pass_kernel<double, SV_AR_PLAIN, 128, 1>,
-                     (const void *)sv_batch_kernel<float, 3, SV_AR_PLAIN>,
-                     (const void *)sv_batch_kernel<float, 4, SV_AR_PLAIN>,
-                     (const void *)sv_batch_kernel<float, 3, SV_AR_COMP>,
-                     (const void *)sv_batch_kernel<double, 1, SV_AR_PLAIN>};
+                     (const void *)plain32_batch(13),
+                     (const void *)plain32_batch(12),
+                     (const void *)sv_batch_kernel<float, 3, SV_AR_COMP, 128>,
+                     (const void *)sv_batch_kernel<double, 1, SV_AR_PLAIN, 128>};
   for (const void *f : k) {
     const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
@@ -662,7 +654,7 @@ void launch_sv_pass(bool fp64, const SvTables &t, uint32_t pass_idx, uint32_t k,
                     void *dst, void *stream, int ar, const void *src_lo, void *dst_lo) {
   const uint32_t tiles = 1u << (n - k);
   if (fp64) ar = SV_AR_PLAIN;
-  const int threads = sv_threads_for_k(k, ar);
+  const int threads = sv_threads_for_k(k, ar, fp64);
   const size_t smem = sv_smem_bytes(fp64, k, ar);
   cudaStream_t s = (cudaStream_t)stream;
   const float2 *sl = (const float2 *)src_lo;
@@ -677,25 +669,23 @@ void launch_sv_pass(bool fp64, const SvTables &t, uint32_t pass_idx, uint32_t k,
     sv_pass_kernel<float, SV_AR_COMP, 128, 3><<<tiles, threads, smem, s>>>(t, pass_idx, (const float2 *)src,
                                                                             (float2 *)dst, nullptr, nullptr);
   } else {
-    sv_pass_kernel<float, SV_AR_PLAIN, 128, 3><<<tiles, threads, smem, s>>>(t, pass_idx, (const float2 *)src,
-                                                                             (float2 *)dst, nullptr, nullptr);
+    sv_pass_kernel<float, SV_AR_PLAIN, SV_NT_PLAIN32, 3><<<tiles, threads, smem, s>>>(
+        t, pass_idx, (const float2 *)src, (float2 *)dst, nullptr, nullptr);
   }
 }
 
 int sv_batch_grid(bool fp64, uint32_t k, int sm_count, int ar) {
   if (fp64 || ar == SV_AR_REM) ar = SV_AR_PLAIN;
-  const int threads = sv_threads_for_k(k, ar);
+  const int threads = sv_threads_for_k(k, ar, fp64);
   const size_t smem = sv_smem_bytes(fp64, k, ar);
   int per_sm = 0;
-  if (fp64) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<double, 1, SV_AR_PLAIN>, threads, smem);
-  } else if (ar == SV_AR_COMP) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float, 3, SV_AR_COMP>, threads, smem);
-  } else if (k <= 12) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float, 4, SV_AR_PLAIN>, threads, smem);
-  } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float, 3, SV_AR_PLAIN>, threads, smem);
-  }
+  if (fp64)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<double, 1, SV_AR_PLAIN, 128>, threads,
+                                                  smem);
+  else if (ar == SV_AR_COMP)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_batch_kernel<float, 3, SV_AR_COMP, 128>, threads, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plain32_batch(k), threads, smem);
   if (per_sm < 1) per_sm = 1;
   return per_sm * sm_count;
 }
@@ -704,21 +694,17 @@ void launch_sv_batch(bool fp64, const SvTables &t, const SvJob *jobs, const SvSe
                      uint32_t total_items, uint32_t k_max, unsigned int *counters, const EnTables &en,
                      int grid, void *stream, int ar) {
   if (fp64 || ar == SV_AR_REM) ar = SV_AR_PLAIN;
-  const int threads = sv_threads_for_k(k_max, ar);
+  const int threads = sv_threads_for_k(k_max, ar, fp64);
   const size_t smem = sv_smem_bytes(fp64, k_max, ar);
   cudaStream_t s = (cudaStream_t)stream;
   if (fp64)
-    sv_batch_kernel<double, 1, SV_AR_PLAIN><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items,
-                                                                        counters, en);
+    sv_batch_kernel<double, 1, SV_AR_PLAIN, 128><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items,
+                                                                             counters, en);
   else if (ar == SV_AR_COMP)
-    sv_batch_kernel<float, 3, SV_AR_COMP><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items,
-                                                                      counters, en);
-  else if (k_max <= 12)
-    sv_batch_kernel<float, 4, SV_AR_PLAIN><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items,
-                                                                       counters, en);
+    sv_batch_kernel<float, 3, SV_AR_COMP, 128><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items,
+                                                                           counters, en);
   else
-    sv_batch_kernel<float, 3, SV_AR_PLAIN><<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items,
-                                                                       counters, en);
+    plain32_batch(k_max)<<<grid, threads, smem, s>>>(t, jobs, segs, seg_bits, total_items, counters, en);
 }
 
 }  // namespace qw
