@@ -236,6 +236,24 @@ def test_noisy_small(eng):
     assert bad == 0
 
 
+def test_noisy_full_trajectory_count_at_14_qubits(eng):
+    # the noisy family's full shape (400 gates, 1024 trajectories with Pauli
+    # noise at p = 1e-3, 100 shots each) at 14 qubits: every trajectory's
+    # samples against the oracle's rerun from |0...0>
+    tasks = W.noisy22_trajectories(n=14)
+    assert len(tasks) == 1024 and tasks[0].shots == 100
+    p, wl = run_plan(eng, tasks)
+    ex = p.explain()
+    assert ex["tasks_reusing"] > 0 and ex["artifacts"] > 1
+    bad = []
+    for i, t in enumerate(tasks):
+        ref = orc.run_task(t, want_state=True)
+        ok, m = sample_agrees(p.samples(i), ref["samples"], ref["state"], t.uniforms)
+        if not ok:
+            bad.append((i, m))
+    assert not bad, bad[:10]
+
+
 def test_qec_small_bit_exact(eng):
     tasks = W.qec_surface_code_tasks(d=5, shared_rounds=8, task_rounds=3, n_tasks=48, p=0.02)
     p, wl = run_plan(eng, tasks)
