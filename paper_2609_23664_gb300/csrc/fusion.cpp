@@ -6,9 +6,10 @@
 // loads a tile (2^k amplitudes with the bits outside Q fixed) into shared
 // memory, applies every gate of the pass and writes the tile back.  Gates
 // are taken out of order only past gates on disjoint qubits (they commute).
-// Inside a pass, gates are grouped into STAGES of at most 5 tile bits; a
-// thread holds the 32 amplitudes of one stage group in registers and applies
-// the whole stage there.  Consecutive single-qubit gates on one qubit are
+// Inside a pass, gates are grouped into STAGES of at most G tile bits (5 for
+// plain passes, 4 for compensated FP32 ones); a thread holds the 2^G
+// amplitudes of one stage group in registers and applies the whole stage
+// there.  Consecutive single-qubit gates on one qubit are
 // multiplied into one 2x2 matrix in double precision.  Permutation gates
 // (CNOT, SWAP, X) are index relabellings: the pass tracks an affine map over
 // GF(2) from logical tile index to slot, and a permutation only changes that

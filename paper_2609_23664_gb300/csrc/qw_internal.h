@@ -64,7 +64,7 @@ bool is_barrier_op(uint32_t op);  // MEASURE / RESET
 // ---------------------------------------------------------------------------
 // statevector program (host-side fusion result and device descriptors)
 // ---------------------------------------------------------------------------
-// Operation kinds applied to the 32 register amplitudes of a stage group.
+// Operation kinds applied to the register amplitudes of a stage group.
 enum SvKind : uint8_t {
   K_U1 = 1,    // general 2x2 on position a: m = {u00r,u00i,u01r,u01i,u10r,u10i,u11r,u11i}
   K_D1 = 2,    // diagonal on a: m = {d0r,d0i,d1r,d1i}
@@ -151,8 +151,9 @@ struct TileConfig {
   uint32_t k_max = 13;  // tile qubits
   uint32_t b = 4;       // contiguous low qubits in every tile
   uint32_t g = SV_G;    // positions per stage
-  // measured time of one pass of the autotuning circuit with this tile
-  // shape and arithmetic (ns, launch included); 0 = not measured
+  // measured time per state of one pass of the autotuning circuits with this
+  // tile shape and arithmetic, several states advanced together in the
+  // persistent launch (ns); 0 = not measured
   double pass_ns = 0;
 };
 

@@ -3,9 +3,10 @@
 // One CTA processes one TILE of a pass: 2^k amplitudes whose non-tile bits
 // are fixed.  The tile is read from HBM in contiguous runs of 2^b amplitudes,
 // kept in shared memory (XOR-swizzled to spread the strided stage accesses
-// over the banks), and every STAGE of the pass is applied with the stage's
-// 32 amplitudes of a group held in registers, so that the gates of a stage
-// cost no shared-memory traffic.  The prefix is executed once (Sec. III-A,
+// over the banks), and every STAGE of the pass is applied with the 2^G
+// amplitudes of a stage group held in registers (32 for plain passes, 16
+// for compensated ones, which hold two FP32 values per amplitude), so that
+// the gates of a stage cost no shared-memory traffic.  The prefix is executed once (Sec. III-A,
 // Fig. 1); the first suffix pass of every task reads its tile from the
 // boundary state and writes the task's own buffer, so the reload of the
 // boundary (C_reload of Eq. 2) costs no separate copy.
