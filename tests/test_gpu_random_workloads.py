@@ -2,7 +2,10 @@
 trie shapes (groups sharing prefixes, sub-groups sharing mid-segments,
 loners), random modes and register sizes, random gate mixes, Pauli errors on
 stabilizer tasks and Clifford prefixes on statevector tasks, under several
-plan options.  Every task is compared with the oracle."""
+plan options.  Every task is compared with the oracle.  Registers of 2-14
+qubits fit one tile; a second set draws 15-20 qubits, so that passes span
+several tiles (tile maps across passes, outside-control CNOTs, multi-pass
+suffixes and boundaries)."""
 import numpy as np
 import pytest
 
@@ -26,12 +29,12 @@ def sv_gates(rng, n, k, clifford=False):
     return W.random_circuit(rng, n, k)
 
 
-def random_workload(seed):
+def random_workload(seed, n_sv=(2, 15)):
     rng = np.random.default_rng(seed)
     tasks = []
     for _ in range(int(rng.integers(3, 7))):                 # families
         mode = int(rng.choice([W.MODE_SV_FP64, W.MODE_SV_FP32, W.MODE_TABLEAU]))
-        n = int(rng.integers(2, 15)) if mode != W.MODE_TABLEAU else int(rng.integers(3, 40))
+        n = int(rng.integers(*n_sv)) if mode != W.MODE_TABLEAU else int(rng.integers(3, 40))
         if mode == W.MODE_TABLEAU:
             pre = W.random_clifford_layers(rng, n, int(rng.integers(1, 6)))
         else:
@@ -99,6 +102,17 @@ def eng():
                                   dict(delta_frac=0.0, dense_boundaries=2)])
 def test_random_workload_matches_oracle(eng, seed, opts):
     tasks = random_workload(1000 + seed)
+    wl = Q.Workload(tasks)
+    p = Q.Plan(eng, wl, **opts)
+    p.run()
+    check(p, tasks)
+    p.close()
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("opts", [dict(), dict(delta_frac=0.0, min_group=2, batched=0)])
+def test_random_workload_multi_tile_registers(eng, seed, opts):
+    tasks = random_workload(2000 + seed, n_sv=(15, 21))
     wl = Q.Workload(tasks)
     p = Q.Plan(eng, wl, **opts)
     p.run()
