@@ -161,11 +161,14 @@ qw_status qw_engine_info(const qw_engine *e, double *hbm_gbs, int32_t *sm_count,
  * allocates and frees its buffer. */
 qw_status qw_engine_probe_l2(qw_engine *e, double *l2_read_gbs);
 /* Tile-shape tuning (the autotuner of the statevector passes: tile qubits,
- * contiguous low qubits, stage width, and the measured time of one pass that
- * calibrates the analytic cost of Eq. 2), kept per (qubit count, precision,
- * FP32 arithmetic, gate mix) and measured on first use.  The gate mix is
- * "layered" (at most 35 % two-qubit gates, hardware-efficient layers) or
- * "entangling" (more), each tuned on a circuit of its kind.  _json writes
+ * contiguous low qubits, stage width, and pass_ns, the measured time per
+ * state of one pass that calibrates the analytic cost of Eq. 2), kept per
+ * (qubit count, precision, FP32 arithmetic, gate mix) and measured on first
+ * use in the persistent suffix launch, with several states advanced
+ * together as a wave's tasks are.  The gate mix is "layered" (at most 35 %
+ * two-qubit gates: hardware-efficient circuits of 1-4 layers) or
+ * "entangling" (more: a random circuit), each tuned on circuits of its kind.
+ * _json writes
  * the engine's tuning as JSON (size-query idiom, as qw_explain_json), with
  * the GPU model it was measured on and the number of shapes this engine
  * timed itself; _load adds the entries of such a record to an engine on the
