@@ -161,11 +161,11 @@ qw_status qw_engine_info(const qw_engine *e, double *hbm_gbs, int32_t *sm_count,
  * allocates and frees its buffer. */
 qw_status qw_engine_probe_l2(qw_engine *e, double *l2_read_gbs);
 /* Tile-shape tuning (the autotuner of the statevector passes: tile qubits,
- * contiguous low qubits, stage width, and pass_ns, the measured time per
- * state of one pass that calibrates the analytic cost of Eq. 2), kept per
+ * contiguous low qubits, stage width, and pass_ns, the measured time of one
+ * pass on one state that calibrates the analytic cost of Eq. 2), kept per
  * (qubit count, precision, FP32 arithmetic, gate mix) and measured on first
- * use in the persistent suffix launch, with several states advanced
- * together as a wave's tasks are.  The gate mix is "layered" (at most 35 %
+ * use.  Shapes are compared in the persistent suffix launch with several
+ * states advanced together, as a wave's tasks are.  The gate mix is "layered" (at most 35 %
  * two-qubit gates: hardware-efficient circuits of 1-4 layers) or
  * "entangling" (more: a random circuit), each tuned on circuits of its kind.
  * _json writes

@@ -1671,7 +1671,6 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar, uint32_t mix) 
       }
       if (tc.b + 2 > tc.k_max || tc.k_max > best_cap) continue;
       float tot = 0;
-      size_t n_passes = 0;
       for (const auto &g : circuits) {
         SvProgram pr = fuse_sv(g.data(), g.size(), key_n, tc);
         SvTableBuilder tb(fp64);
@@ -1724,14 +1723,44 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar, uint32_t mix) 
         }
         CK(cudaStreamSynchronize(s));
         dar.release();
-        n_passes += pr.passes.size() * chains;
       }
       if (tot < best_ms) {
         best_ms = tot;
         best = tc;
-        best.pass_ns = (double)tot * 1e6 / 2.0 / std::max<double>(1.0, (double)n_passes);
       }
     }
+  }
+  // the analytic cost's calibration (Eq. 2): the chosen shape's time per
+  // pass on one state, its passes launched one by one, as the cost probe
+  // times the segments of one task
+  {
+    float tot = 0;
+    size_t n_passes = 0;
+    for (const auto &g : circuits) {
+      SvProgram pr = fuse_sv(g.data(), g.size(), key_n, best);
+      SvTableBuilder tb(fp64);
+      tb.add(pr);
+      SvTables T;
+      DevArena dar;
+      T.passes = dar.upload(tb.passes, s);
+      T.stages = dar.upload(tb.stages, s);
+      T.ops = fp64 ? (const void *)dar.upload(tb.ops64, s) : (const void *)dar.upload(tb.ops32, s);
+      T.ops_lo = fp64 ? nullptr : dar.upload(tb.ops32lo, s);
+      for (int r = 0; r < 3; r++) {  // one warm-up, two timed
+        cudaEventRecord(e0, s);
+        for (size_t p = 0; p < pr.passes.size(); p++)
+          launch_sv_pass(fp64, T, (uint32_t)p, (uint32_t)pr.passes[p].q.size(), key_n, buf, buf, s, ar);
+        cudaEventRecord(e1, s);
+        CK(cudaEventSynchronize(e1));
+        float ms;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r) tot += ms;
+      }
+      CK(cudaStreamSynchronize(s));
+      dar.release();
+      n_passes += pr.passes.size();
+    }
+    best.pass_ns = (double)tot * 1e6 / 2.0 / std::max<double>(1.0, (double)n_passes);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

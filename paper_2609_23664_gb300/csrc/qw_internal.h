@@ -151,9 +151,9 @@ struct TileConfig {
   uint32_t k_max = 13;  // tile qubits
   uint32_t b = 4;       // contiguous low qubits in every tile
   uint32_t g = SV_G;    // positions per stage
-  // measured time per state of one pass of the autotuning circuits with this
-  // tile shape and arithmetic, several states advanced together in the
-  // persistent launch (ns); 0 = not measured
+  // measured time of one pass of the autotuning circuits with this tile
+  // shape and arithmetic on one state, pass by pass (ns, launch included);
+  // 0 = not measured
   double pass_ns = 0;
 };
 
