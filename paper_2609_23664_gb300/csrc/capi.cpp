@@ -141,8 +141,29 @@ qw_status qw_engine_tuning_json(const qw_engine *e, char *buf, size_t cap, size_
   return put_json(s, buf, cap, needed);
 }
 
+// JSON text without the whitespace outside strings (a record may have been
+// pretty-printed since qw_engine_tuning_json wrote it)
+static std::string json_compact(const char *json) {
+  std::string out;
+  bool in_str = false, esc = false;
+  for (const char *c = json; *c; c++) {
+    if (in_str) {
+      out += *c;
+      if (esc) esc = false;
+      else if (*c == '\\') esc = true;
+      else if (*c == '"') in_str = false;
+    } else if (*c == '"') {
+      in_str = true;
+      out += *c;
+    } else if (*c != ' ' && *c != '\t' && *c != '\n' && *c != '\r') {
+      out += *c;
+    }
+  }
+  return out;
+}
+
 static void load_tuning(qw_engine *e, const char *json) {
-  const std::string s(json);
+  const std::string s = json_compact(json);
   const std::string dev = "\"device\":\"" + device_tag(e->e.device) + "\"";
   if (s.find("\"type\":\"QuWARP:Tuning\"") == std::string::npos)
     fail(QW_ERR_INVALID_ARG, "not a tuning record of this library");

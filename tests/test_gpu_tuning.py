@@ -69,7 +69,9 @@ def test_gate_mix_keys_and_transfer():
         assert t["pass_ns"] > 0 and t["b"] + 2 <= t["k"]
 
     b = Q.Engine(0)
-    b.load_tuning(json.loads(json.dumps(rec)))
+    # a pretty-printed record loads as well (whitespace outside strings is ignored)
+    pretty = json.dumps(rec, indent=2).encode()
+    assert Q.lib().qw_engine_tuning_load(b.h, pretty) == 0
     tl_b, el_b = run(b, layered_tasks())
     te_b, ee_b = run(b, entangling_tasks())
     assert b.tuning()["tuning_runs"] == 0           # no shape was timed
