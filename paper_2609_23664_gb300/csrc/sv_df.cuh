@@ -78,7 +78,9 @@ __device__ __forceinline__ void df_renorm(float2 &h, float2 &l) {
 // m / ml: the op's parameters (see SvKind) and their FP32 remainders.
 
 // real 2x2 {r00, r01; r10, r11} on position P, then (when phase) diag(1, p)
-// with p = (m[4], m[5]): K_RP layout {r00, r01, r10, r11, pr, pi}
+// with p = (m[4], m[5]): K_RP layout {r00, r01, r10, r11, pr, pi}.  Every
+// pair's rotation is issued before the phase products, which depend on them
+// (measured: 442 ms against 463 ms for the 256-task suffix launch)
 template <int P, int N>
 __device__ __forceinline__ void dfop_rp(float2 (&h)[N], float2 (&l)[N], const float (&m)[8], const float (&ml)[8],
                                         bool phase) {
@@ -91,7 +93,11 @@ __device__ __forceinline__ void dfop_rp(float2 (&h)[N], float2 (&l)[N], const fl
     const float2 xh = h[i], xl = l[i], yh = h[j], yl = l[j];
     df_lin2(r00, e00, xh, xl, r01, e01, yh, yl, h[i], l[i]);
     df_lin2(r10, e10, xh, xl, r11, e11, yh, yl, h[j], l[j]);
-    if (phase) df_cmul(m[4], ml[4], m[5], ml[5], h[j], l[j]);
+  }
+  if (phase) {
+#pragma unroll
+    for (int i = 0; i < N; i++)
+      if (i & (1 << P)) df_cmul(m[4], ml[4], m[5], ml[5], h[i], l[i]);
   }
 }
 // K_R layout {r00, 0, r01, 0, r10, 0, r11, 0}
