@@ -63,6 +63,7 @@ struct SvTableBuilder {
   std::vector<SvStageDesc> stages;
   std::vector<SvOpDesc<float>> ops32;
   std::vector<float> ops32lo;  // m[t] - (float)m[t] per FP32 op (compensated passes)
+  std::vector<float> ph;       // phase products of full rotation-and-phase stages (FP32)
   std::vector<SvOpDesc<double>> ops64;
   bool fp64;
   explicit SvTableBuilder(bool f) : fp64(f) {}
@@ -223,6 +224,26 @@ struct SvTableBuilder {
             }
         }
         sd.rp_mask = rp_stage ? rp_mask : 0u;
+        // a stage of four-position groups with a rotation-and-phase op on
+        // every position is D R3 R2 R1 R0 with D the product of the ops'
+        // |1>-phases (each diagonal on its own position, so it commutes
+        // with the other positions' rotations): amplitude e of the group
+        // takes the product of the phases of its set positions, computed
+        // here in FP64 and stored as double-float pairs
+        sd.ph_block = 0xFFFFFFFFu;
+        if (!fp64 && pr.g == 4 && rp_stage && rp_mask == 0xFu) {
+          sd.ph_block = (uint32_t)(ph.size() / 64);
+          for (uint32_t e = 0; e < 16; e++) {
+            std::complex<double> q(1.0, 0.0);
+            for (const HostOp &o : sops)
+              if ((e >> o.a) & 1u) q *= std::complex<double>(o.m[4], o.m[5]);
+            const float rh = (float)q.real(), ih = (float)q.imag();
+            ph.push_back(rh);
+            ph.push_back((float)(q.real() - (double)rh));
+            ph.push_back(ih);
+            ph.push_back((float)(q.imag() - (double)ih));
+          }
+        }
         sd.n_ops = (uint32_t)sops.size();
         sd.op_begin = (uint32_t)(fp64 ? ops64.size() : ops32.size());
         for (const HostOp &o : sops) {
@@ -415,6 +436,21 @@ static double pass_flops(const HostPass &hp, uint32_t n, uint32_t g, int ar) {
   double f = 0;
   for (const HostStage &st : hp.stages) {
     double fg = comp ? A * 6.0 : 0.0;
+    // a compensated four-position stage with a rotation (and phase) on
+    // every position: four rotations and one product per amplitude from the
+    // stage's phase table (every amplitude but the first)
+    if (comp && g == 4 && st.ops.size() == 4) {
+      uint32_t mask = 0;
+      bool rot = true;
+      for (const HostOp &o : st.ops) {
+        rot = rot && (o.kind == K_RP || o.kind == K_R) && !(mask & (1u << o.a));
+        mask |= 1u << o.a;
+      }
+      if (rot && mask == 0xFu) {
+        f += (fg + 4.0 * A * lin + (A - 1.0) * cm) * groups;
+        continue;
+      }
+    }
     for (const HostOp &o : st.ops) {
       switch (o.kind) {
         case K_R: case K_RX: fg += A * lin; break;
@@ -538,6 +574,7 @@ static void prepare(qw_plan *P) {
   D->t32.stages = D->arena.upload(b32.stages, s);
   D->t32.ops = D->arena.upload(b32.ops32, s);
   D->t32.ops_lo = D->arena.upload(b32.ops32lo, s);
+  D->t32.ph = D->arena.upload(b32.ph, s);
   D->t64.passes = D->arena.upload(b64.passes, s);
   D->t64.stages = D->arena.upload(b64.stages, s);
   D->t64.ops = D->arena.upload(b64.ops64, s);
@@ -1681,6 +1718,7 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar, uint32_t mix) 
         T.stages = dar.upload(tb.stages, s);
         T.ops = fp64 ? (const void *)dar.upload(tb.ops64, s) : (const void *)dar.upload(tb.ops32, s);
         T.ops_lo = fp64 ? nullptr : dar.upload(tb.ops32lo, s);
+        T.ph = fp64 ? nullptr : dar.upload(tb.ph, s);
         // timed in the persistent batch kernel that runs the suffixes: each
         // state's passes a chain of jobs (each waiting for the last), the
         // chains interleaved pass by pass
@@ -1746,6 +1784,7 @@ TileConfig Engine::tile_config(uint32_t n_eff, bool fp64, int ar, uint32_t mix) 
       T.stages = dar.upload(tb.stages, s);
       T.ops = fp64 ? (const void *)dar.upload(tb.ops64, s) : (const void *)dar.upload(tb.ops32, s);
       T.ops_lo = fp64 ? nullptr : dar.upload(tb.ops32lo, s);
+      T.ph = fp64 ? nullptr : dar.upload(tb.ph, s);
       for (int r = 0; r < 3; r++) {  // one warm-up, two timed
         cudaEventRecord(e0, s);
         for (size_t p = 0; p < pr.passes.size(); p++)
@@ -1927,6 +1966,7 @@ void costmodel_probe(Engine *E, const Workload &W, float *feat, float *tgt, floa
       Tt.stages = ar.upload(tb.stages, s);
       Tt.ops = fp64 ? (const void *)ar.upload(tb.ops64, s) : (const void *)ar.upload(tb.ops32, s);
       Tt.ops_lo = fp64 ? nullptr : ar.upload(tb.ops32lo, s);
+      Tt.ph = fp64 ? nullptr : ar.upload(tb.ph, s);
       float best = 1e30f;
       for (int r = 0; r < 3; r++) {
         cudaEventRecord(e0, s);
@@ -1998,6 +2038,7 @@ qw_status sv_apply_dev(Engine *E, uint32_t mode, uint32_t n, void *state, const 
   SvStageDesc *ds = stream_upload(tb.stages, s);
   void *dop = fp64 ? (void *)stream_upload(tb.ops64, s) : (void *)stream_upload(tb.ops32, s);
   float *dlo = fp64 ? nullptr : stream_upload(tb.ops32lo, s);
+  float *dph = fp64 ? nullptr : stream_upload(tb.ph, s);
   const size_t np = pr.passes.size();
   void *rem = nullptr;
   if (ar == SV_AR_REM && np > 1) CK(cudaMallocAsync(&rem, sv_state_bytes(false, n), s));
@@ -2005,6 +2046,7 @@ qw_status sv_apply_dev(Engine *E, uint32_t mode, uint32_t n, void *state, const 
   T.stages = ds;
   T.ops = dop;
   T.ops_lo = dlo;
+  T.ph = dph;
   for (size_t p = 0; p < np; p++)
     launch_sv_pass(fp64, T, (uint32_t)p, (uint32_t)pr.passes[p].q.size(), n,
                    (p == 0 && init) ? nullptr : state, state, s, ar, p > 0 ? rem : nullptr,
@@ -2012,6 +2054,7 @@ qw_status sv_apply_dev(Engine *E, uint32_t mode, uint32_t n, void *state, const 
   CK(cudaGetLastError());
   CK(cudaFreeAsync(dp, s));
   CK(cudaFreeAsync(ds, s));
+  if (dph) CK(cudaFreeAsync(dph, s));
   CK(cudaFreeAsync(dop, s));
   if (dlo) CK(cudaFreeAsync(dlo, s));
   if (rem) CK(cudaFreeAsync(rem, s));

@@ -197,7 +197,12 @@ struct alignas(16) SvStageDesc {
   // nonzero: the stage's ops are K_RP ops on the positions of this mask,
   // one per position in ascending order (run without dispatch)
   uint32_t rp_mask;
-  uint32_t pad[2];
+  // compensated FP32 stage with a K_RP op on every position: block of the
+  // phase table (16 entries) holding, for each amplitude index e of the
+  // stage group, the product of the |1>-phases of e's set positions;
+  // 0xFFFFFFFF = none
+  uint32_t ph_block;
+  uint32_t pad;
   // per-tile terms of cst: XOR ctl_w[i] when bit ctl_tb[i] of the tile index is set
   uint32_t ctl_tb[SV_MAX_OUT_CTL], ctl_w[SV_MAX_OUT_CTL];
 };
@@ -308,10 +313,13 @@ void stabilizers_from_inverse(uint32_t n, const uint64_t *rows, const uint8_t *s
 // kernel launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
 struct SvTables {
-  const SvPassDesc *passes;
-  const SvStageDesc *stages;
-  const void *ops;       // SvOpDesc<T>*
-  const float *ops_lo;   // FP32: m[t] - (float)m[t] of every op, 8 floats per op (compensated passes)
+  const SvPassDesc *passes = nullptr;
+  const SvStageDesc *stages = nullptr;
+  const void *ops = nullptr;       // SvOpDesc<T>*
+  const float *ops_lo = nullptr;   // FP32: m[t] - (float)m[t] of every op, 8 floats per op (compensated passes)
+  // compensated FP32: phase products per stage block, 16 entries of
+  // {re, re - (float)re, im, im - (float)im} (see SvStageDesc::ph_block)
+  const float *ph = nullptr;
 };
 // Arithmetic of FP32 statevector passes.  PLAIN: FP32 registers.  COMP:
 // double-float registers (every op exact to about 2^-48), the amplitude

@@ -226,7 +226,7 @@ template <int AR, int G>
 __device__ __forceinline__ void sv_stage_df(char *smw, uint32_t lo_off, uint32_t sbB, const uint32_t (&roff)[SV_G],
                                             const SvOpDesc<float> *__restrict__ ops,
                                             const float *__restrict__ ops_lo, uint32_t op_begin, uint32_t nops,
-                                            uint32_t rp_mask) {
+                                            uint32_t rp_mask, const float *__restrict__ ph, uint32_t ph_block) {
   constexpr int N = 1 << G;
   float2 h[N], l[N];
 #pragma unroll
@@ -244,7 +244,29 @@ __device__ __forceinline__ void sv_stage_df(char *smw, uint32_t lo_off, uint32_t
     ml[0] = u.x; ml[1] = u.y; ml[2] = u.z; ml[3] = u.w;
     ml[4] = v.x; ml[5] = v.y; ml[6] = v.z; ml[7] = v.w;
   };
-  if (rp_mask) {
+  if (G == 4 && rp_mask == 0xFu) {
+    // a rotation-and-phase op on every position: the four rotations, then
+    // the stage's combined diagonal (amplitude e times the product of the
+    // phases of its set positions, from the host's table) when there is one
+    const bool table = ph != nullptr && ph_block != 0xFFFFFFFFu;
+    float m[8], ml[8];
+    load_ml(op_begin, m, ml);
+    dfop_rp<0, N>(h, l, m, ml, !table);
+    load_ml(op_begin + 1, m, ml);
+    dfop_rp<1, N>(h, l, m, ml, !table);
+    load_ml(op_begin + 2, m, ml);
+    dfop_rp<2, N>(h, l, m, ml, !table);
+    load_ml(op_begin + 3, m, ml);
+    dfop_rp<3, N>(h, l, m, ml, !table);
+    if (table) {
+      const float4 *q = (const float4 *)ph + 16 * (size_t)ph_block;
+#pragma unroll
+      for (int e = 1; e < N; e++) {
+        const float4 w = __ldg(q + e);
+        df_cmul(w.x, w.y, w.z, w.w, h[e], l[e]);
+      }
+    }
+  } else if (rp_mask) {
     uint32_t o = op_begin;
 #pragma unroll
     for (int P = 0; P < G; P++) {
@@ -281,6 +303,7 @@ __device__ __forceinline__ void sv_stage_df(char *smw, uint32_t lo_off, uint32_t
 template <typename T, int AR, int G>
 __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__restrict__ stages,
                         const SvOpDesc<T> *__restrict__ ops, const float *__restrict__ ops_lo,
+                        const float *__restrict__ ph,
                         typename V2<T>::t *sm, const typename V2<T>::t *src, typename V2<T>::t *dst,
                         const float2 *src_lo, float2 *dst_lo, uint32_t tile) {
   typedef typename V2<T>::t C;
@@ -365,7 +388,7 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
     // the map's constant, with the per-tile terms of outside-control CNOTs
     const uint32_t cst = (w3.z ^ (((tile >> w5.x) & 1u) ? w6.x : 0u) ^ (((tile >> w5.y) & 1u) ? w6.y : 0u) ^
                           (((tile >> w5.z) & 1u) ? w6.z : 0u) ^ (((tile >> w5.w) & 1u) ? w6.w : 0u)) & tm;
-    const uint32_t nops = w3.w, op_begin = w4.x, rp_mask = w4.y;
+    const uint32_t nops = w3.w, op_begin = w4.x, rp_mask = w4.y, ph_block = w4.z;
     static_assert(SV_MAX_GBITS == 9 && SV_MAX_OUT_CTL == 4 && sizeof(SvStageDesc) == 112,
                   "stage descriptor read as seven 16-byte words");
     for (uint32_t grp = threadIdx.x; grp < n_groups; grp += nt) {
@@ -373,7 +396,7 @@ __device__ void sv_tile(const SvPassDesc *__restrict__ pd, const SvStageDesc *__
 #pragma unroll
       for (int t = 0; t < SV_MAX_GBITS; t++) sbB ^= ((grp >> t) & 1u) ? gcol[t] : 0u;
       if constexpr (AR != SV_AR_PLAIN) {
-        sv_stage_df<AR, G>(smw, lo_off, sbB, roff, ops, ops_lo, op_begin, nops, rp_mask);
+        sv_stage_df<AR, G>(smw, lo_off, sbB, roff, ops, ops_lo, op_begin, nops, rp_mask, ph, ph_block);
       } else {
       constexpr int N = 1 << G;
       C a[N];
@@ -501,7 +524,7 @@ sv_pass_kernel(SvTables t, uint32_t pass, const typename V2<T>::t *src, typename
   extern __shared__ __align__(16) unsigned char smraw[];
   typedef typename V2<T>::t C;
   sv_tile<T, AR, sv_stage_width(AR, sizeof(T) == 8)>(t.passes + pass, t.stages, (const SvOpDesc<T> *)t.ops, t.ops_lo,
-                                                     (C *)smraw, src, dst, src_lo, dst_lo, blockIdx.x);
+                                                     t.ph, (C *)smraw, src, dst, src_lo, dst_lo, blockIdx.x);
 }
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const unsigned int *p) {
@@ -585,8 +608,8 @@ sv_batch_kernel(SvTables t, const SvJob *__restrict__ jobs, const SvSeg *__restr
       }
     } else {
       sv_tile<T, AR, sv_stage_width(AR, sizeof(T) == 8)>(t.passes + job.pass, t.stages, (const SvOpDesc<T> *)t.ops,
-                                                         t.ops_lo, (C *)smraw, (const C *)job.src, (C *)job.dst,
-                                                         nullptr, nullptr, s_unit);
+                                                         t.ops_lo, t.ph, (C *)smraw, (const C *)job.src,
+                                                         (C *)job.dst, nullptr, nullptr, s_unit);
     }
     // every thread's writes of the unit precede thread 0's release through
     // the barrier (bar.sync orders them at CTA scope; the fence is
