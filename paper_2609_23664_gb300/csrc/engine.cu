@@ -447,7 +447,11 @@ static double pass_flops(const HostPass &hp, uint32_t n, uint32_t g, int ar) {
         mask |= 1u << o.a;
       }
       if (rot && mask == 0xFu) {
-        f += (fg + 4.0 * A * lin + (A - 1.0) * cm) * groups;
+        // rounded amplitudes enter a SV_AR_COMP stage with zero remainders:
+        // its first rotation has no remainder products (2 packed FMAs, 8
+        // flops, per output)
+        const double first = (ar == SV_AR_COMP) ? lin - 8.0 : lin;
+        f += (fg + A * first + 3.0 * A * lin + (A - 1.0) * cm) * groups;
         continue;
       }
     }

@@ -31,6 +31,8 @@ __device__ __forceinline__ float2 f2swap(float2 a) { return make_float2(a.y, a.x
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, f2neg(b)); }
 
 // r = c1 * x + c2 * y, componentwise; coefficients and operands double-float
+// (ZL: the operands' remainders xl, yl are zero and not read)
+template <bool ZL = false>
 __device__ __forceinline__ void df_lin2(float2 c1h, float2 c1l, float2 xh, float2 xl, float2 c2h, float2 c2l,
                                         float2 yh, float2 yl, float2 &rh, float2 &rl) {
   const float2 p = __fmul2_rn(c1h, xh);
@@ -40,8 +42,11 @@ __device__ __forceinline__ void df_lin2(float2 c1h, float2 c1l, float2 xh, float
   const float2 s = __fadd2_rn(p, q);                // TwoSum: p + q = s + es exactly
   const float2 z = f2sub(s, p);
   const float2 es = __fadd2_rn(f2sub(p, f2sub(s, z)), f2sub(q, z));
-  float2 l = __ffma2_rn(c1h, xl, ep);
-  l = __ffma2_rn(c2h, yl, l);
+  float2 l = ep;
+  if constexpr (!ZL) {
+    l = __ffma2_rn(c1h, xl, l);
+    l = __ffma2_rn(c2h, yl, l);
+  }
   l = __ffma2_rn(c1l, xh, l);
   l = __ffma2_rn(c2l, yh, l);
   rl = __fadd2_rn(l, __fadd2_rn(eq, es));
@@ -81,7 +86,9 @@ __device__ __forceinline__ void df_renorm(float2 &h, float2 &l) {
 // with p = (m[4], m[5]): K_RP layout {r00, r01, r10, r11, pr, pi}.  Every
 // pair's rotation is issued before the phase products, which depend on them
 // (measured: 442 ms against 463 ms for the 256-task suffix launch)
-template <int P, int N>
+// (ZL: every remainder l is zero on entry, as in the first op of a stage
+// that reads rounded amplitudes)
+template <int P, int N, bool ZL = false>
 __device__ __forceinline__ void dfop_rp(float2 (&h)[N], float2 (&l)[N], const float (&m)[8], const float (&ml)[8],
                                         bool phase) {
   const float2 r00 = f2s(m[0]), r01 = f2s(m[1]), r10 = f2s(m[2]), r11 = f2s(m[3]);
@@ -91,8 +98,8 @@ __device__ __forceinline__ void dfop_rp(float2 (&h)[N], float2 (&l)[N], const fl
     if (i & (1 << P)) continue;
     const int j = i | (1 << P);
     const float2 xh = h[i], xl = l[i], yh = h[j], yl = l[j];
-    df_lin2(r00, e00, xh, xl, r01, e01, yh, yl, h[i], l[i]);
-    df_lin2(r10, e10, xh, xl, r11, e11, yh, yl, h[j], l[j]);
+    df_lin2<ZL>(r00, e00, xh, xl, r01, e01, yh, yl, h[i], l[i]);
+    df_lin2<ZL>(r10, e10, xh, xl, r11, e11, yh, yl, h[j], l[j]);
   }
   if (phase) {
 #pragma unroll

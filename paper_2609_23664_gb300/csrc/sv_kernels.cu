@@ -251,7 +251,7 @@ __device__ __forceinline__ void sv_stage_df(char *smw, uint32_t lo_off, uint32_t
     const bool table = ph != nullptr && ph_block != 0xFFFFFFFFu;
     float m[8], ml[8];
     load_ml(op_begin, m, ml);
-    dfop_rp<0, N>(h, l, m, ml, !table);
+    dfop_rp<0, N, AR == SV_AR_COMP>(h, l, m, ml, !table);
     load_ml(op_begin + 1, m, ml);
     dfop_rp<1, N>(h, l, m, ml, !table);
     load_ml(op_begin + 2, m, ml);
