@@ -231,10 +231,13 @@ struct SvTableBuilder {
         // takes the product of the phases of its set positions, computed
         // here in FP64 and stored as double-float pairs
         sd.ph_block = 0xFFFFFFFFu;
+        if ((hs.gphase[0] != 1.0 || hs.gphase[1] != 0.0) && (fp64 || pr.g != 4 || !rp_stage || rp_mask != 0xFu))
+          fail(QW_ERR_STATE, "internal: a global phase on a stage without a phase table");
         if (!fp64 && pr.g == 4 && rp_stage && rp_mask == 0xFu) {
-          sd.ph_block = (uint32_t)(ph.size() / 64);
+          const bool gfold = hs.gphase[0] != 1.0 || hs.gphase[1] != 0.0;
+          sd.ph_block = (uint32_t)(ph.size() / 64) | (gfold ? 0x80000000u : 0u);
           for (uint32_t e = 0; e < 16; e++) {
-            std::complex<double> q(1.0, 0.0);
+            std::complex<double> q(hs.gphase[0], hs.gphase[1]);
             for (const HostOp &o : sops)
               if ((e >> o.a) & 1u) q *= std::complex<double>(o.m[4], o.m[5]);
             const float rh = (float)q.real(), ih = (float)q.imag();
@@ -451,7 +454,8 @@ static double pass_flops(const HostPass &hp, uint32_t n, uint32_t g, int ar) {
         // its first rotation has no remainder products (2 packed FMAs, 8
         // flops, per output)
         const double first = (ar == SV_AR_COMP) ? lin - 8.0 : lin;
-        f += (fg + A * first + 3.0 * A * lin + (A - 1.0) * cm) * groups;
+        const bool gfold = st.gphase[0] != 1.0 || st.gphase[1] != 0.0;
+        f += (fg + A * first + 3.0 * A * lin + (gfold ? A : A - 1.0) * cm) * groups;
         continue;
       }
     }

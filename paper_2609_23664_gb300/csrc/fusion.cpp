@@ -397,6 +397,26 @@ SvProgram fuse_sv(const qw_gate *gates, uint64_t n_gates, uint32_t n_eff, const 
   // fold the global phase into one single-qubit op (every amplitude is in
   // exactly one of its pairs): the first general op if there is one, else
   // the first single-qubit op of any kind
+  // (compensated programs, stages of four positions: carried by the first
+  // stage with a rotation on every position, whose phase table multiplies
+  // every amplitude anyway, so that its ops stay rotations)
+  if (gphase != cd(1.0, 0.0) && G == (uint32_t)SV_G_COMP && SV_G_PLAIN32 != SV_G_COMP) {
+    for (auto &ps : prog.passes)
+      for (auto &st : ps.stages) {
+        if (gphase == cd(1.0, 0.0) || st.ops.size() != 4) continue;
+        uint32_t mask = 0;
+        bool rot = true;
+        for (const HostOp &o : st.ops) {
+          rot = rot && (o.kind == K_RP || o.kind == K_R) && !(mask & (1u << o.a));
+          mask |= 1u << o.a;
+        }
+        if (rot && mask == 0xFu) {
+          st.gphase[0] = gphase.real();
+          st.gphase[1] = gphase.imag();
+          gphase = cd(1.0, 0.0);
+        }
+      }
+  }
   if (gphase != cd(1.0, 0.0)) {
     HostOp *target = nullptr;
     for (auto &ps : prog.passes)

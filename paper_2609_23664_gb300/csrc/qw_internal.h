@@ -127,6 +127,10 @@ struct HostStage {
   uint32_t mc = 0;    // and its constant c
   uint32_t ctl_w[SV_MAX_OUT_CTL] = {0, 0, 0, 0};  // per-tile terms of c (pass's ctl_q)
   std::vector<HostOp> ops;
+  // global phase the stage applies to every amplitude (compensated stages
+  // with a rotation on every position carry the program's, in their phase
+  // table)
+  double gphase[2] = {1.0, 0.0};
   HostStage() { for (uint32_t t = 0; t < 32; t++) mcol[t] = 1u << t; }
 };
 struct HostPass {
@@ -199,8 +203,9 @@ struct alignas(16) SvStageDesc {
   uint32_t rp_mask;
   // compensated FP32 stage with a K_RP op on every position: block of the
   // phase table (16 entries) holding, for each amplitude index e of the
-  // stage group, the product of the |1>-phases of e's set positions;
-  // 0xFFFFFFFF = none
+  // stage group, the product of the |1>-phases of e's set positions (times
+  // the program's global phase when bit 31 is set: then entry 0 applies
+  // too); 0xFFFFFFFF = none
   uint32_t ph_block;
   uint32_t pad;
   // per-tile terms of cst: XOR ctl_w[i] when bit ctl_tb[i] of the tile index is set

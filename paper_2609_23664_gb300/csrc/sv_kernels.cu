@@ -259,7 +259,11 @@ __device__ __forceinline__ void sv_stage_df(char *smw, uint32_t lo_off, uint32_t
     load_ml(op_begin + 3, m, ml);
     dfop_rp<3, N>(h, l, m, ml, !table);
     if (table) {
-      const float4 *q = (const float4 *)ph + 16 * (size_t)ph_block;
+      const float4 *q = (const float4 *)ph + 16 * (size_t)(ph_block & 0x7FFFFFFFu);
+      if (ph_block >> 31) {  // the program's global phase: entry 0 too
+        const float4 w = __ldg(q);
+        df_cmul(w.x, w.y, w.z, w.w, h[0], l[0]);
+      }
 #pragma unroll
       for (int e = 1; e < N; e++) {
         const float4 w = __ldg(q + e);
