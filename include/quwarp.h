@@ -484,7 +484,7 @@ qw_status qw_sv_sample_dev(qw_engine *e, uint32_t mode, uint32_t n, const void *
  * QW_ERR_INVALID_ARG; n > QW_NOALLOC_MAX_QUBITS or more terms than
  * QW_NOALLOC_MAX_TERMS return QW_ERR_BUDGET.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress), which loads
- * the module; make that first call before any stream capture.  Every call
+ * the module.  Every call
  * uses the same array: calls whose work overlaps on the GPU (different
  * streams, or host threads without ordering) race and corrupt each other's
  * results; serialize them on one stream.  The array keeps the last call's
