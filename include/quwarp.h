@@ -51,7 +51,7 @@ enum {
   QW_ERR_STATE = -6,            /* call made in the wrong order             */
   QW_ERR_BUFFER_TOO_SMALL = -7, /* output capacity too small (see *needed)  */
   QW_ERR_NOT_FOUND = -8,        /* unknown task id / result not requested   */
-  QW_ERR_UNSUPPORTED = -9       /* valid request this build does not run    */
+  QW_ERR_UNSUPPORTED = -9       /* valid request the library does not run   */
 };
 
 /* ---- input records (byte layout is part of the ABI) ---------------------- */
